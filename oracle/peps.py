@@ -171,7 +171,7 @@ def zipper(mpo: RowMPO, A, lognorm, chi_cap):
     out = [None] * C
     for c in range(C - 1, -1, -1):
         W = mpo.dense(c)
-        theta = np.einsum("abus,sij,bjk->aiuk", W, A[c], K)
+        theta = np.einsum("abus,sij,bjk->aiuk", W, A[c], K, optimize=True)
         bl, al, u, kk = theta.shape
         Uu, s, Vh = np.linalg.svd(theta.reshape(bl * al, u * kk), full_matrices=False)
         k = keep_count(s, chi_cap)
@@ -185,15 +185,24 @@ def zipper(mpo: RowMPO, A, lognorm, chi_cap):
 
 
 def _opt(L, W, A, R):
-    return np.einsum("abi,bBus,sij,cBj->uac", L, W, A, R, optimize=True)
+    """Optimal one-site tensor phi_c[u, a, a'] = sum L[a,bl,i] W[bl,br,u,s] A[s,i,j] R[a',br,j]."""
+    t = np.einsum("sij,cBj->siBc", A, R)                 # [s, i, br, a']
+    t = np.einsum("bBus,siBc->buic", W, t, optimize=True)  # [bl, u, i, a']
+    return np.einsum("abi,buic->uac", L, t, optimize=True)
 
 
 def _upd_L(L, phi, W, A):
-    return np.einsum("abi,uac,bBus,sij->cBj", L, phi, W, A, optimize=True)
+    """L_{c+1}[a', br, j] = sum L[a,bl,i] phi[u,a,a'] W[bl,br,u,s] A[s,i,j]."""
+    t = np.einsum("abi,uac->biuc", L, phi, optimize=True)     # [bl, i, u, a']
+    t = np.einsum("biuc,bBus->icBs", t, W, optimize=True)     # [i, a', br, s]
+    return np.einsum("icBs,sij->cBj", t, A, optimize=True)
 
 
 def _upd_R(R, phi, W, A):
-    return np.einsum("uac,bBus,sij,cBj->abi", phi, W, A, R, optimize=True)
+    """R_{c-1}[a, bl, i] = sum phi[u,a,a'] W[bl,br,u,s] A[s,i,j] R[a',br,j]."""
+    t = np.einsum("sij,cBj->siBc", A, R)                 # [s, i, br, a']
+    t = np.einsum("bBus,siBc->buic", W, t, optimize=True)  # [bl, u, i, a']
+    return np.einsum("uac,buic->abi", phi, t, optimize=True)
 
 
 def right_canonical(phi):
@@ -296,7 +305,7 @@ def top_row_log_overlap(mpo0: RowMPO, A, lognorm):
     E = np.ones((1, 1))
     for c in range(len(A)):
         W = mpo0.dense(c)
-        E = np.einsum("ai,abs,sij->bj", E, W[:, :, 0, :], A[c])
+        E = np.einsum("ai,abs,sij->bj", E, W[:, :, 0, :], A[c], optimize=True)
     val = float(E.reshape(()))
     if not val > 0:
         raise FloatingPointError("non-positive partition function")

@@ -1,0 +1,143 @@
+"""Conditional marginals and the branch-and-bound search (paper Sec. III.A, Eqs. 5-8, Figs. 3 and 6).
+
+Clusters are placed in row-major order (the sweep of Fig. 3, "row after
+row"), top-left first.  For a branch k (a partial configuration) and the next
+cluster n+1 = (r, c), the unnormalised conditional score of state x is the
+contraction of Fig. 6(b):
+
+    s_k(x) = < f_k | W_0^(x_0) ... W_{c-1}^(x_{c-1}) W_c^(x) W_{c+1} ... W_{C-1} | psi_r >
+
+where W_j are the dense MPO columns of row r (see ``peps``), W^(x) the slice of
+one cluster state, psi_r the boundary MPS of the rows below, and f_k the
+product vector on the up legs that carries the Boltzmann factors between the
+fixed row r-1 of branch k and row r.  The conditional is
+p(x | x_n) = s_k(x) / sum_x' s_k(x'), and the chain rule (Eq. 6) gives
+log p(x_{n+1}) = log p(x_n) + log p(x | x_n).
+
+Bounding (Fig. 3d-e): candidates are grouped by their boundary
+(Eq. 7: the classes P^{kl}(x_k) over coupled pairs with k placed, l not yet
+placed); only the most probable of each group survives; then the M most
+probable survive.  p_d is the largest log-probability ever discarded (Sec.
+III.A, last paragraph).
+
+Readings: negative scores (possible with an approximate boundary MPS) are
+clamped to zero and counted; ties in log p are broken toward the
+lexicographically smaller configuration (placement order, state index
+ascending), in merging and in the top-M cut alike.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .peps import boundary_mps
+from .potts import DIRS, PottsModel
+
+
+def _B(pm, beta, r, c, dname):
+    E = pm.ebar(r, c, dname)
+    return np.exp(-beta * (E - E.min()) / pm.inst.denom)
+
+
+def upper_vectors(pm: PottsModel, beta, r, row_above_states):
+    """f[c'][u]: Boltzmann factors between the fixed row r-1 and class u of the up exposure of (r, c')."""
+    out = []
+    for cc in range(pm.C):
+        S = pm.site(r, cc)
+        U = pm.joint(r, cc, ("u", "ul", "ur"))
+        f = np.ones(U.n)
+        if r > 0:
+            xa = row_above_states
+            pu = pm.component(U, S, "u")
+            f = f * _B(pm, beta, r - 1, cc, "d")[pm.site(r - 1, cc).proj["d"].of_state[xa[cc]], pu]
+            if cc - 1 >= 0:
+                pul = pm.component(U, S, "ul")
+                f = f * _B(pm, beta, r - 1, cc - 1, "dr")[pm.site(r - 1, cc - 1).proj["dr"].of_state[xa[cc - 1]], pul]
+            if cc + 1 < pm.C:
+                pur = pm.component(U, S, "ur")
+                f = f * _B(pm, beta, r - 1, cc + 1, "dl")[pm.site(r - 1, cc + 1).proj["dl"].of_state[xa[cc + 1]], pur]
+        out.append(f)
+    return out
+
+
+def conditional_scores(pm, beta, mpo, psi, cfg, r, c):
+    """Unnormalised scores s_k(x) of every state x of cluster (r, c) for partial configuration cfg."""
+    A, _ = psi
+    C = pm.C
+    above = [cfg[(r - 1) * C + j] for j in range(C)] if r > 0 else None
+    f = upper_vectors(pm, beta, r, above)
+    E = np.ones((1, 1))
+    for j in range(c):
+        x = cfg[r * C + j]
+        Wx = mpo.state_term(j, x)
+        E = f[j][mpo.cols[j]["u_x"][x]] * np.einsum("ai,abs,sij->bj", E, Wx, A[j], optimize=True)
+    F = np.ones((1, 1))
+    for j in range(C - 1, c, -1):
+        Wf = np.einsum("u,abus->abs", f[j], mpo.dense(j))
+        F = np.einsum("abs,sij,bj->ai", Wf, A[j], F, optimize=True)
+    M = np.einsum("ai,sij,bj->abs", E, A[c], F, optimize=True)         # [bl, br, sigma]
+    col = mpo.cols[c]
+    d = col["T"].shape[0]
+    Tr = col["T"].reshape(d, -1, col["nsig"])           # [x, br, sigma]
+    sig = np.arange(col["nsig"])
+    rows = col["lam_x"][:, None] * col["nGl"] + col["pul"][None, :]
+    Mg = M[rows, :, sig[None, :]]                        # [x, sigma, br]
+    return f[c][col["u_x"]] * np.einsum("xbs,xsb->x", Tr, Mg)
+
+
+def boundary_pairs(pm: PottsModel, n):
+    """Coupled ordered pairs (p, l, dir) with p placed (index <= n) and l not placed (Eq. 7)."""
+    C = pm.C
+    out = []
+    for p in range(n + 1):
+        r, c = divmod(p, C)
+        for dname, (dr, dc) in DIRS.items():
+            rr, cc = r + dr, c + dc
+            if 0 <= rr < pm.R and 0 <= cc < C:
+                l = rr * C + cc
+                if l > n and pm.sites[p].coupled[dname]:
+                    out.append((p, l, dname))
+    return sorted(out)
+
+
+def boundary_key(pm, pairs, cfg):
+    return tuple(pm.sites[p].proj[d].of_state[cfg[p]] for (p, l, d) in pairs)
+
+
+def search(inst, beta, chi, M, n_sweeps=2, states=None, psis=None):
+    """Branch and bound over all clusters; returns the final beam sorted by (-log p, configuration)."""
+    pm = PottsModel(inst, states)
+    logz, psis_, mpos = boundary_mps(pm, beta, chi, n_sweeps)
+    psis = psis_ if psis is None else psis
+    C = pm.C
+    beam = [((), 0.0)]
+    pd = -np.inf
+    clamps = 0
+    for n in range(pm.R * C):
+        r, c = divmod(n, C)
+        pairs = boundary_pairs(pm, n)
+        best = {}
+        for cfg, lp in beam:
+            s = conditional_scores(pm, beta, mpos[r], psis[r], cfg, r, c)
+            clamps += int(np.sum(s < 0))
+            s = np.maximum(s, 0.0)
+            tot = s.sum()
+            for x in np.nonzero(s > 0)[0]:
+                cand = cfg + (int(x),)
+                lq = lp + float(np.log(s[x] / tot))
+                key = boundary_key(pm, pairs, cand)
+                old = best.get(key)
+                if old is None:
+                    best[key] = (cand, lq)
+                else:
+                    keep, drop = ((cand, lq), old) if (-lq, cand) < (-old[1], old[0]) else (old, (cand, lq))
+                    best[key] = keep
+                    pd = max(pd, drop[1])
+        surv = sorted(best.values(), key=lambda t: (-t[1], t[0]))
+        for t in surv[M:]:
+            pd = max(pd, t[1])
+        beam = surv[:M]
+    configs = [b[0] for b in beam]
+    spins = np.array([pm.spins_of_config(cfg) for cfg in configs], dtype=np.int8)
+    energies = np.array([inst.energy_num(s) for s in spins], dtype=np.int64)
+    return dict(configs=configs, logp=np.array([b[1] for b in beam]), pd=pd, spins=spins,
+                energy_num=energies, logz=logz, clamps=clamps, pm=pm, psis=psis, mpos=mpos)
