@@ -1,0 +1,230 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each test pins one part of the oracle to the mathematics or to numbers the
+paper prints: brute-force enumeration (Eq. 9, Eq. 5), closed forms of 1D
+chains, beta = 0, gauge invariance, decoupled rows, the Pegasus dimensions of
+Sec. III.B.1, and the exact-dynamic-programming property of the search.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import brute
+from oracle.peps import boundary_mps
+from oracle.potts import PottsModel
+from oracle.search import conditional_scores, search
+from paper_2411_16431_b300 import lattices as L
+
+
+# --- generators ------------------------------------------------------------
+
+def test_chimera_counts():
+    inst = L.chimera_grid(4, 4, 0)
+    assert inst.n_spins == 128 and inst.n_edges == 352
+    assert set(np.abs(inst.j_num)) <= set(range(1, 8))
+
+
+def test_pegasus_counts_and_degree():
+    # nice subgraph of P_M has 24 (M-1)^2 nodes; max degree 15 (Sec. II)
+    for m, n in ((4, 216), (6, 600), (16, 5400)):
+        assert L.pegasus_nice(m, 0).n_spins == n
+    q, e = L.pegasus_graph(8)
+    deg = np.zeros(len(q), int)
+    idx = {x: i for i, x in enumerate(q)}
+    for a, b in e:
+        deg[idx[a]] += 1
+        deg[idx[b]] += 1
+    assert deg.max() == 15
+    # the 5616-qubit device has "over 40000" couplers; the full P16 fabric must have more
+    assert len(L.pegasus_graph(16)[1]) > 40135
+
+
+def test_pegasus_dims_match_paper():
+    """Site-tensor legs (l,u,r,d) = (2^18, 2^14, 2^14, 2^18) and the mediating projector
+    dims 2^4, 2^12, 2^0 / 2^0, 2^18, 2^8 printed in Sec. III.B.1, for a bulk cell."""
+    inst = L.pegasus_nice(6, 0)
+    pm = PottsModel(inst, states_per_site=[np.zeros(1, np.int64)] * 25)  # no enumeration needed
+    S = pm.site(2, 2)
+    k = {d: len(S.coupled[d]) for d in S.coupled}
+    union = lambda *ds: len(set().union(*[S.coupled[d] for d in ds]))
+    assert (union("l", "ul", "dl"), union("u", "ul", "ur"), union("r", "ur", "dr"), union("d", "dl", "dr")) == (18, 14, 14, 18)
+    assert (k["ur"], k["u"], k["ul"]) == (4, 12, 0)
+    assert (k["dr"], k["d"], k["dl"]) == (0, 18, 8)
+
+
+def test_planted_energy_is_ground():
+    base = L.slice_cells(L.chimera_grid(2, 2, 5), 2, 1)
+    inst = L.planted(base, 11)
+    _, e = brute.ground_state(inst)
+    assert inst.planted_energy_num == e == inst.meta["loop_bound_num"]
+
+
+# --- clustering (Eqs. 2-4) --------------------------------------------------
+
+def test_cluster_energies_match_spin_energies():
+    inst = L.kings_grid(3, 3, 7)
+    inst2 = L.slice_cells(L.chimera_grid(2, 2, 3), 2, 1)
+    rng = np.random.default_rng(0)
+    for I in (inst, inst2):
+        pm = PottsModel(I)
+        for _ in range(50):
+            cfg = [int(rng.integers(S.d)) for S in pm.sites]
+            e = sum(int(pm.sites[i].E[x]) for i, x in enumerate(cfg))
+            for r in range(pm.R):
+                for c in range(pm.C):
+                    for d, (dr, dc) in (("r", (0, 1)), ("d", (1, 0)), ("dr", (1, 1)), ("dl", (1, -1))):
+                        T = pm.site(r + dr, c + dc)
+                        if T is None:
+                            continue
+                        S = pm.site(r, c)
+                        Eb = pm.ebar(r, c, d)
+                        from oracle.potts import OPP
+                        a = S.proj[d].of_state[cfg[r * pm.C + c]]
+                        b = T.proj[OPP[d]].of_state[cfg[(r + dr) * pm.C + c + dc]]
+                        e += int(Eb[a, b])
+            assert e == I.energy_num(pm.spins_of_config(cfg))
+
+
+def test_projector_classes_by_enumeration():
+    inst = L.chimera_grid(2, 2, 1)
+    pm = PottsModel(inst)
+    S = pm.site(0, 0)
+    # the cell's spins 4..7 couple right, 0..3 couple down (Chimera reading)
+    assert S.coupled["r"] == [4, 5, 6, 7] and S.coupled["d"] == [0, 1, 2, 3]
+    for x in range(S.d):
+        bits = [(x >> b) & 1 for b in range(8)]
+        assert S.proj["r"].of_state[x] == sum(bits[4 + j] << j for j in range(4))
+
+
+# --- log Z (Eq. 9) -------------------------------------------------------------
+
+SMALL = [L.square_grid(3, 3, 1), L.kings_grid(4, 4, 3), L.square_grid(4, 4, 4, fields=False),
+         L.slice_cells(L.chimera_grid(4, 4, 0), 2, 1), L.slice_cells(L.chimera_grid(4, 4, 0), 1, 2),
+         L.kings_grid(2, 5, 9)]
+
+
+@pytest.mark.parametrize("inst", SMALL, ids=lambda i: i.name)
+@pytest.mark.parametrize("beta", [0.3, 1.0, 2.5])
+def test_exact_logz_equals_brute_force(inst, beta):
+    lz, _, _ = boundary_mps(PottsModel(inst), beta, chi=64, n_sweeps=1)
+    assert abs(lz - brute.log_z(inst, beta)) < 1e-11 * max(1.0, abs(lz))
+
+
+def test_beta_zero_gives_two_to_n():
+    inst = L.chimera_grid(3, 3, 2)
+    lz, _, _ = boundary_mps(PottsModel(inst), 0.0, chi=4, n_sweeps=1)
+    assert abs(lz - inst.n_spins * np.log(2)) < 1e-10
+
+
+def test_open_chain_closed_form():
+    # one row of single spins, h = 0: Z = 2 prod_i 2 cosh(beta J_i)
+    inst = L.square_grid(1, 9, 5, fields=False)
+    beta = 0.8
+    lz, _, _ = boundary_mps(PottsModel(inst), beta, chi=2, n_sweeps=1)
+    J = inst.j_num / 7.0
+    assert abs(lz - (np.log(2) + np.sum(np.log(2 * np.cosh(beta * J))))) < 1e-12
+
+
+def test_chain_with_fields_transfer_matrix():
+    # a column of single spins with fields: 2x2 transfer-matrix product
+    inst = L.square_grid(7, 1, 6)
+    beta = 1.3
+    lz, _, _ = boundary_mps(PottsModel(inst), beta, chi=2, n_sweeps=1)
+    s = np.array([1.0, -1.0])
+    h = inst.h_num / 7.0
+    J = inst.j_num / 7.0
+    v = np.exp(-beta * h[0] * s)
+    for i in range(1, 7):
+        T = np.exp(-beta * J[i - 1] * np.outer(s, s)) * np.exp(-beta * h[i] * s)[None, :]
+        v = v @ T
+    assert abs(lz - np.log(v.sum())) < 1e-12
+
+
+def test_decoupled_rows_factorise():
+    inst = L.square_grid(3, 4, 8)
+    keep = np.array([(inst.site_of_spin[a] // 4) == (inst.site_of_spin[b] // 4) for a, b in zip(inst.ei, inst.ej)])
+    inst.j_num = np.where(keep, inst.j_num, 0).astype(np.int32)
+    beta = 1.1
+    lz, _, _ = boundary_mps(PottsModel(inst), beta, chi=3, n_sweeps=1)
+    rows = [L.slice_cells(inst, 1, 4)]
+    tot = 0.0
+    for r in range(3):
+        sub = L.Instance(4, np.arange(3, dtype=np.int32), np.arange(1, 4, dtype=np.int32),
+                         inst.j_num[[k for k in range(inst.n_edges) if inst.ei[k] // 4 == r and inst.ej[k] // 4 == r]],
+                         inst.h_num[4 * r:4 * r + 4], 7, np.arange(4, dtype=np.int32), 1, 4)
+        tot += brute.log_z(sub, beta)
+    assert abs(lz - tot) < 1e-11
+
+
+def test_gauge_invariance_truncated():
+    inst = L.chimera_grid(4, 4, 0)
+    rng = np.random.default_rng(3)
+    g = rng.choice([-1, 1], inst.n_spins)
+    inst2 = L.Instance(inst.n_spins, inst.ei, inst.ej, (inst.j_num * g[inst.ei] * g[inst.ej]).astype(np.int32),
+                       (inst.h_num * g).astype(np.int32), 7, inst.site_of_spin, 4, 4)
+    a, _, _ = boundary_mps(PottsModel(inst), 1.0, chi=6, n_sweeps=1)
+    b, _, _ = boundary_mps(PottsModel(inst2), 1.0, chi=6, n_sweeps=1)
+    assert abs(a - b) < 1e-10 * abs(a)
+
+
+def test_truncation_converges_to_exact():
+    inst = L.kings_grid(5, 5, 4)
+    lz_ex, _, _ = boundary_mps(PottsModel(inst), 1.0, chi=64, n_sweeps=1)
+    errs = [abs(boundary_mps(PottsModel(inst), 1.0, chi=c, n_sweeps=2)[0] - lz_ex) for c in (1, 2, 4, 32)]
+    assert errs[-1] < 1e-10 and errs[0] > 1e-6
+
+
+# --- conditionals (Fig. 6) and search (Fig. 3) -----------------------------------
+
+def _brute_conditional(inst, pm, cfg, n, beta):
+    """p(x_{n+1} | x_<=n) by summing exp(-beta H) over all completions."""
+    S = brute.all_spins(inst.n_spins)
+    E = brute.energies_num(inst, S) / inst.denom
+    w = np.exp(-beta * (E - E.min()))
+    site = pm.sites[n]
+    # which spin states agree with cfg on the placed clusters
+    ok = np.ones(len(S), bool)
+    for p, x in enumerate(cfg):
+        Sp = pm.sites[p]
+        ok &= np.all(S[:, Sp.spins] == Sp.spinvals[x][None, :], axis=1)
+    out = np.zeros(site.d)
+    for x in range(site.d):
+        m = ok & np.all(S[:, site.spins] == site.spinvals[x][None, :], axis=1)
+        out[x] = w[m].sum()
+    return out / out.sum()
+
+
+@pytest.mark.parametrize("inst", [L.kings_grid(3, 3, 2), L.slice_cells(L.chimera_grid(4, 4, 1), 2, 1)], ids=lambda i: i.name)
+def test_exact_conditionals_match_brute_force(inst):
+    beta = 0.9
+    pm = PottsModel(inst)
+    _, psis, mpos = boundary_mps(pm, beta, chi=64, n_sweeps=1)
+    rng = np.random.default_rng(1)
+    for n in range(pm.R * pm.C):
+        r, c = divmod(n, pm.C)
+        cfg = tuple(int(rng.integers(pm.sites[p].d)) for p in range(n))
+        s = conditional_scores(pm, beta, mpos[r], psis[r], cfg, r, c)
+        p = s / s.sum()
+        assert np.allclose(p, _brute_conditional(inst, pm, cfg, n, beta), rtol=1e-10, atol=1e-14)
+
+
+@pytest.mark.parametrize("inst", [L.kings_grid(4, 4, 3), L.square_grid(4, 4, 12),
+                                  L.slice_cells(L.chimera_grid(4, 4, 0), 2, 1),
+                                  L.planted(L.slice_cells(L.chimera_grid(2, 2, 5), 1, 2), 4)], ids=lambda i: i.name)
+def test_exact_search_is_dynamic_programming(inst):
+    """With exact marginals and no top-M cut, merging keeps the best completion of each boundary,
+    so the search returns the brute-force ground state and log p = -beta E - log Z."""
+    beta = 1.7
+    res = search(inst, beta, chi=256, M=10 ** 9, n_sweeps=1)
+    _, e = brute.ground_state(inst)
+    assert int(res["energy_num"][0]) == e
+    lz = brute.log_z(inst, beta)
+    assert abs(res["logp"][0] + beta * e / inst.denom + lz) < 1e-9
+    assert res["pd"] <= res["logp"][0] + 1e-12
+
+
+def test_search_config1_smoke():
+    res = search(L.chimera_grid(4, 4, 0), 1.0, chi=16, M=64, n_sweeps=2)
+    assert res["energy_num"][0] == res["pm"].state_energy_num(res["configs"][0])
+    assert res["pd"] < 0 and len(res["configs"]) == 1
