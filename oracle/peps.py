@@ -29,7 +29,8 @@ values of each dashed-box tensor (dense SVD here: the plain definition of the
 optimal rank-k truncation); ``n_sweeps`` one-site variational sweeps
 maximising the overlap with T_r psi_r (Fig. 8d); cut to chi by an SVD sweep;
 ``n_sweeps`` more sweeps at chi.  Singular values below ``RANK_TOL`` times the
-largest are dropped (exact zeros would otherwise leave the bond gauge free).
+largest are dropped, in truncations and in every orthonormalisation (exact
+zeros would otherwise leave part of a bond basis arbitrary).
 log Z = offset + log-norms + log <T_0 | psi_0>.
 """
 from __future__ import annotations
@@ -141,11 +142,23 @@ def trivial_mps(C):
     return [np.ones((1, 1, 1)) for _ in range(C)], 0.0
 
 
+def orthonormalise(M):
+    """M = Q R with Q an isometry, through the SVD, dropping directions below RANK_TOL.
+
+    A QR would leave an arbitrary basis for exactly dependent columns, which a
+    later variational update could then use; the trimmed SVD basis spans only
+    the column space of M, so the result is fixed up to a rotation.
+    """
+    U, s, Vh = np.linalg.svd(M, full_matrices=False)
+    k = keep_count(s, s.size)
+    return U[:, :k], s[:k, None] * Vh[:k]
+
+
 def left_canonical(A, lognorm):
     A = [a.copy() for a in A]
     for c in range(len(A) - 1):
         s, l, r = A[c].shape
-        Q, R = np.linalg.qr(A[c].reshape(s * l, r))
+        Q, R = orthonormalise(A[c].reshape(s * l, r))
         A[c] = Q.reshape(s, l, Q.shape[1])
         A[c + 1] = np.einsum("ij,sjk->sik", R, A[c + 1])
     n = np.linalg.norm(A[-1])
@@ -209,7 +222,7 @@ def right_canonical(phi):
     phi = [p.copy() for p in phi]
     for c in range(len(phi) - 1, 0, -1):
         u, a, b = phi[c].shape
-        Q, R = np.linalg.qr(phi[c].transpose(1, 0, 2).reshape(a, u * b).T)
+        Q, R = orthonormalise(phi[c].transpose(1, 0, 2).reshape(a, u * b).T)
         phi[c] = Q.T.reshape(Q.shape[1], u, b).transpose(1, 0, 2)
         phi[c - 1] = np.einsum("uab,bk->uak", phi[c - 1], R.T)
     return phi
@@ -235,7 +248,7 @@ def variational_sweep(mpo: RowMPO, A, phi):
         t = _opt(L[c], Ws[c], A[c], R[c])
         if c < C - 1:
             u, a, b = t.shape
-            Q, _ = np.linalg.qr(t.reshape(u * a, b))
+            Q, _ = orthonormalise(t.reshape(u * a, b))
             phi[c] = Q.reshape(u, a, Q.shape[1])
             L[c + 1] = _upd_L(L[c], phi[c], Ws[c], A[c])
         else:
@@ -245,7 +258,7 @@ def variational_sweep(mpo: RowMPO, A, phi):
         t = _opt(L[c], Ws[c], A[c], Rc)
         if c > 0:
             u, a, b = t.shape
-            Q, _ = np.linalg.qr(t.transpose(1, 0, 2).reshape(a, u * b).T)
+            Q, _ = orthonormalise(t.transpose(1, 0, 2).reshape(a, u * b).T)
             phi[c] = Q.T.reshape(Q.shape[1], u, b).transpose(1, 0, 2)
             Rc = _upd_R(Rc, phi[c], Ws[c], A[c])
         else:
