@@ -1,0 +1,133 @@
+/*
+ * sgtn -- tensor-network branch-and-bound for Ising spin glasses on
+ * quasi-2D lattices of unit cells (arXiv:2411.16431), CUDA for sm_103a.
+ *
+ * C ABI.  All functions return an sgtn_status (0 on success); no exception
+ * crosses the boundary.  A failed call leaves the handle usable and
+ * sgtn_last_error() returns a text description.  Calls out of order (a
+ * search before set_beta, ...) return SGTN_ERR_STATE.  A handle is bound to
+ * the CUDA device that was current at sgtn_build_instance and to the stream
+ * given there; handles are not thread-safe.
+ *
+ * Conventions shared by every entry point
+ *  - H(s) = sum_{<ij>} J_ij s_i s_j + sum_i h_i s_i        (Sec. II, Eq. 1)
+ *    with J_ij = j_num / denom, h_i = h_num / denom, s_i = +-1; lower energy
+ *    is better and p(s) ~ exp(-beta H(s))                (Sec. III.A, Eq. 5).
+ *  - Spins are grouped into an R x C grid of clusters ("sites"); site (r, c)
+ *    has index r*C + c.  Couplings may join a site only to its eight
+ *    king's-graph neighbours (nearest and diagonal, Sec. III, Fig. 1b/d);
+ *    anything else is SGTN_ERR_ARG.
+ *  - A cluster state is a bit pattern over the site's spins in increasing
+ *    global index; bit value 0 means s = +1, bit value 1 means s = -1.
+ *  - Host input arrays are copied during the call; the caller keeps
+ *    ownership.  Output pointers are host pointers owned by the caller.
+ */
+#ifndef SGTN_H
+#define SGTN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgtn_inst* sgtn_h;
+
+typedef enum {
+  SGTN_OK = 0,
+  SGTN_ERR_ARG = -1,        /* bad size, pointer or lattice                */
+  SGTN_ERR_STATE = -2,      /* call out of order                           */
+  SGTN_ERR_OOM = -3,        /* device allocation failed                    */
+  SGTN_ERR_NUMERICAL = -4,  /* NaN / zero norm / SVD did not converge      */
+  SGTN_ERR_TIMEOUT = -5,    /* a bounded device-side loop gave up          */
+  SGTN_ERR_CUDA = -6        /* any other CUDA error                        */
+} sgtn_status;
+
+typedef enum { SGTN_FP64 = 0, SGTN_TF32 = 1, SGTN_BF16 = 2 } sgtn_precision;
+
+/* Build the generalized Potts model of Sec. III, Eqs. (2)-(4): cluster
+ * states, intra-cluster energies E_x, projectors P^{mn} onto the spins that
+ * couple to each neighbour, and compressed energies Ebar^{mn}.
+ *   n_spins, n_edges          sizes; edges (ei[k], ej[k]) with ei < ej
+ *   j_num[n_edges], h_num[n_spins], denom > 0
+ *   site_of_spin[n_spins]     r*cols + c
+ *   state_offsets, states     optional (both NULL or both set): explicit
+ *                             state list of each site, site s owning
+ *                             states[state_offsets[s] .. state_offsets[s+1]),
+ *                             each a bit pattern as above (used for cells of
+ *                             more than 16 spins or for reduced state sets);
+ *                             when NULL every site enumerates all 2^k states
+ *                             and k must be <= 16.
+ *   stream                    cudaStream_t to run on (NULL = legacy stream)
+ * On success *out receives a new handle (free with sgtn_destroy). */
+int sgtn_build_instance(int32_t n_spins, int64_t n_edges, const int32_t* ei, const int32_t* ej,
+                        const int32_t* j_num, const int32_t* h_num, int32_t denom,
+                        const int32_t* site_of_spin, int32_t rows, int32_t cols,
+                        const int64_t* state_offsets, const int64_t* states, void* stream,
+                        sgtn_h* out);
+
+/* Inverse temperature of Eq. (5).  Forms on the device the shifted site
+ * weights w_x = exp(-beta (E_x - min E)) and bond factors
+ * exp(-beta (Ebar - min Ebar)); the removed minima are kept as a log offset.
+ * Invalidates boundary MPSs computed for another beta. */
+int sgtn_set_beta(sgtn_h h, double beta);
+
+/* Boundary-MPS contraction of Sec. III.B (Figs. 6-8): for r = R-1 .. 1,
+ * psi_{r-1} ~ T_r psi_r by the right-to-left zipper keeping 2*chi singular
+ * values, n_sweeps one-site variational sweeps, a cut to chi and n_sweeps
+ * more sweeps.  All boundary MPSs stay resident on the device for the
+ * branch step.  precision: SGTN_FP64 (everything in double) or a mixed mode
+ * (contractions on tensor cores, truncation and log-norms in double).
+ *   out_logz            log Z of Eq. (9) (may be NULL)
+ *   out_worst_trunc_sv  largest, over all cuts, of the smallest retained
+ *                       singular value relative to the largest (may be NULL) */
+int sgtn_contract_boundary(sgtn_h h, int32_t chi, int32_t precision, int32_t n_sweeps,
+                           double* out_logz, double* out_worst_trunc_sv);
+
+/* Conditional marginals p(x_{n+1} | x_n) of Eq. (6) / Fig. 6 for a set of
+ * partial configurations.  step = n+1 is the row-major index of the cluster
+ * being placed; configs[count][step] holds the state index (position in the
+ * site's state list) of every already placed cluster.  out_p[count][d] with
+ * d the number of states of cluster `step`.  Requires contract_boundary. */
+int sgtn_conditionals(sgtn_h h, int32_t step, int32_t count, const int32_t* configs, double* out_p);
+
+/* One branch-and-bound step (Sec. III.A, Fig. 3): branch every input
+ * configuration over all states of cluster `step`, score candidates with the
+ * chain rule (Eq. 6), keep the most probable candidate of every boundary
+ * (Eq. 7), then the M most probable; ties go to the lexicographically smaller
+ * configuration.
+ *   in_configs[in_count][step], in_logp[in_count]
+ *   out_configs[M][step+1], out_logp[M], *out_count <= M
+ *   *io_pd: on entry the largest discarded log-probability so far (or
+ *           -inf), on exit updated with this step's discards. */
+int sgtn_branch_step(sgtn_h h, int32_t step, int32_t M, int32_t in_count, const int32_t* in_configs,
+                     const double* in_logp, int32_t* out_configs, double* out_logp, int32_t* out_count,
+                     double* io_pd);
+
+/* Full search: all R*C steps from the empty configuration.  Writes up to
+ * n_out final configurations (the search's merging leaves one at the end)
+ *   out_spins[n_out][n_spins] (+1/-1), out_energy_num[n_out] (exact
+ *   H * denom, int64), out_logp[n_out]; *out_pd = largest discarded log p;
+ *   *out_count = number written. */
+int sgtn_search(sgtn_h h, int32_t M, int32_t n_out, int8_t* out_spins, int64_t* out_energy_num,
+                double* out_logp, double* out_pd, int32_t* out_count);
+
+/* Exact int64 energies (numerators over denom) of n configurations of +-1
+ * spins, computed on the device: out[k] = sum j_num s_i s_j + sum h_num s_i. */
+int sgtn_energies(sgtn_h h, int32_t n, const int8_t* spins, int64_t* out);
+
+/* Introspection for tests.  sgtn_site_dims: number of states of a site.
+ * sgtn_mps_shape: physical and bond dimensions of the boundary MPS psi_row
+ * (phys[cols], bond[cols+1]) and its log-norm.  sgtn_mps_tensor copies
+ * column `col` of psi_row to out ([phys][bond_l][bond_r], double). */
+int sgtn_site_dims(sgtn_h h, int32_t site, int32_t* d);
+int sgtn_mps_shape(sgtn_h h, int32_t row, int32_t* phys, int32_t* bond, double* lognorm);
+int sgtn_mps_tensor(sgtn_h h, int32_t row, int32_t col, double* out);
+
+const char* sgtn_last_error(sgtn_h h);
+void sgtn_destroy(sgtn_h h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,186 @@
+// C ABI of the sgtn library: argument checks, error capture, dispatch.
+#include <cmath>
+#include <cstring>
+
+#include "../../include/sgtn.h"
+#include "handle.h"
+
+namespace sgtn {
+
+namespace {
+// H = sum j s_i s_j + sum h s_i, exact in int64, one block per configuration
+__global__ void energy_kernel(int N, long long nE, const int8_t* spins, const int32_t* ei, const int32_t* ej,
+                              const int32_t* jn, const int32_t* hn, long long* out) {
+  const int8_t* s = spins + (long long)blockIdx.x * N;
+  long long a = 0;
+  for (long long e = threadIdx.x; e < nE; e += blockDim.x) a += (long long)jn[e] * s[ei[e]] * s[ej[e]];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) a += (long long)hn[i] * s[i];
+  __shared__ long long red[32];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[blockIdx.x] = t;
+  }
+}
+}  // namespace
+
+void energies(sgtn_inst* h, int n, const int8_t* spins, int64_t* out) {
+  if (n <= 0) return;
+  for (long long i = 0; i < (long long)n * h->M.N; ++i)
+    if (spins[i] != 1 && spins[i] != -1) throw SgtnError(-1, "spins must be +1 or -1");
+  static_assert(sizeof(long long) == sizeof(int64_t), "int64");
+  int8_t* ds = nullptr;
+  long long* dout = nullptr;
+  SGTN_CUDA(cudaMalloc(&ds, size_t(n) * h->M.N));
+  SGTN_CUDA(cudaMalloc(&dout, size_t(n) * sizeof(long long)));
+  SGTN_CUDA(cudaMemcpyAsync(ds, spins, size_t(n) * h->M.N, cudaMemcpyHostToDevice, h->st));
+  std::vector<int32_t> z(1, 0);
+  const int32_t* ei = h->M.ei.empty() ? nullptr : h->upload(h->M.ei);
+  const int32_t* ej = h->M.ej.empty() ? nullptr : h->upload(h->M.ej);
+  const int32_t* jn = h->M.jn.empty() ? nullptr : h->upload(h->M.jn);
+  const int32_t* hn = h->upload(h->M.hn);
+  energy_kernel<<<n, 256, 0, h->st>>>(h->M.N, (long long)h->M.ei.size(), ds, ei, ej, jn, hn, dout);
+  h->check();
+  SGTN_CUDA(cudaMemcpyAsync(out, dout, size_t(n) * sizeof(long long), cudaMemcpyDeviceToHost, h->st));
+  h->sync();
+  cudaFree(ds);
+  cudaFree(dout);
+}
+
+}  // namespace sgtn
+
+using namespace sgtn;
+
+namespace {
+template <class F>
+int guarded(sgtn_h h, F&& f) {
+  if (!h) return SGTN_ERR_ARG;
+  try {
+    SGTN_CUDA(cudaSetDevice(h->device));
+    f();
+    h->err.clear();
+    return SGTN_OK;
+  } catch (const SgtnError& e) {
+    h->err = e.what();
+    cudaGetLastError();
+    return e.code;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return SGTN_ERR_CUDA;
+  }
+}
+}  // namespace
+
+extern "C" {
+
+int sgtn_build_instance(int32_t n_spins, int64_t n_edges, const int32_t* ei, const int32_t* ej, const int32_t* j_num,
+                        const int32_t* h_num, int32_t denom, const int32_t* site_of_spin, int32_t rows, int32_t cols,
+                        const int64_t* state_offsets, const int64_t* states, void* stream, sgtn_h* out) {
+  if (!out) return SGTN_ERR_ARG;
+  *out = nullptr;
+  sgtn_inst* h = new sgtn_inst();
+  cudaGetDevice(&h->device);
+  h->st = static_cast<cudaStream_t>(stream);
+  std::string e = h->M.build(n_spins, n_edges, ei, ej, j_num, h_num, denom, site_of_spin, rows, cols, state_offsets,
+                             states);
+  if (!e.empty()) {
+    delete h;
+    return SGTN_ERR_ARG;
+  }
+  int rc = guarded(h, [&] { setup_device(h); });
+  if (rc != SGTN_OK) {
+    sgtn_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return SGTN_OK;
+}
+
+int sgtn_set_beta(sgtn_h h, double beta) {
+  if (h && !(std::isfinite(beta) && beta >= 0)) {
+    h->err = "beta must be finite and >= 0";
+    return SGTN_ERR_ARG;
+  }
+  return guarded(h, [&] { set_beta_device(h, beta); });
+}
+
+int sgtn_contract_boundary(sgtn_h h, int32_t chi, int32_t precision, int32_t n_sweeps, double* out_logz,
+                           double* out_worst_trunc_sv) {
+  return guarded(h, [&] {
+    if (!h->beta_set) throw SgtnError(SGTN_ERR_STATE, "set_beta must run first");
+    if (chi < 1 || n_sweeps < 0 || n_sweeps > 100) throw SgtnError(SGTN_ERR_ARG, "bad chi or n_sweeps");
+    if (precision != SGTN_FP64) throw SgtnError(SGTN_ERR_ARG, "only SGTN_FP64 is available in this build");
+    h->precision = precision;
+    contract_boundary(h, chi, n_sweeps);
+    if (out_logz) *out_logz = h->logz;
+    if (out_worst_trunc_sv) *out_worst_trunc_sv = h->worst_sv;
+  });
+}
+
+int sgtn_conditionals(sgtn_h h, int32_t step, int32_t count, const int32_t* configs, double* out_p) {
+  return guarded(h, [&] { conditionals(h, step, count, configs, out_p); });
+}
+
+int sgtn_branch_step(sgtn_h h, int32_t step, int32_t M, int32_t in_count, const int32_t* in_configs,
+                     const double* in_logp, int32_t* out_configs, double* out_logp, int32_t* out_count,
+                     double* io_pd) {
+  return guarded(h, [&] { branch_step(h, step, M, in_count, in_configs, in_logp, out_configs, out_logp, out_count, io_pd); });
+}
+
+int sgtn_search(sgtn_h h, int32_t M, int32_t n_out, int8_t* out_spins, int64_t* out_energy_num, double* out_logp,
+                double* out_pd, int32_t* out_count) {
+  return guarded(h, [&] { search(h, M, n_out, out_spins, out_energy_num, out_logp, out_pd, out_count); });
+}
+
+int sgtn_energies(sgtn_h h, int32_t n, const int8_t* spins, int64_t* out) {
+  return guarded(h, [&] {
+    if (n < 0 || (n > 0 && (!spins || !out))) throw SgtnError(SGTN_ERR_ARG, "bad argument");
+    energies(h, n, spins, out);
+  });
+}
+
+int sgtn_site_dims(sgtn_h h, int32_t site, int32_t* d) {
+  return guarded(h, [&] {
+    if (site < 0 || site >= h->M.R * h->M.C || !d) throw SgtnError(SGTN_ERR_ARG, "bad site");
+    *d = h->M.sites[site].d;
+  });
+}
+
+int sgtn_mps_shape(sgtn_h h, int32_t row, int32_t* phys, int32_t* bond, double* lognorm) {
+  return guarded(h, [&] {
+    if (!h->boundary_ok) throw SgtnError(SGTN_ERR_STATE, "no boundary MPS");
+    if (row < 0 || row >= h->M.R || !phys || !bond) throw SgtnError(SGTN_ERR_ARG, "bad row");
+    const MPS& m = h->psi[row];
+    for (int c = 0; c < m.C; ++c) phys[c] = m.phys[c];
+    for (int c = 0; c <= m.C; ++c) bond[c] = m.bond[c];
+    if (lognorm) *lognorm = m.lognorm;
+  });
+}
+
+int sgtn_mps_tensor(sgtn_h h, int32_t row, int32_t col, double* out) {
+  return guarded(h, [&] {
+    if (!h->boundary_ok) throw SgtnError(SGTN_ERR_STATE, "no boundary MPS");
+    if (row < 0 || row >= h->M.R || col < 0 || col >= h->M.C || !out) throw SgtnError(SGTN_ERR_ARG, "bad index");
+    const MPS& m = h->psi[row];
+    size_t n = size_t(m.phys[col]) * m.bond[col] * m.bond[col + 1];
+    SGTN_CUDA(cudaMemcpyAsync(out, m.t[col], n * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    h->sync();
+  });
+}
+
+const char* sgtn_last_error(sgtn_h h) { return h ? h->err.c_str() : "null handle"; }
+
+void sgtn_destroy(sgtn_h h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->st);
+  for (auto& m : h->psi) free_mps(m);
+  h->ws.release();
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,585 @@
+// Boundary-MPS contraction of the Boltzmann-weight PEPS (paper Sec. III.B,
+// Figs. 5-8), double precision.
+//
+// Conventions (shared with the branch step):
+//  * psi_r (r = 0..R-1) stands for rows r+1..R-1; its physical index at
+//    column c is the class of site (r+1, c) restricted to the spins coupled to
+//    row r ("up exposure", Column::nSig); psi_{R-1} is the trivial MPS.
+//  * MPO bond (c, c+1) of row r carries (lam, g): lam = left exposure of site
+//    (r, c+1) (its spins coupled to (r, c) or (r+1, c)), g = class of site
+//    (r+1, c+1) toward (r, c).  Diagonal couplings therefore travel on the
+//    horizontal bond -- the job of the mediating tensors of Fig. 5.
+//  * Sparse site diagram (Fig. 7b):  Theta[(bl, al), (u, k')] =
+//      sum_{x: Lam(x)=lam, U(x)=u} w_x sum_e Ahat[(pd_x, e, g)] Ktil[(pr_x, e, pdr_x)]
+//    with the projected MPS Ahat = Wa A  (bond factors to the row below
+//    applied, Wa[(pd,e,g), sigma] = [pi_ul sigma = g] Bv[pd, pi_u sigma] Bdl[e, pi_ur sigma])
+//    and the absorbed right tensor Ktil = Wk K (Wk[(pr,e,pdr), (lam',g')] =
+//    [pi_dl lam' = e] Bh[pr, pi_l lam'] Bdr[pdr, g']).  Cost 2 chi^3 per term.
+//  * Zipper (Fig. 8c): right to left from a 1x1x1 connecting tensor, SVD of
+//    Theta keeping 2 chi values; then one-site variational sweeps (Fig. 8d),
+//    an SVD cut to chi and more sweeps.  Singular values below 1e-12 of the
+//    largest are dropped everywhere, orthonormalisations included.
+//  * MPS tensors are stored [phys][bond_l][bond_r]; the approximation being
+//    built (phi) is kept bond-major [bond_l][phys][bond_r].
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "handle.h"
+
+namespace sgtn {
+
+namespace {
+
+constexpr double RANK_TOL = 1e-12;
+
+struct Ten {
+  double* p = nullptr;
+  int a = 1, u = 1, b = 1;   // [a][u][b]
+  long long n() const { return (long long)a * u * b; }
+};
+
+double* dmalloc(long long n) {
+  double* p = nullptr;
+  SGTN_CUDA(cudaMalloc(&p, size_t(n > 0 ? n : 1) * sizeof(double)));
+  return p;
+}
+void dfree(double*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+struct SvdOut {
+  int k = 0;
+  double* US = nullptr;   // m x k
+  double* Vt = nullptr;   // k x n
+  double* dsig = nullptr; // k sigmas then k inverse sigmas (device)
+  std::vector<double> sig;
+  void release() {
+    dfree(US);
+    dfree(Vt);
+    dfree(dsig);
+  }
+};
+
+// Truncated SVD of a dense row-major m x n matrix by one-sided Jacobi on the
+// shorter side.  Keeps at most cap singular values, none below RANK_TOL.
+SvdOut svd(sgtn_inst* h, const double* Th, int m, int n, int cap) {
+  cudaStream_t st = h->st;
+  SvdOut o;
+  double* T2 = h->ws.get<double>("svd_T2", size_t(m) * n);
+  copy(T2, Th, (long long)m * n, st);
+  int* status = h->ws.get<int>("svd_status", 1);
+  int p = std::min(m, n);
+  double* dsigall = h->ws.get<double>("svd_sig", p);
+  double* V = nullptr;
+  if (m <= n) {
+    jacobi(T2, n, m, 1, n, nullptr, 60, status, st);
+    vec_norms(T2, n, m, 1, n, dsigall, st);
+  } else {
+    V = h->ws.get<double>("svd_V", size_t(n) * n);
+    jacobi(T2, m, n, n, 1, V, 60, status, st);
+    vec_norms(T2, m, n, n, 1, dsigall, st);
+  }
+  h->check();
+  std::vector<double> s(p);
+  int hs = 0;
+  SGTN_CUDA(cudaMemcpyAsync(s.data(), dsigall, p * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SGTN_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  h->sync();
+  if (hs < 0) throw SgtnError(-4, "Jacobi SVD did not converge");
+  std::vector<int> idx(p);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return s[a] > s[b]; });
+  double smax = p ? s[idx[0]] : 0.0;
+  if (!(smax > 0.0) || !std::isfinite(smax)) throw SgtnError(-4, "zero or non-finite tensor in truncation");
+  int cnt = 0;
+  for (int i = 0; i < p; ++i)
+    if (s[idx[i]] > RANK_TOL * smax) ++cnt;
+  int k = std::min(cap, cnt);
+  o.k = k;
+  std::vector<double> sv(2 * k);
+  std::vector<int32_t> perm(k);
+  for (int i = 0; i < k; ++i) {
+    perm[i] = idx[i];
+    sv[i] = s[idx[i]];
+    sv[k + i] = 1.0 / s[idx[i]];
+    o.sig.push_back(s[idx[i]]);
+  }
+  int32_t* dperm = h->ws.get<int32_t>("svd_perm", k);
+  o.dsig = dmalloc(2 * k);
+  SGTN_CUDA(cudaMemcpyAsync(dperm, perm.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  SGTN_CUDA(cudaMemcpyAsync(o.dsig, sv.data(), 2 * k * sizeof(double), cudaMemcpyHostToDevice, st));
+  o.US = dmalloc((long long)m * k);
+  o.Vt = dmalloc((long long)k * n);
+  if (m <= n) {
+    gather_vecs(T2, n, 1, n, dperm, o.dsig + k, k, o.Vt, 1, n, st);        // rows / sigma
+    gemm(Th, false, n, o.Vt, true, n, o.US, k, m, k, n, 1.0, 0, st);      // Theta Vt^T = U S
+  } else {
+    double* ones = h->ws.get<double>("svd_ones", k);
+    fill(ones, k, 1.0, st);
+    gather_vecs(V, n, 1, n, dperm, ones, k, o.Vt, 1, n, st);
+    gather_vecs(T2, m, n, 1, dperm, ones, k, o.US, k, 1, st);
+  }
+  h->check();
+  // the host waits on the next transfer anyway; keep perm alive until then
+  h->sync();
+  return o;
+}
+
+// Q = US / sigma (m x k)
+double* left_factor(sgtn_inst* h, const SvdOut& o, int m) {
+  double* Q = dmalloc((long long)m * o.k);
+  gather_vecs(o.US, m, o.k, 1, h->iota, o.dsig + o.k, o.k, Q, o.k, 1, h->st);
+  return Q;
+}
+// R = sigma Vt (k x n)
+double* right_factor(sgtn_inst* h, const SvdOut& o, int n) {
+  double* Rm = dmalloc((long long)o.k * n);
+  gather_vecs(o.Vt, n, 1, n, h->iota, o.dsig, o.k, Rm, 1, n, h->st);
+  return Rm;
+}
+
+double norm_host(sgtn_inst* h, const double* x, long long n) {
+  double* d = h->ws.get<double>("norm_out", 1);
+  fro_norm(x, n, d, h->st);
+  double v = 0;
+  SGTN_CUDA(cudaMemcpyAsync(&v, d, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  h->sync();
+  if (!(v > 0.0) || !std::isfinite(v)) throw SgtnError(-4, "zero or non-finite norm");
+  return v;
+}
+void normalise(sgtn_inst* h, double* x, long long n, double& lognorm) {
+  double v = norm_host(h, x, n);
+  lognorm += std::log(v);
+  scale_by_inv(x, n, h->ws.get<double>("norm_out", 1), h->st);
+}
+
+struct RowCtx {
+  sgtn_inst* h;
+  int r;
+  const MPS* A;                 // psi_r, left-canonical
+  std::vector<double*> Ahat;    // per column [nA][chl][chr]
+  const Column& col(int c) const { return h->cols[r * h->M.C + c]; }
+  int chl(int c) const { return A->bond[c]; }
+  int chr(int c) const { return A->bond[c + 1]; }
+};
+
+// Ktil = Wk * K   with K [nBR][chr][kp]
+double* absorb(RowCtx& X, int c, const double* K, int kp, const char* name) {
+  const Column& K_ = X.col(c);
+  double* Kt = X.h->ws.get<double>(name, size_t(K_.nK()) * X.chr(c) * kp);
+  gemm(K_.Wk, false, K_.nBR(), K, false, (long long)X.chr(c) * kp, Kt, (long long)X.chr(c) * kp, K_.nK(),
+       X.chr(c) * kp, K_.nBR(), 1.0, 0, X.h->st);
+  return Kt;
+}
+
+// Theta [(bl, chl) x (u, kp)] of the sparse site diagram
+void site_diagram(RowCtx& X, int c, const double* Kt, int kp, double* Th) {
+  const Column& K_ = X.col(c);
+  int chl = X.chl(c), chr = X.chr(c);
+  long long m = (long long)K_.nBL() * chl, n = (long long)K_.nU * kp;
+  SGTN_CUDA(cudaMemsetAsync(Th, 0, size_t(m * n) * sizeof(double), X.h->st));
+  SegGemm a;
+  a.X = X.Ahat[c];
+  a.Y = Kt;
+  a.O = Th;
+  a.p = chl;
+  a.q = chr;
+  a.s = kp;
+  a.xs_i = chr;
+  a.xs_k = 1;
+  a.xrs = (long long)chl * chr;
+  a.ys_k = kp;
+  a.ys_j = 1;
+  a.yrs = (long long)chr * kp;
+  a.os_i = n;
+  a.os_j = 1;
+  a.ors = (long long)chl * n;
+  a.ocs = kp;
+  a.seg_ptr = K_.theta.seg_ptr;
+  a.seg_or = K_.theta.seg_or;
+  a.seg_oc = K_.theta.seg_oc;
+  a.xr = K_.theta.xr;
+  a.xc = K_.theta.xc;
+  a.yr = K_.theta.yr;
+  a.yc = K_.theta.yc;
+  a.cidx = K_.theta.cidx;
+  a.coef = X.h->ds[X.r * X.h->M.C + c].w;
+  a.nseg = K_.theta.nseg;
+  seg_gemm(a, X.h->st);
+}
+
+// Theta for column c with right tensor K ([nBR][chr][kp]); returns scratch pointer
+double* theta_of(RowCtx& X, int c, const double* K, int kp) {
+  double* Kt = absorb(X, c, K, kp, "ktil");
+  const Column& K_ = X.col(c);
+  double* Th = X.h->ws.get<double>("theta", size_t(K_.nBL()) * X.chl(c) * K_.nU * kp);
+  site_diagram(X, c, Kt, kp, Th);
+  return Th;
+}
+
+// L env update: Lnext [b][br][chr] from L [a][bl][chl] and phi_c [a][u][b]
+double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
+  sgtn_inst* h = X.h;
+  const Column& K_ = X.col(c);
+  int chl = X.chl(c), chr = X.chr(c);
+  long long nbl = K_.nBL();
+  // N[(u,b), (bl,chl)] = sum_a phi[a][(u,b)] L[a][(bl,chl)]
+  long long nub = (long long)phi.u * phi.b;
+  double* N = h->ws.get<double>("lupd_N", size_t(nub * nbl * chl));
+  gemm(phi.p, true, nub, L, false, nbl * chl, N, nbl * chl, int(nub), int(nbl * chl), phi.a, 1.0, 0, h->st);
+  // Ltil[(pr,e,pdr)][b][chr] = sum_terms w_x N[(u_x, bl)] Ahat[(pd,e,g)]
+  double* Lt = h->ws.get<double>("lupd_Lt", size_t(K_.nK()) * phi.b * chr);
+  SGTN_CUDA(cudaMemsetAsync(Lt, 0, size_t(K_.nK()) * phi.b * chr * sizeof(double), h->st));
+  SegGemm a;
+  a.X = N;
+  a.p = phi.b;
+  a.q = chl;
+  a.xs_i = nbl * chl;
+  a.xs_k = 1;
+  a.xrs = (long long)phi.b * nbl * chl;
+  a.xcs = chl;
+  a.Y = X.Ahat[c];
+  a.s = chr;
+  a.ys_k = chr;
+  a.ys_j = 1;
+  a.yrs = (long long)chl * chr;
+  a.O = Lt;
+  a.os_i = chr;
+  a.os_j = 1;
+  a.ors = (long long)phi.b * chr;
+  a.seg_ptr = K_.lupd.seg_ptr;
+  a.seg_or = K_.lupd.seg_or;
+  a.seg_oc = K_.lupd.seg_oc;
+  a.xr = K_.lupd.xr;
+  a.xc = K_.lupd.xc;
+  a.yr = K_.lupd.yr;
+  a.yc = K_.lupd.yc;
+  a.cidx = K_.lupd.cidx;
+  a.coef = h->ds[X.r * h->M.C + c].w;
+  a.nseg = K_.lupd.nseg;
+  seg_gemm(a, h->st);
+  // Lnext[b][br][chr] = sum_k Wk[k][br] Ltil[k][b][chr]   (batched over b)
+  double* Ln = dmalloc((long long)phi.b * K_.nBR() * chr);
+  SegGemm g;
+  g.X = K_.Wk;
+  g.p = K_.nBR();
+  g.q = K_.nK();
+  g.xs_i = 1;
+  g.xs_k = K_.nBR();
+  g.xrs = 0;
+  g.Y = Lt;
+  g.s = chr;
+  g.ys_k = (long long)phi.b * chr;
+  g.ys_j = 1;
+  g.yrs = chr;
+  g.O = Ln;
+  g.os_i = chr;
+  g.os_j = 1;
+  g.ors = (long long)K_.nBR() * chr;
+  g.nseg = phi.b;
+  seg_gemm(g, h->st);
+  return Ln;
+}
+
+// R env update: Rprev[(bl, chl)][a] = Theta_R phi^T
+double* update_R(RowCtx& X, int c, const double* ThR, const Ten& phi) {
+  const Column& K_ = X.col(c);
+  long long m = (long long)K_.nBL() * X.chl(c), n = (long long)K_.nU * phi.b;
+  double* Rp = dmalloc(m * phi.a);
+  gemm(ThR, false, n, phi.p, true, n, Rp, phi.a, int(m), phi.a, int(n), 1.0, 0, X.h->st);
+  return Rp;
+}
+
+void right_canonical(RowCtx& X, std::vector<Ten>& phi) {
+  sgtn_inst* h = X.h;
+  for (int c = (int)phi.size() - 1; c > 0; --c) {
+    Ten& t = phi[c];
+    SvdOut o = svd(h, t.p, t.a, t.u * t.b, 1 << 30);
+    Ten& l = phi[c - 1];
+    double* nl = dmalloc((long long)l.a * l.u * o.k);
+    gemm(l.p, false, l.b, o.US, false, o.k, nl, o.k, l.a * l.u, o.k, l.b, 1.0, 0, h->st);
+    dfree(l.p);
+    l.p = nl;
+    l.b = o.k;
+    dfree(t.p);
+    t.p = o.Vt;
+    o.Vt = nullptr;
+    t.a = o.k;
+    o.release();
+  }
+}
+
+// One left-right-left sweep of one-site overlap maximisation (Fig. 8d).
+void variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
+  sgtn_inst* h = X.h;
+  const int C = (int)phi.size();
+  right_canonical(X, phi);
+  std::vector<double*> Renv(C, nullptr), Lenv(C, nullptr);
+  Renv[C - 1] = dmalloc(1);
+  fill(Renv[C - 1], 1, 1.0, h->st);
+  for (int c = C - 1; c > 0; --c) {
+    double* Th = theta_of(X, c, Renv[c], phi[c].b);
+    Renv[c - 1] = update_R(X, c, Th, phi[c]);
+  }
+  Lenv[0] = dmalloc(1);
+  fill(Lenv[0], 1, 1.0, h->st);
+  for (int c = 0; c < C; ++c) {
+    const Column& K_ = X.col(c);
+    double* Th = theta_of(X, c, Renv[c], phi[c].b);
+    int a = phi[c].a;
+    long long n = (long long)K_.nU * phi[c].b;
+    double* t = dmalloc(a * n);
+    gemm(Lenv[c], false, (long long)K_.nBL() * X.chl(c), Th, false, n, t, n, a, int(n),
+         K_.nBL() * X.chl(c), 1.0, 0, h->st);
+    dfree(phi[c].p);
+    phi[c].p = t;
+    phi[c].u = K_.nU;
+    if (c < C - 1) {
+      SvdOut o = svd(h, t, a * K_.nU, phi[c].b, 1 << 30);
+      double* Q = left_factor(h, o, a * K_.nU);
+      dfree(phi[c].p);
+      phi[c].p = Q;
+      phi[c].b = o.k;
+      o.release();
+      Lenv[c + 1] = update_L(X, c, Lenv[c], phi[c]);
+      // the next site's left bond is now o.k; its right bond is unchanged
+      phi[c + 1].a = phi[c].b;
+    }
+  }
+  for (auto& p : Renv) dfree(p);
+  double* Rc = dmalloc(1);
+  fill(Rc, 1, 1.0, h->st);
+  for (int c = C - 1; c >= 0; --c) {
+    const Column& K_ = X.col(c);
+    double* Th = theta_of(X, c, Rc, phi[c].b);
+    int a = phi[c].a;
+    long long n = (long long)K_.nU * phi[c].b;
+    double* t = dmalloc(a * n);
+    gemm(Lenv[c], false, (long long)K_.nBL() * X.chl(c), Th, false, n, t, n, a, int(n),
+         K_.nBL() * X.chl(c), 1.0, 0, h->st);
+    dfree(phi[c].p);
+    phi[c].p = t;
+    if (c > 0) {
+      SvdOut o = svd(h, t, a, int(n), 1 << 30);
+      dfree(phi[c].p);
+      phi[c].p = o.Vt;
+      o.Vt = nullptr;
+      phi[c].a = o.k;
+      o.release();
+      double* Rn = update_R(X, c, Th, phi[c]);
+      dfree(Rc);
+      Rc = Rn;
+      phi[c - 1].b = phi[c].a;
+    }
+  }
+  dfree(Rc);
+  for (auto& p : Lenv) dfree(p);
+}
+
+// cut a right-canonical phi (centre 0) to bond chi; returns worst retained ratio
+double svd_cut(RowCtx& X, std::vector<Ten>& phi, int chi) {
+  sgtn_inst* h = X.h;
+  double worst = 0.0;
+  for (int c = 0; c + 1 < (int)phi.size(); ++c) {
+    Ten& t = phi[c];
+    SvdOut o = svd(h, t.p, t.a * t.u, t.b, chi);
+    worst = std::max(worst, o.sig.back() / o.sig.front());
+    double* Q = left_factor(h, o, t.a * t.u);
+    double* Rm = right_factor(h, o, t.b);
+    dfree(t.p);
+    t.p = Q;
+    Ten& n = phi[c + 1];
+    double* nn = dmalloc((long long)o.k * n.u * n.b);
+    gemm(Rm, false, t.b, n.p, false, (long long)n.u * n.b, nn, (long long)n.u * n.b, o.k, n.u * n.b, t.b, 1.0, 0,
+         h->st);
+    dfree(Rm);
+    dfree(n.p);
+    n.p = nn;
+    n.a = o.k;
+    t.b = o.k;
+    o.release();
+  }
+  return worst;
+}
+
+void left_canonical(sgtn_inst* h, MPS& A) {
+  const int C = A.C;
+  for (int c = 0; c + 1 < C; ++c) {
+    int s = A.phys[c], l = A.bond[c], r = A.bond[c + 1];
+    SvdOut o = svd(h, A.t[c], s * l, r, 1 << 30);
+    double* Q = left_factor(h, o, s * l);
+    double* Rm = right_factor(h, o, r);
+    cudaFree(A.t[c]);
+    A.t[c] = Q;
+    int s2 = A.phys[c + 1], r2 = A.bond[c + 2];
+    double* nn = dmalloc((long long)s2 * o.k * r2);
+    // nn[s][k][r2] = sum_r Rm[k][r] A[s][r][r2]   (batched over s)
+    SegGemm g;
+    g.X = Rm;
+    g.p = o.k;
+    g.q = r;
+    g.xs_i = r;
+    g.xs_k = 1;
+    g.xrs = 0;
+    g.Y = A.t[c + 1];
+    g.s = r2;
+    g.ys_k = r2;
+    g.ys_j = 1;
+    g.yrs = (long long)r * r2;
+    g.O = nn;
+    g.os_i = r2;
+    g.os_j = 1;
+    g.ors = (long long)o.k * r2;
+    g.nseg = s2;
+    seg_gemm(g, h->st);
+    dfree(Rm);
+    cudaFree(A.t[c + 1]);
+    A.t[c + 1] = nn;
+    A.bond[c + 1] = o.k;
+    o.release();
+  }
+  long long nl = (long long)A.phys[C - 1] * A.bond[C - 1] * A.bond[C];
+  normalise(h, A.t[C - 1], nl, A.lognorm);
+}
+
+void compute_ahat(RowCtx& X) {
+  const int C = X.h->M.C;
+  X.Ahat.assign(C, nullptr);
+  for (int c = 0; c < C; ++c) {
+    const Column& K_ = X.col(c);
+    long long blk = (long long)X.chl(c) * X.chr(c);
+    X.Ahat[c] = dmalloc(K_.nA() * blk);
+    gemm(K_.Wa, false, K_.nSig, X.A->t[c], false, blk, X.Ahat[c], blk, K_.nA(), int(blk), K_.nSig, 1.0, 0,
+         X.h->st);
+  }
+}
+
+// psi_{r-1} ~ T_r psi_r
+void row_step(sgtn_inst* h, int r, int chi, int n_sweeps, MPS& out, double& worst) {
+  const int C = h->M.C;
+  MPS& A = h->psi[r];
+  left_canonical(h, A);
+  RowCtx X{h, r, &A, {}};
+  compute_ahat(X);
+  // zipper
+  std::vector<Ten> phi(C);
+  double* K = dmalloc(1);
+  fill(K, 1, 1.0, h->st);
+  int kp = 1;
+  double ln = A.lognorm;
+  for (int c = C - 1; c >= 0; --c) {
+    const Column& K_ = X.col(c);
+    double* Th = theta_of(X, c, K, kp);
+    int m = K_.nBL() * X.chl(c), n = K_.nU * kp;
+    SvdOut o = svd(h, Th, m, n, 2 * chi);
+    phi[c].p = o.Vt;
+    o.Vt = nullptr;
+    phi[c].a = o.k;
+    phi[c].u = K_.nU;
+    phi[c].b = kp;
+    dfree(K);
+    K = o.US;
+    o.US = nullptr;
+    normalise(h, K, (long long)m * o.k, ln);
+    kp = o.k;
+    o.release();
+  }
+  {
+    double kv = 0;
+    SGTN_CUDA(cudaMemcpyAsync(&kv, K, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    h->sync();
+    if (kv < 0) {
+      double* m1 = h->ws.get<double>("minus_one", 1);
+      fill(m1, 1, -1.0, h->st);
+      scale_by_inv(phi[0].p, phi[0].n(), m1, h->st);
+    }
+  }
+  dfree(K);
+  for (int s = 0; s < n_sweeps; ++s) {
+    variational_sweep(X, phi);
+    ln = A.lognorm;
+    normalise(h, phi[0].p, phi[0].n(), ln);
+  }
+  worst = std::max(worst, svd_cut(X, phi, chi));
+  normalise(h, phi[C - 1].p, phi[C - 1].n(), ln);
+  for (int s = 0; s < n_sweeps; ++s) {
+    variational_sweep(X, phi);
+    ln = A.lognorm;
+    normalise(h, phi[0].p, phi[0].n(), ln);
+  }
+  for (double* p : X.Ahat) cudaFree(p);
+  // store as [phys][bond_l][bond_r]
+  free_mps(out);
+  out.C = C;
+  out.phys.assign(C, 1);
+  out.bond.assign(C + 1, 1);
+  out.t.assign(C, nullptr);
+  for (int c = 0; c < C; ++c) {
+    out.phys[c] = phi[c].u;
+    out.bond[c] = phi[c].a;
+    out.bond[c + 1] = phi[c].b;
+    out.t[c] = dmalloc(phi[c].n());
+    permute3(phi[c].p, phi[c].a, phi[c].u, phi[c].b, out.t[c], h->st);
+    dfree(phi[c].p);
+  }
+  out.lognorm = ln;
+  out.valid = true;
+  h->check();
+}
+
+double top_overlap(sgtn_inst* h) {
+  const int C = h->M.C;
+  MPS& A = h->psi[0];
+  RowCtx X{h, 0, &A, {}};
+  compute_ahat(X);
+  double ln = A.lognorm;
+  double* Rc = dmalloc(1);
+  fill(Rc, 1, 1.0, h->st);
+  for (int c = C - 1; c >= 0; --c) {
+    const Column& K_ = X.col(c);
+    double* Th = theta_of(X, c, Rc, 1);
+    long long m = (long long)K_.nBL() * X.chl(c);
+    double* Rn = dmalloc(m);
+    copy(Rn, Th, m, h->st);  // nU = 1 in the top row
+    dfree(Rc);
+    Rc = Rn;
+    if (c > 0) normalise(h, Rc, m, ln);
+  }
+  double v = 0;
+  SGTN_CUDA(cudaMemcpyAsync(&v, Rc, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  h->sync();
+  dfree(Rc);
+  for (double* p : X.Ahat) cudaFree(p);
+  if (!(v > 0.0) || !std::isfinite(v)) throw SgtnError(-4, "non-positive partition function");
+  return ln + std::log(v);
+}
+
+}  // namespace
+
+void contract_boundary(sgtn_inst* h, int chi, int n_sweeps) {
+  const int R = h->M.R, C = h->M.C;
+  for (auto& m : h->psi) free_mps(m);
+  h->psi.assign(R, MPS());
+  MPS& last = h->psi[R - 1];
+  last.C = C;
+  last.phys.assign(C, 1);
+  last.bond.assign(C + 1, 1);
+  last.t.assign(C, nullptr);
+  for (int c = 0; c < C; ++c) {
+    last.t[c] = dmalloc(1);
+    fill(last.t[c], 1, 1.0, h->st);
+  }
+  last.lognorm = 0.0;
+  last.valid = true;
+  double worst = 0.0;
+  for (int r = R - 1; r >= 1; --r) row_step(h, r, chi, n_sweeps, h->psi[r - 1], worst);
+  h->logz = h->log_offset + top_overlap(h);
+  h->worst_sv = worst;
+  h->chi = chi;
+  h->n_sweeps = n_sweeps;
+  h->boundary_ok = true;
+}
+
+}  // namespace sgtn

@@ -1,0 +1,688 @@
+// Branch-and-bound step (paper Sec. III.A, Fig. 3) on the device.
+//
+// For partial configurations k (the beam) and the next cluster n = (r, c):
+//  1. f_k[c'][u]  Boltzmann factors between the fixed row r-1 of branch k and
+//     class u of the up exposure of (r, c')  (1 in the top row).
+//  2. E_k  left environment: row r's placed columns < c contracted with
+//     psi_r (Fig. 6b); F_k right environment: the unplaced columns > c summed
+//     over their states with the factors f_k, contracted with psi_r.
+//  3. s_k(x) = f_k[c][U x] w_x sum_{g,e} E_k[(Lam x, g)] Ahat[(pd x, e, g)] Ftil_k[(pr x, e, pdr x)]
+//     and the chain rule log p = log p_k + log(s_k(x) / sum_x' s_k(x'))  (Eq. 6);
+//     negative scores (possible with an approximate psi) are clamped to 0.
+//  4. Merge (Eq. 7): the boundary of candidate (k, x) is the pair
+//     (boundary classes of k that stay on the boundary, merge class of x);
+//     the first part is turned into an exact parent class id by comparing
+//     the class vectors of all branches, so the merge key is exact (no hash).
+//     The most probable candidate of each key survives; ties go to the
+//     lexicographically smaller configuration.
+//  5. Top-M by (log p desc, configuration asc) through a radix select on the
+//     ordered bits of log p; p_d = largest log p among valid candidates that
+//     did not survive.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <numeric>
+
+#include "handle.h"
+
+namespace sgtn {
+
+namespace {
+
+__device__ __host__ inline unsigned long long ord_key(double v) {
+  unsigned long long u;
+  memcpy(&u, &v, sizeof(u));
+  return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+inline double key_to_double(unsigned long long k) {
+  unsigned long long u = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+  double v;
+  memcpy(&v, &u, sizeof(v));
+  return v;
+}
+
+__global__ void upper_f_kernel(int K, int nU, int r, int cc, int C, const int32_t* cfg, int cfg_ld,
+                               const int32_t* up_pd, const double* Bv, int bv_nb, const int32_t* U_u,
+                               const int32_t* ul_pdr, const double* Bdr, int bdr_nb, const int32_t* U_ul,
+                               const int32_t* ur_pdl, const double* Bdl, int bdl_nb, const int32_t* U_ur,
+                               double* f) {
+  long long n = (long long)nU * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    int k = int(e % K), u = int(e / K);
+    double v = 1.0;
+    if (r > 0) {
+      const int32_t* row = cfg + (long long)k * cfg_ld + (r - 1) * C;
+      v *= Bv[(long long)up_pd[row[cc]] * bv_nb + U_u[u]];
+      if (ul_pdr) v *= Bdr[(long long)ul_pdr[row[cc - 1]] * bdr_nb + U_ul[u]];
+      if (ur_pdl) v *= Bdl[(long long)ur_pdl[row[cc + 1]] * bdl_nb + U_ur[u]];
+    }
+    f[e] = v;
+  }
+}
+
+// new left environment for branch kk (parent par[kk], state xs[kk]) at column c:
+// Eout[(lam',g')][ar][kk] = sum_e [pi_dl lam' = e] Bh[pr_x, pi_l lam'] Bdr[pdr_x, g'] v[e][ar],
+// v[e][ar] = sum_g sum_al Ein[(lam_x, g)][al][par] Ahat[(pd_x, e, g)][al][ar]; normalised by max |.|
+__global__ void lenv_kernel(int Kin, int Kout, const int32_t* par, const int32_t* xs, const double* Ein, int chl,
+                            int chr, int nG, int nE, int nPdr, int nLR, int nGR, const double* Ahat,
+                            const int32_t* lam_x, const int32_t* pd_x, const int32_t* pr_x, const int32_t* pdr_x,
+                            const int32_t* l_pl, const int32_t* l_pdl, const double* Bh, int bh_nb, const double* Bdr,
+                            int bdr_nb, double* Eout) {
+  extern __shared__ double sm[];
+  double* v = sm;                  // [nE][chr]
+  __shared__ double red[32];
+  int kk = blockIdx.x;
+  int k = par[kk], x = xs[kk];
+  for (int i = threadIdx.x; i < nE * chr; i += blockDim.x) {
+    int e = i / chr, ar = i % chr;
+    double s = 0;
+    for (int g = 0; g < nG; ++g) {
+      const double* A = Ahat + (((long long)pd_x[x] * nE + e) * nG + g) * chl * chr;
+      const double* E = Ein + (long long)(lam_x[x] * nG + g) * chl * Kin;
+      for (int al = 0; al < chl; ++al) s = fma(E[(long long)al * Kin + k], A[(long long)al * chr + ar], s);
+    }
+    v[i] = s;
+  }
+  __syncthreads();
+  int nBR = nLR * nGR;
+  double mx = 0;
+  for (int i = threadIdx.x; i < nBR * chr; i += blockDim.x) {
+    int br = i / chr, ar = i % chr;
+    int lam = br / nGR, gp = br % nGR;
+    double val = Bh[(long long)pr_x[x] * bh_nb + l_pl[lam]] * Bdr[(long long)pdr_x[x] * bdr_nb + gp] *
+                 v[l_pdl[lam] * chr + ar];
+    Eout[(long long)i * Kout + kk] = val;
+    mx = fmax(mx, fabs(val));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    red[0] = m > 0 ? 1.0 / m : 1.0;
+  }
+  __syncthreads();
+  double s = red[0];
+  for (int i = threadIdx.x; i < nBR * chr; i += blockDim.x) Eout[(long long)i * Kout + kk] *= s;
+}
+
+// divide every column k of X[rows][K] by its max |.|
+__global__ void colnorm_kernel(double* X, long long rows, int K) {
+  int k = blockIdx.x;
+  __shared__ double red[32];
+  double mx = 0;
+  for (long long i = threadIdx.x; i < rows; i += blockDim.x) mx = fmax(mx, fabs(X[i * K + k]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    red[0] = m > 0 ? 1.0 / m : 1.0;
+  }
+  __syncthreads();
+  double s = red[0];
+  for (long long i = threadIdx.x; i < rows; i += blockDim.x) X[i * K + k] *= s;
+}
+
+// s[k][x] for all branches k (threads) of one state x (block)
+__global__ void score_kernel(int K, int d, int chl, int chr, int nG, int nE, int nPdr, const double* E,
+                             const double* Ahat, const double* Ft, const double* f, const double* w,
+                             const int32_t* lam_x, const int32_t* u_x, const int32_t* pd_x, const int32_t* pr_x,
+                             const int32_t* pdr_x, double* s) {
+  extern __shared__ double As[];   // chl * chr
+  int x = blockIdx.x;
+  double acc[4] = {0, 0, 0, 0};
+  for (int g = 0; g < nG; ++g)
+    for (int e = 0; e < nE; ++e) {
+      const double* A = Ahat + (((long long)pd_x[x] * nE + e) * nG + g) * chl * chr;
+      __syncthreads();
+      for (int i = threadIdx.x; i < chl * chr; i += blockDim.x) As[i] = A[i];
+      __syncthreads();
+      const double* Eb = E + (long long)(lam_x[x] * nG + g) * chl * K;
+      const double* Fb = Ft + (((long long)pr_x[x] * nE + e) * nPdr + pdr_x[x]) * chr * K;
+      for (int j = 0; j < 4; ++j) {
+        int k = threadIdx.x + j * blockDim.x;
+        if (k >= K) break;
+        double a2 = 0;
+        for (int ar = 0; ar < chr; ++ar) {
+          double t = 0;
+          for (int al = 0; al < chl; ++al) t = fma(Eb[(long long)al * K + k], As[al * chr + ar], t);
+          a2 = fma(t, Fb[(long long)ar * K + k], a2);
+        }
+        acc[j] += a2;
+      }
+    }
+  for (int j = 0; j < 4; ++j) {
+    int k = threadIdx.x + j * blockDim.x;
+    if (k >= K) break;
+    s[(long long)k * d + x] = f[(long long)u_x[x] * K + k] * w[x] * acc[j];
+  }
+}
+
+// log p of every candidate; invalid (score <= 0) -> key 0
+__global__ void logp_kernel(int K, int d, const double* s, const double* logp_in, double* lp,
+                            unsigned long long* key, int* clamps) {
+  int k = blockIdx.x;
+  __shared__ double red[32];
+  double z = 0;
+  int neg = 0;
+  for (int x = threadIdx.x; x < d; x += blockDim.x) {
+    double v = s[(long long)k * d + x];
+    if (v > 0) z += v;
+    if (v < 0) ++neg;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    z += __shfl_xor_sync(0xffffffffu, z, o);
+    neg += __shfl_xor_sync(0xffffffffu, neg, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = z;
+    if (neg) atomicAdd(clamps, neg);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    red[0] = t;
+  }
+  __syncthreads();
+  double Z = red[0];
+  double base = logp_in[k];
+  for (int x = threadIdx.x; x < d; x += blockDim.x) {
+    double v = s[(long long)k * d + x];
+    long long i = (long long)k * d + x;
+    if (v > 0 && Z > 0) {
+      double l = base + log(v / Z);
+      lp[i] = l;
+      key[i] = ord_key(l);
+    } else {
+      lp[i] = -INFINITY;
+      key[i] = 0ull;
+    }
+  }
+}
+
+// parent class: smallest branch index with the same vector of remaining boundary classes;
+// parent rank: position of the configuration in lexicographic order
+__global__ void parent_kernel(int K, int n, const int32_t* cfg, int cfg_ld, int npairs, const int32_t* pair_site,
+                              const int32_t* const* pair_cls, int32_t* pc, int32_t* prank) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const int32_t* a = cfg + (long long)k * cfg_ld;
+  int cls = k;
+  for (int k2 = 0; k2 < k; ++k2) {
+    const int32_t* b = cfg + (long long)k2 * cfg_ld;
+    bool eq = true;
+    for (int j = 0; j < npairs && eq; ++j) {
+      int p = pair_site[j];
+      eq = pair_cls[j][a[p]] == pair_cls[j][b[p]];
+    }
+    if (eq) {
+      cls = k2;
+      break;
+    }
+  }
+  pc[k] = cls;
+  int rank = 0;
+  for (int k2 = 0; k2 < K; ++k2) {
+    if (k2 == k) continue;
+    const int32_t* b = cfg + (long long)k2 * cfg_ld;
+    int cmp = 0;
+    for (int j = 0; j < n && cmp == 0; ++j) cmp = (b[j] < a[j]) ? -1 : (b[j] > a[j]) ? 1 : 0;
+    if (cmp < 0 || (cmp == 0 && k2 < k)) ++rank;
+  }
+  prank[k] = rank;
+}
+
+__global__ void merge1_kernel(int K, int d, int nX, const unsigned long long* key, const int32_t* pc,
+                              const int32_t* xk, unsigned long long* best) {
+  long long n = (long long)K * d;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (!key[i]) continue;
+    int k = int(i / d), x = int(i % d);
+    atomicMax(best + (long long)pc[k] * nX + xk[x], key[i]);
+  }
+}
+__global__ void merge2_kernel(int K, int d, int nX, const unsigned long long* key, const int32_t* pc,
+                              const int32_t* prank, const int32_t* xk, const unsigned long long* best, int* mn) {
+  long long n = (long long)K * d;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (!key[i]) continue;
+    int k = int(i / d), x = int(i % d);
+    long long slot = (long long)pc[k] * nX + xk[x];
+    if (key[i] == best[slot]) atomicMin(mn + slot, prank[k] * d + x);
+  }
+}
+// winners: key stays, losers: key -> 0 after recording them in `lost`
+__global__ void merge3_kernel(int K, int d, int nX, unsigned long long* key, const int32_t* pc, const int32_t* prank,
+                              const int32_t* xk, const int* mn, unsigned long long* lost) {
+  long long n = (long long)K * d;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (!key[i]) continue;
+    int k = int(i / d), x = int(i % d);
+    long long slot = (long long)pc[k] * nX + xk[x];
+    if (mn[slot] != prank[k] * d + x) {
+      atomicMax(lost, key[i]);
+      key[i] = 0ull;
+    }
+  }
+}
+
+// histogram of digit `shift` among keys matching prefix on the higher bits
+__global__ void hist_kernel(long long n, const unsigned long long* key, int shift, unsigned long long prefix,
+                            unsigned long long pmask, unsigned int* hist) {
+  __shared__ unsigned int h[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long k = key[i];
+    if (!k || (k & pmask) != prefix) continue;
+    atomicAdd(&h[(k >> shift) & 255], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (h[i]) atomicAdd(hist + i, h[i]);
+}
+
+// above threshold: selected; equal: appended to the tie list; non-selected valid: p_d
+__global__ void select_kernel(long long n, int d, const unsigned long long* key, const int32_t* prank,
+                              unsigned long long T, int* nsel, long long* sel, int* ntie, long long* tie,
+                              unsigned long long* lost, int cap) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long k = key[i];
+    if (!k) continue;
+    if (k > T) {
+      int j = atomicAdd(nsel, 1);
+      if (j < cap) sel[j] = i;
+    } else if (k == T) {
+      int j = atomicAdd(ntie, 1);
+      if (j < cap) tie[j] = i;
+    } else {
+      atomicMax(lost, k);
+    }
+  }
+}
+
+inline int nblk(long long n, int t = 256) {
+  long long b = (n + t - 1) / t;
+  return int(std::max(1ll, std::min(b, 148ll * 16)));
+}
+
+struct Step {
+  sgtn_inst* h;
+  int r, c, n, K;
+  int32_t* dcfg = nullptr;   // [K][n] (n may be 0)
+  int cfg_ld = 1;
+  std::vector<double*> f;    // per column [nU][K]
+  std::vector<double*> Ahat; // per column
+  double* E = nullptr;       // left env [nBL(c)][chl(c)][K]
+  double* Ft = nullptr;      // [nK(c)][chr(c)][K]
+  double* s = nullptr;       // [K][d]
+  const MPS* A = nullptr;
+  std::vector<void*> owned;
+  template <class T>
+  T* alloc(size_t n) {
+    void* p = nullptr;
+    SGTN_CUDA(cudaMalloc(&p, (n ? n : 1) * sizeof(T)));
+    owned.push_back(p);
+    return static_cast<T*>(p);
+  }
+  ~Step() {
+    for (void* p : owned) cudaFree(p);
+  }
+  const Column& col(int cc) const { return h->cols[r * h->M.C + cc]; }
+};
+
+// everything up to the unnormalised scores s[k][x]
+void prepare_scores(Step& S, const int32_t* hcfg) {
+  sgtn_inst* h = S.h;
+  cudaStream_t st = h->st;
+  const int C = h->M.C, R = h->M.R;
+  const int r = S.r, c = S.c, K = S.K;
+  if (!h->boundary_ok) throw SgtnError(-2, "contract_boundary must run first");
+  S.A = &h->psi[r];
+  S.cfg_ld = std::max(S.n, 1);
+  S.dcfg = S.alloc<int32_t>(size_t(K) * S.cfg_ld);
+  if (S.n > 0)
+    SGTN_CUDA(cudaMemcpyAsync(S.dcfg, hcfg, size_t(K) * S.n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  // projected MPS of psi_r, every column
+  S.Ahat.assign(C, nullptr);
+  for (int cc = 0; cc < C; ++cc) {
+    const Column& K_ = S.col(cc);
+    long long blk = (long long)S.A->bond[cc] * S.A->bond[cc + 1];
+    S.Ahat[cc] = S.alloc<double>(size_t(K_.nA() * blk));
+    gemm(K_.Wa, false, K_.nSig, S.A->t[cc], false, blk, S.Ahat[cc], blk, K_.nA(), int(blk), K_.nSig, 1.0, 0, st);
+  }
+  // upper factors
+  S.f.assign(C, nullptr);
+  for (int cc = 0; cc < C; ++cc) {
+    const Column& K_ = S.col(cc);
+    S.f[cc] = S.alloc<double>(size_t(K_.nU) * K);
+    const DSite* up = r > 0 ? &h->ds[(r - 1) * C + cc] : nullptr;
+    const DSite& me = h->ds[r * C + cc];
+    const int32_t *ul_pdr = nullptr, *ur_pdl = nullptr;
+    const double *Bv = nullptr, *Bdr = nullptr, *Bdl = nullptr;
+    int bv_nb = 1, bdr_nb = 1, bdl_nb = 1;
+    const int32_t* up_pd = nullptr;
+    if (r > 0) {
+      up_pd = up->cls[DD];
+      Bv = h->dB[size_t((r - 1) * C + cc) * 4 + 1];
+      bv_nb = h->M.tab[size_t((r - 1) * C + cc) * 4 + 1].nB;
+      if (cc - 1 >= 0) {
+        ul_pdr = h->ds[(r - 1) * C + cc - 1].cls[DDR];
+        Bdr = h->dB[size_t((r - 1) * C + cc - 1) * 4 + 2];
+        bdr_nb = h->M.tab[size_t((r - 1) * C + cc - 1) * 4 + 2].nB;
+      }
+      if (cc + 1 < C) {
+        ur_pdl = h->ds[(r - 1) * C + cc + 1].cls[DDL];
+        Bdl = h->dB[size_t((r - 1) * C + cc + 1) * 4 + 3];
+        bdl_nb = h->M.tab[size_t((r - 1) * C + cc + 1) * 4 + 3].nB;
+      }
+    }
+    upper_f_kernel<<<nblk((long long)K_.nU * K), 256, 0, st>>>(K, K_.nU, r, cc, C, S.dcfg, S.cfg_ld, up_pd, Bv, bv_nb,
+                                                              me.U_u, ul_pdr, Bdr, bdr_nb, me.U_ul, ur_pdl, Bdl,
+                                                              bdl_nb, me.U_ur, S.f[cc]);
+  }
+  // left environment at column c
+  {
+    S.E = S.alloc<double>(K);
+    fill(S.E, K, 1.0, st);
+    int32_t* par = S.alloc<int32_t>(K);
+    int32_t* xs = S.alloc<int32_t>(K);
+    SGTN_CUDA(cudaMemcpyAsync(par, h->iota, K * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    for (int cc = 0; cc < c; ++cc) {
+      const Column& K_ = S.col(cc);
+      std::vector<int32_t> hx(K);
+      for (int k = 0; k < K; ++k) hx[k] = hcfg[(long long)k * S.n + r * C + cc];
+      SGTN_CUDA(cudaMemcpyAsync(xs, hx.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+      int chl = S.A->bond[cc], chr = S.A->bond[cc + 1];
+      double* En = S.alloc<double>(size_t(K_.nBR()) * chr * K);
+      const DSite& D = h->ds[r * C + cc];
+      size_t smem = size_t(K_.nE) * chr * sizeof(double);
+      lenv_kernel<<<K, 128, smem, st>>>(K, K, par, xs, S.E, chl, chr, K_.nG, K_.nE, K_.nPdr, K_.nLR, K_.nGR,
+                                        S.Ahat[cc], D.lam_x, D.cls[DD], D.cls[DR_], D.cls[DDR], K_.l_pl, K_.l_pdl,
+                                        h->dB[size_t(r * C + cc) * 4 + 0], K_.bh_nb, h->dB[size_t(r * C + cc) * 4 + 2],
+                                        K_.bdr_nb, En);
+      S.E = En;
+      h->sync();  // xs is reused
+    }
+  }
+  // right environment at bond (c, c+1)
+  double* F = S.alloc<double>(K);
+  fill(F, K, 1.0, st);
+  for (int cc = C - 1; cc > c; --cc) {
+    const Column& K_ = S.col(cc);
+    int chl = S.A->bond[cc], chr = S.A->bond[cc + 1];
+    double* Ftl = S.alloc<double>(size_t(K_.nK()) * chr * K);
+    gemm(K_.Wk, false, K_.nBR(), F, false, (long long)chr * K, Ftl, (long long)chr * K, K_.nK(), chr * K, K_.nBR(), 1.0,
+         0, st);
+    double* Fn = S.alloc<double>(size_t(K_.nBL()) * chl * K);
+    SGTN_CUDA(cudaMemsetAsync(Fn, 0, size_t(K_.nBL()) * chl * K * sizeof(double), st));
+    SegGemm a;
+    a.X = S.Ahat[cc];
+    a.p = chl;
+    a.q = chr;
+    a.xs_i = chr;
+    a.xs_k = 1;
+    a.xrs = (long long)chl * chr;
+    a.Y = Ftl;
+    a.s = K;
+    a.ys_k = K;
+    a.ys_j = 1;
+    a.yrs = (long long)chr * K;
+    a.O = Fn;
+    a.os_i = K;
+    a.os_j = 1;
+    a.ors = (long long)chl * K;
+    a.seg_ptr = K_.renv.seg_ptr;
+    a.seg_or = K_.renv.seg_or;
+    a.seg_oc = K_.renv.seg_oc;
+    a.xr = K_.renv.xr;
+    a.xc = K_.renv.xc;
+    a.yr = K_.renv.yr;
+    a.yc = K_.renv.yc;
+    a.cidx = K_.renv.cidx;
+    a.csrow = K_.renv.csrow;
+    a.coef = h->ds[r * C + cc].w;
+    a.cs = S.f[cc];
+    a.cs_ld = K;
+    a.nseg = K_.renv.nseg;
+    seg_gemm(a, st);
+    colnorm_kernel<<<K, 256, 0, st>>>(Fn, (long long)K_.nBL() * chl, K);
+    F = Fn;
+  }
+  const Column& Kc = S.col(c);
+  int chl = S.A->bond[c], chr = S.A->bond[c + 1];
+  S.Ft = S.alloc<double>(size_t(Kc.nK()) * chr * K);
+  gemm(Kc.Wk, false, Kc.nBR(), F, false, (long long)chr * K, S.Ft, (long long)chr * K, Kc.nK(), chr * K, Kc.nBR(), 1.0, 0,
+       st);
+  const DSite& D = h->ds[r * C + c];
+  S.s = S.alloc<double>(size_t(K) * D.d);
+  int thr = std::min(256, std::max(32, ((K + 3) / 4 + 31) / 32 * 32));
+  if (K > 4 * thr) throw SgtnError(-1, "beam too large for the score kernel");
+  score_kernel<<<D.d, thr, size_t(chl) * chr * sizeof(double), st>>>(K, D.d, chl, chr, Kc.nG, Kc.nE, Kc.nPdr, S.E,
+                                                                      S.Ahat[c], S.Ft, S.f[c], D.w, D.lam_x, D.u_x,
+                                                                      D.cls[DD], D.cls[DR_], D.cls[DDR], S.s);
+  h->check();
+  (void)R;
+}
+
+void check_configs(sgtn_inst* h, int step, int count, const int32_t* cfg) {
+  const int RC = h->M.R * h->M.C;
+  if (step < 0 || step >= RC) throw SgtnError(-1, "step out of range");
+  if (count <= 0) throw SgtnError(-1, "count must be positive");
+  if (step > 0 && !cfg) throw SgtnError(-1, "configs is NULL");
+  for (long long k = 0; k < count; ++k)
+    for (int p = 0; p < step; ++p) {
+      int x = cfg[k * step + p];
+      if (x < 0 || x >= h->M.sites[p].d) throw SgtnError(-1, "state index out of range");
+    }
+}
+
+}  // namespace
+
+void conditionals(sgtn_inst* h, int step, int count, const int32_t* configs, double* out_p) {
+  check_configs(h, step, count, configs);
+  if (!out_p) throw SgtnError(-1, "out_p is NULL");
+  Step S;
+  S.h = h;
+  S.n = step;
+  S.r = step / h->M.C;
+  S.c = step % h->M.C;
+  S.K = count;
+  prepare_scores(S, configs);
+  int d = h->M.sites[step].d;
+  std::vector<double> s(size_t(count) * d);
+  SGTN_CUDA(cudaMemcpyAsync(s.data(), S.s, s.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  h->sync();
+  for (int k = 0; k < count; ++k) {
+    double z = 0;
+    for (int x = 0; x < d; ++x) z += std::max(0.0, s[size_t(k) * d + x]);
+    for (int x = 0; x < d; ++x) out_p[size_t(k) * d + x] = z > 0 ? std::max(0.0, s[size_t(k) * d + x]) / z : 0.0;
+  }
+}
+
+void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_configs, const double* in_logp,
+                 int32_t* out_configs, double* out_logp, int32_t* out_count, double* io_pd) {
+  check_configs(h, step, in_count, in_configs);
+  if (M <= 0 || !in_logp || !out_configs || !out_logp || !out_count || !io_pd) throw SgtnError(-1, "bad argument");
+  cudaStream_t st = h->st;
+  const int C = h->M.C;
+  Step S;
+  S.h = h;
+  S.n = step;
+  S.r = step / C;
+  S.c = step % C;
+  S.K = in_count;
+  const int K = in_count;
+  prepare_scores(S, in_configs);
+  const HSite& site = h->M.sites[step];
+  const int d = site.d;
+  const long long ncand = (long long)K * d;
+  double* dlp_in = S.alloc<double>(K);
+  SGTN_CUDA(cudaMemcpyAsync(dlp_in, in_logp, K * sizeof(double), cudaMemcpyHostToDevice, st));
+  double* lp = S.alloc<double>(ncand);
+  unsigned long long* key = S.alloc<unsigned long long>(ncand);
+  int* clamps = S.alloc<int>(1);
+  SGTN_CUDA(cudaMemsetAsync(clamps, 0, sizeof(int), st));
+  logp_kernel<<<K, 256, 0, st>>>(K, d, S.s, dlp_in, lp, key, clamps);
+  // parent classes from the boundary pairs (p, dir) with p < step < l (Eq. 7)
+  std::vector<int32_t> psite;
+  std::vector<const int32_t*> pcls;
+  for (int p = 0; p < step; ++p) {
+    const HSite& P = h->M.sites[p];
+    for (int dd = 0; dd < 8; ++dd) {
+      int rr = P.r + kDr[dd], cc = P.c + kDc[dd];
+      if (rr < 0 || rr >= h->M.R || cc < 0 || cc >= C) continue;
+      int l = rr * C + cc;
+      if (l > step && !P.coupled[dd].empty()) {
+        psite.push_back(p);
+        pcls.push_back(h->ds[p].cls[dd]);
+      }
+    }
+  }
+  int npairs = int(psite.size());
+  int32_t* dps = S.alloc<int32_t>(npairs);
+  const int32_t** dpc = S.alloc<const int32_t*>(npairs);
+  if (npairs) {
+    SGTN_CUDA(cudaMemcpyAsync(dps, psite.data(), npairs * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    SGTN_CUDA(cudaMemcpyAsync(dpc, pcls.data(), npairs * sizeof(int32_t*), cudaMemcpyHostToDevice, st));
+  }
+  int32_t* pc = S.alloc<int32_t>(K);
+  int32_t* prank = S.alloc<int32_t>(K);
+  parent_kernel<<<(K + 127) / 128, 128, 0, st>>>(K, step, S.dcfg, S.cfg_ld, npairs, dps, dpc, pc, prank);
+  const int nX = site.Xk.n;
+  long long nslot = (long long)K * nX;
+  unsigned long long* best = S.alloc<unsigned long long>(nslot);
+  int* mn = S.alloc<int>(nslot);
+  SGTN_CUDA(cudaMemsetAsync(best, 0, nslot * sizeof(unsigned long long), st));
+  SGTN_CUDA(cudaMemsetAsync(mn, 0x7f, nslot * sizeof(int), st));
+  unsigned long long* lost = S.alloc<unsigned long long>(1);
+  SGTN_CUDA(cudaMemsetAsync(lost, 0, sizeof(unsigned long long), st));
+  merge1_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, pc, h->ds[step].xk_x, best);
+  merge2_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, pc, prank, h->ds[step].xk_x, best, mn);
+  merge3_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, pc, prank, h->ds[step].xk_x, mn, lost);
+  // radix select of the M-th largest key
+  unsigned int* hist = S.alloc<unsigned int>(256);
+  unsigned long long prefix = 0, pmask = 0;
+  long long need = M;
+  long long total_valid = 0;
+  {
+    // count valid survivors first (histogram of the top digit with empty prefix)
+    SGTN_CUDA(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned int), st));
+    hist_kernel<<<nblk(ncand), 256, 0, st>>>(ncand, key, 56, 0ull, 0ull, hist);
+    std::vector<unsigned int> hh(256);
+    SGTN_CUDA(cudaMemcpyAsync(hh.data(), hist, 256 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    h->sync();
+    for (auto v : hh) total_valid += v;
+    if (total_valid == 0) throw SgtnError(-4, "no candidate with a positive score");
+    unsigned long long T = 0;
+    if (total_valid > M) {
+      for (int shift = 56; shift >= 0; shift -= 8) {
+        if (shift != 56) {
+          SGTN_CUDA(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned int), st));
+          hist_kernel<<<nblk(ncand), 256, 0, st>>>(ncand, key, shift, prefix, pmask, hist);
+          SGTN_CUDA(cudaMemcpyAsync(hh.data(), hist, 256 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+          h->sync();
+        }
+        int b = 255;
+        for (; b >= 0; --b) {
+          if ((long long)hh[b] >= need) break;
+          need -= hh[b];
+        }
+        prefix |= (unsigned long long)b << shift;
+        pmask |= 255ull << shift;
+      }
+      T = prefix;   // M-th largest key; `need` of the keys equal to T are taken
+    } else {
+      T = 0;        // everything valid is above T
+      need = 0;
+    }
+    int* nsel = S.alloc<int>(2);
+    SGTN_CUDA(cudaMemsetAsync(nsel, 0, 2 * sizeof(int), st));
+    int cap = M + 1;
+    long long* sel = S.alloc<long long>(cap);
+    long long* tie = S.alloc<long long>(std::max<long long>(cap, 1));
+    select_kernel<<<nblk(ncand), 256, 0, st>>>(ncand, d, key, prank, T, nsel, sel, nsel + 1, tie, lost, cap);
+    int hn[2];
+    SGTN_CUDA(cudaMemcpyAsync(hn, nsel, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    h->sync();
+    int n_above = hn[0], n_tie = hn[1];
+    if (n_above > M || n_tie > cap) throw SgtnError(-4, "too many tied candidates at the top-M cut");
+    std::vector<long long> hsel(n_above), htie(n_tie);
+    if (n_above) SGTN_CUDA(cudaMemcpyAsync(hsel.data(), sel, n_above * sizeof(long long), cudaMemcpyDeviceToHost, st));
+    if (n_tie) SGTN_CUDA(cudaMemcpyAsync(htie.data(), tie, n_tie * sizeof(long long), cudaMemcpyDeviceToHost, st));
+    std::vector<int32_t> hprank(K);
+    SGTN_CUDA(cudaMemcpyAsync(hprank.data(), prank, K * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    std::vector<double> hlp(ncand);
+    SGTN_CUDA(cudaMemcpyAsync(hlp.data(), lp, ncand * sizeof(double), cudaMemcpyDeviceToHost, st));
+    unsigned long long hlost = 0;
+    SGTN_CUDA(cudaMemcpyAsync(&hlost, lost, sizeof(hlost), cudaMemcpyDeviceToHost, st));
+    h->sync();
+    // candidates ordered by (log p desc, parent rank asc, state asc)
+    auto order = [&](long long a, long long b) {
+      if (hlp[a] != hlp[b]) return hlp[a] > hlp[b];
+      long long ca = (long long)hprank[a / d] * d + a % d, cb = (long long)hprank[b / d] * d + b % d;
+      return ca < cb;
+    };
+    std::sort(htie.begin(), htie.end(), order);
+    std::vector<long long> keep = hsel;
+    for (int i = 0; i < n_tie; ++i) {
+      if ((long long)keep.size() < M && (T != 0 || need != 0 || total_valid <= M))
+        keep.push_back(htie[i]);
+      else
+        hlost = std::max(hlost, ord_key(hlp[htie[i]]));
+    }
+    std::sort(keep.begin(), keep.end(), order);
+    if ((long long)keep.size() > M) keep.resize(M);
+    int outc = int(keep.size());
+    for (int i = 0; i < outc; ++i) {
+      long long ci = keep[i];
+      int k = int(ci / d), x = int(ci % d);
+      for (int p = 0; p < step; ++p) out_configs[(long long)i * (step + 1) + p] = in_configs[(long long)k * step + p];
+      out_configs[(long long)i * (step + 1) + step] = x;
+      out_logp[i] = hlp[ci];
+    }
+    *out_count = outc;
+    if (hlost) *io_pd = std::max(*io_pd, key_to_double(hlost));
+  }
+  h->check();
+}
+
+void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_energy, double* out_logp, double* out_pd,
+            int32_t* out_count) {
+  if (!h->boundary_ok) throw SgtnError(-2, "contract_boundary must run first");
+  if (M <= 0 || n_out <= 0 || !out_spins || !out_energy || !out_logp || !out_pd || !out_count)
+    throw SgtnError(-1, "bad argument");
+  const int RC = h->M.R * h->M.C;
+  std::vector<int32_t> cfg(1, 0), ncfg;
+  std::vector<double> lp(1, 0.0), nlp;
+  int count = 1;
+  double pd = -INFINITY;
+  for (int step = 0; step < RC; ++step) {
+    ncfg.assign(size_t(M) * (step + 1), 0);
+    nlp.assign(M, 0.0);
+    int oc = 0;
+    branch_step(h, step, M, count, cfg.data(), lp.data(), ncfg.data(), nlp.data(), &oc, &pd);
+    cfg.assign(ncfg.begin(), ncfg.begin() + size_t(oc) * (step + 1));
+    lp.assign(nlp.begin(), nlp.begin() + oc);
+    count = oc;
+  }
+  int nw = std::min(n_out, count);
+  std::vector<int8_t> spins(size_t(nw) * h->M.N);
+  for (int i = 0; i < nw; ++i)
+    for (int s = 0; s < RC; ++s) {
+      const HSite& S = h->M.sites[s];
+      int64_t st = S.states[cfg[size_t(i) * RC + s]];
+      for (size_t j = 0; j < S.spins.size(); ++j) spins[size_t(i) * h->M.N + S.spins[j]] = ((st >> j) & 1) ? -1 : 1;
+    }
+  energies(h, nw, spins.data(), out_energy);
+  std::copy(spins.begin(), spins.end(), out_spins);
+  for (int i = 0; i < nw; ++i) out_logp[i] = lp[i];
+  *out_pd = pd;
+  *out_count = nw;
+}
+
+}  // namespace sgtn

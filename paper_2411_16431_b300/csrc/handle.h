@@ -1,0 +1,117 @@
+// The opaque handle behind sgtn_h (internal).
+#pragma once
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "kern.h"
+#include "model.h"
+
+struct SgtnError : std::runtime_error {
+  int code;
+  SgtnError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define SGTN_CUDA(x)                                                                              \
+  do {                                                                                            \
+    cudaError_t e_ = (x);                                                                         \
+    if (e_ != cudaSuccess)                                                                        \
+      throw SgtnError(e_ == cudaErrorMemoryAllocation ? -3 : -6,                                  \
+                      std::string(#x) + ": " + cudaGetErrorString(e_));                           \
+  } while (0)
+
+namespace sgtn {
+
+struct DSite {
+  int d = 0;
+  int64_t* E = nullptr;
+  double* w = nullptr;
+  int32_t* cls[8] = {};                   // class toward each direction, per state
+  int32_t *lam_x = nullptr, *u_x = nullptr, *xk_x = nullptr;
+  int32_t *U_u = nullptr, *U_ul = nullptr, *U_ur = nullptr, *Lam_l = nullptr, *Lam_dl = nullptr;
+};
+
+// Named growable device scratch buffers.
+struct Scratch {
+  std::map<std::string, std::pair<void*, size_t>> bufs;
+  void* get(const std::string& name, size_t bytes) {
+    auto& b = bufs[name];
+    if (b.second < bytes) {
+      if (b.first) cudaFree(b.first);
+      b.first = nullptr;
+      size_t nb = bytes + bytes / 4 + 256;
+      SGTN_CUDA(cudaMalloc(&b.first, nb));
+      b.second = nb;
+    }
+    return b.first;
+  }
+  template <class T>
+  T* get(const std::string& name, size_t count) {
+    return static_cast<T*>(get(name, count * sizeof(T)));
+  }
+  void release() {
+    for (auto& kv : bufs)
+      if (kv.second.first) cudaFree(kv.second.first);
+    bufs.clear();
+  }
+};
+
+}  // namespace sgtn
+
+struct sgtn_inst {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  std::string err;
+  sgtn::Model M;
+  std::vector<sgtn::DSite> ds;
+  std::vector<int64_t*> dE;               // [site*4+k] compressed energies
+  std::vector<double*> dB;                // [site*4+k] bond factors exp(-beta (Ebar - min))
+  std::vector<sgtn::Column> cols;         // [r*C + c]
+  std::vector<void*> allocs;              // static allocations
+  double beta = 0.0;
+  bool beta_set = false;
+  double log_offset = 0.0;
+  std::vector<sgtn::MPS> psi;             // psi[r] covers rows r+1..R-1
+  int chi = 0, precision = 0, n_sweeps = 0;
+  bool boundary_ok = false;
+  double logz = 0.0, worst_sv = 0.0;
+  sgtn::Scratch ws;
+  int32_t* iota = nullptr;                // 0..iota_n-1
+  int iota_n = 0;
+
+  template <class T>
+  T* upload(const std::vector<T>& v) {
+    T* p = nullptr;
+    size_t n = v.empty() ? 1 : v.size();
+    SGTN_CUDA(cudaMalloc(&p, n * sizeof(T)));
+    allocs.push_back(p);
+    if (!v.empty()) SGTN_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return p;
+  }
+  template <class T>
+  T* dalloc(size_t n) {
+    T* p = nullptr;
+    SGTN_CUDA(cudaMalloc(&p, (n ? n : 1) * sizeof(T)));
+    allocs.push_back(p);
+    return p;
+  }
+  void sync() { SGTN_CUDA(cudaStreamSynchronize(st)); }
+  void check() { SGTN_CUDA(cudaGetLastError()); }
+};
+
+namespace sgtn {
+// setup.cu
+void setup_device(sgtn_inst* h);
+void set_beta_device(sgtn_inst* h, double beta);
+void free_mps(MPS& m);
+// boundary.cu
+void contract_boundary(sgtn_inst* h, int chi, int n_sweeps);
+// branch.cu
+void conditionals(sgtn_inst* h, int step, int count, const int32_t* configs, double* out_p);
+void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_configs, const double* in_logp,
+                 int32_t* out_configs, double* out_logp, int32_t* out_count, double* io_pd);
+void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_energy, double* out_logp, double* out_pd,
+            int32_t* out_count);
+void energies(sgtn_inst* h, int n, const int8_t* spins, int64_t* out);
+}  // namespace sgtn

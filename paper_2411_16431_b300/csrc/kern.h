@@ -1,0 +1,64 @@
+// Host wrappers of the device kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace sgtn {
+
+// Segmented gathered GEMM, double precision:
+//   O[seg] (+)= alpha * sum_{t in seg} coef[cidx[t]] * X_t * (Y_t diag(cs[csrow[t]]))
+// Blocks: X_t is p x q, Y_t is q x s, O_seg is p x s, addressed with element
+// strides (xs_i, xs_k), (ys_k, ys_j), (os_i, os_j) from block offsets
+//   xoff = xr*xrs + xc*xcs, yoff = yr*yrs + yc*ycs, ooff = or*ors + oc*ocs.
+// Table mode when seg_ptr != nullptr; otherwise uniform batch mode: segment b
+// has a single term with xr = yr = or = b and xc = yc = oc = 0, coefficient 1.
+struct SegGemm {
+  const double* X = nullptr;
+  const double* Y = nullptr;
+  double* O = nullptr;
+  int p = 0, q = 0, s = 0;
+  long long xs_i = 0, xs_k = 0, ys_k = 0, ys_j = 0, os_i = 0, os_j = 0;
+  long long xrs = 0, xcs = 0, yrs = 0, ycs = 0, ors = 0, ocs = 0;
+  const int32_t *seg_ptr = nullptr, *seg_or = nullptr, *seg_oc = nullptr;
+  const int32_t *xr = nullptr, *xc = nullptr, *yr = nullptr, *yc = nullptr, *cidx = nullptr, *csrow = nullptr;
+  const double* coef = nullptr;
+  const double* cs = nullptr;
+  long long cs_ld = 0;
+  int nseg = 1;
+  double alpha = 1.0;
+  int accumulate = 0;
+};
+void seg_gemm(const SegGemm& a, cudaStream_t st);
+
+// Plain row-major GEMM helper on top of seg_gemm: O[m x n] = alpha * op(X) op(Y)
+void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, long long ldy, double* O,
+          long long ldo, int m, int n, int k, double alpha, int accumulate, cudaStream_t st);
+
+// One-sided Jacobi (Hestenes) on the p vectors of a matrix: vector j has
+// element i at X[i*si + j*sj], i < len.  On return the vectors are mutually
+// orthogonal; V (p x p, column j at V[j*p], may be null) accumulates the
+// rotations.  status[0] = sweeps used, or -1 if max_sweeps ran out.
+void jacobi(double* X, int len, int p, long long si, long long sj, double* V, int max_sweeps, int* status,
+            cudaStream_t st);
+void vec_norms(const double* X, int len, int p, long long si, long long sj, double* out, cudaStream_t st);
+// out[i*oi + jj*oj] = scale[jj] * X[i*si + perm[jj]*sj]
+void gather_vecs(const double* X, int len, long long si, long long sj, const int32_t* perm, const double* scale,
+                 int k, double* out, long long oi, long long oj, cudaStream_t st);
+// out[b][a][c] = in[a][b][c]
+void permute3(const double* in, int A, int B, int Cd, double* out, cudaStream_t st);
+// Frobenius norm (deterministic), result on device in *out
+void fro_norm(const double* x, long long n, double* out, cudaStream_t st);
+void scale_by_inv(double* x, long long n, const double* norm, cudaStream_t st);
+void fill(double* x, long long n, double v, cudaStream_t st);
+void copy(double* dst, const double* src, long long n, cudaStream_t st);
+
+// exp(-beta (E - Emin) / denom)
+void boltzmann(const int64_t* E, long long n, int64_t Emin, double beta_over_denom, double* out, cudaStream_t st);
+// dense weight matrices of a column (see boundary.cu)
+void build_Wa(double* Wa, int nPd, int nE, int nG, int nSig, const int32_t* s_pu, const int32_t* s_pul,
+              const int32_t* s_pur, const double* Bv, int bv_nb, const double* Bdl, int bdl_nb, cudaStream_t st);
+void build_Wk(double* Wk, int nPr, int nE, int nPdr, int nLR, int nGR, const int32_t* l_pl, const int32_t* l_pdl,
+              const double* Bh, int bh_nb, const double* Bdr, int bdr_nb, cudaStream_t st);
+
+}  // namespace sgtn

@@ -1,0 +1,362 @@
+// Double-precision kernels of the sgtn library: the segmented gathered GEMM
+// that evaluates the sparse site diagrams of Fig. 7 (and plain GEMMs), the
+// one-sided Jacobi SVD used for every truncation and orthonormalisation
+// (Hestenes 1958; Demmel & Veselic 1992), and small helpers.
+#include <cmath>
+
+#include "kern.h"
+
+namespace sgtn {
+
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 16;
+
+struct SegDev {
+  SegGemm a;
+};
+
+__global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
+  __shared__ double Xs[TK][TM + 1];
+  __shared__ double Ys[TK][TN + 1];
+  const int seg = blockIdx.x;
+  const int i0 = blockIdx.y * TM, j0 = blockIdx.z * TN;
+  const int tid = threadIdx.x;
+  const int ty = tid / 16, tx = tid % 16;
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+  int t0, t1;
+  long long ooff;
+  if (a.seg_ptr) {
+    t0 = a.seg_ptr[seg];
+    t1 = a.seg_ptr[seg + 1];
+    ooff = (long long)a.seg_or[seg] * a.ors + (long long)a.seg_oc[seg] * a.ocs;
+  } else {
+    t0 = seg;
+    t1 = seg + 1;
+    ooff = (long long)seg * a.ors;
+  }
+  for (int t = t0; t < t1; ++t) {
+    long long xoff, yoff;
+    double cf = 1.0;
+    const double* cs = nullptr;
+    if (a.seg_ptr) {
+      xoff = (long long)a.xr[t] * a.xrs + (long long)a.xc[t] * a.xcs;
+      yoff = (long long)a.yr[t] * a.yrs + (long long)a.yc[t] * a.ycs;
+      if (a.coef) cf = a.coef[a.cidx[t]];
+      if (a.cs) cs = a.cs + (long long)a.csrow[t] * a.cs_ld;
+    } else {
+      xoff = (long long)t * a.xrs;
+      yoff = (long long)t * a.yrs;
+    }
+    for (int k0 = 0; k0 < a.q; k0 += TK) {
+      // X tile: TM x TK ; Y tile: TK x TN
+      for (int e = tid; e < TM * TK; e += 256) {
+        int ii = e / TK, kk = e % TK;
+        int i = i0 + ii, k = k0 + kk;
+        Xs[kk][ii] = (i < a.p && k < a.q) ? a.X[xoff + i * a.xs_i + k * a.xs_k] : 0.0;
+      }
+      for (int e = tid; e < TK * TN; e += 256) {
+        int kk = e / TN, jj = e % TN;
+        int k = k0 + kk, j = j0 + jj;
+        double v = 0.0;
+        if (k < a.q && j < a.s) {
+          v = cf * a.Y[yoff + k * a.ys_k + j * a.ys_j];
+          if (cs) v *= cs[j];
+        }
+        Ys[kk][jj] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < TK; ++kk) {
+        double xv[4], yv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = Xs[kk][ty * 4 + u];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) yv[v] = Ys[kk][tx * 4 + v];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fma(xv[u], yv[v], acc[u][v]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int i = i0 + ty * 4 + u;
+    if (i >= a.p) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int j = j0 + tx * 4 + v;
+      if (j >= a.s) continue;
+      double* o = a.O + ooff + i * a.os_i + j * a.os_j;
+      double val = a.alpha * acc[u][v];
+      *o = a.accumulate ? *o + val : val;
+    }
+  }
+}
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Single-CTA cyclic one-sided Jacobi with a round-robin pairing.
+__global__ void __launch_bounds__(1024) jacobi_kernel(double* X, int len, int p, long long si, long long sj,
+                                                      double* V, int max_sweeps, double tol, int* status) {
+  __shared__ int rotated;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  if (V)
+    for (long long e = threadIdx.x; e < (long long)p * p; e += blockDim.x)
+      V[e] = ((e / p) == (e % p)) ? 1.0 : 0.0;
+  const int pp = p + (p & 1);
+  int sweep = 0;
+  bool done = (p < 2);
+  __syncthreads();
+  while (!done && sweep < max_sweeps) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int t = 0; t < pp - 1; ++t) {
+      for (int w = warp; w < pp / 2; w += nwarp) {
+        int pa = w, pb = pp - 1 - w;
+        int ca = pa == 0 ? 0 : 1 + (pa - 1 + t) % (pp - 1);
+        int cb = pb == 0 ? 0 : 1 + (pb - 1 + t) % (pp - 1);
+        if (ca >= p || cb >= p) continue;
+        double* xa = X + ca * sj;
+        double* xb = X + cb * sj;
+        double al = 0, be = 0, ga = 0;
+        for (int i = lane; i < len; i += 32) {
+          double u = xa[i * si], v = xb[i * si];
+          al = fma(u, u, al);
+          be = fma(v, v, be);
+          ga = fma(u, v, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
+          double zeta = (be - al) / (2.0 * ga);
+          double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
+          for (int i = lane; i < len; i += 32) {
+            double u = xa[i * si], v = xb[i * si];
+            xa[i * si] = c * u - s * v;
+            xb[i * si] = s * u + c * v;
+          }
+          if (V) {
+            double* va = V + (long long)ca * p;
+            double* vb = V + (long long)cb * p;
+            for (int i = lane; i < p; i += 32) {
+              double u = va[i], v = vb[i];
+              va[i] = c * u - s * v;
+              vb[i] = s * u + c * v;
+            }
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    ++sweep;
+    done = (rotated == 0);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) status[0] = done ? sweep : -1;
+}
+
+__global__ void vec_norms_kernel(const double* X, int len, int p, long long si, long long sj, double* out) {
+  int j = blockIdx.x;
+  double a = 0;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    double v = X[i * si + j * sj];
+    a = fma(v, v, a);
+  }
+  __shared__ double red[32];
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double b = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    b = warp_sum(b);
+    if (threadIdx.x == 0) out[j] = sqrt(b);
+  }
+}
+
+__global__ void gather_vecs_kernel(const double* X, int len, long long si, long long sj, const int32_t* perm,
+                                   const double* scale, int k, double* out, long long oi, long long oj) {
+  long long n = (long long)len * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    int jj = int(e / len), i = int(e % len);
+    out[i * oi + jj * oj] = scale[jj] * X[i * si + (long long)perm[jj] * sj];
+  }
+}
+
+__global__ void permute3_kernel(const double* in, int A, int B, int Cd, double* out) {
+  long long n = (long long)A * B * Cd;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    int c = int(e % Cd);
+    long long r = e / Cd;
+    int b = int(r % B), a = int(r / B);
+    out[((long long)b * A + a) * Cd + c] = in[e];
+  }
+}
+
+__global__ void fro_norm_kernel(const double* x, long long n, double* out) {
+  __shared__ double red[32];
+  double a = 0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) a = fma(x[i], x[i], a);
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double b = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    b = warp_sum(b);
+    if (threadIdx.x == 0) out[0] = sqrt(b);
+  }
+}
+
+__global__ void scale_by_inv_kernel(double* x, long long n, const double* norm) {
+  double s = 1.0 / norm[0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] *= s;
+}
+
+__global__ void fill_kernel(double* x, long long n, double v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+__global__ void copy_kernel(double* d, const double* s, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    d[i] = s[i];
+}
+
+__global__ void boltzmann_kernel(const int64_t* E, long long n, int64_t Emin, double bd, double* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = exp(-bd * double(E[i] - Emin));
+}
+
+__global__ void build_Wa_kernel(double* Wa, int nPd, int nE, int nG, int nSig, const int32_t* s_pu,
+                                const int32_t* s_pul, const int32_t* s_pur, const double* Bv, int bv_nb,
+                                const double* Bdl, int bdl_nb) {
+  long long n = (long long)nPd * nE * nG * nSig;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    int sg = int(e % nSig);
+    long long r = e / nSig;
+    int g = int(r % nG);
+    r /= nG;
+    int ee = int(r % nE);
+    int pd = int(r / nE);
+    double v = 0.0;
+    if (s_pul[sg] == g) v = Bv[(long long)pd * bv_nb + s_pu[sg]] * Bdl[(long long)ee * bdl_nb + s_pur[sg]];
+    Wa[e] = v;
+  }
+}
+
+__global__ void build_Wk_kernel(double* Wk, int nPr, int nE, int nPdr, int nLR, int nGR, const int32_t* l_pl,
+                                const int32_t* l_pdl, const double* Bh, int bh_nb, const double* Bdr, int bdr_nb) {
+  long long nBR = (long long)nLR * nGR;
+  long long n = (long long)nPr * nE * nPdr * nBR;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    long long br = e % nBR;
+    long long r = e / nBR;
+    int pdr = int(r % nPdr);
+    r /= nPdr;
+    int ee = int(r % nE);
+    int pr = int(r / nE);
+    int lam = int(br / nGR), gp = int(br % nGR);
+    double v = 0.0;
+    if (l_pdl[lam] == ee) v = Bh[(long long)pr * bh_nb + l_pl[lam]] * Bdr[(long long)pdr * bdr_nb + gp];
+    Wk[e] = v;
+  }
+}
+
+inline int blocks_for(long long n, int t = 256) {
+  long long b = (n + t - 1) / t;
+  if (b < 1) b = 1;
+  if (b > 148 * 32) b = 148 * 32;
+  return int(b);
+}
+
+}  // namespace
+
+void seg_gemm(const SegGemm& a, cudaStream_t st) {
+  if (a.nseg <= 0 || a.p <= 0 || a.s <= 0) return;
+  dim3 grid(a.nseg, (a.p + TM - 1) / TM, (a.s + TN - 1) / TN);
+  seg_gemm_kernel<<<grid, 256, 0, st>>>(a);
+}
+
+void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, long long ldy, double* O, long long ldo,
+          int m, int n, int k, double alpha, int accumulate, cudaStream_t st) {
+  SegGemm a;
+  a.X = X;
+  a.Y = Y;
+  a.O = O;
+  a.p = m;
+  a.q = k;
+  a.s = n;
+  a.xs_i = tx ? 1 : ldx;
+  a.xs_k = tx ? ldx : 1;
+  a.ys_k = ty ? 1 : ldy;
+  a.ys_j = ty ? ldy : 1;
+  a.os_i = ldo;
+  a.os_j = 1;
+  a.nseg = 1;
+  a.alpha = alpha;
+  a.accumulate = accumulate;
+  seg_gemm(a, st);
+}
+
+void jacobi(double* X, int len, int p, long long si, long long sj, double* V, int max_sweeps, int* status,
+            cudaStream_t st) {
+  double tol = 1e-15 * sqrt(double(len > 1 ? len : 1));
+  jacobi_kernel<<<1, 1024, 0, st>>>(X, len, p, si, sj, V, max_sweeps, tol, status);
+}
+
+void vec_norms(const double* X, int len, int p, long long si, long long sj, double* out, cudaStream_t st) {
+  if (p > 0) vec_norms_kernel<<<p, 256, 0, st>>>(X, len, p, si, sj, out);
+}
+
+void gather_vecs(const double* X, int len, long long si, long long sj, const int32_t* perm, const double* scale, int k,
+                 double* out, long long oi, long long oj, cudaStream_t st) {
+  gather_vecs_kernel<<<blocks_for((long long)len * k), 256, 0, st>>>(X, len, si, sj, perm, scale, k, out, oi, oj);
+}
+
+void permute3(const double* in, int A, int B, int Cd, double* out, cudaStream_t st) {
+  permute3_kernel<<<blocks_for((long long)A * B * Cd), 256, 0, st>>>(in, A, B, Cd, out);
+}
+
+void fro_norm(const double* x, long long n, double* out, cudaStream_t st) { fro_norm_kernel<<<1, 1024, 0, st>>>(x, n, out); }
+
+void scale_by_inv(double* x, long long n, const double* norm, cudaStream_t st) {
+  scale_by_inv_kernel<<<blocks_for(n), 256, 0, st>>>(x, n, norm);
+}
+
+void fill(double* x, long long n, double v, cudaStream_t st) { fill_kernel<<<blocks_for(n), 256, 0, st>>>(x, n, v); }
+
+void copy(double* dst, const double* src, long long n, cudaStream_t st) {
+  copy_kernel<<<blocks_for(n), 256, 0, st>>>(dst, src, n);
+}
+
+void boltzmann(const int64_t* E, long long n, int64_t Emin, double bd, double* out, cudaStream_t st) {
+  boltzmann_kernel<<<blocks_for(n), 256, 0, st>>>(E, n, Emin, bd, out);
+}
+
+void build_Wa(double* Wa, int nPd, int nE, int nG, int nSig, const int32_t* s_pu, const int32_t* s_pul,
+              const int32_t* s_pur, const double* Bv, int bv_nb, const double* Bdl, int bdl_nb, cudaStream_t st) {
+  long long n = (long long)nPd * nE * nG * nSig;
+  build_Wa_kernel<<<blocks_for(n), 256, 0, st>>>(Wa, nPd, nE, nG, nSig, s_pu, s_pul, s_pur, Bv, bv_nb, Bdl, bdl_nb);
+}
+
+void build_Wk(double* Wk, int nPr, int nE, int nPdr, int nLR, int nGR, const int32_t* l_pl, const int32_t* l_pdl,
+              const double* Bh, int bh_nb, const double* Bdr, int bdr_nb, cudaStream_t st) {
+  long long n = (long long)nPr * nE * nPdr * nLR * nGR;
+  build_Wk_kernel<<<blocks_for(n), 256, 0, st>>>(Wk, nPr, nE, nPdr, nLR, nGR, l_pl, l_pdl, Bh, bh_nb, Bdr, bdr_nb);
+}
+
+}  // namespace sgtn

@@ -1,0 +1,164 @@
+"""Thin ctypes binding of libsgtn.so (C ABI declared in include/sgtn.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  There is no CPU fallback: if the library cannot be loaded the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsgtn.so")
+_lib = None
+
+FP64, TF32, BF16 = 0, 1, 2
+
+_I32P = ct.POINTER(ct.c_int32)
+_I64P = ct.POINTER(ct.c_int64)
+_F64P = ct.POINTER(ct.c_double)
+_I8P = ct.POINTER(ct.c_int8)
+
+
+def load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run paper_2411_16431_b300/build.py (no CPU fallback exists)")
+    L = ct.CDLL(LIB_PATH)
+    L.sgtn_build_instance.argtypes = [ct.c_int32, ct.c_int64, _I32P, _I32P, _I32P, _I32P, ct.c_int32, _I32P,
+                                      ct.c_int32, ct.c_int32, _I64P, _I64P, ct.c_void_p, ct.POINTER(ct.c_void_p)]
+    L.sgtn_set_beta.argtypes = [ct.c_void_p, ct.c_double]
+    L.sgtn_contract_boundary.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, _F64P, _F64P]
+    L.sgtn_conditionals.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I32P, _F64P]
+    L.sgtn_branch_step.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, _I32P, _F64P, _I32P, _F64P,
+                                   _I32P, _F64P]
+    L.sgtn_search.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I8P, _I64P, _F64P, _F64P, _I32P]
+    L.sgtn_energies.argtypes = [ct.c_void_p, ct.c_int32, _I8P, _I64P]
+    L.sgtn_site_dims.argtypes = [ct.c_void_p, ct.c_int32, _I32P]
+    L.sgtn_mps_shape.argtypes = [ct.c_void_p, ct.c_int32, _I32P, _I32P, _F64P]
+    L.sgtn_mps_tensor.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _F64P]
+    L.sgtn_last_error.argtypes = [ct.c_void_p]
+    L.sgtn_last_error.restype = ct.c_char_p
+    L.sgtn_destroy.argtypes = [ct.c_void_p]
+    L.sgtn_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+class SgtnError(RuntimeError):
+    pass
+
+
+class Handle:
+    """One instance on one device/stream; wraps the C ABI calls one to one."""
+
+    def __init__(self, inst, states_per_site=None, stream=None):
+        L = load()
+        self.L = L
+        self.inst = inst
+        ei = np.ascontiguousarray(inst.ei, np.int32)
+        ej = np.ascontiguousarray(inst.ej, np.int32)
+        jn = np.ascontiguousarray(inst.j_num, np.int32)
+        hn = np.ascontiguousarray(inst.h_num, np.int32)
+        site = np.ascontiguousarray(inst.site_of_spin, np.int32)
+        offs = sts = None
+        if states_per_site is not None:
+            lens = [len(s) for s in states_per_site]
+            offs = np.zeros(len(lens) + 1, np.int64)
+            offs[1:] = np.cumsum(lens)
+            sts = np.ascontiguousarray(np.concatenate([np.asarray(s, np.int64) for s in states_per_site]))
+        h = ct.c_void_p()
+        rc = L.sgtn_build_instance(inst.n_spins, inst.n_edges, _p(ei, _I32P), _p(ej, _I32P), _p(jn, _I32P),
+                                   _p(hn, _I32P), inst.denom, _p(site, _I32P), inst.rows, inst.cols,
+                                   _p(offs, _I64P), _p(sts, _I64P), stream, ct.byref(h))
+        if rc != 0:
+            raise SgtnError(f"sgtn_build_instance failed ({rc})")
+        self.h = h
+        self.d = []
+        for s in range(inst.rows * inst.cols):
+            d = ct.c_int32()
+            self._ck(L.sgtn_site_dims(h, s, ct.byref(d)))
+            self.d.append(d.value)
+
+    def _ck(self, rc):
+        if rc != 0:
+            raise SgtnError(f"sgtn error {rc}: {self.L.sgtn_last_error(self.h).decode()}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.sgtn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_beta(self, beta):
+        self._ck(self.L.sgtn_set_beta(self.h, float(beta)))
+
+    def contract_boundary(self, chi, precision=FP64, n_sweeps=2):
+        lz = ct.c_double()
+        ws = ct.c_double()
+        self._ck(self.L.sgtn_contract_boundary(self.h, chi, precision, n_sweeps, ct.byref(lz), ct.byref(ws)))
+        return lz.value, ws.value
+
+    def conditionals(self, step, configs):
+        configs = np.ascontiguousarray(np.asarray(configs, np.int32).reshape(-1, step) if step else
+                                       np.zeros((len(configs), 0), np.int32))
+        count = configs.shape[0]
+        out = np.zeros((count, self.d[step]))
+        self._ck(self.L.sgtn_conditionals(self.h, step, count, _p(configs, _I32P), _p(out, _F64P)))
+        return out
+
+    def branch_step(self, step, M, configs, logp, pd=-np.inf):
+        configs = np.ascontiguousarray(np.asarray(configs, np.int32).reshape(len(logp), step))
+        logp = np.ascontiguousarray(logp, np.float64)
+        oc = np.zeros((M, step + 1), np.int32)
+        ol = np.zeros(M)
+        cnt = ct.c_int32()
+        pdv = ct.c_double(pd)
+        self._ck(self.L.sgtn_branch_step(self.h, step, M, len(logp), _p(configs, _I32P), _p(logp, _F64P),
+                                         _p(oc, _I32P), _p(ol, _F64P), ct.byref(cnt), ct.byref(pdv)))
+        return oc[:cnt.value], ol[:cnt.value], pdv.value
+
+    def search(self, M, n_out=1):
+        N = self.inst.n_spins
+        sp = np.zeros((n_out, N), np.int8)
+        en = np.zeros(n_out, np.int64)
+        lp = np.zeros(n_out)
+        pd = ct.c_double()
+        cnt = ct.c_int32()
+        self._ck(self.L.sgtn_search(self.h, M, n_out, _p(sp, _I8P), _p(en, _I64P), _p(lp, _F64P), ct.byref(pd),
+                                    ct.byref(cnt)))
+        k = cnt.value
+        return dict(spins=sp[:k], energy_num=en[:k], logp=lp[:k], pd=pd.value)
+
+    def energies(self, spins):
+        spins = np.ascontiguousarray(np.asarray(spins, np.int8).reshape(-1, self.inst.n_spins))
+        out = np.zeros(spins.shape[0], np.int64)
+        self._ck(self.L.sgtn_energies(self.h, spins.shape[0], _p(spins, _I8P), _p(out, _I64P)))
+        return out
+
+    def mps(self, row):
+        C = self.inst.cols
+        phys = np.zeros(C, np.int32)
+        bond = np.zeros(C + 1, np.int32)
+        ln = ct.c_double()
+        self._ck(self.L.sgtn_mps_shape(self.h, row, _p(phys, _I32P), _p(bond, _I32P), ct.byref(ln)))
+        ts = []
+        for c in range(C):
+            t = np.zeros((phys[c], bond[c], bond[c + 1]))
+            self._ck(self.L.sgtn_mps_tensor(self.h, row, c, _p(t, _F64P)))
+            ts.append(t)
+        return ts, ln.value

@@ -1,0 +1,164 @@
+"""Parity of the CUDA library (through the C ABI) with the CPU oracle.
+
+FP64 path: log Z and conditional marginals within 1e-10 relative, boundary
+MPSs equal as vectors (gauge invariant), configurations and int64 energies
+bit-exact.
+"""
+import numpy as np
+import pytest
+
+from oracle import brute
+from oracle.peps import boundary_mps, mps_dense
+from oracle.potts import PottsModel
+from oracle.search import conditional_scores, search as oracle_search
+from paper_2411_16431_b300 import lattices as L
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def Handle():
+    from paper_2411_16431_b300.sgtn import Handle as H
+    return H
+
+
+EXACT = [L.square_grid(3, 3, 1), L.kings_grid(4, 4, 3), L.slice_cells(L.chimera_grid(4, 4, 0), 2, 1),
+         L.kings_grid(2, 5, 9), L.square_grid(1, 6, 2), L.square_grid(5, 1, 3)]
+
+
+@pytest.mark.parametrize("inst", EXACT, ids=lambda i: i.name)
+def test_exact_logz_matches_brute_force(Handle, inst):
+    h = Handle(inst)
+    for beta in (0.4, 1.5):
+        h.set_beta(beta)
+        lz, _ = h.contract_boundary(64, n_sweeps=1)
+        assert abs(lz - brute.log_z(inst, beta)) < RTOL * abs(lz)
+
+
+CASES = [(L.chimera_grid(4, 4, 0), 1.0, 16, 2), (L.chimera_grid(3, 4, 7), 2.0, 4, 1),
+         (L.kings_grid(5, 6, 4), 1.0, 3, 2), (L.square_grid(6, 5, 8), 3.0, 2, 2),
+         (L.planted(L.chimera_grid(3, 3, 5), 2), 1.5, 6, 1)]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0].name}_chi{c[2]}")
+def test_truncated_boundary_matches_oracle(Handle, case):
+    inst, beta, chi, ns = case
+    lz_o, psis, _ = boundary_mps(PottsModel(inst), beta, chi, ns)
+    h = Handle(inst)
+    h.set_beta(beta)
+    lz, worst = h.contract_boundary(chi, n_sweeps=ns)
+    assert abs(lz - lz_o) < RTOL * abs(lz_o)
+    assert 0 <= worst <= 1
+    for r in range(inst.rows):
+        ts, ln = h.mps(r)
+        A, lno = psis[r]
+        if np.prod([t.shape[0] for t in ts]) > 2 ** 20:
+            continue
+        v = mps_dense(ts, ln - lno)
+        vo = mps_dense(A)
+        assert np.allclose(v, vo, rtol=1e-8, atol=1e-10 * np.abs(vo).max())
+
+
+@pytest.mark.parametrize("case", CASES[:3], ids=lambda c: f"{c[0].name}_chi{c[2]}")
+def test_conditionals_match_oracle(Handle, case):
+    inst, beta, chi, ns = case
+    pm = PottsModel(inst)
+    _, psis, mpos = boundary_mps(pm, beta, chi, ns)
+    h = Handle(inst)
+    h.set_beta(beta)
+    h.contract_boundary(chi, n_sweeps=ns)
+    rng = np.random.default_rng(5)
+    for n in range(inst.rows * inst.cols):
+        r, c = divmod(n, inst.cols)
+        cfgs = np.array([[rng.integers(pm.sites[p].d) for p in range(n)] for _ in range(5)], np.int32).reshape(5, n)
+        p = h.conditionals(n, cfgs)
+        for k in range(5):
+            s = np.maximum(conditional_scores(pm, beta, mpos[r], psis[r], tuple(cfgs[k]), r, c), 0)
+            po = s / s.sum()
+            big = po > 1e-300
+            assert np.allclose(p[k][big], po[big], rtol=RTOL, atol=0)
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0].name}_chi{c[2]}")
+def test_search_matches_oracle(Handle, case):
+    inst, beta, chi, ns = case
+    M = 16
+    ref = oracle_search(inst, beta, chi=chi, M=M, n_sweeps=ns)
+    h = Handle(inst)
+    h.set_beta(beta)
+    h.contract_boundary(chi, n_sweeps=ns)
+    res = h.search(M)
+    assert np.array_equal(res["spins"], ref["spins"])
+    assert np.array_equal(res["energy_num"], ref["energy_num"])
+    assert np.allclose(res["logp"], ref["logp"], rtol=RTOL)
+    assert abs(res["pd"] - ref["pd"]) <= RTOL * abs(ref["pd"])
+    if inst.planted is not None:
+        assert res["energy_num"][0] >= inst.planted_energy_num
+
+
+def test_branch_steps_match_oracle(Handle):
+    """Every intermediate beam of the search, step by step (configurations, log p, p_d)."""
+    inst, beta, chi, M = L.chimera_grid(4, 4, 0), 1.0, 16, 64
+    from oracle.search import boundary_key, boundary_pairs
+    pm = PottsModel(inst)
+    _, psis, mpos = boundary_mps(pm, beta, chi, 2)
+    h = Handle(inst)
+    h.set_beta(beta)
+    h.contract_boundary(chi, n_sweeps=2)
+    beam = [((), 0.0)]
+    pd_o = -np.inf
+    cfg = np.zeros((1, 0), np.int32)
+    lp = np.zeros(1)
+    pd = -np.inf
+    for n in range(inst.rows * inst.cols):
+        r, c = divmod(n, inst.cols)
+        pairs = boundary_pairs(pm, n)
+        best = {}
+        for cf, l0 in beam:
+            s = np.maximum(conditional_scores(pm, beta, mpos[r], psis[r], cf, r, c), 0)
+            for x in np.nonzero(s > 0)[0]:
+                cand = cf + (int(x),)
+                lq = l0 + float(np.log(s[x] / s.sum()))
+                key = boundary_key(pm, pairs, cand)
+                old = best.get(key)
+                if old is None or (-lq, cand) < (-old[1], old[0]):
+                    if old is not None:
+                        pd_o = max(pd_o, old[1])
+                    best[key] = (cand, lq)
+                else:
+                    pd_o = max(pd_o, lq)
+        surv = sorted(best.values(), key=lambda t: (-t[1], t[0]))
+        for t in surv[M:]:
+            pd_o = max(pd_o, t[1])
+        beam = surv[:M]
+        cfg, lp, pd = h.branch_step(n, M, cfg, lp, pd)
+        assert [tuple(x) for x in cfg.tolist()] == [b[0] for b in beam], n
+        assert np.allclose(lp, [b[1] for b in beam], rtol=RTOL)
+        assert abs(pd - pd_o) <= RTOL * abs(pd_o)
+
+
+def test_energies_exact(Handle):
+    inst = L.chimera_grid(4, 4, 3)
+    h = Handle(inst)
+    rng = np.random.default_rng(0)
+    S = rng.choice(np.array([-1, 1], np.int8), size=(7, inst.n_spins))
+    assert np.array_equal(h.energies(S), [inst.energy_num(s) for s in S])
+
+
+def test_call_order_and_argument_errors(Handle):
+    from paper_2411_16431_b300.sgtn import SgtnError
+    inst = L.chimera_grid(2, 2, 1)
+    h = Handle(inst)
+    with pytest.raises(SgtnError, match="-2"):
+        h.contract_boundary(4)
+    h.set_beta(1.0)
+    with pytest.raises(SgtnError, match="-2"):
+        h.search(4)
+    with pytest.raises(SgtnError, match="-1"):
+        h.contract_boundary(0)
+    h.contract_boundary(4)
+    with pytest.raises(SgtnError, match="-1"):
+        h.conditionals(1, np.array([[9999]], np.int32))
+    h.search(4)   # still usable after errors
