@@ -21,9 +21,14 @@ probable survive.  p_d is the largest log-probability ever discarded (Sec.
 III.A, last paragraph).
 
 Readings: negative scores (possible with an approximate boundary MPS) are
-clamped to zero and counted; ties in log p are broken toward the
-lexicographically smaller configuration (placement order, state index
-ascending), in merging and in the top-M cut alike.
+clamped to zero and counted.  Integer couplings make exactly degenerate
+candidates common, and two correct implementations round differently, so
+log-probabilities within TIE_REL (relative) of each other count as equal and
+are ordered by configuration (lexicographically smaller first, in placement
+order): in a merge group every candidate within tolerance of the group's
+maximum is a tie and the smallest configuration wins; at the top-M cut the
+candidates within tolerance of the M-th value form a tie class filled in
+configuration order.
 """
 from __future__ import annotations
 
@@ -99,6 +104,43 @@ def boundary_pairs(pm: PottsModel, n):
     return sorted(out)
 
 
+TIE_REL = 1e-10
+
+
+def tie_tol(lp):
+    return TIE_REL * max(1.0, abs(lp))
+
+
+def merge_and_cut(cands, M):
+    """Bounding of Fig. 3(d-e) on a dict key -> list of (config, log p).
+
+    Returns (kept beam sorted by (-log p, config), largest discarded log p).
+    """
+    pd = -np.inf
+    surv = []
+    for group in cands.values():
+        top = max(lq for _, lq in group)
+        tied = [t for t in group if t[1] >= top - tie_tol(top)]
+        win = min(tied, key=lambda t: t[0])
+        surv.append(win)
+        for t in group:
+            if t is not win:
+                pd = max(pd, t[1])
+    surv.sort(key=lambda t: (-t[1], t[0]))
+    if len(surv) > M:
+        T = surv[M - 1][1]
+        tol = tie_tol(T)
+        sure = [t for t in surv if t[1] > T + tol]
+        tie = sorted([t for t in surv if T - tol <= t[1] <= T + tol], key=lambda t: t[0])
+        keep = sure + tie[:M - len(sure)]
+        kept = set(id(t) for t in keep)
+        for t in surv:
+            if id(t) not in kept:
+                pd = max(pd, t[1])
+        surv = sorted(keep, key=lambda t: (-t[1], t[0]))
+    return surv, pd
+
+
 def boundary_key(pm, pairs, cfg):
     return tuple(pm.sites[p].proj[d].of_state[cfg[p]] for (p, l, d) in pairs)
 
@@ -115,7 +157,7 @@ def search(inst, beta, chi, M, n_sweeps=2, states=None, psis=None):
     for n in range(pm.R * C):
         r, c = divmod(n, C)
         pairs = boundary_pairs(pm, n)
-        best = {}
+        cands = {}
         for cfg, lp in beam:
             s = conditional_scores(pm, beta, mpos[r], psis[r], cfg, r, c)
             clamps += int(np.sum(s < 0))
@@ -123,19 +165,10 @@ def search(inst, beta, chi, M, n_sweeps=2, states=None, psis=None):
             tot = s.sum()
             for x in np.nonzero(s > 0)[0]:
                 cand = cfg + (int(x),)
-                lq = lp + float(np.log(s[x] / tot))
-                key = boundary_key(pm, pairs, cand)
-                old = best.get(key)
-                if old is None:
-                    best[key] = (cand, lq)
-                else:
-                    keep, drop = ((cand, lq), old) if (-lq, cand) < (-old[1], old[0]) else (old, (cand, lq))
-                    best[key] = keep
-                    pd = max(pd, drop[1])
-        surv = sorted(best.values(), key=lambda t: (-t[1], t[0]))
-        for t in surv[M:]:
-            pd = max(pd, t[1])
-        beam = surv[:M]
+                cands.setdefault(boundary_key(pm, pairs, cand), []).append(
+                    (cand, lp + float(np.log(s[x] / tot))))
+        beam, pd_step = merge_and_cut(cands, M)
+        pd = max(pd, pd_step)
     configs = [b[0] for b in beam]
     spins = np.array([pm.spins_of_config(cfg) for cfg in configs], dtype=np.int8)
     energies = np.array([inst.energy_num(s) for s in spins], dtype=np.int64)

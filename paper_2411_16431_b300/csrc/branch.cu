@@ -34,7 +34,9 @@ __device__ __host__ inline unsigned long long ord_key(double v) {
   memcpy(&u, &v, sizeof(u));
   return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
 }
-inline double key_to_double(unsigned long long k) {
+constexpr double TIE_REL = 1e-10;   // log p within this (relative) count as tied
+__device__ __host__ inline double tie_tol(double lp) { return TIE_REL * fmax(1.0, fabs(lp)); }
+__device__ __host__ inline double key_to_double(unsigned long long k) {
   unsigned long long u = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
   double v;
   memcpy(&v, &u, sizeof(v));
@@ -245,14 +247,17 @@ __global__ void merge1_kernel(int K, int d, int nX, const unsigned long long* ke
     atomicMax(best + (long long)pc[k] * nX + xk[x], key[i]);
   }
 }
-__global__ void merge2_kernel(int K, int d, int nX, const unsigned long long* key, const int32_t* pc,
-                              const int32_t* prank, const int32_t* xk, const unsigned long long* best, int* mn) {
+// every candidate within the tie tolerance of its group's maximum competes on configuration order
+__global__ void merge2_kernel(int K, int d, int nX, const unsigned long long* key, const double* lp,
+                              const int32_t* pc, const int32_t* prank, const int32_t* xk,
+                              const unsigned long long* best, int* mn) {
   long long n = (long long)K * d;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     if (!key[i]) continue;
     int k = int(i / d), x = int(i % d);
     long long slot = (long long)pc[k] * nX + xk[x];
-    if (key[i] == best[slot]) atomicMin(mn + slot, prank[k] * d + x);
+    double top = key_to_double(best[slot]);
+    if (lp[i] >= top - tie_tol(top)) atomicMin(mn + slot, prank[k] * d + x);
   }
 }
 // winners: key stays, losers: key -> 0 after recording them in `lost`
@@ -286,21 +291,21 @@ __global__ void hist_kernel(long long n, const unsigned long long* key, int shif
     if (h[i]) atomicAdd(hist + i, h[i]);
 }
 
-// above threshold: selected; equal: appended to the tie list; non-selected valid: p_d
-__global__ void select_kernel(long long n, int d, const unsigned long long* key, const int32_t* prank,
-                              unsigned long long T, int* nsel, long long* sel, int* ntie, long long* tie,
-                              unsigned long long* lost, int cap) {
+// above T + tol: selected; within T +- tol: tie class; other valid ones: p_d
+__global__ void select_kernel(long long n, const unsigned long long* key, const double* lp, double T, double tol,
+                              int* nsel, long long* sel, int* ntie, long long* tie, unsigned long long* lost,
+                              int cap_sel, int cap_tie) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    unsigned long long k = key[i];
-    if (!k) continue;
-    if (k > T) {
+    if (!key[i]) continue;
+    double v = lp[i];
+    if (v > T + tol) {
       int j = atomicAdd(nsel, 1);
-      if (j < cap) sel[j] = i;
-    } else if (k == T) {
+      if (j < cap_sel) sel[j] = i;
+    } else if (v >= T - tol) {
       int j = atomicAdd(ntie, 1);
-      if (j < cap) tie[j] = i;
+      if (j < cap_tie) tie[j] = i;
     } else {
-      atomicMax(lost, k);
+      atomicMax(lost, key[i]);
     }
   }
 }
@@ -562,7 +567,7 @@ void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_
   unsigned long long* lost = S.alloc<unsigned long long>(1);
   SGTN_CUDA(cudaMemsetAsync(lost, 0, sizeof(unsigned long long), st));
   merge1_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, pc, h->ds[step].xk_x, best);
-  merge2_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, pc, prank, h->ds[step].xk_x, best, mn);
+  merge2_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, lp, pc, prank, h->ds[step].xk_x, best, mn);
   merge3_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, pc, prank, h->ds[step].xk_x, mn, lost);
   // radix select of the M-th largest key
   unsigned int* hist = S.alloc<unsigned int>(256);
@@ -578,7 +583,7 @@ void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_
     h->sync();
     for (auto v : hh) total_valid += v;
     if (total_valid == 0) throw SgtnError(-4, "no candidate with a positive score");
-    unsigned long long T = 0;
+    double T = -INFINITY, tol = 0.0;
     if (total_valid > M) {
       for (int shift = 56; shift >= 0; shift -= 8) {
         if (shift != 56) {
@@ -595,22 +600,21 @@ void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_
         prefix |= (unsigned long long)b << shift;
         pmask |= 255ull << shift;
       }
-      T = prefix;   // M-th largest key; `need` of the keys equal to T are taken
-    } else {
-      T = 0;        // everything valid is above T
-      need = 0;
+      T = key_to_double(prefix);   // the M-th largest log p
+      tol = tie_tol(T);
     }
     int* nsel = S.alloc<int>(2);
     SGTN_CUDA(cudaMemsetAsync(nsel, 0, 2 * sizeof(int), st));
-    int cap = M + 1;
-    long long* sel = S.alloc<long long>(cap);
-    long long* tie = S.alloc<long long>(std::max<long long>(cap, 1));
-    select_kernel<<<nblk(ncand), 256, 0, st>>>(ncand, d, key, prank, T, nsel, sel, nsel + 1, tie, lost, cap);
+    int cap_sel = M + 1, cap_tie = 4 * M + 4096;
+    long long* sel = S.alloc<long long>(cap_sel);
+    long long* tie = S.alloc<long long>(cap_tie);
+    select_kernel<<<nblk(ncand), 256, 0, st>>>(ncand, key, lp, T, tol, nsel, sel, nsel + 1, tie, lost, cap_sel,
+                                               cap_tie);
     int hn[2];
     SGTN_CUDA(cudaMemcpyAsync(hn, nsel, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     h->sync();
     int n_above = hn[0], n_tie = hn[1];
-    if (n_above > M || n_tie > cap) throw SgtnError(-4, "too many tied candidates at the top-M cut");
+    if (n_above > M || n_tie > cap_tie) throw SgtnError(-4, "too many tied candidates at the top-M cut");
     std::vector<long long> hsel(n_above), htie(n_tie);
     if (n_above) SGTN_CUDA(cudaMemcpyAsync(hsel.data(), sel, n_above * sizeof(long long), cudaMemcpyDeviceToHost, st));
     if (n_tie) SGTN_CUDA(cudaMemcpyAsync(htie.data(), tie, n_tie * sizeof(long long), cudaMemcpyDeviceToHost, st));
@@ -621,22 +625,20 @@ void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_
     unsigned long long hlost = 0;
     SGTN_CUDA(cudaMemcpyAsync(&hlost, lost, sizeof(hlost), cudaMemcpyDeviceToHost, st));
     h->sync();
-    // candidates ordered by (log p desc, parent rank asc, state asc)
-    auto order = [&](long long a, long long b) {
-      if (hlp[a] != hlp[b]) return hlp[a] > hlp[b];
-      long long ca = (long long)hprank[a / d] * d + a % d, cb = (long long)hprank[b / d] * d + b % d;
-      return ca < cb;
-    };
-    std::sort(htie.begin(), htie.end(), order);
+    auto cfg_order = [&](long long a) { return (long long)hprank[a / d] * d + a % d; };
+    // the tie class is filled in configuration order
+    std::sort(htie.begin(), htie.end(), [&](long long a, long long b) { return cfg_order(a) < cfg_order(b); });
     std::vector<long long> keep = hsel;
     for (int i = 0; i < n_tie; ++i) {
-      if ((long long)keep.size() < M && (T != 0 || need != 0 || total_valid <= M))
+      if ((long long)keep.size() < M)
         keep.push_back(htie[i]);
       else
         hlost = std::max(hlost, ord_key(hlp[htie[i]]));
     }
-    std::sort(keep.begin(), keep.end(), order);
-    if ((long long)keep.size() > M) keep.resize(M);
+    std::sort(keep.begin(), keep.end(), [&](long long a, long long b) {
+      if (hlp[a] != hlp[b]) return hlp[a] > hlp[b];
+      return cfg_order(a) < cfg_order(b);
+    });
     int outc = int(keep.size());
     for (int i = 0; i < outc; ++i) {
       long long ci = keep[i];

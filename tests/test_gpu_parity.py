@@ -98,15 +98,17 @@ def test_search_matches_oracle(Handle, case):
         assert res["energy_num"][0] >= inst.planted_energy_num
 
 
-def test_branch_steps_match_oracle(Handle):
+@pytest.mark.parametrize("case", [(L.chimera_grid(4, 4, 0), 1.0, 16, 64, 2), (L.chimera_grid(3, 4, 7), 2.0, 4, 16, 1),
+                                  (L.kings_grid(4, 5, 2), 2.0, 3, 8, 1)], ids=lambda c: c[0].name)
+def test_branch_steps_match_oracle(Handle, case):
     """Every intermediate beam of the search, step by step (configurations, log p, p_d)."""
-    inst, beta, chi, M = L.chimera_grid(4, 4, 0), 1.0, 16, 64
-    from oracle.search import boundary_key, boundary_pairs
+    inst, beta, chi, M, ns = case
+    from oracle.search import boundary_key, boundary_pairs, merge_and_cut
     pm = PottsModel(inst)
-    _, psis, mpos = boundary_mps(pm, beta, chi, 2)
+    _, psis, mpos = boundary_mps(pm, beta, chi, ns)
     h = Handle(inst)
     h.set_beta(beta)
-    h.contract_boundary(chi, n_sweeps=2)
+    h.contract_boundary(chi, n_sweeps=ns)
     beam = [((), 0.0)]
     pd_o = -np.inf
     cfg = np.zeros((1, 0), np.int32)
@@ -115,27 +117,19 @@ def test_branch_steps_match_oracle(Handle):
     for n in range(inst.rows * inst.cols):
         r, c = divmod(n, inst.cols)
         pairs = boundary_pairs(pm, n)
-        best = {}
+        cands = {}
         for cf, l0 in beam:
             s = np.maximum(conditional_scores(pm, beta, mpos[r], psis[r], cf, r, c), 0)
             for x in np.nonzero(s > 0)[0]:
                 cand = cf + (int(x),)
-                lq = l0 + float(np.log(s[x] / s.sum()))
-                key = boundary_key(pm, pairs, cand)
-                old = best.get(key)
-                if old is None or (-lq, cand) < (-old[1], old[0]):
-                    if old is not None:
-                        pd_o = max(pd_o, old[1])
-                    best[key] = (cand, lq)
-                else:
-                    pd_o = max(pd_o, lq)
-        surv = sorted(best.values(), key=lambda t: (-t[1], t[0]))
-        for t in surv[M:]:
-            pd_o = max(pd_o, t[1])
-        beam = surv[:M]
+                cands.setdefault(boundary_key(pm, pairs, cand), []).append((cand, l0 + float(np.log(s[x] / s.sum()))))
+        beam, pds = merge_and_cut(cands, M)
+        pd_o = max(pd_o, pds)
         cfg, lp, pd = h.branch_step(n, M, cfg, lp, pd)
-        assert [tuple(x) for x in cfg.tolist()] == [b[0] for b in beam], n
-        assert np.allclose(lp, [b[1] for b in beam], rtol=RTOL)
+        got = sorted(zip(map(tuple, cfg.tolist()), lp.tolist()))
+        want = sorted(beam)
+        assert [g[0] for g in got] == [w[0] for w in want], n
+        assert np.allclose([g[1] for g in got], [w[1] for w in want], rtol=RTOL)
         assert abs(pd - pd_o) <= RTOL * abs(pd_o)
 
 
