@@ -1,0 +1,271 @@
+"""Benchmark of the hot path: boundary-MPS contraction + branch-and-bound search.
+
+One step = set_beta + contract_boundary + search on one instance resident in
+HBM (every kernel of the path).  ``value`` = conditional marginals evaluated
+per second over the whole job (all ranks); the boundary contraction's
+algorithmic TFLOP/s is reported beside it.  Multi-GPU runs are independent
+replicas (one instance per rank, different seeds): the method has no data
+exchange between instances.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl native|reference] [--workload NAME]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2411_16431_b300 import lattices as L  # noqa: E402
+
+# Workloads: sizes of the benchmark configurations.
+WORKLOADS = {
+    "chimera4x4": dict(desc="4x4 grid of K44 cells (128 spins), iid J,h in {+-1..+-7}/7, beta=1, chi=16, M=64, FP64",
+                       make=lambda seed: L.chimera_grid(4, 4, seed), beta=1.0, chi=16, M=64, sweeps=2),
+}
+DEFAULT = "chimera4x4"
+# FP64 peak of a B300 derived from unit counts: 148 SMs x 2 DFMA/clk/SM x 2 flop x 2032 MHz
+FP64_PEAK_GFLOPS = 148 * 2 * 2 * 2.032
+
+
+def clocks_sampler(dev_index):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", "-i", str(dev_index), f"--query-gpu={q}", "--format=csv,noheader",
+                                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except Exception:
+        return None
+
+
+def clocks_summary(proc):
+    if proc is None:
+        return None
+    proc.terminate()
+    out, _ = proc.communicate(timeout=10)
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1].split()[0]))
+            mx.append(float(f[2].split()[0]))
+        except ValueError:
+            continue
+        for n, v in zip(names, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle(wl, seed, budget_s=15.0, max_runs=5):
+    """Oracle search timed on the host cores: marginals evaluated per second."""
+    from oracle.search import search as oracle_search
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([t.get("num_threads", 1) for t in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    inst = wl["make"](seed)
+    runs, t_tot, evals = 0, 0.0, 0
+    while runs < max_runs and (t_tot < budget_s or runs == 0):
+        t0 = time.perf_counter()
+        res = oracle_search(inst, wl["beta"], chi=wl["chi"], M=wl["M"], n_sweeps=wl["sweeps"])
+        t_tot += time.perf_counter() - t0
+        evals += res["evals"]
+        runs += 1
+    return {"value": evals / t_tot, "unit": "marginal evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{runs} full oracle search(es) of the bench workload ({evals} evaluations, {t_tot:.1f} s)"}
+
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle.search import search as oracle_search
+    inst = wl["make"](args.seed)
+    for _ in range(args.warmup):
+        oracle_search(inst, wl["beta"], chi=wl["chi"], M=wl["M"], n_sweeps=wl["sweeps"])
+    t_tot, evals = 0.0, 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        res = oracle_search(inst, wl["beta"], chi=wl["chi"], M=wl["M"], n_sweeps=wl["sweeps"])
+        t_tot += time.perf_counter() - t0
+        evals += res["evals"]
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([t.get("num_threads", 1) for t in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    v = evals / t_tot
+    line = {"impl": "reference", "metric": "marginal evals/s", "value": v, "unit": "marginal evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": wl["desc"], "instances_per_rank": 1},
+            "cpu_baseline": {"value": v, "unit": "marginal evals/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full oracle searches ({evals} evaluations)"},
+            "e2e": {"value": v, "unit": "marginal evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args, wl):
+    import torch
+    import torch.distributed as dist
+    from paper_2411_16431_b300 import sgtn
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    inst = wl["make"](args.seed + rank)
+    h = sgtn.Handle(inst, stream=stream.cuda_stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > 126 MB L2
+
+    def step():
+        h.set_beta(wl["beta"])
+        h.contract_boundary(wl["chi"], n_sweeps=wl["sweeps"])
+        return h.search(wl["M"])
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    l0, f0, e0 = sgtn.stats()
+    sgtn.kernel_timing(True, reset=True)
+    clk = clocks_sampler(local)
+    times = []
+    bflops = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.set_beta(wl["beta"])
+        fa = sgtn.stats()[1]
+        h.contract_boundary(wl["chi"], n_sweeps=wl["sweeps"])
+        bflops += sgtn.stats()[1] - fa
+        res = h.search(wl["M"])
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    clocks = clocks_summary(clk)
+    sgtn.kernel_timing(False)
+    l1, f1, e1 = sgtn.stats()
+    t_ms = sum(times)
+    evals = e1 - e0
+    if ws > 1:
+        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ev = torch.tensor([evals], device="cuda", dtype=torch.float64)
+        dist.all_reduce(ev, op=dist.ReduceOp.SUM)
+        t_ms, evals_all = float(tt.item()), float(ev.item())
+    else:
+        evals_all = evals
+    kt = {n: sgtn.kernel_time(n) for n in ("seg_gemm_f64", "jacobi_f64", "score_f64")}
+    # boundary contraction timed alone for its TFLOP/s
+    torch.cuda.synchronize()
+    h.set_beta(wl["beta"])
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    h.contract_boundary(wl["chi"], n_sweeps=wl["sweeps"])
+    b.record(stream)
+    torch.cuda.synchronize()
+    bound_ms = a.elapsed_time(b)
+    # end to end through the public API from host buffers: build (H2D) .. results (D2H)
+    e2e_times = []
+    h2d = inst.ei.nbytes + inst.ej.nbytes + inst.j_num.nbytes + inst.h_num.nbytes + inst.site_of_spin.nbytes
+    d2h = 0
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2 = sgtn.Handle(inst, stream=stream.cuda_stream)
+        h2.set_beta(wl["beta"])
+        h2.contract_boundary(wl["chi"], n_sweeps=wl["sweeps"])
+        r2 = h2.search(wl["M"])
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        d2h = r2["spins"].nbytes + r2["energy_num"].nbytes + r2["logp"].nbytes + 8
+        h2.close()
+    e2e_val = (evals / args.steps) / statistics.median(e2e_times) * ws
+    if rank != 0:
+        if ws > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    # roofline of the dominant contraction kernel (FP64 ALU bound)
+    seg = kt["seg_gemm_f64"]
+    roof = None
+    if seg and seg[1] > 0:
+        achieved = (seg[2] / seg[1]) / (seg[0] / seg[1] * 1e-3) / 1e12   # TFLOP/s per launch average
+        peak = FP64_PEAK_GFLOPS / 1e3
+        roof = {"kernel": "seg_gemm_f64", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2032 MHz (no measured FP64 peak)"}
+    shares = {}
+    tot_k = sum(v[0] for v in kt.values() if v)
+    for n, v in kt.items():
+        if v:
+            shares[n] = {"ms": v[0], "launches": v[1], "share_of_timed_kernels": v[0] / tot_k if tot_k else None}
+    line = {"metric": "marginal evals/s", "value": evals_all / (t_ms * 1e-3), "unit": "marginal evals/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": wl["desc"], "instances_per_rank": 1,
+                       "parallelism": f"replicas{ws}", "l2": "flushed between timed steps (256 MB write)"},
+            "boundary_tflops": (bflops / args.steps) / (bound_ms * 1e-3) / 1e12,
+            "boundary_ms": bound_ms,
+            "roofline": roof, "kernel_times": shares,
+            "e2e": {"value": e2e_val, "unit": "marginal evals/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int((l1 - l0) / args.steps),
+            "clocks": clocks,
+            "result": {"energy_num": int(res["energy_num"][0]), "logp": float(res["logp"][0])}}
+    if ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle(wl, args.seed)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_native(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -124,6 +124,23 @@ int sgtn_site_dims(sgtn_h h, int32_t site, int32_t* d);
 int sgtn_mps_shape(sgtn_h h, int32_t row, int32_t* phys, int32_t* bond, double* lognorm);
 int sgtn_mps_tensor(sgtn_h h, int32_t row, int32_t col, double* out);
 
+/* Process-wide diagnostics (the paper has no counterpart): cumulative
+ * number of kernel launches issued by this library, algorithmic
+ * floating-point operations of its contractions (2 m n k per gathered
+ * matrix product, no padding; SVD work excluded) and number of conditional
+ * marginals evaluated (one per branch x cluster state).  Any pointer may be
+ * NULL.  Not synchronised: read it from the thread that issues the work. */
+void sgtn_stats(int64_t* launches, double* flops, int64_t* evals);
+
+/* Optional per-kernel timing (the paper has no counterpart): when enabled,
+ * every launch of the named kernels ("seg_gemm_f64", "jacobi_f64",
+ * "score_f64") is bracketed by CUDA events on its stream; reset clears the
+ * totals.  sgtn_kernel_time returns the summed device time in ms, the number
+ * of timed launches and their algorithmic flops (SGTN_ERR_ARG if the kernel
+ * was not timed). */
+void sgtn_kernel_timing(int32_t enable, int32_t reset);
+int sgtn_kernel_time(const char* name, double* ms, int64_t* launches, double* flops);
+
 const char* sgtn_last_error(sgtn_h h);
 void sgtn_destroy(sgtn_h h);
 

@@ -154,12 +154,14 @@ def search(inst, beta, chi, M, n_sweeps=2, states=None, psis=None):
     beam = [((), 0.0)]
     pd = -np.inf
     clamps = 0
+    evals = 0
     for n in range(pm.R * C):
         r, c = divmod(n, C)
         pairs = boundary_pairs(pm, n)
         cands = {}
         for cfg, lp in beam:
             s = conditional_scores(pm, beta, mpos[r], psis[r], cfg, r, c)
+            evals += s.size
             clamps += int(np.sum(s < 0))
             s = np.maximum(s, 0.0)
             tot = s.sum()
@@ -173,4 +175,4 @@ def search(inst, beta, chi, M, n_sweeps=2, states=None, psis=None):
     spins = np.array([pm.spins_of_config(cfg) for cfg in configs], dtype=np.int8)
     energies = np.array([inst.energy_num(s) for s in spins], dtype=np.int64)
     return dict(configs=configs, logp=np.array([b[1] for b in beam]), pd=pd, spins=spins,
-                energy_num=energies, logz=logz, clamps=clamps, pm=pm, psis=psis, mpos=mpos)
+                energy_num=energies, logz=logz, clamps=clamps, evals=evals, pm=pm, psis=psis, mpos=mpos)

@@ -43,6 +43,7 @@ void energies(sgtn_inst* h, int n, const int8_t* spins, int64_t* out) {
   const int32_t* jn = h->M.jn.empty() ? nullptr : h->upload(h->M.jn);
   const int32_t* hn = h->upload(h->M.hn);
   energy_kernel<<<n, 256, 0, h->st>>>(h->M.N, (long long)h->M.ei.size(), ds, ei, ej, jn, hn, dout);
+  ++g_count.launches;
   h->check();
   SGTN_CUDA(cudaMemcpyAsync(out, dout, size_t(n) * sizeof(long long), cudaMemcpyDeviceToHost, h->st));
   h->sync();
@@ -169,6 +170,25 @@ int sgtn_mps_tensor(sgtn_h h, int32_t row, int32_t col, double* out) {
     SGTN_CUDA(cudaMemcpyAsync(out, m.t[col], n * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     h->sync();
   });
+}
+
+void sgtn_stats(int64_t* launches, double* flops, int64_t* evals) {
+  if (launches) *launches = g_count.launches;
+  if (flops) *flops = g_count.flops;
+  if (evals) *evals = g_count.evals;
+}
+
+void sgtn_kernel_timing(int32_t enable, int32_t reset) {
+  if (reset) ktimer_reset();
+  ktimer_enable(enable != 0);
+}
+
+int sgtn_kernel_time(const char* name, double* ms, int64_t* launches, double* flops) {
+  if (!name || !ms || !launches || !flops) return SGTN_ERR_ARG;
+  long long n = 0;
+  if (!ktimer_read(name, ms, &n, flops)) return SGTN_ERR_ARG;
+  *launches = n;
+  return SGTN_OK;
 }
 
 const char* sgtn_last_error(sgtn_h h) { return h ? h->err.c_str() : "null handle"; }

@@ -207,6 +207,7 @@ void site_diagram(RowCtx& X, int c, const double* Kt, int kp, double* Th) {
   a.cidx = K_.theta.cidx;
   a.coef = X.h->ds[X.r * X.h->M.C + c].w;
   a.nseg = K_.theta.nseg;
+  a.nterm = K_.theta.nterm;
   seg_gemm(a, X.h->st);
 }
 
@@ -259,6 +260,7 @@ double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
   a.cidx = K_.lupd.cidx;
   a.coef = h->ds[X.r * h->M.C + c].w;
   a.nseg = K_.lupd.nseg;
+  a.nterm = K_.lupd.nterm;
   seg_gemm(a, h->st);
   // Lnext[b][br][chr] = sum_k Wk[k][br] Ltil[k][b][chr]   (batched over b)
   double* Ln = dmalloc((long long)phi.b * K_.nBR() * chr);

@@ -388,7 +388,7 @@ void prepare_scores(Step& S, const int32_t* hcfg) {
     }
     upper_f_kernel<<<nblk((long long)K_.nU * K), 256, 0, st>>>(K, K_.nU, r, cc, C, S.dcfg, S.cfg_ld, up_pd, Bv, bv_nb,
                                                               me.U_u, ul_pdr, Bdr, bdr_nb, me.U_ul, ur_pdl, Bdl,
-                                                              bdl_nb, me.U_ur, S.f[cc]);
+                                                              bdl_nb, me.U_ur, S.f[cc]); ++g_count.launches;
   }
   // left environment at column c
   {
@@ -409,7 +409,7 @@ void prepare_scores(Step& S, const int32_t* hcfg) {
       lenv_kernel<<<K, 128, smem, st>>>(K, K, par, xs, S.E, chl, chr, K_.nG, K_.nE, K_.nPdr, K_.nLR, K_.nGR,
                                         S.Ahat[cc], D.lam_x, D.cls[DD], D.cls[DR_], D.cls[DDR], K_.l_pl, K_.l_pdl,
                                         h->dB[size_t(r * C + cc) * 4 + 0], K_.bh_nb, h->dB[size_t(r * C + cc) * 4 + 2],
-                                        K_.bdr_nb, En);
+                                        K_.bdr_nb, En); ++g_count.launches;
       S.E = En;
       h->sync();  // xs is reused
     }
@@ -454,8 +454,9 @@ void prepare_scores(Step& S, const int32_t* hcfg) {
     a.cs = S.f[cc];
     a.cs_ld = K;
     a.nseg = K_.renv.nseg;
+    a.nterm = K_.renv.nterm;
     seg_gemm(a, st);
-    colnorm_kernel<<<K, 256, 0, st>>>(Fn, (long long)K_.nBL() * chl, K);
+    colnorm_kernel<<<K, 256, 0, st>>>(Fn, (long long)K_.nBL() * chl, K); ++g_count.launches;
     F = Fn;
   }
   const Column& Kc = S.col(c);
@@ -467,9 +468,10 @@ void prepare_scores(Step& S, const int32_t* hcfg) {
   S.s = S.alloc<double>(size_t(K) * D.d);
   int thr = std::min(256, std::max(32, ((K + 3) / 4 + 31) / 32 * 32));
   if (K > 4 * thr) throw SgtnError(-1, "beam too large for the score kernel");
+  KTimer tsc("score_f64", st, 2.0 * K * D.d * (double)Kc.nG * Kc.nE * chl * (chr + 1));
   score_kernel<<<D.d, thr, size_t(chl) * chr * sizeof(double), st>>>(K, D.d, chl, chr, Kc.nG, Kc.nE, Kc.nPdr, S.E,
                                                                       S.Ahat[c], S.Ft, S.f[c], D.w, D.lam_x, D.u_x,
-                                                                      D.cls[DD], D.cls[DR_], D.cls[DDR], S.s);
+                                                                      D.cls[DD], D.cls[DR_], D.cls[DDR], S.s); ++g_count.launches;
   h->check();
   (void)R;
 }
@@ -533,6 +535,7 @@ void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_
   int* clamps = S.alloc<int>(1);
   SGTN_CUDA(cudaMemsetAsync(clamps, 0, sizeof(int), st));
   logp_kernel<<<K, 256, 0, st>>>(K, d, S.s, dlp_in, lp, key, clamps);
+  g_count.evals += ncand; ++g_count.launches;
   // parent classes from the boundary pairs (p, dir) with p < step < l (Eq. 7)
   std::vector<int32_t> psite;
   std::vector<const int32_t*> pcls;
@@ -557,7 +560,7 @@ void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_
   }
   int32_t* pc = S.alloc<int32_t>(K);
   int32_t* prank = S.alloc<int32_t>(K);
-  parent_kernel<<<(K + 127) / 128, 128, 0, st>>>(K, step, S.dcfg, S.cfg_ld, npairs, dps, dpc, pc, prank);
+  parent_kernel<<<(K + 127) / 128, 128, 0, st>>>(K, step, S.dcfg, S.cfg_ld, npairs, dps, dpc, pc, prank); ++g_count.launches;
   const int nX = site.Xk.n;
   long long nslot = (long long)K * nX;
   unsigned long long* best = S.alloc<unsigned long long>(nslot);
@@ -566,9 +569,9 @@ void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_
   SGTN_CUDA(cudaMemsetAsync(mn, 0x7f, nslot * sizeof(int), st));
   unsigned long long* lost = S.alloc<unsigned long long>(1);
   SGTN_CUDA(cudaMemsetAsync(lost, 0, sizeof(unsigned long long), st));
-  merge1_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, pc, h->ds[step].xk_x, best);
-  merge2_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, lp, pc, prank, h->ds[step].xk_x, best, mn);
-  merge3_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, pc, prank, h->ds[step].xk_x, mn, lost);
+  merge1_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, pc, h->ds[step].xk_x, best); ++g_count.launches;
+  merge2_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, lp, pc, prank, h->ds[step].xk_x, best, mn); ++g_count.launches;
+  merge3_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, pc, prank, h->ds[step].xk_x, mn, lost); ++g_count.launches;
   // radix select of the M-th largest key
   unsigned int* hist = S.alloc<unsigned int>(256);
   unsigned long long prefix = 0, pmask = 0;
@@ -577,7 +580,7 @@ void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_
   {
     // count valid survivors first (histogram of the top digit with empty prefix)
     SGTN_CUDA(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned int), st));
-    hist_kernel<<<nblk(ncand), 256, 0, st>>>(ncand, key, 56, 0ull, 0ull, hist);
+    hist_kernel<<<nblk(ncand), 256, 0, st>>>(ncand, key, 56, 0ull, 0ull, hist); ++g_count.launches;
     std::vector<unsigned int> hh(256);
     SGTN_CUDA(cudaMemcpyAsync(hh.data(), hist, 256 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     h->sync();
@@ -588,7 +591,7 @@ void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_
       for (int shift = 56; shift >= 0; shift -= 8) {
         if (shift != 56) {
           SGTN_CUDA(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned int), st));
-          hist_kernel<<<nblk(ncand), 256, 0, st>>>(ncand, key, shift, prefix, pmask, hist);
+          hist_kernel<<<nblk(ncand), 256, 0, st>>>(ncand, key, shift, prefix, pmask, hist); ++g_count.launches;
           SGTN_CUDA(cudaMemcpyAsync(hh.data(), hist, 256 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
           h->sync();
         }
@@ -609,7 +612,7 @@ void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_
     long long* sel = S.alloc<long long>(cap_sel);
     long long* tie = S.alloc<long long>(cap_tie);
     select_kernel<<<nblk(ncand), 256, 0, st>>>(ncand, key, lp, T, tol, nsel, sel, nsel + 1, tie, lost, cap_sel,
-                                               cap_tie);
+                                               cap_tie); ++g_count.launches;
     int hn[2];
     SGTN_CUDA(cudaMemcpyAsync(hn, nsel, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     h->sync();

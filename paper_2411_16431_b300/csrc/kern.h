@@ -3,8 +3,32 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 namespace sgtn {
+
+// Process-wide diagnostics: kernel launches issued by this library and the
+// algorithmic floating-point operations of its contractions.
+struct Counters {
+  long long launches = 0;
+  double flops = 0.0;
+  long long evals = 0;
+};
+extern Counters g_count;
+
+// Optional per-kernel timing with CUDA events on the launching stream.
+// KTimer brackets one launch; pairs are resolved when read.
+void ktimer_begin(const char* name, cudaStream_t st);
+void ktimer_end(cudaStream_t st, double flops);
+void ktimer_enable(bool on);
+void ktimer_reset();
+bool ktimer_read(const char* name, double* ms, long long* n, double* flops);
+struct KTimer {
+  cudaStream_t st;
+  double flops;
+  KTimer(const char* name, cudaStream_t s, double f = 0.0) : st(s), flops(f) { ktimer_begin(name, s); }
+  ~KTimer() { ktimer_end(st, flops); }
+};
 
 // Segmented gathered GEMM, double precision:
 //   O[seg] (+)= alpha * sum_{t in seg} coef[cidx[t]] * X_t * (Y_t diag(cs[csrow[t]]))
@@ -26,6 +50,7 @@ struct SegGemm {
   const double* cs = nullptr;
   long long cs_ld = 0;
   int nseg = 1;
+  long long nterm = 0;   // host-side term count for the FLOP counter (table mode)
   double alpha = 1.0;
   int accumulate = 0;
 };

@@ -2,7 +2,11 @@
 // that evaluates the sparse site diagrams of Fig. 7 (and plain GEMMs), the
 // one-sided Jacobi SVD used for every truncation and orthonormalisation
 // (Hestenes 1958; Demmel & Veselic 1992), and small helpers.
+#include <array>
 #include <cmath>
+#include <map>
+#include <string>
+#include <vector>
 
 #include "kern.h"
 
@@ -285,10 +289,97 @@ inline int blocks_for(long long n, int t = 256) {
 
 }  // namespace
 
+Counters g_count;
+
+namespace {
+struct Pending {
+  std::string name;
+  cudaEvent_t a, b;
+  double flops;
+};
+struct TimerState {
+  bool on = false;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  std::map<std::string, std::array<double, 3>> acc;   // ms, launches, flops
+  const char* cur = nullptr;
+  cudaEvent_t cur_a = nullptr;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void resolve() {
+    for (auto& p : pending) {
+      cudaEventSynchronize(p.b);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, p.a, p.b);
+      auto& v = acc[p.name];
+      v[0] += ms;
+      v[1] += 1;
+      v[2] += p.flops;
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+};
+TimerState g_timer;
+}  // namespace
+
+void ktimer_begin(const char* name, cudaStream_t st) {
+  if (!g_timer.on) return;
+  g_timer.cur = name;
+  g_timer.cur_a = g_timer.get();
+  cudaEventRecord(g_timer.cur_a, st);
+}
+void ktimer_end(cudaStream_t st, double flops) {
+  if (!g_timer.on || !g_timer.cur) return;
+  cudaEvent_t b = g_timer.get();
+  cudaEventRecord(b, st);
+  g_timer.pending.push_back({g_timer.cur, g_timer.cur_a, b, flops});
+  g_timer.cur = nullptr;
+  if (g_timer.pending.size() > 4096) g_timer.resolve();
+}
+void ktimer_enable(bool on) {
+  g_timer.resolve();
+  g_timer.on = on;
+}
+void ktimer_reset() {
+  g_timer.resolve();
+  g_timer.acc.clear();
+}
+bool ktimer_read(const char* name, double* ms, long long* n, double* flops) {
+  g_timer.resolve();
+  auto it = g_timer.acc.find(name);
+  if (it == g_timer.acc.end()) return false;
+  *ms = it->second[0];
+  *n = (long long)it->second[1];
+  *flops = it->second[2];
+  return true;
+}
+std::string ktimer_names() {
+  g_timer.resolve();
+  std::string o;
+  for (auto& kv : g_timer.acc) o += kv.first + ",";
+  return o;
+}
+
 void seg_gemm(const SegGemm& a, cudaStream_t st) {
   if (a.nseg <= 0 || a.p <= 0 || a.s <= 0) return;
   dim3 grid(a.nseg, (a.p + TM - 1) / TM, (a.s + TN - 1) / TN);
-  seg_gemm_kernel<<<grid, 256, 0, st>>>(a);
+  double fl = 2.0 * a.p * a.q * a.s * double(a.seg_ptr ? a.nterm : a.nseg);
+  {
+    KTimer t("seg_gemm_f64", st, fl);
+    seg_gemm_kernel<<<grid, 256, 0, st>>>(a);
+  }
+  ++g_count.launches;
+  g_count.flops += fl;
 }
 
 void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, long long ldy, double* O, long long ldo,
@@ -315,48 +406,62 @@ void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, lon
 void jacobi(double* X, int len, int p, long long si, long long sj, double* V, int max_sweeps, int* status,
             cudaStream_t st) {
   double tol = 1e-15 * sqrt(double(len > 1 ? len : 1));
-  jacobi_kernel<<<1, 1024, 0, st>>>(X, len, p, si, sj, V, max_sweeps, tol, status);
+  {
+    KTimer t("jacobi_f64", st);
+    jacobi_kernel<<<1, 1024, 0, st>>>(X, len, p, si, sj, V, max_sweeps, tol, status);
+  }
+  ++g_count.launches;
 }
 
 void vec_norms(const double* X, int len, int p, long long si, long long sj, double* out, cudaStream_t st) {
   if (p > 0) vec_norms_kernel<<<p, 256, 0, st>>>(X, len, p, si, sj, out);
+  ++g_count.launches;
 }
 
 void gather_vecs(const double* X, int len, long long si, long long sj, const int32_t* perm, const double* scale, int k,
                  double* out, long long oi, long long oj, cudaStream_t st) {
   gather_vecs_kernel<<<blocks_for((long long)len * k), 256, 0, st>>>(X, len, si, sj, perm, scale, k, out, oi, oj);
+  ++g_count.launches;
 }
 
 void permute3(const double* in, int A, int B, int Cd, double* out, cudaStream_t st) {
   permute3_kernel<<<blocks_for((long long)A * B * Cd), 256, 0, st>>>(in, A, B, Cd, out);
+  ++g_count.launches;
 }
 
-void fro_norm(const double* x, long long n, double* out, cudaStream_t st) { fro_norm_kernel<<<1, 1024, 0, st>>>(x, n, out); }
+void fro_norm(const double* x, long long n, double* out, cudaStream_t st) { fro_norm_kernel<<<1, 1024, 0, st>>>(x, n, out);
+  ++g_count.launches; }
 
 void scale_by_inv(double* x, long long n, const double* norm, cudaStream_t st) {
   scale_by_inv_kernel<<<blocks_for(n), 256, 0, st>>>(x, n, norm);
+  ++g_count.launches;
 }
 
-void fill(double* x, long long n, double v, cudaStream_t st) { fill_kernel<<<blocks_for(n), 256, 0, st>>>(x, n, v); }
+void fill(double* x, long long n, double v, cudaStream_t st) { fill_kernel<<<blocks_for(n), 256, 0, st>>>(x, n, v);
+  ++g_count.launches; }
 
 void copy(double* dst, const double* src, long long n, cudaStream_t st) {
   copy_kernel<<<blocks_for(n), 256, 0, st>>>(dst, src, n);
+  ++g_count.launches;
 }
 
 void boltzmann(const int64_t* E, long long n, int64_t Emin, double bd, double* out, cudaStream_t st) {
   boltzmann_kernel<<<blocks_for(n), 256, 0, st>>>(E, n, Emin, bd, out);
+  ++g_count.launches;
 }
 
 void build_Wa(double* Wa, int nPd, int nE, int nG, int nSig, const int32_t* s_pu, const int32_t* s_pul,
               const int32_t* s_pur, const double* Bv, int bv_nb, const double* Bdl, int bdl_nb, cudaStream_t st) {
   long long n = (long long)nPd * nE * nG * nSig;
   build_Wa_kernel<<<blocks_for(n), 256, 0, st>>>(Wa, nPd, nE, nG, nSig, s_pu, s_pul, s_pur, Bv, bv_nb, Bdl, bdl_nb);
+  ++g_count.launches;
 }
 
 void build_Wk(double* Wk, int nPr, int nE, int nPdr, int nLR, int nGR, const int32_t* l_pl, const int32_t* l_pdl,
               const double* Bh, int bh_nb, const double* Bdr, int bdr_nb, cudaStream_t st) {
   long long n = (long long)nPr * nE * nPdr * nLR * nGR;
   build_Wk_kernel<<<blocks_for(n), 256, 0, st>>>(Wk, nPr, nE, nPdr, nLR, nGR, l_pl, l_pdl, Bh, bh_nb, Bdr, bdr_nb);
+  ++g_count.launches;
 }
 
 }  // namespace sgtn

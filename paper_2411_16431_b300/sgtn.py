@@ -42,6 +42,11 @@ def load():
     L.sgtn_site_dims.argtypes = [ct.c_void_p, ct.c_int32, _I32P]
     L.sgtn_mps_shape.argtypes = [ct.c_void_p, ct.c_int32, _I32P, _I32P, _F64P]
     L.sgtn_mps_tensor.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _F64P]
+    L.sgtn_stats.argtypes = [_I64P, _F64P, _I64P]
+    L.sgtn_stats.restype = None
+    L.sgtn_kernel_timing.argtypes = [ct.c_int32, ct.c_int32]
+    L.sgtn_kernel_timing.restype = None
+    L.sgtn_kernel_time.argtypes = [ct.c_char_p, _F64P, _I64P, _F64P]
     L.sgtn_last_error.argtypes = [ct.c_void_p]
     L.sgtn_last_error.restype = ct.c_char_p
     L.sgtn_destroy.argtypes = [ct.c_void_p]
@@ -52,6 +57,26 @@ def load():
 
 def _p(a, t):
     return a.ctypes.data_as(t) if a is not None else None
+
+
+def stats():
+    """(kernel launches, algorithmic flops, marginal evaluations) issued by the library so far."""
+    L = load()
+    a, b, c = ct.c_int64(), ct.c_double(), ct.c_int64()
+    L.sgtn_stats(ct.byref(a), ct.byref(b), ct.byref(c))
+    return a.value, b.value, c.value
+
+
+def kernel_timing(enable, reset=False):
+    load().sgtn_kernel_timing(int(enable), int(reset))
+
+
+def kernel_time(name):
+    """(device ms, launches, algorithmic flops) of a timed kernel, or None."""
+    ms, n, fl = ct.c_double(), ct.c_int64(), ct.c_double()
+    if load().sgtn_kernel_time(name.encode(), ct.byref(ms), ct.byref(n), ct.byref(fl)) != 0:
+        return None
+    return ms.value, n.value, fl.value
 
 
 class SgtnError(RuntimeError):

@@ -76,6 +76,9 @@ def test_conditionals_match_oracle(Handle, case):
         p = h.conditionals(n, cfgs)
         for k in range(5):
             s = np.maximum(conditional_scores(pm, beta, mpos[r], psis[r], tuple(cfgs[k]), r, c), 0)
+            if s.sum() == 0:
+                assert not p[k].any()
+                continue
             po = s / s.sum()
             big = po > 1e-300
             assert np.allclose(p[k][big], po[big], rtol=RTOL, atol=0)
@@ -93,7 +96,7 @@ def test_search_matches_oracle(Handle, case):
     assert np.array_equal(res["spins"], ref["spins"])
     assert np.array_equal(res["energy_num"], ref["energy_num"])
     assert np.allclose(res["logp"], ref["logp"], rtol=RTOL)
-    assert abs(res["pd"] - ref["pd"]) <= RTOL * abs(ref["pd"])
+    assert res["pd"] == ref["pd"] or abs(res["pd"] - ref["pd"]) <= RTOL * abs(ref["pd"])
     if inst.planted is not None:
         assert res["energy_num"][0] >= inst.planted_energy_num
 
@@ -130,7 +133,7 @@ def test_branch_steps_match_oracle(Handle, case):
         want = sorted(beam)
         assert [g[0] for g in got] == [w[0] for w in want], n
         assert np.allclose([g[1] for g in got], [w[1] for w in want], rtol=RTOL)
-        assert abs(pd - pd_o) <= RTOL * abs(pd_o)
+        assert pd == pd_o or abs(pd - pd_o) <= RTOL * abs(pd_o)
 
 
 def test_energies_exact(Handle):
