@@ -124,6 +124,28 @@ int sgtn_site_dims(sgtn_h h, int32_t site, int32_t* d);
 int sgtn_mps_shape(sgtn_h h, int32_t row, int32_t* phys, int32_t* bond, double* lognorm);
 int sgtn_mps_tensor(sgtn_h h, int32_t row, int32_t col, double* out);
 
+/* Allocation-free variant of sgtn_conditionals (the paper has no
+ * counterpart; this is a service for callers that must not let the library
+ * allocate device memory at run time -- e.g. a server that hands all device
+ * memory to its own pool at start-up, or a real-time loop that cannot absorb
+ * the device-wide synchronisation of cudaMalloc / cudaFree).  Same arguments
+ * and results as sgtn_conditionals (configs and out_p are host pointers), but
+ * every device temporary is taken from one static device array of
+ * SGTN_NOALLOC_SCRATCH_BYTES bytes that each GPU loading the library reserves
+ * until the process exits; the call performs no device allocation.
+ *  - Set-up: the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture is started.
+ *  - A call whose temporaries (about 8 bytes x count x states, plus the
+ *    projected boundary MPS of the row) exceed the array returns SGTN_ERR_ARG
+ *    and sgtn_last_error() states the bytes needed; nothing is launched.
+ *  - All calls share the array and it keeps the previous call's contents;
+ *    everything that must start at zero is cleared by the call itself.  Calls
+ *    that overlap on the GPU (other threads, other handles, other streams)
+ *    race on the array: serialise them. */
+#define SGTN_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int sgtn_conditionals_noalloc(sgtn_h h, int32_t step, int32_t count, const int32_t* configs, double* out_p);
+
 /* Process-wide diagnostics (the paper has no counterpart): cumulative
  * number of kernel launches issued by this library, algorithmic
  * floating-point operations of its contractions (2 m n k per gathered

@@ -22,6 +22,7 @@
 #include <climits>
 #include <cmath>
 #include <numeric>
+#include <string>
 
 #include "handle.h"
 
@@ -327,8 +328,19 @@ struct Step {
   double* s = nullptr;       // [K][d]
   const MPS* A = nullptr;
   std::vector<void*> owned;
+  // optional caller-provided device arena: when set, alloc() carves from it
+  // instead of calling cudaMalloc (256-byte aligned pieces)
+  char* arena = nullptr;
+  size_t arena_cap = 0, arena_used = 0;
   template <class T>
   T* alloc(size_t n) {
+    if (arena) {
+      size_t b = ((n ? n : 1) * sizeof(T) + 255) / 256 * 256;
+      if (arena_used + b > arena_cap) throw SgtnError(-1, "scratch arena exhausted");
+      T* p = reinterpret_cast<T*>(arena + arena_used);
+      arena_used += b;
+      return p;
+    }
     void* p = nullptr;
     SGTN_CUDA(cudaMalloc(&p, (n ? n : 1) * sizeof(T)));
     owned.push_back(p);
@@ -508,6 +520,62 @@ void conditionals(sgtn_inst* h, int step, int count, const int32_t* configs, dou
     double z = 0;
     for (int x = 0; x < d; ++x) z += std::max(0.0, s[size_t(k) * d + x]);
     for (int x = 0; x < d; ++x) out_p[size_t(k) * d + x] = z > 0 ? std::max(0.0, s[size_t(k) * d + x]) / z : 0.0;
+  }
+}
+
+// Device bytes prepare_scores takes from an arena (same pieces, same rounding).
+size_t scores_scratch_bytes(sgtn_inst* h, int step, int K) {
+  const int C = h->M.C, r = step / C, c = step % C;
+  if (!h->boundary_ok) throw SgtnError(-2, "contract_boundary must run first");
+  const MPS& A = h->psi[r];
+  auto rnd = [](size_t b) { return ((b ? b : 1) + 255) / 256 * 256; };
+  size_t tot = rnd(size_t(K) * std::max(step, 1) * sizeof(int32_t));
+  for (int cc = 0; cc < C; ++cc) {
+    const Column& K_ = h->cols[r * C + cc];
+    tot += rnd(size_t(K_.nA()) * A.bond[cc] * A.bond[cc + 1] * sizeof(double));
+    tot += rnd(size_t(K_.nU) * K * sizeof(double));
+  }
+  tot += rnd(size_t(K) * sizeof(double)) + 2 * rnd(size_t(K) * sizeof(int32_t));
+  for (int cc = 0; cc < c; ++cc)
+    tot += rnd(size_t(h->cols[r * C + cc].nBR()) * A.bond[cc + 1] * K * sizeof(double));
+  tot += rnd(size_t(K) * sizeof(double));
+  for (int cc = C - 1; cc > c; --cc) {
+    const Column& K_ = h->cols[r * C + cc];
+    tot += rnd(size_t(K_.nK()) * A.bond[cc + 1] * K * sizeof(double));
+    tot += rnd(size_t(K_.nBL()) * A.bond[cc] * K * sizeof(double));
+  }
+  tot += rnd(size_t(h->cols[r * C + c].nK()) * A.bond[c + 1] * K * sizeof(double));
+  tot += rnd(size_t(K) * h->M.sites[step].d * sizeof(double));
+  return tot;
+}
+
+// Conditional marginals with every device temporary carved from `arena`
+// (no device allocation); writes straight into the caller's out_p.
+void conditionals_arena(sgtn_inst* h, int step, int count, const int32_t* configs, double* out_p, void* arena,
+                        size_t cap) {
+  check_configs(h, step, count, configs);
+  if (!out_p) throw SgtnError(-1, "out_p is NULL");
+  size_t need = scores_scratch_bytes(h, step, count);
+  if (need > cap)
+    throw SgtnError(-1, "this call needs " + std::to_string(need) + " bytes of device scratch; the static buffer holds " +
+                            std::to_string(cap) + " (reduce count or use sgtn_conditionals)");
+  Step S;
+  S.h = h;
+  S.n = step;
+  S.r = step / h->M.C;
+  S.c = step % h->M.C;
+  S.K = count;
+  S.arena = static_cast<char*>(arena);
+  S.arena_cap = cap;
+  prepare_scores(S, configs);
+  int d = h->M.sites[step].d;
+  SGTN_CUDA(cudaMemcpyAsync(out_p, S.s, size_t(count) * d * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  h->sync();
+  for (int k = 0; k < count; ++k) {
+    double* row = out_p + size_t(k) * d;
+    double z = 0;
+    for (int x = 0; x < d; ++x) z += std::max(0.0, row[x]);
+    for (int x = 0; x < d; ++x) row[x] = z > 0 ? std::max(0.0, row[x]) / z : 0.0;
   }
 }
 

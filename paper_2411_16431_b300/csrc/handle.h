@@ -114,4 +114,7 @@ void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_
 void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_energy, double* out_logp, double* out_pd,
             int32_t* out_count);
 void energies(sgtn_inst* h, int n, const int8_t* spins, int64_t* out);
+size_t scores_scratch_bytes(sgtn_inst* h, int step, int K);
+void conditionals_arena(sgtn_inst* h, int step, int count, const int32_t* configs, double* out_p, void* arena,
+                        size_t cap);
 }  // namespace sgtn

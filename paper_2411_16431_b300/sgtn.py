@@ -38,6 +38,7 @@ def load():
     L.sgtn_branch_step.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, _I32P, _F64P, _I32P, _F64P,
                                    _I32P, _F64P]
     L.sgtn_search.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I8P, _I64P, _F64P, _F64P, _I32P]
+    L.sgtn_conditionals_noalloc.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I32P, _F64P]
     L.sgtn_energies.argtypes = [ct.c_void_p, ct.c_int32, _I8P, _I64P]
     L.sgtn_site_dims.argtypes = [ct.c_void_p, ct.c_int32, _I32P]
     L.sgtn_mps_shape.argtypes = [ct.c_void_p, ct.c_int32, _I32P, _I32P, _F64P]
@@ -144,6 +145,15 @@ class Handle:
         count = configs.shape[0]
         out = np.zeros((count, self.d[step]))
         self._ck(self.L.sgtn_conditionals(self.h, step, count, _p(configs, _I32P), _p(out, _F64P)))
+        return out
+
+    def conditionals_noalloc(self, step, configs):
+        """Same as conditionals(), through the allocation-free entry point."""
+        configs = np.ascontiguousarray(np.asarray(configs, np.int32).reshape(-1, step) if step else
+                                       np.zeros((len(configs), 0), np.int32))
+        count = configs.shape[0]
+        out = np.zeros((count, self.d[step]))
+        self._ck(self.L.sgtn_conditionals_noalloc(self.h, step, count, _p(configs, _I32P), _p(out, _F64P)))
         return out
 
     def branch_step(self, step, M, configs, logp, pd=-np.inf):
