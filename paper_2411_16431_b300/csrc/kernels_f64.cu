@@ -110,14 +110,34 @@ __device__ inline double warp_sum(double v) {
   return v;
 }
 
-// Single-CTA cyclic one-sided Jacobi with a round-robin pairing.
-__global__ void __launch_bounds__(1024) jacobi_kernel(double* X, int len, int p, long long si, long long sj,
-                                                      double* V, int max_sweeps, double tol, int* status) {
+// Single-CTA cyclic one-sided Jacobi with a round-robin pairing.  Columns
+// whose squared norm is below (eps * ||X||_F)^2 are numerically zero: they are
+// never rotated (they would otherwise trade rounding noise forever) and the
+// caller drops them with the rank rule.
+__device__ void jacobi_body(double* X, int len, int p, long long si, long long sj, double* V, int max_sweeps,
+                            double tol, int* status) {
   __shared__ int rotated;
+  __shared__ double red[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   if (V)
     for (long long e = threadIdx.x; e < (long long)p * p; e += blockDim.x)
       V[e] = ((e / p) == (e % p)) ? 1.0 : 0.0;
+  // ||X||_F^2
+  double fro = 0;
+  for (long long e = threadIdx.x; e < (long long)len * p; e += blockDim.x) {
+    double v = X[(e % len) * si + (e / len) * sj];
+    fro = fma(v, v, fro);
+  }
+  fro = warp_sum(fro);
+  if (lane == 0) red[warp] = fro;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < nwarp; ++w) t += red[w];
+    red[0] = t;
+  }
+  __syncthreads();
+  const double zero2 = red[0] * 1e-30;   // (1e-15 ||X||_F)^2
   const int pp = p + (p & 1);
   int sweep = 0;
   bool done = (p < 2);
@@ -143,7 +163,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* X, int len, int p,
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
+        if (al > zero2 && be > zero2 && fabs(ga) > tol * sqrt(al * be)) {
           double zeta = (be - al) / (2.0 * ga);
           double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
@@ -171,6 +191,32 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* X, int len, int p,
     __syncthreads();
   }
   if (threadIdx.x == 0) status[0] = done ? sweep : -1;
+}
+
+__global__ void __launch_bounds__(1024) jacobi_kernel(double* X, int len, int p, long long si, long long sj,
+                                                      double* V, int max_sweeps, double tol, int* status) {
+  jacobi_body(X, len, p, si, sj, V, max_sweeps, tol, status);
+}
+
+// Same, with the matrix (and V) staged in shared memory, column-major.
+__global__ void __launch_bounds__(1024) jacobi_smem_kernel(double* X, int len, int p, long long si, long long sj,
+                                                           double* V, int max_sweeps, double tol, int* status) {
+  extern __shared__ double sm[];
+  double* Xs = sm;
+  double* Vs = V ? sm + (long long)len * p : nullptr;
+  for (long long e = threadIdx.x; e < (long long)len * p; e += blockDim.x) {
+    long long j = e / len, i = e % len;
+    Xs[e] = X[i * si + j * sj];
+  }
+  __syncthreads();
+  jacobi_body(Xs, len, p, 1, len, Vs, max_sweeps, tol, status);
+  __syncthreads();
+  for (long long e = threadIdx.x; e < (long long)len * p; e += blockDim.x) {
+    long long j = e / len, i = e % len;
+    X[i * si + j * sj] = Xs[e];
+  }
+  if (V)
+    for (long long e = threadIdx.x; e < (long long)p * p; e += blockDim.x) V[e] = Vs[e];
 }
 
 __global__ void vec_norms_kernel(const double* X, int len, int p, long long si, long long sj, double* out) {
@@ -406,9 +452,19 @@ void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, lon
 void jacobi(double* X, int len, int p, long long si, long long sj, double* V, int max_sweeps, int* status,
             cudaStream_t st) {
   double tol = 1e-15 * sqrt(double(len > 1 ? len : 1));
+  size_t smem = (size_t(len) * p + (V ? size_t(p) * p : 0)) * sizeof(double);
+  static bool attr_set = false;
+  const size_t kMaxSmem = 220 * 1024;
+  if (!attr_set) {
+    cudaFuncSetAttribute(jacobi_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxSmem));
+    attr_set = true;
+  }
   {
     KTimer t("jacobi_f64", st);
-    jacobi_kernel<<<1, 1024, 0, st>>>(X, len, p, si, sj, V, max_sweeps, tol, status);
+    if (smem <= kMaxSmem)
+      jacobi_smem_kernel<<<1, 1024, smem, st>>>(X, len, p, si, sj, V, max_sweeps, tol, status);
+    else
+      jacobi_kernel<<<1, 1024, 0, st>>>(X, len, p, si, sj, V, max_sweeps, tol, status);
   }
   ++g_count.launches;
 }
