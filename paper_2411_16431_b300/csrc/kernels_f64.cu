@@ -217,18 +217,19 @@ __global__ void __launch_bounds__(1024) jacobi_smem_kernel(double* X, int len, i
     for (long long e = threadIdx.x; e < (long long)p * p; e += blockDim.x) V[e] = Vs[e];
 }
 
-// Cooperative multi-CTA variant for many columns: every CTA rotates one pair
+// Cooperative multi-CTA variant for many columns: one warp rotates one pair
 // per round, rounds are separated by grid-wide barriers (the launch is
 // cooperative, so all CTAs are resident).  flags[s] counts rotations in sweep
 // s and must be zero on entry.
-__global__ void __launch_bounds__(256) jacobi_coop_kernel(double* X, int len, int p, long long si, long long sj,
+__global__ void __launch_bounds__(128) jacobi_coop_kernel(double* X, int len, int p, long long si, long long sj,
                                                           double* V, int max_sweeps, double tol, int* status,
                                                           int* flags, double* fro_out) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
-  __shared__ double red[3][8];
+  __shared__ double red[4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
+  const int gw = blockIdx.x * nw + warp, ngw = gridDim.x * nw;
   if (V)
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)p * p;
          e += (long long)gridDim.x * blockDim.x)
@@ -240,11 +241,11 @@ __global__ void __launch_bounds__(256) jacobi_coop_kernel(double* X, int len, in
       f = fma(v, v, f);
     }
     f = warp_sum(f);
-    if (lane == 0) red[0][warp] = f;
+    if (lane == 0) red[warp] = f;
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0;
-      for (int w = 0; w < nw; ++w) t += red[0][w];
+      for (int w = 0; w < nw; ++w) t += red[w];
       fro_out[0] = t;
     }
   }
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(256) jacobi_coop_kernel(double* X, int len, in
   bool done = (p < 2);
   while (!done && sweep < max_sweeps) {
     for (int t = 0; t < pp - 1; ++t) {
-      for (int w = blockIdx.x; w < pp / 2; w += gridDim.x) {
+      for (int w = gw; w < pp / 2; w += ngw) {
         int pa = w, pb = pp - 1 - w;
         int ca = pa == 0 ? 0 : 1 + (pa - 1 + t) % (pp - 1);
         int cb = pb == 0 ? 0 : 1 + (pb - 1 + t) % (pp - 1);
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(256) jacobi_coop_kernel(double* X, int len, in
         double* xa = X + ca * sj;
         double* xb = X + cb * sj;
         double al = 0, be = 0, ga = 0;
-        for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        for (int i = lane; i < len; i += 32) {
           double u = xa[i * si], v = xb[i * si];
           al = fma(u, u, al);
           be = fma(v, v, be);
@@ -272,24 +273,11 @@ __global__ void __launch_bounds__(256) jacobi_coop_kernel(double* X, int len, in
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (lane == 0) {
-          red[0][warp] = al;
-          red[1][warp] = be;
-          red[2][warp] = ga;
-        }
-        __syncthreads();
-        al = be = ga = 0;
-        for (int q = 0; q < nw; ++q) {
-          al += red[0][q];
-          be += red[1][q];
-          ga += red[2][q];
-        }
-        __syncthreads();
         if (al > zero2 && be > zero2 && fabs(ga) > tol * sqrt(al * be)) {
           double zeta = (be - al) / (2.0 * ga);
           double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
-          for (int i = threadIdx.x; i < len; i += blockDim.x) {
+          for (int i = lane; i < len; i += 32) {
             double u = xa[i * si], v = xb[i * si];
             xa[i * si] = c * u - s * v;
             xb[i * si] = s * u + c * v;
@@ -297,13 +285,13 @@ __global__ void __launch_bounds__(256) jacobi_coop_kernel(double* X, int len, in
           if (V) {
             double* va = V + (long long)ca * p;
             double* vb = V + (long long)cb * p;
-            for (int i = threadIdx.x; i < p; i += blockDim.x) {
+            for (int i = lane; i < p; i += 32) {
               double u = va[i], v = vb[i];
               va[i] = c * u - s * v;
               vb[i] = s * u + c * v;
             }
           }
-          if (threadIdx.x == 0) atomicAdd(flags + sweep, 1);
+          if (lane == 0) atomicAdd(flags + sweep, 1);
         }
       }
       grid.sync();
@@ -568,9 +556,9 @@ void jacobi(double* X, int len, int p, long long si, long long sj, double* V, in
       }
       cudaMemsetAsync(flags, 0, 256 * sizeof(int), st);
       int ms = max_sweeps > 256 ? 256 : max_sweeps;
-      int nblk = (p + 1) / 2;
+      int nblk = ((p + 1) / 2 + 3) / 4;   // 4 warps (pairs) per CTA
       int per_sm = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel, 256, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel, 128, 0);
       int dev = 0, nsm = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -578,7 +566,7 @@ void jacobi(double* X, int len, int p, long long si, long long sj, double* V, in
       if (nblk > cap) nblk = cap;
       if (nblk < 1) nblk = 1;
       void* args[] = {&X, &len, &p, &si, &sj, &V, &ms, &tol, &status, &flags, &fro};
-      cudaLaunchCooperativeKernel((void*)jacobi_coop_kernel, dim3(nblk), dim3(256), args, 0, st);
+      cudaLaunchCooperativeKernel((void*)jacobi_coop_kernel, dim3(nblk), dim3(128), args, 0, st);
     }
   }
   ++g_count.launches;

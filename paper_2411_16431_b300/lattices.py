@@ -322,3 +322,37 @@ def slice_cells(inst: Instance, rows: int, cols: int) -> Instance:
                     np.array([j for _, _, j in sel], dtype=np.int32),
                     inst.h_num[keep].copy(), inst.denom, np.array(site, dtype=np.int32), rows, cols,
                     inst.name + f"_slice{rows}x{cols}")
+
+
+def hamming_ball_states(inst: Instance, d: int, seed: int = 0, reference: Optional[np.ndarray] = None):
+    """Per-cluster state lists of (at most) d states nearest to a reference configuration.
+
+    For cells too large to enumerate (24-spin Pegasus cells) the Potts model
+    runs on a reduced state set.  This draws one synthetic such set: the d
+    patterns closest in Hamming distance to the reference (the planted state
+    if any, else a seeded random configuration), ordered by (distance,
+    pattern).  Bit j of a pattern is 1 when the j-th spin of the cluster (in
+    increasing global index) is -1.
+    """
+    import itertools
+    if reference is None:
+        if inst.planted is not None:
+            reference = inst.planted
+        else:
+            rng = SplitMix64(seed)
+            reference = np.array([1 if rng.below(2) == 0 else -1 for _ in range(inst.n_spins)], dtype=np.int8)
+    spins_of = [[] for _ in range(inst.rows * inst.cols)]
+    for i, s in enumerate(inst.site_of_spin.tolist()):
+        spins_of[s].append(i)
+    out = []
+    for sp in spins_of:
+        k = len(sp)
+        ref = sum(1 << j for j, g in enumerate(sp) if reference[g] < 0)
+        states = []
+        for dist in range(k + 1):
+            level = sorted(ref ^ sum(1 << b for b in flip) for flip in itertools.combinations(range(k), dist))
+            states.extend(level)
+            if len(states) >= d:
+                break
+        out.append(np.array(states[:d], dtype=np.int64))
+    return out

@@ -42,6 +42,32 @@ CASES = [(L.chimera_grid(4, 4, 0), 1.0, 16, 2), (L.chimera_grid(3, 4, 7), 2.0, 4
          (L.planted(L.chimera_grid(3, 3, 5), 2), 1.5, 6, 1)]
 
 
+PEG = L.pegasus_nice(4, 11)
+PEG_STATES = L.hamming_ball_states(PEG, 12, seed=3)
+PEGP = L.planted(L.pegasus_nice(4, 6), 7, loops_per_cell=4)
+PEGP_STATES = L.hamming_ball_states(PEGP, 16)
+PEG_CASES = [(PEG, PEG_STATES, 0.8, 6, 1), (PEGP, PEGP_STATES, 2.0, 8, 2)]
+
+
+@pytest.mark.parametrize("case", PEG_CASES, ids=lambda c: f"{c[0].name}_chi{c[3]}")
+def test_pegasus_boundary_and_search_match_oracle(Handle, case):
+    """Pegasus nice cells (24 spins, one diagonal) on reduced state sets."""
+    inst, states, beta, chi, ns = case
+    pm = PottsModel(inst, states)
+    lz_o, _, _ = boundary_mps(pm, beta, chi, ns)
+    h = Handle(inst, states)
+    h.set_beta(beta)
+    lz, _ = h.contract_boundary(chi, n_sweeps=ns)
+    assert abs(lz - lz_o) < RTOL * abs(lz_o)
+    ref = oracle_search(inst, beta, chi=chi, M=16, n_sweeps=ns, states=states)
+    res = h.search(16)
+    assert np.array_equal(res["spins"], ref["spins"])
+    assert np.array_equal(res["energy_num"], ref["energy_num"])
+    assert np.allclose(res["logp"], ref["logp"], rtol=RTOL)
+    if inst.planted is not None:
+        assert res["energy_num"][0] >= inst.planted_energy_num
+
+
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0].name}_chi{c[2]}")
 def test_truncated_boundary_matches_oracle(Handle, case):
     inst, beta, chi, ns = case

@@ -228,3 +228,33 @@ def test_search_config1_smoke():
     res = search(L.chimera_grid(4, 4, 0), 1.0, chi=16, M=64, n_sweeps=2)
     assert res["energy_num"][0] == res["pm"].state_energy_num(res["configs"][0])
     assert res["pd"] < 0 and len(res["configs"]) == 1
+
+
+def test_pegasus_restricted_logz_by_enumeration():
+    """Pegasus P3 (2x2 cells of 24 spins, one diagonal) on reduced state sets: the exact
+    contraction equals the brute-force sum of exp(-beta H) over the restricted product space."""
+    inst = L.pegasus_nice(3, 4)
+    states = L.hamming_ball_states(inst, 10, seed=1)
+    pm = PottsModel(inst, states)
+    beta = 0.7
+    lz, _, _ = boundary_mps(pm, beta, chi=256, n_sweeps=1)
+    # brute force over all 10^4 combinations, energies from spins only
+    sp_of = [[i for i in range(inst.n_spins) if inst.site_of_spin[i] == s] for s in range(4)]
+    E = []
+    for combo in itertools.product(*[range(len(s)) for s in states]):
+        spins = np.zeros(inst.n_spins, np.int64)
+        for s, x in enumerate(combo):
+            pat = int(states[s][x])
+            spins[sp_of[s]] = [1 - 2 * ((pat >> j) & 1) for j in range(len(sp_of[s]))]
+        E.append(inst.energy_num(spins))
+    E = np.array(E) / 7.0
+    m = (-beta * E).max()
+    ref = m + np.log(np.exp(-beta * E - m).sum())
+    assert abs(lz - ref) < 1e-11 * abs(ref)
+
+
+def test_pegasus_restricted_search_finds_restricted_ground_state():
+    inst = L.planted(L.pegasus_nice(3, 2), 5, loops_per_cell=4)
+    states = L.hamming_ball_states(inst, 12)          # ball around the planted state
+    res = search(inst, 2.0, chi=256, M=10 ** 6, n_sweeps=1, states=states)
+    assert int(res["energy_num"][0]) == inst.planted_energy_num
