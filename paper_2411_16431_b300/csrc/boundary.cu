@@ -62,9 +62,21 @@ struct SvdOut {
   }
 };
 
-// Truncated SVD of a dense row-major m x n matrix by one-sided Jacobi on the
-// shorter side.  Keeps at most cap singular values, none below RANK_TOL.
+double norm_host(sgtn_inst* h, const double* x, long long n, bool allow_zero);
+SvdOut svd_dense(sgtn_inst* h, const double* Th, int m, int n, int cap);
+SvdOut svd_subspace(sgtn_inst* h, const double* Th, int m, int n, int cap);
+
+// Truncated SVD of a dense row-major m x n matrix: exact one-sided Jacobi on
+// the shorter side when it is short, otherwise subspace iteration with a
+// Rayleigh-Ritz step (converged to the same top singular subspace).
 SvdOut svd(sgtn_inst* h, const double* Th, int m, int n, int cap) {
+  int p = std::min(m, n);
+  if (p <= h->dense_svd_max || cap >= p) return svd_dense(h, Th, m, n, cap);
+  return svd_subspace(h, Th, m, n, cap);
+}
+
+// Exact truncated SVD by one-sided Jacobi on the shorter side.
+SvdOut svd_dense(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   cudaStream_t st = h->st;
   SvdOut o;
   double* T2 = h->ws.get<double>("svd_T2", size_t(m) * n);
@@ -127,6 +139,96 @@ SvdOut svd(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   return o;
 }
 
+// Top-k right singular subspace of Theta (m x n) by block subspace iteration:
+// Q <- orth(Theta^T Theta Q) with a block of s = min(p, k + 32) vectors from a
+// fixed pseudo-random start, until the subspace moves by less than 1e-13
+// (largest principal-angle sine); then Rayleigh-Ritz: the SVD of Theta Q (s
+// columns, exact Jacobi) gives the singular values and Q V the vectors.
+SvdOut svd_subspace(sgtn_inst* h, const double* Th, int m, int n, int cap) {
+  cudaStream_t st = h->st;
+  const int p = std::min(m, n);
+  const int s = std::min(p, cap + 32);
+  double* Q = h->ws.get<double>("ss_Q", size_t(n) * s);
+  double* Qn = h->ws.get<double>("ss_Qn", size_t(n) * s);
+  double* Y = h->ws.get<double>("ss_Y", size_t(m) * s);
+  double* G = h->ws.get<double>("ss_G", size_t(s) * s);
+  double* sig = h->ws.get<double>("ss_sig", s);
+  int* status = h->ws.get<int>("ss_status", 1);
+  pseudo_random(Q, (long long)n * s, 12345, st);
+  int k_active = s;
+  auto orth = [&](double* Z, int len, int& kk, double* out) {
+    // Z (len x kk, row-major) -> orthonormal columns in out (len x kk') by Jacobi
+    jacobi(Z, len, kk, kk, 1, nullptr, 60, status, st);
+    vec_norms(Z, len, kk, kk, 1, sig, st);
+    std::vector<double> hs(kk);
+    SGTN_CUDA(cudaMemcpyAsync(hs.data(), sig, kk * sizeof(double), cudaMemcpyDeviceToHost, st));
+    h->sync();
+    std::vector<int> idx(kk);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return hs[a] > hs[b]; });
+    double mx = hs[idx[0]];
+    if (!(mx > 0) || !std::isfinite(mx)) throw SgtnError(-4, "zero or non-finite block in subspace iteration");
+    int k2 = 0;
+    std::vector<int32_t> perm;
+    std::vector<double> inv;
+    for (int i = 0; i < kk; ++i)
+      if (hs[idx[i]] > 1e-14 * mx) {
+        perm.push_back(idx[i]);
+        inv.push_back(1.0 / hs[idx[i]]);
+        ++k2;
+      }
+    int32_t* dperm = h->ws.get<int32_t>("ss_perm", k2);
+    double* dinv = h->ws.get<double>("ss_inv", k2);
+    SGTN_CUDA(cudaMemcpyAsync(dperm, perm.data(), k2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    SGTN_CUDA(cudaMemcpyAsync(dinv, inv.data(), k2 * sizeof(double), cudaMemcpyHostToDevice, st));
+    gather_vecs(Z, len, kk, 1, dperm, dinv, k2, out, k2, 1, st);
+    h->sync();
+    kk = k2;
+  };
+  {
+    double* Z0 = h->ws.get<double>("ss_Z", size_t(n) * s);
+    copy(Z0, Q, (long long)n * s, st);
+    orth(Z0, n, k_active, Q);
+  }
+  const int maxit = 300;
+  int it = 0;
+  for (; it < maxit; ++it) {
+    gemm(Th, false, n, Q, false, k_active, Y, k_active, m, k_active, n, 1.0, 0, st);          // Y = Theta Q
+    double* Z = h->ws.get<double>("ss_Z", size_t(n) * k_active);
+    gemm(Th, true, n, Y, false, k_active, Z, k_active, n, k_active, m, 1.0, 0, st);           // Z = Theta^T Y
+    int kn = k_active;
+    orth(Z, n, kn, Qn);
+    // subspace change of the leading min(cap, kn) directions: || Qk - Qn (Qn^T Qk) ||
+    int kc = std::min(cap, std::min(kn, k_active));
+    gemm(Qn, true, kn, Q, false, k_active, G, kc, kn, kc, n, 1.0, 0, st);                    // Qn^T Q[:, :kc]
+    double* Rr = h->ws.get<double>("ss_R", size_t(n) * kc);
+    // Rr = Q[:, :kc] - Qn G   (Q row-major n x k_active: first kc columns via ldx)
+    gemm(Qn, false, kn, G, false, kc, Rr, kc, n, kc, kn, -1.0, 0, st);   // Rr = -Qn G
+    add_cols(Rr, Q, n, kc, k_active, st);                                  // Rr += Q[:, :kc]
+    double ch = norm_host(h, Rr, (long long)n * kc, true);
+    std::swap(Q, Qn);
+    k_active = kn;
+    if (it >= 2 && ch < 1e-13 * std::sqrt(double(kc))) break;
+  }
+  if (it >= maxit) throw SgtnError(-4, "subspace iteration did not converge (no gap at the cut?)");
+  // Rayleigh-Ritz: B = Theta Q (m x s), exact SVD of B
+  gemm(Th, false, n, Q, false, k_active, Y, k_active, m, k_active, n, 1.0, 0, st);
+  SvdOut ob = svd_dense(h, Y, m, k_active, cap);    // Y = U S W^T  (W: Vt rows, length k_active)
+  SvdOut o;
+  o.k = ob.k;
+  o.sig = ob.sig;
+  o.US = ob.US;
+  ob.US = nullptr;
+  o.dsig = ob.dsig;
+  ob.dsig = nullptr;
+  // right vectors of Theta: rows of (Q W)^T = W Q^T  -> Vt = ob.Vt (k x s) * Q^T (s x n)
+  o.Vt = dmalloc((long long)o.k * n);
+  gemm(ob.Vt, false, k_active, Q, true, k_active, o.Vt, n, o.k, n, k_active, 1.0, 0, st);
+  ob.release();
+  h->check();
+  return o;
+}
+
 // Q = US / sigma (m x k)
 double* left_factor(sgtn_inst* h, const SvdOut& o, int m) {
   double* Q = dmalloc((long long)m * o.k);
@@ -140,17 +242,17 @@ double* right_factor(sgtn_inst* h, const SvdOut& o, int n) {
   return Rm;
 }
 
-double norm_host(sgtn_inst* h, const double* x, long long n) {
+double norm_host(sgtn_inst* h, const double* x, long long n, bool allow_zero) {
   double* d = h->ws.get<double>("norm_out", 1);
   fro_norm(x, n, d, h->st);
   double v = 0;
   SGTN_CUDA(cudaMemcpyAsync(&v, d, sizeof(double), cudaMemcpyDeviceToHost, h->st));
   h->sync();
-  if (!(v > 0.0) || !std::isfinite(v)) throw SgtnError(-4, "zero or non-finite norm");
+  if (!std::isfinite(v) || (!allow_zero && !(v > 0.0))) throw SgtnError(-4, "zero or non-finite norm");
   return v;
 }
 void normalise(sgtn_inst* h, double* x, long long n, double& lognorm) {
-  double v = norm_host(h, x, n);
+  double v = norm_host(h, x, n, false);
   lognorm += std::log(v);
   scale_by_inv(x, n, h->ws.get<double>("norm_out", 1), h->st);
 }

@@ -78,6 +78,7 @@ struct sgtn_inst {
   double logz = 0.0, worst_sv = 0.0;
   sgtn::Scratch ws;
   int32_t* iota = nullptr;                // 0..iota_n-1
+  int dense_svd_max = 320;                // exact Jacobi up to this many vectors, subspace iteration above
   int iota_n = 0;
 
   template <class T>

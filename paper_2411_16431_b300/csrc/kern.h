@@ -70,6 +70,10 @@ void vec_norms(const double* X, int len, int p, long long si, long long sj, doub
 // out[i*oi + jj*oj] = scale[jj] * X[i*si + perm[jj]*sj]
 void gather_vecs(const double* X, int len, long long si, long long sj, const int32_t* perm, const double* scale,
                  int k, double* out, long long oi, long long oj, cudaStream_t st);
+// deterministic pseudo-random numbers in [-1, 1] (SplitMix64 of seed + index)
+void pseudo_random(double* x, long long n, unsigned long long seed, cudaStream_t st);
+// R[i][j] += Q[i*ldq + j] for j < k  (R is rows x k, Q is rows x ldq)
+void add_cols(double* R, const double* Q, int rows, int k, int ldq, cudaStream_t st);
 // out[b][a][c] = in[a][b][c]
 void permute3(const double* in, int A, int B, int Cd, double* out, cudaStream_t st);
 // Frobenius norm (deterministic), result on device in *out

@@ -359,6 +359,24 @@ __global__ void scale_by_inv_kernel(double* x, long long n, const double* norm) 
     x[i] *= s;
 }
 
+__global__ void pseudo_random_kernel(double* x, long long n, unsigned long long seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[i] = double(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+
+__global__ void add_cols_kernel(double* R, const double* Q, int rows, int k, int ldq) {
+  long long n = (long long)rows * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    long long i = e / k, j = e % k;
+    R[e] += Q[i * ldq + j];
+  }
+}
+
 __global__ void fill_kernel(double* x, long long n, double v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     x[i] = v;
@@ -593,6 +611,16 @@ void fro_norm(const double* x, long long n, double* out, cudaStream_t st) { fro_
 
 void scale_by_inv(double* x, long long n, const double* norm, cudaStream_t st) {
   scale_by_inv_kernel<<<blocks_for(n), 256, 0, st>>>(x, n, norm);
+  ++g_count.launches;
+}
+
+void pseudo_random(double* x, long long n, unsigned long long seed, cudaStream_t st) {
+  pseudo_random_kernel<<<blocks_for(n), 256, 0, st>>>(x, n, seed);
+  ++g_count.launches;
+}
+
+void add_cols(double* R, const double* Q, int rows, int k, int ldq, cudaStream_t st) {
+  add_cols_kernel<<<blocks_for((long long)rows * k), 256, 0, st>>>(R, Q, rows, k, ldq);
   ++g_count.launches;
 }
 

@@ -185,3 +185,23 @@ def test_call_order_and_argument_errors(Handle):
     with pytest.raises(SgtnError, match="-1"):
         h.conditionals(1, np.array([[9999]], np.int32))
     h.search(4)   # still usable after errors
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[2], PEG_CASES[1]], ids=lambda c: c[0].name)
+def test_subspace_iteration_truncation_matches_oracle(Handle, case, monkeypatch):
+    """Force the iterative truncated SVD (used for large tensors) on small cases."""
+    monkeypatch.setenv("SGTN_DENSE_SVD_MAX", "8")
+    if len(case) == 4:
+        inst, beta, chi, ns = case
+        states = None
+    else:
+        inst, states, beta, chi, ns = case
+    lz_o, _, _ = boundary_mps(PottsModel(inst, states), beta, chi, ns)
+    h = Handle(inst, states)
+    h.set_beta(beta)
+    lz, _ = h.contract_boundary(chi, n_sweeps=ns)
+    assert abs(lz - lz_o) < RTOL * abs(lz_o)
+    ref = oracle_search(inst, beta, chi=chi, M=16, n_sweeps=ns, states=states)
+    res = h.search(16)
+    assert np.array_equal(res["energy_num"], ref["energy_num"])
+    assert np.allclose(res["logp"], ref["logp"], rtol=RTOL)
