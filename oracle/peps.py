@@ -45,13 +45,16 @@ RANK_TOL = 1e-12
 class RowMPO:
     """Dense MPO columns of row r, plus per-state terms for the branch step."""
 
-    def __init__(self, pm: PottsModel, r: int, beta: float):
+    def __init__(self, pm: PottsModel, r: int, beta: float, mods=None):
+        """``mods`` (optional) multiplies factors entrywise: key ('w', c) -> array over the
+        states of site (r, c); key ('B', r', c', dir) -> array shaped like that bond table."""
         self.pm, self.r, self.beta = pm, r, beta
+        self.mods = mods or {}
         self.cols = [self._column(r, c) for c in range(pm.C)]
 
     def _B(self, r, c, dname):
         E = self.pm.ebar(r, c, dname)
-        return np.exp(-self.beta * (E - E.min()) / self.pm.inst.denom)
+        return np.exp(-self.beta * (E - E.min()) / self.pm.inst.denom) * self.mods.get(("B", r, c, dname), 1.0)
 
     def _column(self, r, c):
         pm = self.pm
@@ -59,7 +62,7 @@ class RowMPO:
         below = pm.site(r + 1, c)
         right = pm.site(r, c + 1)
         below_right = pm.site(r + 1, c + 1)
-        w = np.exp(-self.beta * (S.E - S.E.min()) / pm.inst.denom)
+        w = np.exp(-self.beta * (S.E - S.E.min()) / pm.inst.denom) * self.mods.get(("w", c), 1.0)
         U = pm.joint(r, c, ("u", "ul", "ur"))
         Lam = pm.joint(r, c, ("l", "dl"))
         # old physical index sigma: up exposure of (r+1, c)
@@ -122,6 +125,35 @@ class RowMPO:
         rows = col["lam_x"][x] * col["nGl"] + col["pul"][sig]
         out[rows, :, sig] = col["T"][x].reshape(-1, col["nsig"]).T
         return out
+
+
+class TransposedRowMPO:
+    """T_r^T: the same dense columns with the up and down physical legs swapped."""
+
+    def __init__(self, mpo: RowMPO):
+        self.base = mpo
+        self.cols = mpo.cols
+        self._W = {}
+
+    def dense(self, c):
+        if c not in self._W:
+            self._W[c] = np.ascontiguousarray(self.base.dense(c).transpose(0, 1, 3, 2))
+        return self._W[c]
+
+
+def upper_boundary_mps(pm: PottsModel, mpos, chi: int, n_sweeps: int = 2):
+    """E_0..E_{R-1}: E_r covers rows 0..r-1 as a function of row r's up classes.
+
+    Built top-down with the same row step (zipper, sweeps, cut) applied to the
+    transposed row MPOs: E_0 is trivial, E_{r+1} ~ Trunc(T_r^T E_r).
+    """
+    R, C = pm.R, pm.C
+    E = [None] * R
+    E[0] = trivial_mps(C)
+    for r in range(R - 1):
+        A, ln = E[r]
+        E[r + 1] = row_step(TransposedRowMPO(mpos[r]), A, ln, chi, n_sweeps)
+    return E
 
 
 def log_offset(pm: PottsModel, beta: float) -> float:

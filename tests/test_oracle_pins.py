@@ -258,3 +258,47 @@ def test_pegasus_restricted_search_finds_restricted_ground_state():
     states = L.hamming_ball_states(inst, 12)          # ball around the planted state
     res = search(inst, 2.0, chi=256, M=10 ** 6, n_sweeps=1, states=states)
     assert int(res["energy_num"][0]) == inst.planted_energy_num
+
+
+# --- gradients (Eq. 9: d log Z/dJ = -beta<ss>, d/dh = -beta<s>, d/dbeta = -<H>) ---------
+
+@pytest.mark.parametrize("inst", [L.kings_grid(3, 3, 2), L.kings_grid(4, 4, 3), L.square_grid(4, 3, 5),
+                                  L.slice_cells(L.chimera_grid(4, 4, 0), 2, 1)], ids=lambda i: i.name)
+def test_exact_gradient_equals_brute_force_correlators(inst):
+    from oracle.grad import logz_grad
+    beta = 0.9
+    _, dJ, dh, db = logz_grad(inst, beta, chi=64, n_sweeps=1)
+    ss, m, H = brute.correlators(inst, beta)
+    assert np.allclose(dJ, -beta * ss, atol=1e-12)
+    assert np.allclose(dh, -beta * m, atol=1e-12)
+    assert abs(db + H) < 1e-11 * max(1, abs(H))
+
+
+def test_truncated_gradient_close_to_finite_differences():
+    """Environment correlators vs central differences (step 1e-4) of the truncated log Z:
+    equal up to the truncation error, so the tolerance is loose; it catches a wrong
+    sign, a dropped factor or a misplaced edge."""
+    from oracle.grad import logz_grad
+    inst, beta, chi = L.chimera_grid(3, 3, 1), 1.0, 4
+    _, dJ, dh, db = logz_grad(inst, beta, chi, n_sweeps=2)
+
+    def lz(jn=None, hn=None, b=beta):
+        I = L.Instance(inst.n_spins, inst.ei, inst.ej, inst.j_num if jn is None else jn,
+                       inst.h_num if hn is None else hn, 7, inst.site_of_spin, inst.rows, inst.cols)
+        return boundary_mps(PottsModel(I), b, chi, 2)[0]
+
+    eps = 1e-4
+    assert abs(db - (lz(b=beta + eps) - lz(b=beta - eps)) / (2 * eps)) < 1e-3 * abs(db)
+    # couplings and fields are integers over denom: refine the grid (denom 7 -> 7 K) and move one by 1/(7 K)
+    K = 20000
+    for kind, e in (("J", 0), ("J", 17), ("J", 45), ("h", 3), ("h", 50)):
+        vals = []
+        for sgn in (+1, -1):
+            jn = inst.j_num.astype(np.int64) * K
+            hn = inst.h_num.astype(np.int64) * K
+            (jn if kind == "J" else hn)[e] += sgn
+            I = L.Instance(inst.n_spins, inst.ei, inst.ej, jn, hn, 7 * K, inst.site_of_spin, inst.rows, inst.cols)
+            vals.append(boundary_mps(PottsModel(I), beta, chi, 2)[0])
+        fd = (vals[0] - vals[1]) / (2.0 / (7 * K))
+        got = dJ[e] if kind == "J" else dh[e]
+        assert abs(got - fd) < 1e-2 * max(1.0, abs(fd)), (kind, e, got, fd)
