@@ -112,6 +112,18 @@ int sgtn_branch_step(sgtn_h h, int32_t step, int32_t M, int32_t in_count, const 
 int sgtn_search(sgtn_h h, int32_t M, int32_t n_out, int8_t* out_spins, int64_t* out_energy_num,
                 double* out_logp, double* out_pd, int32_t* out_count);
 
+/* Gradient of log Z (Eq. 9): dJ[k] = d log Z / dJ_k = -beta <s_i s_j> for edge
+ * k, dh[i] = -beta <s_i>, *dbeta = -<H>, evaluated as environment
+ * correlators: row r is averaged in the sandwich <E_r| T_r |psi_r> of the
+ * bottom-up boundary MPS psi_r and an upper boundary MPS E_r built top-down
+ * with the same chi and sweeps.  Exact when the contraction is exact; with
+ * truncation it differs from the derivative of the computed log Z by the
+ * truncation error.  Requires contract_boundary with n_sweeps >= 1; the row
+ * MPO columns are handled densely here, so each column tensor
+ * (left bond x right bond x up classes x down classes) must stay below 2^26
+ * entries (SGTN_ERR_ARG otherwise).  dJ[n_edges], dh[n_spins]: host buffers. */
+int sgtn_logz_grad(sgtn_h h, double* dJ, double* dh, double* dbeta);
+
 /* Exact int64 energies (numerators over denom) of n configurations of +-1
  * spins, computed on the device: out[k] = sum j_num s_i s_j + sum h_num s_i. */
 int sgtn_energies(sgtn_h h, int32_t n, const int8_t* spins, int64_t* out);

@@ -38,11 +38,13 @@ void energies(sgtn_inst* h, int n, const int8_t* spins, int64_t* out) {
   SGTN_CUDA(cudaMalloc(&ds, size_t(n) * h->M.N));
   SGTN_CUDA(cudaMalloc(&dout, size_t(n) * sizeof(long long)));
   SGTN_CUDA(cudaMemcpyAsync(ds, spins, size_t(n) * h->M.N, cudaMemcpyHostToDevice, h->st));
-  std::vector<int32_t> z(1, 0);
-  const int32_t* ei = h->M.ei.empty() ? nullptr : h->upload(h->M.ei);
-  const int32_t* ej = h->M.ej.empty() ? nullptr : h->upload(h->M.ej);
-  const int32_t* jn = h->M.jn.empty() ? nullptr : h->upload(h->M.jn);
-  const int32_t* hn = h->upload(h->M.hn);
+  if (!h->d_ei) {
+    h->d_ei = h->M.ei.empty() ? nullptr : h->upload(h->M.ei);
+    h->d_ej = h->M.ej.empty() ? nullptr : h->upload(h->M.ej);
+    h->d_jn = h->M.jn.empty() ? nullptr : h->upload(h->M.jn);
+    h->d_hn = h->upload(h->M.hn);
+  }
+  const int32_t *ei = h->d_ei, *ej = h->d_ej, *jn = h->d_jn, *hn = h->d_hn;
   energy_kernel<<<n, 256, 0, h->st>>>(h->M.N, (long long)h->M.ei.size(), ds, ei, ej, jn, hn, dout);
   ++g_count.launches;
   h->check();
@@ -136,6 +138,13 @@ int sgtn_branch_step(sgtn_h h, int32_t step, int32_t M, int32_t in_count, const 
 int sgtn_search(sgtn_h h, int32_t M, int32_t n_out, int8_t* out_spins, int64_t* out_energy_num, double* out_logp,
                 double* out_pd, int32_t* out_count) {
   return guarded(h, [&] { search(h, M, n_out, out_spins, out_energy_num, out_logp, out_pd, out_count); });
+}
+
+int sgtn_logz_grad(sgtn_h h, double* dJ, double* dh, double* dbeta) {
+  return guarded(h, [&] {
+    if (!dh || !dbeta || (!dJ && !h->M.ei.empty())) throw SgtnError(SGTN_ERR_ARG, "null output");
+    logz_grad(h, dJ, dh, dbeta);
+  });
 }
 
 int sgtn_energies(sgtn_h h, int32_t n, const int8_t* spins, int64_t* out) {

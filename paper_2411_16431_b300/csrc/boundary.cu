@@ -27,17 +27,10 @@
 
 #include "handle.h"
 
+#include "rowstep.h"
+
 namespace sgtn {
-
-namespace {
-
-constexpr double RANK_TOL = 1e-12;
-
-struct Ten {
-  double* p = nullptr;
-  int a = 1, u = 1, b = 1;   // [a][u][b]
-  long long n() const { return (long long)a * u * b; }
-};
+namespace detail {
 
 double* dmalloc(long long n) {
   double* p = nullptr;
@@ -48,19 +41,6 @@ void dfree(double*& p) {
   if (p) cudaFree(p);
   p = nullptr;
 }
-
-struct SvdOut {
-  int k = 0;
-  double* US = nullptr;   // m x k
-  double* Vt = nullptr;   // k x n
-  double* dsig = nullptr; // k sigmas then k inverse sigmas (device)
-  std::vector<double> sig;
-  void release() {
-    dfree(US);
-    dfree(Vt);
-    dfree(dsig);
-  }
-};
 
 double norm_host(sgtn_inst* h, const double* x, long long n, bool allow_zero);
 SvdOut svd_dense(sgtn_inst* h, const double* Th, int m, int n, int cap);
@@ -229,6 +209,12 @@ SvdOut svd_subspace(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   return o;
 }
 
+void SvdOut::release() {
+  dfree(US);
+  dfree(Vt);
+  dfree(dsig);
+}
+
 // Q = US / sigma (m x k)
 double* left_factor(sgtn_inst* h, const SvdOut& o, int m) {
   double* Q = dmalloc((long long)m * o.k);
@@ -256,16 +242,6 @@ void normalise(sgtn_inst* h, double* x, long long n, double& lognorm) {
   lognorm += std::log(v);
   scale_by_inv(x, n, h->ws.get<double>("norm_out", 1), h->st);
 }
-
-struct RowCtx {
-  sgtn_inst* h;
-  int r;
-  const MPS* A;                 // psi_r, left-canonical
-  std::vector<double*> Ahat;    // per column [nA][chl][chr]
-  const Column& col(int c) const { return h->cols[r * h->M.C + c]; }
-  int chl(int c) const { return A->bond[c]; }
-  int chr(int c) const { return A->bond[c + 1]; }
-};
 
 // Ktil = Wk * K   with K [nBR][chr][kp]
 double* absorb(RowCtx& X, int c, const double* K, int kp, const char* name) {
@@ -315,6 +291,7 @@ void site_diagram(RowCtx& X, int c, const double* Kt, int kp, double* Th) {
 
 // Theta for column c with right tensor K ([nBR][chr][kp]); returns scratch pointer
 double* theta_of(RowCtx& X, int c, const double* K, int kp) {
+  if (X.dense) return theta_dense(X, c, K, kp);
   double* Kt = absorb(X, c, K, kp, "ktil");
   const Column& K_ = X.col(c);
   double* Th = X.h->ws.get<double>("theta", size_t(K_.nBL()) * X.chl(c) * K_.nU * kp);
@@ -324,6 +301,7 @@ double* theta_of(RowCtx& X, int c, const double* K, int kp) {
 
 // L env update: Lnext [b][br][chr] from L [a][bl][chl] and phi_c [a][u][b]
 double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
+  if (X.dense) return update_L_dense(X, c, L, phi);
   sgtn_inst* h = X.h;
   const Column& K_ = X.col(c);
   int chl = X.chl(c), chr = X.chr(c);
@@ -390,7 +368,7 @@ double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
 // R env update: Rprev[(bl, chl)][a] = Theta_R phi^T
 double* update_R(RowCtx& X, int c, const double* ThR, const Ten& phi) {
   const Column& K_ = X.col(c);
-  long long m = (long long)K_.nBL() * X.chl(c), n = (long long)K_.nU * phi.b;
+  long long m = (long long)K_.nBL() * X.chl(c), n = (long long)X.nout(c) * phi.b;
   double* Rp = dmalloc(m * phi.a);
   gemm(ThR, false, n, phi.p, true, n, Rp, phi.a, int(m), phi.a, int(n), 1.0, 0, X.h->st);
   return Rp;
@@ -433,16 +411,16 @@ void variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
     const Column& K_ = X.col(c);
     double* Th = theta_of(X, c, Renv[c], phi[c].b);
     int a = phi[c].a;
-    long long n = (long long)K_.nU * phi[c].b;
+    long long n = (long long)X.nout(c) * phi[c].b;
     double* t = dmalloc(a * n);
     gemm(Lenv[c], false, (long long)K_.nBL() * X.chl(c), Th, false, n, t, n, a, int(n),
          K_.nBL() * X.chl(c), 1.0, 0, h->st);
     dfree(phi[c].p);
     phi[c].p = t;
-    phi[c].u = K_.nU;
+    phi[c].u = X.nout(c);
     if (c < C - 1) {
-      SvdOut o = svd(h, t, a * K_.nU, phi[c].b, 1 << 30);
-      double* Q = left_factor(h, o, a * K_.nU);
+      SvdOut o = svd(h, t, a * X.nout(c), phi[c].b, 1 << 30);
+      double* Q = left_factor(h, o, a * X.nout(c));
       dfree(phi[c].p);
       phi[c].p = Q;
       phi[c].b = o.k;
@@ -459,7 +437,7 @@ void variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
     const Column& K_ = X.col(c);
     double* Th = theta_of(X, c, Rc, phi[c].b);
     int a = phi[c].a;
-    long long n = (long long)K_.nU * phi[c].b;
+    long long n = (long long)X.nout(c) * phi[c].b;
     double* t = dmalloc(a * n);
     gemm(Lenv[c], false, (long long)K_.nBL() * X.chl(c), Th, false, n, t, n, a, int(n),
          K_.nBL() * X.chl(c), 1.0, 0, h->st);
@@ -560,13 +538,13 @@ void compute_ahat(RowCtx& X) {
   }
 }
 
-// psi_{r-1} ~ T_r psi_r
-void row_step(sgtn_inst* h, int r, int chi, int n_sweeps, MPS& out, double& worst) {
+// out ~ T A (T = the row MPO of X, possibly transposed / dense); A is left-canonicalised in place
+void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& worst) {
+  sgtn_inst* h = X.h;
   const int C = h->M.C;
-  MPS& A = h->psi[r];
   left_canonical(h, A);
-  RowCtx X{h, r, &A, {}};
-  compute_ahat(X);
+  X.A = &A;
+  if (!X.dense) compute_ahat(X);
   // zipper
   std::vector<Ten> phi(C);
   double* K = dmalloc(1);
@@ -576,12 +554,12 @@ void row_step(sgtn_inst* h, int r, int chi, int n_sweeps, MPS& out, double& wors
   for (int c = C - 1; c >= 0; --c) {
     const Column& K_ = X.col(c);
     double* Th = theta_of(X, c, K, kp);
-    int m = K_.nBL() * X.chl(c), n = K_.nU * kp;
+    int m = K_.nBL() * X.chl(c), n = X.nout(c) * kp;
     SvdOut o = svd(h, Th, m, n, 2 * chi);
     phi[c].p = o.Vt;
     o.Vt = nullptr;
     phi[c].a = o.k;
-    phi[c].u = K_.nU;
+    phi[c].u = X.nout(c);
     phi[c].b = kp;
     dfree(K);
     K = o.US;
@@ -614,6 +592,7 @@ void row_step(sgtn_inst* h, int r, int chi, int n_sweeps, MPS& out, double& wors
     normalise(h, phi[0].p, phi[0].n(), ln);
   }
   for (double* p : X.Ahat) cudaFree(p);
+  X.Ahat.clear();
   // store as [phys][bond_l][bond_r]
   free_mps(out);
   out.C = C;
@@ -633,10 +612,21 @@ void row_step(sgtn_inst* h, int r, int chi, int n_sweeps, MPS& out, double& wors
   h->check();
 }
 
+// psi_{r-1} ~ T_r psi_r (sparse projector form)
+void row_step(sgtn_inst* h, int r, int chi, int n_sweeps, MPS& out, double& worst) {
+  RowCtx X;
+  X.h = h;
+  X.r = r;
+  row_step_ctx(X, h->psi[r], chi, n_sweeps, out, worst);
+}
+
 double top_overlap(sgtn_inst* h) {
   const int C = h->M.C;
   MPS& A = h->psi[0];
-  RowCtx X{h, 0, &A, {}};
+  RowCtx X;
+  X.h = h;
+  X.r = 0;
+  X.A = &A;
   compute_ahat(X);
   double ln = A.lognorm;
   double* Rc = dmalloc(1);
@@ -660,7 +650,9 @@ double top_overlap(sgtn_inst* h) {
   return ln + std::log(v);
 }
 
-}  // namespace
+}  // namespace detail
+
+using namespace detail;
 
 void contract_boundary(sgtn_inst* h, int chi, int n_sweeps) {
   const int R = h->M.R, C = h->M.C;

@@ -78,7 +78,8 @@ struct sgtn_inst {
   double logz = 0.0, worst_sv = 0.0;
   sgtn::Scratch ws;
   int32_t* iota = nullptr;                // 0..iota_n-1
-  int dense_svd_max = 320;                // exact Jacobi up to this many vectors, subspace iteration above
+  int dense_svd_max = 320;
+  int32_t *d_ei = nullptr, *d_ej = nullptr, *d_jn = nullptr, *d_hn = nullptr;   // edges for energies                // exact Jacobi up to this many vectors, subspace iteration above
   int iota_n = 0;
 
   template <class T>
@@ -115,6 +116,7 @@ void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_
 void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_energy, double* out_logp, double* out_pd,
             int32_t* out_count);
 void energies(sgtn_inst* h, int n, const int8_t* spins, int64_t* out);
+void logz_grad(sgtn_inst* h, double* dJ, double* dh, double* dbeta);
 size_t scores_scratch_bytes(sgtn_inst* h, int step, int K);
 void conditionals_arena(sgtn_inst* h, int step, int count, const int32_t* configs, double* out_p, void* arena,
                         size_t cap);

@@ -74,6 +74,8 @@ void gather_vecs(const double* X, int len, long long si, long long sj, const int
 void pseudo_random(double* x, long long n, unsigned long long seed, cudaStream_t st);
 // R[i][j] += Q[i*ldq + j] for j < k  (R is rows x k, Q is rows x ldq)
 void add_cols(double* R, const double* Q, int rows, int k, int ldq, cudaStream_t st);
+// generic permutation of an nd-array (nd <= 6): out axis k = in axis perm[k]
+void permute_nd(const double* in, int nd, const int* dims, const int* perm, double* out, cudaStream_t st);
 // out[b][a][c] = in[a][b][c]
 void permute3(const double* in, int A, int B, int Cd, double* out, cudaStream_t st);
 // Frobenius norm (deterministic), result on device in *out

@@ -339,6 +339,24 @@ __global__ void permute3_kernel(const double* in, int A, int B, int Cd, double* 
   }
 }
 
+struct PermArgs {
+  int nd;
+  long long in_stride[6];    // stride in `in` of each OUTPUT axis
+  long long out_dim[6];
+};
+
+__global__ void permute_nd_kernel(const double* in, double* out, long long n, PermArgs pa) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    long long rem = e, src = 0;
+    for (int k = pa.nd - 1; k >= 0; --k) {
+      long long ik = rem % pa.out_dim[k];
+      rem /= pa.out_dim[k];
+      src += ik * pa.in_stride[k];
+    }
+    out[e] = in[src];
+  }
+}
+
 __global__ void fro_norm_kernel(const double* x, long long n, double* out) {
   __shared__ double red[32];
   double a = 0;
@@ -603,6 +621,23 @@ void gather_vecs(const double* X, int len, long long si, long long sj, const int
 
 void permute3(const double* in, int A, int B, int Cd, double* out, cudaStream_t st) {
   permute3_kernel<<<blocks_for((long long)A * B * Cd), 256, 0, st>>>(in, A, B, Cd, out);
+  ++g_count.launches;
+}
+
+void permute_nd(const double* in, int nd, const int* dims, const int* perm, double* out, cudaStream_t st) {
+  PermArgs pa;
+  pa.nd = nd;
+  long long stride[6];
+  long long s = 1;
+  for (int k = nd - 1; k >= 0; --k) {
+    stride[k] = s;
+    s *= dims[k];
+  }
+  for (int k = 0; k < nd; ++k) {
+    pa.in_stride[k] = stride[perm[k]];
+    pa.out_dim[k] = dims[perm[k]];
+  }
+  permute_nd_kernel<<<blocks_for(s), 256, 0, st>>>(in, out, s, pa);
   ++g_count.launches;
 }
 

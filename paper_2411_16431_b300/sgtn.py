@@ -40,6 +40,7 @@ def load():
     L.sgtn_search.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I8P, _I64P, _F64P, _F64P, _I32P]
     L.sgtn_conditionals_noalloc.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I32P, _F64P]
     L.sgtn_energies.argtypes = [ct.c_void_p, ct.c_int32, _I8P, _I64P]
+    L.sgtn_logz_grad.argtypes = [ct.c_void_p, _F64P, _F64P, _F64P]
     L.sgtn_site_dims.argtypes = [ct.c_void_p, ct.c_int32, _I32P]
     L.sgtn_mps_shape.argtypes = [ct.c_void_p, ct.c_int32, _I32P, _I32P, _F64P]
     L.sgtn_mps_tensor.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _F64P]
@@ -178,6 +179,14 @@ class Handle:
                                     ct.byref(cnt)))
         k = cnt.value
         return dict(spins=sp[:k], energy_num=en[:k], logp=lp[:k], pd=pd.value)
+
+    def logz_grad(self):
+        """(dlogZ/dJ[n_edges], dlogZ/dh[n_spins], dlogZ/dbeta) for the current beta and boundary."""
+        dJ = np.zeros(max(self.inst.n_edges, 1))
+        dh = np.zeros(self.inst.n_spins)
+        db = ct.c_double()
+        self._ck(self.L.sgtn_logz_grad(self.h, _p(dJ, _F64P), _p(dh, _F64P), ct.byref(db)))
+        return dJ[:self.inst.n_edges], dh, db.value
 
     def energies(self, spins):
         spins = np.ascontiguousarray(np.asarray(spins, np.int8).reshape(-1, self.inst.n_spins))

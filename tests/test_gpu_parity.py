@@ -205,3 +205,34 @@ def test_subspace_iteration_truncation_matches_oracle(Handle, case, monkeypatch)
     res = h.search(16)
     assert np.array_equal(res["energy_num"], ref["energy_num"])
     assert np.allclose(res["logp"], ref["logp"], rtol=RTOL)
+
+
+GRAD_CASES = [(L.kings_grid(4, 4, 3), None, 0.9, 64, 1), (L.chimera_grid(3, 3, 1), None, 1.0, 4, 2),
+              (L.square_grid(5, 4, 8), None, 1.5, 2, 2), (PEG, PEG_STATES, 0.8, 6, 1),
+              (L.slice_cells(L.chimera_grid(4, 4, 0), 2, 2), None, 2.0, 8, 2)]
+
+
+@pytest.mark.parametrize("case", GRAD_CASES, ids=lambda c: f"{c[0].name}_chi{c[3]}")
+def test_logz_grad_matches_oracle(Handle, case):
+    from oracle.grad import logz_grad
+    inst, states, beta, chi, ns = case
+    _, dJ_o, dh_o, db_o = logz_grad(inst, beta, chi, ns, states=states)
+    h = Handle(inst, states)
+    h.set_beta(beta)
+    h.contract_boundary(chi, n_sweeps=ns)
+    dJ, dh, db = h.logz_grad()
+    assert np.allclose(dJ, dJ_o, rtol=1e-9, atol=1e-10)
+    assert np.allclose(dh, dh_o, rtol=1e-9, atol=1e-10)
+    assert abs(db - db_o) < 1e-9 * max(1.0, abs(db_o))
+
+
+def test_logz_grad_exact_equals_brute_force(Handle):
+    inst, beta = L.slice_cells(L.chimera_grid(4, 4, 2), 2, 1), 1.3
+    h = Handle(inst)
+    h.set_beta(beta)
+    h.contract_boundary(64, n_sweeps=1)
+    dJ, dh, db = h.logz_grad()
+    ss, m, H = brute.correlators(inst, beta)
+    assert np.allclose(dJ, -beta * ss, atol=1e-11)
+    assert np.allclose(dh, -beta * m, atol=1e-11)
+    assert abs(db + H) < 1e-10 * abs(H)
