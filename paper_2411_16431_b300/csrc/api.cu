@@ -89,6 +89,7 @@ int sgtn_build_instance(int32_t n_spins, int64_t n_edges, const int32_t* ei, con
   cudaGetDevice(&h->device);
   h->st = static_cast<cudaStream_t>(stream);
   if (const char* e = std::getenv("SGTN_DENSE_SVD_MAX")) h->dense_svd_max = std::max(1, std::atoi(e));
+  if (const char* e = std::getenv("SGTN_BS_MIN_ENTRIES")) h->bs_min_entries = std::max(0ll, std::atoll(e));
   std::string e = h->M.build(n_spins, n_edges, ei, ej, j_num, h_num, denom, site_of_spin, rows, cols, state_offsets,
                              states);
   if (!e.empty()) {

@@ -23,6 +23,7 @@
 //    built (phi) is kept bond-major [bond_l][phys][bond_r].
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <numeric>
 
 #include "handle.h"
@@ -45,6 +46,8 @@ void dfree(double*& p) {
 double norm_host(sgtn_inst* h, const double* x, long long n, bool allow_zero);
 SvdOut svd_dense(sgtn_inst* h, const double* Th, int m, int n, int cap);
 SvdOut svd_subspace(sgtn_inst* h, const double* Th, int m, int n, int cap);
+using MatFn = std::function<void(const double* Q, int s, double* Y)>;
+SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, const MatFn& tmul);
 
 // Truncated SVD of a dense row-major m x n matrix: exact one-sided Jacobi on
 // the shorter side when it is short, otherwise subspace iteration with a
@@ -125,6 +128,13 @@ SvdOut svd_dense(sgtn_inst* h, const double* Th, int m, int n, int cap) {
 // (largest principal-angle sine); then Rayleigh-Ritz: the SVD of Theta Q (s
 // columns, exact Jacobi) gives the singular values and Q V the vectors.
 SvdOut svd_subspace(sgtn_inst* h, const double* Th, int m, int n, int cap) {
+  MatFn mul = [=](const double* Q, int s, double* Y) { gemm(Th, false, n, Q, false, s, Y, s, m, s, n, 1.0, 0, h->st); };
+  MatFn tmul = [=](const double* Y, int s, double* Z) { gemm(Th, true, n, Y, false, s, Z, s, n, s, m, 1.0, 0, h->st); };
+  return svd_subspace_op(h, m, n, cap, mul, tmul);
+}
+
+// Same, with Theta given only through Y = Theta Q and Z = Theta^T Y.
+SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, const MatFn& tmul) {
   cudaStream_t st = h->st;
   const int p = std::min(m, n);
   const int s = std::min(p, cap + 32);
@@ -173,9 +183,9 @@ SvdOut svd_subspace(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   const int maxit = 300;
   int it = 0;
   for (; it < maxit; ++it) {
-    gemm(Th, false, n, Q, false, k_active, Y, k_active, m, k_active, n, 1.0, 0, st);          // Y = Theta Q
+    mul(Q, k_active, Y);                                                                     // Y = Theta Q
     double* Z = h->ws.get<double>("ss_Z", size_t(n) * k_active);
-    gemm(Th, true, n, Y, false, k_active, Z, k_active, n, k_active, m, 1.0, 0, st);           // Z = Theta^T Y
+    tmul(Y, k_active, Z);                                                                    // Z = Theta^T Y
     int kn = k_active;
     orth(Z, n, kn, Qn);
     // subspace change of the leading min(cap, kn) directions: || Qk - Qn (Qn^T Qk) ||
@@ -192,7 +202,7 @@ SvdOut svd_subspace(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   }
   if (it >= maxit) throw SgtnError(-4, "subspace iteration did not converge (no gap at the cut?)");
   // Rayleigh-Ritz: B = Theta Q (m x s), exact SVD of B
-  gemm(Th, false, n, Q, false, k_active, Y, k_active, m, k_active, n, 1.0, 0, st);
+  mul(Q, k_active, Y);
   SvdOut ob = svd_dense(h, Y, m, k_active, cap);    // Y = U S W^T  (W: Vt rows, length k_active)
   SvdOut o;
   o.k = ob.k;
@@ -393,6 +403,227 @@ void right_canonical(RowCtx& X, std::vector<Ten>& phi) {
   }
 }
 
+// The site-diagram result Theta [(bl, chl) x (out, kp)], dense or block-sparse
+// (one chl x kp block per (bl, u) segment of the column's term table: most
+// (bl, u) pairs never occur, so the block form holds far fewer entries).
+struct ThetaOp {
+  bool bs = false;
+  double* dense = nullptr;
+  double* blocks = nullptr;
+  int m = 0, n = 0, chl = 0, kp = 0, nseg = 0, nbl = 0, nout = 0;
+};
+
+ThetaOp theta_op(RowCtx& X, int c, const double* K, int kp) {
+  ThetaOp T;
+  const Column& K_ = X.col(c);
+  T.chl = X.chl(c);
+  T.kp = kp;
+  T.nbl = K_.nBL();
+  T.nout = X.nout(c);
+  T.m = T.nbl * T.chl;
+  T.n = T.nout * kp;
+  sgtn_inst* h = X.h;
+  if (X.dense || (long long)T.m * T.n <= h->bs_min_entries) {
+    T.dense = theta_of(X, c, K, kp);
+    return T;
+  }
+  T.bs = true;
+  T.nseg = K_.theta.nseg;
+  double* Kt = absorb(X, c, K, kp, "ktil");
+  T.blocks = h->ws.get<double>("theta_bs", size_t(T.nseg) * T.chl * kp);
+  SegGemm a;
+  a.X = X.Ahat[c];
+  a.Y = Kt;
+  a.O = T.blocks;
+  a.p = T.chl;
+  a.q = X.chr(c);
+  a.s = kp;
+  a.xs_i = X.chr(c);
+  a.xs_k = 1;
+  a.xrs = (long long)T.chl * X.chr(c);
+  a.ys_k = kp;
+  a.ys_j = 1;
+  a.yrs = (long long)X.chr(c) * kp;
+  a.os_i = kp;
+  a.os_j = 1;
+  a.ors = (long long)T.chl * kp;
+  a.out_by_seg = 1;
+  a.seg_ptr = K_.theta.seg_ptr;
+  a.seg_or = K_.theta.seg_or;
+  a.seg_oc = K_.theta.seg_oc;
+  a.xr = K_.theta.xr;
+  a.xc = K_.theta.xc;
+  a.yr = K_.theta.yr;
+  a.yc = K_.theta.yc;
+  a.cidx = K_.theta.cidx;
+  a.coef = h->ds[X.r * h->M.C + c].w;
+  a.nseg = K_.theta.nseg;
+  a.nterm = K_.theta.nterm;
+  seg_gemm(a, h->st);
+  return T;
+}
+
+// Y (m x s) = Theta Q (Q: n x s)
+void theta_mul(RowCtx& X, int c, const ThetaOp& T, const double* Q, int s, double* Y) {
+  if (!T.bs) {
+    gemm(T.dense, false, T.n, Q, false, s, Y, s, T.m, s, T.n, 1.0, 0, X.h->st);
+    return;
+  }
+  const TermTable& t = X.col(c).bs_rows;
+  SGTN_CUDA(cudaMemsetAsync(Y, 0, size_t(T.m) * s * sizeof(double), X.h->st));
+  SegGemm a;
+  a.X = T.blocks;
+  a.p = T.chl;
+  a.q = T.kp;
+  a.xs_i = T.kp;
+  a.xs_k = 1;
+  a.xrs = (long long)T.chl * T.kp;
+  a.Y = Q;
+  a.s = s;
+  a.ys_k = s;
+  a.ys_j = 1;
+  a.yrs = (long long)T.kp * s;
+  a.O = Y;
+  a.os_i = s;
+  a.os_j = 1;
+  a.ors = (long long)T.chl * s;
+  a.seg_ptr = t.seg_ptr;
+  a.seg_or = t.seg_or;
+  a.seg_oc = t.seg_oc;
+  a.xr = t.xr;
+  a.xc = t.xc;
+  a.yr = t.yr;
+  a.yc = t.yc;
+  a.nseg = t.nseg;
+  a.nterm = t.nterm;
+  seg_gemm(a, X.h->st);
+}
+
+// Z (n x s) = Theta^T Y (Y: m x s)
+void theta_tmul(RowCtx& X, int c, const ThetaOp& T, const double* Y, int s, double* Z) {
+  if (!T.bs) {
+    gemm(T.dense, true, T.n, Y, false, s, Z, s, T.n, s, T.m, 1.0, 0, X.h->st);
+    return;
+  }
+  const TermTable& t = X.col(c).bs_cols;
+  SGTN_CUDA(cudaMemsetAsync(Z, 0, size_t(T.n) * s * sizeof(double), X.h->st));
+  SegGemm a;
+  a.X = T.blocks;
+  a.p = T.kp;
+  a.q = T.chl;
+  a.xs_i = 1;
+  a.xs_k = T.kp;
+  a.xrs = (long long)T.chl * T.kp;
+  a.Y = Y;
+  a.s = s;
+  a.ys_k = s;
+  a.ys_j = 1;
+  a.yrs = (long long)T.chl * s;
+  a.O = Z;
+  a.os_i = s;
+  a.os_j = 1;
+  a.ors = (long long)T.kp * s;
+  a.seg_ptr = t.seg_ptr;
+  a.seg_or = t.seg_or;
+  a.seg_oc = t.seg_oc;
+  a.xr = t.xr;
+  a.xc = t.xc;
+  a.yr = t.yr;
+  a.yc = t.yc;
+  a.nseg = t.nseg;
+  a.nterm = t.nterm;
+  seg_gemm(a, X.h->st);
+}
+
+// t (a x n) = L_mat (a x m) Theta
+double* theta_left(RowCtx& X, int c, const ThetaOp& T, const double* L, int a_dim) {
+  double* t = dmalloc((long long)a_dim * T.n);
+  if (!T.bs) {
+    gemm(L, false, T.m, T.dense, false, T.n, t, T.n, a_dim, T.n, T.m, 1.0, 0, X.h->st);
+    return t;
+  }
+  const TermTable& tt = X.col(c).bs_cols;
+  SGTN_CUDA(cudaMemsetAsync(t, 0, size_t(a_dim) * T.n * sizeof(double), X.h->st));
+  SegGemm a;
+  a.X = L;
+  a.p = a_dim;
+  a.q = T.chl;
+  a.xs_i = T.m;
+  a.xs_k = 1;
+  a.xcs = T.chl;
+  a.Y = T.blocks;
+  a.s = T.kp;
+  a.ys_k = T.kp;
+  a.ys_j = 1;
+  a.ycs = (long long)T.chl * T.kp;
+  a.O = t;
+  a.os_i = T.n;
+  a.os_j = 1;
+  a.ors = T.kp;
+  a.seg_ptr = tt.seg_ptr;
+  a.seg_or = tt.seg_or;
+  a.seg_oc = tt.seg_oc;
+  a.xr = tt.xr;
+  a.xc = tt.xc;
+  a.yr = tt.yr;
+  a.yc = tt.yc;
+  a.nseg = tt.nseg;
+  a.nterm = tt.nterm;
+  seg_gemm(a, X.h->st);
+  return t;
+}
+
+// R (m x a) = Theta phi_mat^T  with phi [a][out][b]
+double* theta_right(RowCtx& X, int c, const ThetaOp& T, const Ten& phi) {
+  if (!T.bs) return update_R(X, c, T.dense, phi);
+  double* Rp = dmalloc((long long)T.m * phi.a);
+  const TermTable& tt = X.col(c).bs_rows;
+  SGTN_CUDA(cudaMemsetAsync(Rp, 0, size_t(T.m) * phi.a * sizeof(double), X.h->st));
+  SegGemm a;
+  a.X = T.blocks;
+  a.p = T.chl;
+  a.q = T.kp;
+  a.xs_i = T.kp;
+  a.xs_k = 1;
+  a.xrs = (long long)T.chl * T.kp;
+  a.Y = phi.p;
+  a.s = phi.a;
+  a.ys_k = 1;
+  a.ys_j = T.n;
+  a.yrs = T.kp;
+  a.O = Rp;
+  a.os_i = phi.a;
+  a.os_j = 1;
+  a.ors = (long long)T.chl * phi.a;
+  a.seg_ptr = tt.seg_ptr;
+  a.seg_or = tt.seg_or;
+  a.seg_oc = tt.seg_oc;
+  a.xr = tt.xr;
+  a.xc = tt.xc;
+  a.yr = tt.yr;
+  a.yc = tt.yc;
+  a.nseg = tt.nseg;
+  a.nterm = tt.nterm;
+  seg_gemm(a, X.h->st);
+  return Rp;
+}
+
+SvdOut theta_svd(RowCtx& X, int c, const ThetaOp& T, int cap) {
+  sgtn_inst* h = X.h;
+  if (!T.bs) return svd(h, T.dense, T.m, T.n, cap);
+  int p = std::min(T.m, T.n);
+  if (p <= h->dense_svd_max || cap >= p) {
+    double* D = h->ws.get<double>("theta_dense_of_bs", size_t(T.m) * T.n);
+    SGTN_CUDA(cudaMemsetAsync(D, 0, size_t(T.m) * T.n * sizeof(double), h->st));
+    const Column& K_ = X.col(c);
+    scatter_blocks(T.blocks, T.nseg, T.chl, T.kp, K_.theta.seg_or, K_.theta.seg_oc, D, T.n, h->st);
+    return svd(h, D, T.m, T.n, cap);
+  }
+  MatFn mul = [&](const double* Q, int s, double* Y) { theta_mul(X, c, T, Q, s, Y); };
+  MatFn tmul = [&](const double* Y, int s, double* Z) { theta_tmul(X, c, T, Y, s, Z); };
+  return svd_subspace_op(h, T.m, T.n, cap, mul, tmul);
+}
+
 // One left-right-left sweep of one-site overlap maximisation (Fig. 8d).
 void variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
   sgtn_inst* h = X.h;
@@ -402,19 +633,17 @@ void variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
   Renv[C - 1] = dmalloc(1);
   fill(Renv[C - 1], 1, 1.0, h->st);
   for (int c = C - 1; c > 0; --c) {
-    double* Th = theta_of(X, c, Renv[c], phi[c].b);
-    Renv[c - 1] = update_R(X, c, Th, phi[c]);
+    ThetaOp T = theta_op(X, c, Renv[c], phi[c].b);
+    Renv[c - 1] = theta_right(X, c, T, phi[c]);
   }
   Lenv[0] = dmalloc(1);
   fill(Lenv[0], 1, 1.0, h->st);
   for (int c = 0; c < C; ++c) {
     const Column& K_ = X.col(c);
-    double* Th = theta_of(X, c, Renv[c], phi[c].b);
+    ThetaOp T = theta_op(X, c, Renv[c], phi[c].b);
     int a = phi[c].a;
-    long long n = (long long)X.nout(c) * phi[c].b;
-    double* t = dmalloc(a * n);
-    gemm(Lenv[c], false, (long long)K_.nBL() * X.chl(c), Th, false, n, t, n, a, int(n),
-         K_.nBL() * X.chl(c), 1.0, 0, h->st);
+    double* t = theta_left(X, c, T, Lenv[c], a);
+    (void)K_;
     dfree(phi[c].p);
     phi[c].p = t;
     phi[c].u = X.nout(c);
@@ -435,12 +664,11 @@ void variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
   fill(Rc, 1, 1.0, h->st);
   for (int c = C - 1; c >= 0; --c) {
     const Column& K_ = X.col(c);
-    double* Th = theta_of(X, c, Rc, phi[c].b);
+    ThetaOp T = theta_op(X, c, Rc, phi[c].b);
     int a = phi[c].a;
     long long n = (long long)X.nout(c) * phi[c].b;
-    double* t = dmalloc(a * n);
-    gemm(Lenv[c], false, (long long)K_.nBL() * X.chl(c), Th, false, n, t, n, a, int(n),
-         K_.nBL() * X.chl(c), 1.0, 0, h->st);
+    double* t = theta_left(X, c, T, Lenv[c], a);
+    (void)K_;
     dfree(phi[c].p);
     phi[c].p = t;
     if (c > 0) {
@@ -450,7 +678,7 @@ void variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
       o.Vt = nullptr;
       phi[c].a = o.k;
       o.release();
-      double* Rn = update_R(X, c, Th, phi[c]);
+      double* Rn = theta_right(X, c, T, phi[c]);
       dfree(Rc);
       Rc = Rn;
       phi[c - 1].b = phi[c].a;
@@ -553,9 +781,9 @@ void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& wo
   double ln = A.lognorm;
   for (int c = C - 1; c >= 0; --c) {
     const Column& K_ = X.col(c);
-    double* Th = theta_of(X, c, K, kp);
-    int m = K_.nBL() * X.chl(c), n = X.nout(c) * kp;
-    SvdOut o = svd(h, Th, m, n, 2 * chi);
+    ThetaOp T = theta_op(X, c, K, kp);
+    int m = K_.nBL() * X.chl(c);
+    SvdOut o = theta_svd(X, c, T, 2 * chi);
     phi[c].p = o.Vt;
     o.Vt = nullptr;
     phi[c].a = o.k;

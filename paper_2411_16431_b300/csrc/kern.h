@@ -50,6 +50,7 @@ struct SegGemm {
   const double* cs = nullptr;
   long long cs_ld = 0;
   int nseg = 1;
+  int out_by_seg = 0;    // table mode: output block offset = segment index * ors
   long long nterm = 0;   // host-side term count for the FLOP counter (table mode)
   double alpha = 1.0;
   int accumulate = 0;
@@ -76,6 +77,9 @@ void pseudo_random(double* x, long long n, unsigned long long seed, cudaStream_t
 void add_cols(double* R, const double* Q, int rows, int k, int ldq, cudaStream_t st);
 // generic permutation of an nd-array (nd <= 6): out axis k = in axis perm[k]
 void permute_nd(const double* in, int nd, const int* dims, const int* perm, double* out, cudaStream_t st);
+// dense[(bl*chl + i)*n + u*kp + j] = blocks[seg][i][j] for seg's (bl, u)
+void scatter_blocks(const double* blocks, int nseg, int chl, int kp, const int32_t* seg_bl, const int32_t* seg_u,
+                    double* dense, long long n, cudaStream_t st);
 // out[b][a][c] = in[a][b][c]
 void permute3(const double* in, int A, int B, int Cd, double* out, cudaStream_t st);
 // Frobenius norm (deterministic), result on device in *out

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
   if (a.seg_ptr) {
     t0 = a.seg_ptr[seg];
     t1 = a.seg_ptr[seg + 1];
-    ooff = (long long)a.seg_or[seg] * a.ors + (long long)a.seg_oc[seg] * a.ocs;
+    ooff = a.out_by_seg ? (long long)seg * a.ors : (long long)a.seg_or[seg] * a.ors + (long long)a.seg_oc[seg] * a.ocs;
   } else {
     t0 = seg;
     t1 = seg + 1;
@@ -357,6 +357,16 @@ __global__ void permute_nd_kernel(const double* in, double* out, long long n, Pe
   }
 }
 
+__global__ void scatter_blocks_kernel(const double* blocks, long long total, int chl, int kp, const int32_t* seg_bl,
+                                      const int32_t* seg_u, double* dense, long long n) {
+  const long long blk = (long long)chl * kp;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    long long sgi = e / blk, r = e % blk;
+    long long i = r / kp, j = r % kp;
+    dense[((long long)seg_bl[sgi] * chl + i) * n + (long long)seg_u[sgi] * kp + j] = blocks[e];
+  }
+}
+
 __global__ void fro_norm_kernel(const double* x, long long n, double* out) {
   __shared__ double red[32];
   double a = 0;
@@ -638,6 +648,13 @@ void permute_nd(const double* in, int nd, const int* dims, const int* perm, doub
     pa.out_dim[k] = dims[perm[k]];
   }
   permute_nd_kernel<<<blocks_for(s), 256, 0, st>>>(in, out, s, pa);
+  ++g_count.launches;
+}
+
+void scatter_blocks(const double* blocks, int nseg, int chl, int kp, const int32_t* seg_bl, const int32_t* seg_u,
+                    double* dense, long long n, cudaStream_t st) {
+  long long total = (long long)nseg * chl * kp;
+  scatter_blocks_kernel<<<blocks_for(total), 256, 0, st>>>(blocks, total, chl, kp, seg_bl, seg_u, dense, n);
   ++g_count.launches;
 }
 

@@ -93,6 +93,8 @@ struct Column {
   int bv_nb = 1, bh_nb = 1, bdl_na = 1, bdl_nb = 1, bdr_nb = 1;
   TermTable theta;   // segments (bl, u), terms (x, e)
   TermTable lupd;    // segments (pr, e, pdr), terms (x, g)
+  TermTable bs_rows; // block-sparse Theta grouped by row block bl: terms (xr = seg, yr = u)
+  TermTable bs_cols; // grouped by column block u: terms (xr = seg, xc = bl, yr = bl, yc = seg)
   TermTable renv;    // segments bl, terms (x, e), column scale row = u
   // per-beta dense weight matrices (device, double)
   double* Wa = nullptr;   // [nA][nSig]

@@ -166,6 +166,17 @@ void setup_device(sgtn_inst* h) {
             tb.add(kblk, kblk, 0, u[x], bl, ablk, 0, x, u[x]);
           }
       tb.finish(h, K.lupd);
+      // groupings of the site-diagram output blocks (one block per theta segment)
+      for (int sg = 0; sg < K.theta.nseg; ++sg) {
+        int bl = K.theta.h_seg_or[sg], uu = K.theta.h_seg_oc[sg];
+        tb.add(bl, bl, 0, sg, 0, uu, 0, 0, 0);
+      }
+      tb.finish(h, K.bs_rows);
+      for (int sg = 0; sg < K.theta.nseg; ++sg) {
+        int bl = K.theta.h_seg_or[sg], uu = K.theta.h_seg_oc[sg];
+        tb.add(uu, uu, 0, sg, bl, bl, sg, 0, 0);
+      }
+      tb.finish(h, K.bs_cols);
       K.Wa = h->dalloc<double>(size_t(K.nA()) * K.nSig);
       K.Wk = h->dalloc<double>(size_t(K.nK()) * K.nBR());
       maxn = std::max({maxn, S.d, K.nU, K.nSig, K.nBL(), K.nBR()});

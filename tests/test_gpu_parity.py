@@ -236,3 +236,26 @@ def test_logz_grad_exact_equals_brute_force(Handle):
     assert np.allclose(dJ, -beta * ss, atol=1e-11)
     assert np.allclose(dh, -beta * m, atol=1e-11)
     assert abs(db + H) < 1e-10 * abs(H)
+
+
+@pytest.mark.parametrize("svd_max", ["320", "8"])
+@pytest.mark.parametrize("case", [CASES[0], CASES[2], PEG_CASES[0], PEG_CASES[1]], ids=lambda c: c[0].name)
+def test_block_sparse_theta_matches_oracle(Handle, case, svd_max, monkeypatch):
+    """Force the block-sparse site-diagram path (used when the dense Theta would be large),
+    with the exact and with the iterative truncated SVD."""
+    monkeypatch.setenv("SGTN_BS_MIN_ENTRIES", "0")
+    monkeypatch.setenv("SGTN_DENSE_SVD_MAX", svd_max)
+    if len(case) == 4:
+        inst, beta, chi, ns = case
+        states = None
+    else:
+        inst, states, beta, chi, ns = case
+    lz_o, _, _ = boundary_mps(PottsModel(inst, states), beta, chi, ns)
+    h = Handle(inst, states)
+    h.set_beta(beta)
+    lz, _ = h.contract_boundary(chi, n_sweeps=ns)
+    assert abs(lz - lz_o) < RTOL * abs(lz_o)
+    ref = oracle_search(inst, beta, chi=chi, M=16, n_sweeps=ns, states=states)
+    res = h.search(16)
+    assert np.array_equal(res["energy_num"], ref["energy_num"])
+    assert np.allclose(res["logp"], ref["logp"], rtol=RTOL)
