@@ -43,7 +43,11 @@ typedef enum {
   SGTN_ERR_CUDA = -6        /* any other CUDA error                        */
 } sgtn_status;
 
-typedef enum { SGTN_FP64 = 0, SGTN_TF32 = 1, SGTN_BF16 = 2 } sgtn_precision;
+/* SGTN_FP64: everything in double.  SGTN_FP32 (mixed): every contraction
+ * (site diagrams, environments, projections, conditional scores) multiplies
+ * and accumulates in FP32 while tensors are stored, truncated (SVD) and
+ * normalised (log-norms) in FP64.  TF32 / BF16 are reserved. */
+typedef enum { SGTN_FP64 = 0, SGTN_TF32 = 1, SGTN_BF16 = 2, SGTN_FP32 = 3 } sgtn_precision;
 
 /* Build the generalized Potts model of Sec. III, Eqs. (2)-(4): cluster
  * states, intra-cluster energies E_x, projectors P^{mn} onto the spins that
@@ -133,6 +137,11 @@ int sgtn_energies(sgtn_h h, int32_t n, const int8_t* spins, int64_t* out);
  * (phys[cols], bond[cols+1]) and its log-norm.  sgtn_mps_tensor copies
  * column `col` of psi_row to out ([phys][bond_l][bond_r], double). */
 int sgtn_site_dims(sgtn_h h, int32_t site, int32_t* d);
+/* After contract_boundary: number of iterative truncations that stopped at
+ * their iteration cap because the singular values at the cut were not
+ * separated (the truncation is then ambiguous; 0 for exact truncations), and
+ * the precision the boundary was computed in. */
+int sgtn_boundary_info(sgtn_h h, int32_t* unconverged_cuts, int32_t* precision);
 int sgtn_mps_shape(sgtn_h h, int32_t row, int32_t* phys, int32_t* bond, double* lognorm);
 int sgtn_mps_tensor(sgtn_h h, int32_t row, int32_t col, double* out);
 

@@ -118,27 +118,50 @@ int sgtn_contract_boundary(sgtn_h h, int32_t chi, int32_t precision, int32_t n_s
   return guarded(h, [&] {
     if (!h->beta_set) throw SgtnError(SGTN_ERR_STATE, "set_beta must run first");
     if (chi < 1 || n_sweeps < 0 || n_sweeps > 100) throw SgtnError(SGTN_ERR_ARG, "bad chi or n_sweeps");
-    if (precision != SGTN_FP64) throw SgtnError(SGTN_ERR_ARG, "only SGTN_FP64 is available in this build");
+    if (precision != SGTN_FP64 && precision != SGTN_FP32)
+      throw SgtnError(SGTN_ERR_ARG, "precision must be SGTN_FP64 or SGTN_FP32 in this build");
     h->precision = precision;
-    contract_boundary(h, chi, n_sweeps);
+    g_compute_f32 = precision == SGTN_FP32;
+    try {
+      contract_boundary(h, chi, n_sweeps);
+    } catch (...) {
+      g_compute_f32 = false;
+      throw;
+    }
+    g_compute_f32 = false;
     if (out_logz) *out_logz = h->logz;
     if (out_worst_trunc_sv) *out_worst_trunc_sv = h->worst_sv;
   });
 }
 
+// The branch step and the search run in the precision of the last contract_boundary.
+struct PrecisionScope {
+  explicit PrecisionScope(sgtn_h h) { g_compute_f32 = h->precision == SGTN_FP32; }
+  ~PrecisionScope() { g_compute_f32 = false; }
+};
+
 int sgtn_conditionals(sgtn_h h, int32_t step, int32_t count, const int32_t* configs, double* out_p) {
-  return guarded(h, [&] { conditionals(h, step, count, configs, out_p); });
+  return guarded(h, [&] {
+    PrecisionScope ps(h);
+    conditionals(h, step, count, configs, out_p);
+  });
 }
 
 int sgtn_branch_step(sgtn_h h, int32_t step, int32_t M, int32_t in_count, const int32_t* in_configs,
                      const double* in_logp, int32_t* out_configs, double* out_logp, int32_t* out_count,
                      double* io_pd) {
-  return guarded(h, [&] { branch_step(h, step, M, in_count, in_configs, in_logp, out_configs, out_logp, out_count, io_pd); });
+  return guarded(h, [&] {
+    PrecisionScope ps(h);
+    branch_step(h, step, M, in_count, in_configs, in_logp, out_configs, out_logp, out_count, io_pd);
+  });
 }
 
 int sgtn_search(sgtn_h h, int32_t M, int32_t n_out, int8_t* out_spins, int64_t* out_energy_num, double* out_logp,
                 double* out_pd, int32_t* out_count) {
-  return guarded(h, [&] { search(h, M, n_out, out_spins, out_energy_num, out_logp, out_pd, out_count); });
+  return guarded(h, [&] {
+    PrecisionScope ps(h);
+    search(h, M, n_out, out_spins, out_energy_num, out_logp, out_pd, out_count);
+  });
 }
 
 int sgtn_logz_grad(sgtn_h h, double* dJ, double* dh, double* dbeta) {
@@ -152,6 +175,13 @@ int sgtn_energies(sgtn_h h, int32_t n, const int8_t* spins, int64_t* out) {
   return guarded(h, [&] {
     if (n < 0 || (n > 0 && (!spins || !out))) throw SgtnError(SGTN_ERR_ARG, "bad argument");
     energies(h, n, spins, out);
+  });
+}
+
+int sgtn_boundary_info(sgtn_h h, int32_t* unconverged_cuts, int32_t* precision) {
+  return guarded(h, [&] {
+    if (unconverged_cuts) *unconverged_cuts = h->unconverged_cuts;
+    if (precision) *precision = h->precision;
   });
 }
 

@@ -33,6 +33,14 @@
 namespace sgtn {
 namespace detail {
 
+// Linear algebra of the truncation (SVDs, orthonormalisations, canonical forms)
+// always runs in FP64, also when the contractions are FP32.
+struct F64Scope {
+  bool saved;
+  F64Scope() : saved(g_compute_f32) { g_compute_f32 = false; }
+  ~F64Scope() { g_compute_f32 = saved; }
+};
+
 double* dmalloc(long long n) {
   double* p = nullptr;
   SGTN_CUDA(cudaMalloc(&p, size_t(n > 0 ? n : 1) * sizeof(double)));
@@ -53,6 +61,7 @@ SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, co
 // the shorter side when it is short, otherwise subspace iteration with a
 // Rayleigh-Ritz step (converged to the same top singular subspace).
 SvdOut svd(sgtn_inst* h, const double* Th, int m, int n, int cap) {
+  F64Scope f64;
   int p = std::min(m, n);
   if (p <= h->dense_svd_max || cap >= p) return svd_dense(h, Th, m, n, cap);
   return svd_subspace(h, Th, m, n, cap);
@@ -135,6 +144,7 @@ SvdOut svd_subspace(sgtn_inst* h, const double* Th, int m, int n, int cap) {
 
 // Same, with Theta given only through Y = Theta Q and Z = Theta^T Y.
 SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, const MatFn& tmul) {
+  F64Scope f64;
   cudaStream_t st = h->st;
   const int p = std::min(m, n);
   const int s = std::min(p, cap + 32);
@@ -180,7 +190,7 @@ SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, co
     copy(Z0, Q, (long long)n * s, st);
     orth(Z0, n, k_active, Q);
   }
-  const int maxit = 300;
+  const int maxit = 200;
   int it = 0;
   for (; it < maxit; ++it) {
     mul(Q, k_active, Y);                                                                     // Y = Theta Q
@@ -200,7 +210,9 @@ SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, co
     k_active = kn;
     if (it >= 2 && ch < 1e-13 * std::sqrt(double(kc))) break;
   }
-  if (it >= maxit) throw SgtnError(-4, "subspace iteration did not converge (no gap at the cut?)");
+  // no gap at the cut: the truncation is ambiguous; keep the Rayleigh-Ritz
+  // result of the last subspace and count the cut
+  if (it >= maxit) ++h->unconverged_cuts;
   // Rayleigh-Ritz: B = Theta Q (m x s), exact SVD of B
   mul(Q, k_active, Y);
   SvdOut ob = svd_dense(h, Y, m, k_active, cap);    // Y = U S W^T  (W: Vt rows, length k_active)
@@ -385,6 +397,7 @@ double* update_R(RowCtx& X, int c, const double* ThR, const Ten& phi) {
 }
 
 void right_canonical(RowCtx& X, std::vector<Ten>& phi) {
+  F64Scope f64;
   sgtn_inst* h = X.h;
   for (int c = (int)phi.size() - 1; c > 0; --c) {
     Ten& t = phi[c];
@@ -690,6 +703,7 @@ void variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
 
 // cut a right-canonical phi (centre 0) to bond chi; returns worst retained ratio
 double svd_cut(RowCtx& X, std::vector<Ten>& phi, int chi) {
+  F64Scope f64;
   sgtn_inst* h = X.h;
   double worst = 0.0;
   for (int c = 0; c + 1 < (int)phi.size(); ++c) {
@@ -715,6 +729,7 @@ double svd_cut(RowCtx& X, std::vector<Ten>& phi, int chi) {
 }
 
 void left_canonical(sgtn_inst* h, MPS& A) {
+  F64Scope f64;
   const int C = A.C;
   for (int c = 0; c + 1 < C; ++c) {
     int s = A.phys[c], l = A.bond[c], r = A.bond[c + 1];
@@ -898,6 +913,7 @@ void contract_boundary(sgtn_inst* h, int chi, int n_sweeps) {
   last.lognorm = 0.0;
   last.valid = true;
   double worst = 0.0;
+  h->unconverged_cuts = 0;
   for (int r = R - 1; r >= 1; --r) row_step(h, r, chi, n_sweeps, h->psi[r - 1], worst);
   h->logz = h->log_offset + top_overlap(h);
   h->worst_sv = worst;

@@ -130,29 +130,31 @@ __global__ void colnorm_kernel(double* X, long long rows, int K) {
 }
 
 // s[k][x] for all branches k (threads) of one state x (block)
+template <class CT>
 __global__ void score_kernel(int K, int d, int chl, int chr, int nG, int nE, int nPdr, const double* E,
                              const double* Ahat, const double* Ft, const double* f, const double* w,
                              const int32_t* lam_x, const int32_t* u_x, const int32_t* pd_x, const int32_t* pr_x,
                              const int32_t* pdr_x, double* s) {
-  extern __shared__ double As[];   // chl * chr
+  extern __shared__ unsigned char smraw[];
+  CT* As = reinterpret_cast<CT*>(smraw);   // chl * chr
   int x = blockIdx.x;
-  double acc[4] = {0, 0, 0, 0};
+  CT acc[4] = {0, 0, 0, 0};
   for (int g = 0; g < nG; ++g)
     for (int e = 0; e < nE; ++e) {
       const double* A = Ahat + (((long long)pd_x[x] * nE + e) * nG + g) * chl * chr;
       __syncthreads();
-      for (int i = threadIdx.x; i < chl * chr; i += blockDim.x) As[i] = A[i];
+      for (int i = threadIdx.x; i < chl * chr; i += blockDim.x) As[i] = CT(A[i]);
       __syncthreads();
       const double* Eb = E + (long long)(lam_x[x] * nG + g) * chl * K;
       const double* Fb = Ft + (((long long)pr_x[x] * nE + e) * nPdr + pdr_x[x]) * chr * K;
       for (int j = 0; j < 4; ++j) {
         int k = threadIdx.x + j * blockDim.x;
         if (k >= K) break;
-        double a2 = 0;
+        CT a2 = 0;
         for (int ar = 0; ar < chr; ++ar) {
-          double t = 0;
-          for (int al = 0; al < chl; ++al) t = fma(Eb[(long long)al * K + k], As[al * chr + ar], t);
-          a2 = fma(t, Fb[(long long)ar * K + k], a2);
+          CT t = 0;
+          for (int al = 0; al < chl; ++al) t = fma(CT(Eb[(long long)al * K + k]), As[al * chr + ar], t);
+          a2 = fma(t, CT(Fb[(long long)ar * K + k]), a2);
         }
         acc[j] += a2;
       }
@@ -160,7 +162,7 @@ __global__ void score_kernel(int K, int d, int chl, int chr, int nG, int nE, int
   for (int j = 0; j < 4; ++j) {
     int k = threadIdx.x + j * blockDim.x;
     if (k >= K) break;
-    s[(long long)k * d + x] = f[(long long)u_x[x] * K + k] * w[x] * acc[j];
+    s[(long long)k * d + x] = f[(long long)u_x[x] * K + k] * w[x] * double(acc[j]);
   }
 }
 
@@ -480,10 +482,19 @@ void prepare_scores(Step& S, const int32_t* hcfg) {
   S.s = S.alloc<double>(size_t(K) * D.d);
   int thr = std::min(256, std::max(32, ((K + 3) / 4 + 31) / 32 * 32));
   if (K > 4 * thr) throw SgtnError(-1, "beam too large for the score kernel");
-  KTimer tsc("score_f64", st, 2.0 * K * D.d * (double)Kc.nG * Kc.nE * chl * (chr + 1));
-  score_kernel<<<D.d, thr, size_t(chl) * chr * sizeof(double), st>>>(K, D.d, chl, chr, Kc.nG, Kc.nE, Kc.nPdr, S.E,
-                                                                      S.Ahat[c], S.Ft, S.f[c], D.w, D.lam_x, D.u_x,
-                                                                      D.cls[DD], D.cls[DR_], D.cls[DDR], S.s); ++g_count.launches;
+  double sc_fl = 2.0 * K * D.d * (double)Kc.nG * Kc.nE * chl * (chr + 1);
+  if (g_compute_f32) {
+    KTimer tsc("score_f32", st, sc_fl);
+    score_kernel<float><<<D.d, thr, size_t(chl) * chr * sizeof(float), st>>>(
+        K, D.d, chl, chr, Kc.nG, Kc.nE, Kc.nPdr, S.E, S.Ahat[c], S.Ft, S.f[c], D.w, D.lam_x, D.u_x, D.cls[DD],
+        D.cls[DR_], D.cls[DDR], S.s);
+  } else {
+    KTimer tsc("score_f64", st, sc_fl);
+    score_kernel<double><<<D.d, thr, size_t(chl) * chr * sizeof(double), st>>>(
+        K, D.d, chl, chr, Kc.nG, Kc.nE, Kc.nPdr, S.E, S.Ahat[c], S.Ft, S.f[c], D.w, D.lam_x, D.u_x, D.cls[DD],
+        D.cls[DR_], D.cls[DDR], S.s);
+  }
+  ++g_count.launches;
   h->check();
   (void)R;
 }

@@ -79,7 +79,8 @@ struct sgtn_inst {
   sgtn::Scratch ws;
   int32_t* iota = nullptr;                // 0..iota_n-1
   int dense_svd_max = 320;
-  long long bs_min_entries = 1ll << 22;   // keep Theta block-sparse when dense would exceed this
+  long long bs_min_entries = 1ll << 22;
+  int unconverged_cuts = 0;               // iterative truncations stopped at their cap (no gap)   // keep Theta block-sparse when dense would exceed this
   int32_t *d_ei = nullptr, *d_ej = nullptr, *d_jn = nullptr, *d_hn = nullptr;   // edges for energies                // exact Jacobi up to this many vectors, subspace iteration above
   int iota_n = 0;
 

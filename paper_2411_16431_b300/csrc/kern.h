@@ -15,6 +15,9 @@ struct Counters {
   long long evals = 0;
 };
 extern Counters g_count;
+// When set, every contraction (seg_gemm / gemm) multiplies and accumulates in
+// FP32; the SVDs, norms and log-norms stay FP64.  Set per call from the handle.
+extern bool g_compute_f32;
 
 // Optional per-kernel timing with CUDA events on the launching stream.
 // KTimer brackets one launch; pairs are resolved when read.
@@ -51,6 +54,7 @@ struct SegGemm {
   long long cs_ld = 0;
   int nseg = 1;
   int out_by_seg = 0;    // table mode: output block offset = segment index * ors
+  int f32 = 0;           // multiply-accumulate in FP32 (inputs and outputs stay FP64)
   long long nterm = 0;   // host-side term count for the FLOP counter (table mode)
   double alpha = 1.0;
   int accumulate = 0;

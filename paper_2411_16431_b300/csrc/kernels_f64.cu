@@ -22,18 +22,19 @@ struct SegDev {
   SegGemm a;
 };
 
+template <class CT>
 __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
-  __shared__ double Xs[TK][TM + 1];
-  __shared__ double Ys[TK][TN + 1];
+  __shared__ CT Xs[TK][TM + 1];
+  __shared__ CT Ys[TK][TN + 1];
   const int seg = blockIdx.x;
   const int i0 = blockIdx.y * TM, j0 = blockIdx.z * TN;
   const int tid = threadIdx.x;
   const int ty = tid / 16, tx = tid % 16;
-  double acc[4][4];
+  CT acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+    for (int v = 0; v < 4; ++v) acc[u][v] = CT(0);
   int t0, t1;
   long long ooff;
   if (a.seg_ptr) {
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
       for (int e = tid; e < TM * TK; e += 256) {
         int ii = e / TK, kk = e % TK;
         int i = i0 + ii, k = k0 + kk;
-        Xs[kk][ii] = (i < a.p && k < a.q) ? a.X[xoff + i * a.xs_i + k * a.xs_k] : 0.0;
+        Xs[kk][ii] = (i < a.p && k < a.q) ? CT(a.X[xoff + i * a.xs_i + k * a.xs_k]) : CT(0);
       }
       for (int e = tid; e < TK * TN; e += 256) {
         int kk = e / TN, jj = e % TN;
@@ -73,12 +74,12 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
           v = cf * a.Y[yoff + k * a.ys_k + j * a.ys_j];
           if (cs) v *= cs[j];
         }
-        Ys[kk][jj] = v;
+        Ys[kk][jj] = CT(v);
       }
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < TK; ++kk) {
-        double xv[4], yv[4];
+        CT xv[4], yv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) xv[u] = Xs[kk][ty * 4 + u];
 #pragma unroll
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
       int j = j0 + tx * 4 + v;
       if (j >= a.s) continue;
       double* o = a.O + ooff + i * a.os_i + j * a.os_j;
-      double val = a.alpha * acc[u][v];
+      double val = a.alpha * double(acc[u][v]);
       *o = a.accumulate ? *o + val : val;
     }
   }
@@ -545,17 +546,24 @@ std::string ktimer_names() {
   return o;
 }
 
-void seg_gemm(const SegGemm& a, cudaStream_t st) {
+void seg_gemm(const SegGemm& a_in, cudaStream_t st) {
+  SegGemm a = a_in;
+  if (g_compute_f32) a.f32 = 1;
   if (a.nseg <= 0 || a.p <= 0 || a.s <= 0) return;
   dim3 grid(a.nseg, (a.p + TM - 1) / TM, (a.s + TN - 1) / TN);
   double fl = 2.0 * a.p * a.q * a.s * double(a.seg_ptr ? a.nterm : a.nseg);
-  {
+  if (a.f32) {
+    KTimer t("seg_gemm_f32", st, fl);
+    seg_gemm_kernel<float><<<grid, 256, 0, st>>>(a);
+  } else {
     KTimer t("seg_gemm_f64", st, fl);
-    seg_gemm_kernel<<<grid, 256, 0, st>>>(a);
+    seg_gemm_kernel<double><<<grid, 256, 0, st>>>(a);
   }
   ++g_count.launches;
   g_count.flops += fl;
 }
+
+bool g_compute_f32 = false;
 
 void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, long long ldy, double* O, long long ldo,
           int m, int n, int k, double alpha, int accumulate, cudaStream_t st) {

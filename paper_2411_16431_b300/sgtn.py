@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsgtn.so")
 _lib = None
 
-FP64, TF32, BF16 = 0, 1, 2
+FP64, TF32, BF16, FP32 = 0, 1, 2, 3
 
 _I32P = ct.POINTER(ct.c_int32)
 _I64P = ct.POINTER(ct.c_int64)
@@ -42,6 +42,7 @@ def load():
     L.sgtn_energies.argtypes = [ct.c_void_p, ct.c_int32, _I8P, _I64P]
     L.sgtn_logz_grad.argtypes = [ct.c_void_p, _F64P, _F64P, _F64P]
     L.sgtn_site_dims.argtypes = [ct.c_void_p, ct.c_int32, _I32P]
+    L.sgtn_boundary_info.argtypes = [ct.c_void_p, _I32P, _I32P]
     L.sgtn_mps_shape.argtypes = [ct.c_void_p, ct.c_int32, _I32P, _I32P, _F64P]
     L.sgtn_mps_tensor.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _F64P]
     L.sgtn_stats.argtypes = [_I64P, _F64P, _I64P]
@@ -139,6 +140,12 @@ class Handle:
         ws = ct.c_double()
         self._ck(self.L.sgtn_contract_boundary(self.h, chi, precision, n_sweeps, ct.byref(lz), ct.byref(ws)))
         return lz.value, ws.value
+
+    def boundary_info(self):
+        """(iterative truncations stopped at their cap, precision of the boundary)."""
+        u, p = ct.c_int32(), ct.c_int32()
+        self._ck(self.L.sgtn_boundary_info(self.h, ct.byref(u), ct.byref(p)))
+        return u.value, p.value
 
     def conditionals(self, step, configs):
         configs = np.ascontiguousarray(np.asarray(configs, np.int32).reshape(-1, step) if step else

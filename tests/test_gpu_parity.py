@@ -259,3 +259,25 @@ def test_block_sparse_theta_matches_oracle(Handle, case, svd_max, monkeypatch):
     res = h.search(16)
     assert np.array_equal(res["energy_num"], ref["energy_num"])
     assert np.allclose(res["logp"], ref["logp"], rtol=RTOL)
+
+
+MIXED_CASES = [(L.chimera_grid(4, 4, 0), None, 1.0, 16, 2), (L.kings_grid(5, 6, 4), None, 1.0, 3, 2),
+               (PEGP, PEGP_STATES, 2.0, 8, 2)]
+
+
+@pytest.mark.parametrize("case", MIXED_CASES, ids=lambda c: c[0].name)
+def test_mixed_precision_error_is_small(Handle, case):
+    """FP32 contractions with FP64 truncation: log Z within 1e-6 relative of the FP64 oracle,
+    marginals within 1e-4, same final configuration and exact int64 energy."""
+    from paper_2411_16431_b300.sgtn import FP32
+    inst, states, beta, chi, ns = case
+    lz_o, psis, mpos = boundary_mps(PottsModel(inst, states), beta, chi, ns)
+    h = Handle(inst, states)
+    h.set_beta(beta)
+    lz, _ = h.contract_boundary(chi, precision=FP32, n_sweeps=ns)
+    assert abs(lz - lz_o) < 1e-6 * abs(lz_o)
+    assert h.boundary_info()[1] == FP32
+    ref = oracle_search(inst, beta, chi=chi, M=16, n_sweeps=ns, states=states)
+    res = h.search(16)
+    assert np.array_equal(res["energy_num"], ref["energy_num"])
+    assert np.allclose(res["logp"], ref["logp"], rtol=1e-4)
