@@ -53,6 +53,7 @@ void dfree(double*& p) {
 
 double norm_host(sgtn_inst* h, const double* x, long long n, bool allow_zero);
 SvdOut svd_dense(sgtn_inst* h, const double* Th, int m, int n, int cap);
+double* left_factor(sgtn_inst* h, const SvdOut& o, int m);
 SvdOut svd_subspace(sgtn_inst* h, const double* Th, int m, int n, int cap);
 using MatFn = std::function<void(const double* Q, int s, double* Y)>;
 SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, const MatFn& tmul);
@@ -67,8 +68,99 @@ SvdOut svd(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   return svd_subspace(h, Th, m, n, cap);
 }
 
-// Exact truncated SVD by one-sided Jacobi on the shorter side.
+SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap);
+bool svd_tall_cqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o);
+
+// Exact truncated SVD: for a tall-skinny (or short-fat) matrix with a short
+// side of at most 110, shifted CholeskyQR3 then a one-sided Jacobi SVD of the
+// small triangular factor; otherwise (or if a Cholesky pivot fails, i.e. the
+// vectors are exactly dependent) one-sided Jacobi on the shorter side.
 SvdOut svd_dense(sgtn_inst* h, const double* Th, int m, int n, int cap) {
+  SvdOut o;
+  int p = std::min(m, n), q = std::max(m, n);
+  if (p <= 110 && q >= 2 * p && q >= 256) {
+    if (m >= n) {
+      if (svd_tall_cqr(h, Th, m, n, cap, o)) return o;
+    } else {
+      // M (m x n, short-fat): factor M^T = U S V^T, then M = V S U^T
+      double* Mt = h->ws.get<double>("svd_Mt", size_t(m) * n);
+      int dims[2] = {m, n}, perm[2] = {1, 0};
+      permute_nd(Th, 2, dims, perm, Mt, h->st);
+      SvdOut t;
+      if (svd_tall_cqr(h, Mt, n, m, cap, t)) {
+        o.k = t.k;
+        o.sig = t.sig;
+        o.dsig = t.dsig;
+        t.dsig = nullptr;
+        // US(M) = (Vt_t)^T S : m x k ; Vt(M) = (US_t / S)^T : k x n
+        o.US = dmalloc((long long)m * o.k);
+        gather_vecs(t.Vt, m, 1, m, h->iota, o.dsig, o.k, o.US, o.k, 1, h->st);
+        o.Vt = dmalloc((long long)o.k * n);
+        gather_vecs(t.US, n, t.k, 1, h->iota, o.dsig + o.k, o.k, o.Vt, 1, n, h->st);
+        t.release();
+        return o;
+      }
+    }
+  }
+  return svd_jacobi(h, Th, m, n, cap);
+}
+
+// M (m x n, m >= n, row-major) = Q R by shifted CholeskyQR3, then R = U S V^T
+// by one-sided Jacobi.  Returns false (nothing allocated) if a pivot fails.
+bool svd_tall_cqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o) {
+  cudaStream_t st = h->st;
+  double* G = h->ws.get<double>("cq_G", size_t(n) * n);
+  double* R = h->ws.get<double>("cq_R", size_t(n) * n);
+  double* Ri = h->ws.get<double>("cq_Ri", size_t(n) * n);
+  double* Racc = h->ws.get<double>("cq_Racc", size_t(n) * n);
+  double* Rtmp = h->ws.get<double>("cq_Rtmp", size_t(n) * n);
+  double* Qa = h->ws.get<double>("cq_Qa", size_t(m) * n);
+  double* Qb = h->ws.get<double>("cq_Qb", size_t(m) * n);
+  int* status = h->ws.get<int>("cq_status", 4);
+  const double* cur = M;
+  double* outQ[3] = {Qa, Qb, Qa};
+  // shift for the first pass: 11 (m n + n (n+1)) eps ||M||_2^2, with ||M||_2^2 <= trace(M^T M)
+  gemm(M, true, n, M, false, n, G, n, n, n, m, 1.0, 0, st);
+  std::vector<double> hG(size_t(n) * n);
+  SGTN_CUDA(cudaMemcpyAsync(hG.data(), G, hG.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  h->sync();
+  double tr = 0;
+  for (int i = 0; i < n; ++i) tr += hG[size_t(i) * n + i];
+  if (!(tr > 0) || !std::isfinite(tr)) return false;
+  double shift = 11.0 * (double(m) * n + double(n) * (n + 1)) * 2.220446049250313e-16 * tr;
+  for (int pass = 0; pass < 3; ++pass) {
+    if (pass > 0) gemm(cur, true, n, cur, false, n, G, n, n, n, m, 1.0, 0, st);
+    cholesky_inv(G, n, pass == 0 ? shift : 0.0, R, Ri, status + pass, st);
+    gemm(cur, false, n, Ri, false, n, outQ[pass], n, m, n, n, 1.0, 0, st);
+    if (pass == 0) {
+      copy(Racc, R, (long long)n * n, st);
+    } else {
+      gemm(R, false, n, Racc, false, n, Rtmp, n, n, n, n, 1.0, 0, st);
+      copy(Racc, Rtmp, (long long)n * n, st);
+    }
+    cur = outQ[pass];
+  }
+  int hs[3];
+  SGTN_CUDA(cudaMemcpyAsync(hs, status, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  h->sync();
+  if (hs[0] || hs[1] || hs[2]) return false;
+  // SVD of the n x n factor: Racc V = W, sigma = |W_j|
+  SvdOut r = svd_jacobi(h, Racc, n, n, cap);
+  // M = Q Racc = (Q U_R) S V^T :  US = Q (U_R S) = Q r.US ; Vt = r.Vt
+  o.k = r.k;
+  o.sig = r.sig;
+  o.dsig = r.dsig;
+  r.dsig = nullptr;
+  o.Vt = r.Vt;
+  r.Vt = nullptr;
+  o.US = dmalloc((long long)m * o.k);
+  gemm(cur, false, n, r.US, false, o.k, o.US, o.k, m, o.k, n, 1.0, 0, st);
+  r.release();
+  return true;
+}
+
+// Exact truncated SVD by one-sided Jacobi on the shorter side.
+SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   cudaStream_t st = h->st;
   SvdOut o;
   double* T2 = h->ws.get<double>("svd_T2", size_t(m) * n);
@@ -156,34 +248,12 @@ SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, co
   int* status = h->ws.get<int>("ss_status", 1);
   pseudo_random(Q, (long long)n * s, 12345, st);
   int k_active = s;
+  // orthonormal basis of the columns of Z (len x kk), ordered by singular value
   auto orth = [&](double* Z, int len, int& kk, double* out) {
-    // Z (len x kk, row-major) -> orthonormal columns in out (len x kk') by Jacobi
-    jacobi(Z, len, kk, kk, 1, nullptr, 60, status, st);
-    vec_norms(Z, len, kk, kk, 1, sig, st);
-    std::vector<double> hs(kk);
-    SGTN_CUDA(cudaMemcpyAsync(hs.data(), sig, kk * sizeof(double), cudaMemcpyDeviceToHost, st));
-    h->sync();
-    std::vector<int> idx(kk);
-    std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return hs[a] > hs[b]; });
-    double mx = hs[idx[0]];
-    if (!(mx > 0) || !std::isfinite(mx)) throw SgtnError(-4, "zero or non-finite block in subspace iteration");
-    int k2 = 0;
-    std::vector<int32_t> perm;
-    std::vector<double> inv;
-    for (int i = 0; i < kk; ++i)
-      if (hs[idx[i]] > 1e-14 * mx) {
-        perm.push_back(idx[i]);
-        inv.push_back(1.0 / hs[idx[i]]);
-        ++k2;
-      }
-    int32_t* dperm = h->ws.get<int32_t>("ss_perm", k2);
-    double* dinv = h->ws.get<double>("ss_inv", k2);
-    SGTN_CUDA(cudaMemcpyAsync(dperm, perm.data(), k2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    SGTN_CUDA(cudaMemcpyAsync(dinv, inv.data(), k2 * sizeof(double), cudaMemcpyHostToDevice, st));
-    gather_vecs(Z, len, kk, 1, dperm, dinv, k2, out, k2, 1, st);
-    h->sync();
-    kk = k2;
+    SvdOut o = svd_dense(h, Z, len, kk, kk);
+    gather_vecs(o.US, len, o.k, 1, h->iota, o.dsig + o.k, o.k, out, o.k, 1, st);
+    kk = o.k;
+    o.release();
   };
   {
     double* Z0 = h->ws.get<double>("ss_Z", size_t(n) * s);

@@ -71,6 +71,10 @@ void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, lon
 // rotations.  status[0] = sweeps used, or -1 if max_sweeps ran out.
 void jacobi(double* X, int len, int p, long long si, long long sj, double* V, int max_sweeps, int* status,
             cudaStream_t st);
+// Upper Cholesky factor R of (G + shift I) (n x n, row-major; R^T R = G + shift I)
+// and R^{-1}, one CTA.  status[0] = 0 on success, j+1 if pivot j was not positive.
+void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv, int* status, cudaStream_t st);
+double* trace_scratch();
 void vec_norms(const double* X, int len, int p, long long si, long long sj, double* out, cudaStream_t st);
 // out[i*oi + jj*oj] = scale[jj] * X[i*si + perm[jj]*sj]
 void gather_vecs(const double* X, int len, long long si, long long sj, const int32_t* perm, const double* scale,

@@ -303,6 +303,53 @@ __global__ void __launch_bounds__(128) jacobi_coop_kernel(double* X, int len, in
   if (blockIdx.x == 0 && threadIdx.x == 0) status[0] = done ? sweep : -1;
 }
 
+// Right-looking upper Cholesky in shared memory, then R^{-1} column by column.
+__global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* G, int n, double shift, double* R,
+                                                            double* Rinv, int* status) {
+  extern __shared__ double A[];   // n x n
+  __shared__ int fail;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int i = e / n, j = e % n;
+    A[e] = G[e] + (i == j ? shift : 0.0);
+  }
+  if (threadIdx.x == 0) fail = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double d = A[j * n + j];
+      if (!(d > 0.0)) {
+        if (!fail) fail = j + 1;
+        A[j * n + j] = 1.0;
+      } else {
+        A[j * n + j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    double r = A[j * n + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[j * n + i] /= r;
+    __syncthreads();
+    int m = n - j - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      int k = j + 1 + e / m, i = j + 1 + e % m;
+      if (i >= k) A[k * n + i] -= A[j * n + k] * A[j * n + i];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int i = e / n, j = e % n;
+    R[e] = j >= i ? A[e] : 0.0;
+  }
+  // R X = I, one column per thread, back substitution
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    for (int i = n - 1; i >= 0; --i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= c; ++k) v -= A[i * n + k] * Rinv[k * n + c];
+      Rinv[i * n + c] = (i <= c) ? v / A[i * n + i] : 0.0;
+    }
+  }
+  if (threadIdx.x == 0) status[0] = fail;
+}
+
 __global__ void vec_norms_kernel(const double* X, int len, int p, long long si, long long sj, double* out) {
   int j = blockIdx.x;
   double a = 0;
@@ -623,6 +670,16 @@ void jacobi(double* X, int len, int p, long long si, long long sj, double* V, in
       cudaLaunchCooperativeKernel((void*)jacobi_coop_kernel, dim3(nblk), dim3(128), args, 0, st);
     }
   }
+  ++g_count.launches;
+}
+
+void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv, int* status, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(cholesky_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr = true;
+  }
+  cholesky_inv_kernel<<<1, 1024, size_t(n) * n * sizeof(double), st>>>(G, n, shift, R, Rinv, status);
   ++g_count.launches;
 }
 

@@ -281,3 +281,19 @@ def test_mixed_precision_error_is_small(Handle, case):
     res = h.search(16)
     assert np.array_equal(res["energy_num"], ref["energy_num"])
     assert np.allclose(res["logp"], ref["logp"], rtol=1e-4)
+
+
+def test_tall_skinny_svd_path_matches_oracle(Handle, monkeypatch):
+    """Cases whose truncations are tall-skinny enough for the CholeskyQR route."""
+    inst, beta, chi = L.chimera_grid(3, 8, 2), 1.2, 8
+    lz_o, _, _ = boundary_mps(PottsModel(inst), beta, chi, 2)
+    h = Handle(inst)
+    h.set_beta(beta)
+    lz, _ = h.contract_boundary(chi, n_sweeps=2)
+    assert abs(lz - lz_o) < RTOL * abs(lz_o)
+    monkeypatch.setenv("SGTN_BS_MIN_ENTRIES", "0")
+    monkeypatch.setenv("SGTN_DENSE_SVD_MAX", "8")
+    h2 = Handle(inst)
+    h2.set_beta(beta)
+    lz2, _ = h2.contract_boundary(chi, n_sweeps=2)
+    assert abs(lz2 - lz_o) < RTOL * abs(lz_o)
