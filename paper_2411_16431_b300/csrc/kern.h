@@ -55,6 +55,7 @@ struct SegGemm {
   int nseg = 1;
   int out_by_seg = 0;    // table mode: output block offset = segment index * ors
   int f32 = 0;           // multiply-accumulate in FP32 (inputs and outputs stay FP64)
+  int splitk = 0;        // uniform mode: segment t sums k in [t*splitk, (t+1)*splitk) of one product
   long long nterm = 0;   // host-side term count for the FLOP counter (table mode)
   double alpha = 1.0;
   int accumulate = 0;

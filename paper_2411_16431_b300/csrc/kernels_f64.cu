@@ -2,6 +2,7 @@
 // that evaluates the sparse site diagrams of Fig. 7 (and plain GEMMs), the
 // one-sided Jacobi SVD used for every truncation and orthonormalisation
 // (Hestenes 1958; Demmel & Veselic 1992), and small helpers.
+#include <algorithm>
 #include <array>
 #include <cmath>
 #include <map>
@@ -37,6 +38,11 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
     for (int v = 0; v < 4; ++v) acc[u][v] = CT(0);
   int t0, t1;
   long long ooff;
+  int qlen = a.q;
+  if (a.splitk) {
+    int k_lo = seg * a.splitk;
+    qlen = min(a.splitk, a.q - k_lo);
+  }
   if (a.seg_ptr) {
     t0 = a.seg_ptr[seg];
     t1 = a.seg_ptr[seg + 1];
@@ -55,22 +61,25 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
       yoff = (long long)a.yr[t] * a.yrs + (long long)a.yc[t] * a.ycs;
       if (a.coef) cf = a.coef[a.cidx[t]];
       if (a.cs) cs = a.cs + (long long)a.csrow[t] * a.cs_ld;
+    } else if (a.splitk) {
+      xoff = (long long)t * a.splitk * a.xs_k;
+      yoff = (long long)t * a.splitk * a.ys_k;
     } else {
       xoff = (long long)t * a.xrs;
       yoff = (long long)t * a.yrs;
     }
-    for (int k0 = 0; k0 < a.q; k0 += TK) {
+    for (int k0 = 0; k0 < qlen; k0 += TK) {
       // X tile: TM x TK ; Y tile: TK x TN
       for (int e = tid; e < TM * TK; e += 256) {
         int ii = e / TK, kk = e % TK;
         int i = i0 + ii, k = k0 + kk;
-        Xs[kk][ii] = (i < a.p && k < a.q) ? CT(a.X[xoff + i * a.xs_i + k * a.xs_k]) : CT(0);
+        Xs[kk][ii] = (i < a.p && k < qlen) ? CT(a.X[xoff + i * a.xs_i + k * a.xs_k]) : CT(0);
       }
       for (int e = tid; e < TK * TN; e += 256) {
         int kk = e / TN, jj = e % TN;
         int k = k0 + kk, j = j0 + jj;
         double v = 0.0;
-        if (k < a.q && j < a.s) {
+        if (k < qlen && j < a.s) {
           v = cf * a.Y[yoff + k * a.ys_k + j * a.ys_j];
           if (cs) v *= cs[j];
         }
@@ -435,6 +444,17 @@ __global__ void scale_by_inv_kernel(double* x, long long n, const double* norm) 
     x[i] *= s;
 }
 
+// O = alpha * sum_t P[t] (+ O)
+__global__ void splitk_reduce_kernel(const double* P, int nsplit, long long mn, int n, double* O, long long ldo,
+                                     double alpha, int accumulate) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mn; e += (long long)gridDim.x * blockDim.x) {
+    double v = 0;
+    for (int t = 0; t < nsplit; ++t) v += P[t * mn + e];
+    double* o = O + (e / n) * ldo + (e % n);
+    *o = accumulate ? *o + alpha * v : alpha * v;
+  }
+}
+
 __global__ void pseudo_random_kernel(double* x, long long n, unsigned long long seed) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
@@ -598,7 +618,7 @@ void seg_gemm(const SegGemm& a_in, cudaStream_t st) {
   if (g_compute_f32) a.f32 = 1;
   if (a.nseg <= 0 || a.p <= 0 || a.s <= 0) return;
   dim3 grid(a.nseg, (a.p + TM - 1) / TM, (a.s + TN - 1) / TN);
-  double fl = 2.0 * a.p * a.q * a.s * double(a.seg_ptr ? a.nterm : a.nseg);
+  double fl = 2.0 * a.p * a.q * a.s * double(a.seg_ptr ? a.nterm : (a.splitk ? 1 : a.nseg));
   if (a.f32) {
     KTimer t("seg_gemm_f32", st, fl);
     seg_gemm_kernel<float><<<grid, 256, 0, st>>>(a);
@@ -630,6 +650,35 @@ void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, lon
   a.nseg = 1;
   a.alpha = alpha;
   a.accumulate = accumulate;
+  long long tiles = (long long)((m + TM - 1) / TM) * ((n + TN - 1) / TN);
+  if (tiles < 148 && k >= 1024) {
+    // few output tiles and a long reduction: split K over CTAs, then reduce
+    int nsplit = int(std::min<long long>((k + 255) / 256, std::max<long long>(2, 592 / tiles)));
+    int chunk = ((k + nsplit - 1) / nsplit + TK - 1) / TK * TK;
+    nsplit = (k + chunk - 1) / chunk;
+    static double* part = nullptr;
+    static size_t part_n = 0;
+    size_t need = size_t(nsplit) * m * n;
+    if (need > part_n) {
+      if (part) cudaFree(part);
+      cudaMalloc(&part, need * sizeof(double));
+      part_n = need;
+    }
+    SegGemm b = a;
+    b.O = part;
+    b.os_i = n;
+    b.os_j = 1;
+    b.ors = (long long)m * n;
+    b.nseg = nsplit;
+    b.splitk = chunk;
+    b.alpha = 1.0;
+    b.accumulate = 0;
+    seg_gemm(b, st);
+    splitk_reduce_kernel<<<blocks_for((long long)m * n), 256, 0, st>>>(part, nsplit, (long long)m * n, n, O, ldo, alpha,
+                                                                        accumulate);
+    ++g_count.launches;
+    return;
+  }
   seg_gemm(a, st);
 }
 
