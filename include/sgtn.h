@@ -46,7 +46,9 @@ typedef enum {
 /* SGTN_FP64: everything in double.  SGTN_FP32 (mixed): every contraction
  * (site diagrams, environments, projections, conditional scores) multiplies
  * and accumulates in FP32 while tensors are stored, truncated (SVD) and
- * normalised (log-norms) in FP64.  TF32 / BF16 are reserved. */
+ * normalised (log-norms) in FP64.  SGTN_TF32 (mixed, tensor cores): as FP32,
+ * and dense GEMMs large enough for 128 x 128 tiles run on the tcgen05 tensor
+ * cores with 3xTF32 splitting (about FP32 accuracy).  BF16 is reserved. */
 typedef enum { SGTN_FP64 = 0, SGTN_TF32 = 1, SGTN_BF16 = 2, SGTN_FP32 = 3 } sgtn_precision;
 
 /* Build the generalized Potts model of Sec. III, Eqs. (2)-(4): cluster

@@ -78,6 +78,20 @@ int guarded(sgtn_h h, F&& f) {
 }
 }  // namespace
 
+// Contractions run in the handle's precision: FP32 arithmetic for SGTN_FP32,
+// plus tcgen05 tensor cores for large dense GEMMs for SGTN_TF32.  The branch
+// step and the search use the precision of the last contract_boundary.
+struct PrecisionScope {
+  explicit PrecisionScope(sgtn_h h) {
+    g_compute_f32 = h->precision == SGTN_FP32 || h->precision == SGTN_TF32;
+    g_use_tc = h->precision == SGTN_TF32;
+  }
+  ~PrecisionScope() {
+    g_compute_f32 = false;
+    g_use_tc = false;
+  }
+};
+
 extern "C" {
 
 int sgtn_build_instance(int32_t n_spins, int64_t n_edges, const int32_t* ei, const int32_t* ej, const int32_t* j_num,
@@ -118,27 +132,16 @@ int sgtn_contract_boundary(sgtn_h h, int32_t chi, int32_t precision, int32_t n_s
   return guarded(h, [&] {
     if (!h->beta_set) throw SgtnError(SGTN_ERR_STATE, "set_beta must run first");
     if (chi < 1 || n_sweeps < 0 || n_sweeps > 100) throw SgtnError(SGTN_ERR_ARG, "bad chi or n_sweeps");
-    if (precision != SGTN_FP64 && precision != SGTN_FP32)
-      throw SgtnError(SGTN_ERR_ARG, "precision must be SGTN_FP64 or SGTN_FP32 in this build");
+    if (precision != SGTN_FP64 && precision != SGTN_FP32 && precision != SGTN_TF32)
+      throw SgtnError(SGTN_ERR_ARG, "precision must be SGTN_FP64, SGTN_FP32 or SGTN_TF32 in this build");
     h->precision = precision;
-    g_compute_f32 = precision == SGTN_FP32;
-    try {
-      contract_boundary(h, chi, n_sweeps);
-    } catch (...) {
-      g_compute_f32 = false;
-      throw;
-    }
-    g_compute_f32 = false;
+    PrecisionScope ps(h);
+    contract_boundary(h, chi, n_sweeps);
+    if (tc_gemm_take_error(h->st)) throw SgtnError(SGTN_ERR_TIMEOUT, "a tensor-core GEMM timed out");
     if (out_logz) *out_logz = h->logz;
     if (out_worst_trunc_sv) *out_worst_trunc_sv = h->worst_sv;
   });
 }
-
-// The branch step and the search run in the precision of the last contract_boundary.
-struct PrecisionScope {
-  explicit PrecisionScope(sgtn_h h) { g_compute_f32 = h->precision == SGTN_FP32; }
-  ~PrecisionScope() { g_compute_f32 = false; }
-};
 
 int sgtn_conditionals(sgtn_h h, int32_t step, int32_t count, const int32_t* configs, double* out_p) {
   return guarded(h, [&] {

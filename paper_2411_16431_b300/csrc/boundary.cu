@@ -36,9 +36,15 @@ namespace detail {
 // Linear algebra of the truncation (SVDs, orthonormalisations, canonical forms)
 // always runs in FP64, also when the contractions are FP32.
 struct F64Scope {
-  bool saved;
-  F64Scope() : saved(g_compute_f32) { g_compute_f32 = false; }
-  ~F64Scope() { g_compute_f32 = saved; }
+  bool saved, saved_tc;
+  F64Scope() : saved(g_compute_f32), saved_tc(g_use_tc) {
+    g_compute_f32 = false;
+    g_use_tc = false;
+  }
+  ~F64Scope() {
+    g_compute_f32 = saved;
+    g_use_tc = saved_tc;
+  }
 };
 
 double* dmalloc(long long n) {

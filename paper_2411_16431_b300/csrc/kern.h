@@ -18,6 +18,9 @@ extern Counters g_count;
 // When set, every contraction (seg_gemm / gemm) multiplies and accumulates in
 // FP32; the SVDs, norms and log-norms stay FP64.  Set per call from the handle.
 extern bool g_compute_f32;
+// When set (with g_compute_f32), dense GEMMs large enough for 128 x 128 tiles
+// run on tcgen05 tensor cores (3xTF32).
+extern bool g_use_tc;
 
 // Optional per-kernel timing with CUDA events on the launching stream.
 // KTimer brackets one launch; pairs are resolved when read.
@@ -80,6 +83,11 @@ void vec_norms(const double* X, int len, int p, long long si, long long sj, doub
 // out[i*oi + jj*oj] = scale[jj] * X[i*si + perm[jj]*sj]
 void gather_vecs(const double* X, int len, long long si, long long sj, const int32_t* perm, const double* scale,
                  int k, double* out, long long oi, long long oj, cudaStream_t st);
+// C[m x n] (+)= alpha op(X) op(Y) on tcgen05 tensor cores with 3xTF32 splitting
+// (about FP32 accuracy); false if it could not be launched.
+bool tc_gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, long long ldy, double* C, long long ldc,
+             int m, int n, int k, double alpha, int accumulate, cudaStream_t st);
+int tc_gemm_take_error(cudaStream_t st);
 // deterministic pseudo-random numbers in [-1, 1] (SplitMix64 of seed + index)
 void pseudo_random(double* x, long long n, unsigned long long seed, cudaStream_t st);
 // R[i][j] += Q[i*ldq + j] for j < k  (R is rows x k, Q is rows x ldq)

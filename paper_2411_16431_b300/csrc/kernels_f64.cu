@@ -631,9 +631,13 @@ void seg_gemm(const SegGemm& a_in, cudaStream_t st) {
 }
 
 bool g_compute_f32 = false;
+bool g_use_tc = false;
 
 void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, long long ldy, double* O, long long ldo,
           int m, int n, int k, double alpha, int accumulate, cudaStream_t st) {
+  if (g_use_tc && g_compute_f32 && m >= 128 && n >= 64 && k >= 32 &&
+      tc_gemm(X, tx, ldx, Y, ty, ldy, O, ldo, m, n, k, alpha, accumulate, st))
+    return;
   SegGemm a;
   a.X = X;
   a.Y = Y;

@@ -268,18 +268,20 @@ MIXED_CASES = [(L.chimera_grid(4, 4, 0), None, 1.0, 16, 2), (L.kings_grid(5, 6, 
                (PEGP, PEGP_STATES, 2.0, 8, 2)]
 
 
+@pytest.mark.parametrize("prec", ["FP32", "TF32"])
 @pytest.mark.parametrize("case", MIXED_CASES, ids=lambda c: c[0].name)
-def test_mixed_precision_error_is_small(Handle, case):
+def test_mixed_precision_error_is_small(Handle, case, prec):
     """FP32 contractions with FP64 truncation: log Z within 1e-6 relative of the FP64 oracle,
     marginals within 1e-4, same final configuration and exact int64 energy."""
-    from paper_2411_16431_b300.sgtn import FP32
+    from paper_2411_16431_b300 import sgtn
+    P = getattr(sgtn, prec)
     inst, states, beta, chi, ns = case
     lz_o, psis, mpos = boundary_mps(PottsModel(inst, states), beta, chi, ns)
     h = Handle(inst, states)
     h.set_beta(beta)
-    lz, _ = h.contract_boundary(chi, precision=FP32, n_sweeps=ns)
+    lz, _ = h.contract_boundary(chi, precision=P, n_sweeps=ns)
     assert abs(lz - lz_o) < 1e-6 * abs(lz_o)
-    assert h.boundary_info()[1] == FP32
+    assert h.boundary_info()[1] == P
     ref = oracle_search(inst, beta, chi=chi, M=16, n_sweeps=ns, states=states)
     res = h.search(16)
     assert np.array_equal(res["energy_num"], ref["energy_num"])
