@@ -24,6 +24,8 @@
 #include <algorithm>
 #include <cmath>
 #include <functional>
+#include <cstdio>
+#include <cstdlib>
 #include <numeric>
 
 #include "handle.h"
@@ -194,6 +196,8 @@ SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   std::iota(idx.begin(), idx.end(), 0);
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return s[a] > s[b]; });
   double smax = p ? s[idx[0]] : 0.0;
+  if (std::getenv("SGTN_TRACE"))
+    fprintf(stderr, "[sgtn] svd_jacobi m=%d n=%d cap=%d smax=%.3e smin=%.3e\n", m, n, cap, smax, p ? s[idx[p - 1]] : 0.0);
   if (!(smax > 0.0) || !std::isfinite(smax)) throw SgtnError(-4, "zero or non-finite tensor in truncation");
   int cnt = 0;
   for (int i = 0; i < p; ++i)
@@ -714,7 +718,10 @@ SvdOut theta_svd(RowCtx& X, int c, const ThetaOp& T, int cap) {
 }
 
 // One left-right-left sweep of one-site overlap maximisation (Fig. 8d).
-void variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
+// Environments are renormalised after every update (they would under- or
+// overflow, in FP32 first); only the right environment's scale reaches the
+// final centre, and its logarithm is returned.
+double variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
   sgtn_inst* h = X.h;
   const int C = (int)phi.size();
   right_canonical(X, phi);
@@ -724,6 +731,8 @@ void variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
   for (int c = C - 1; c > 0; --c) {
     ThetaOp T = theta_op(X, c, Renv[c], phi[c].b);
     Renv[c - 1] = theta_right(X, c, T, phi[c]);
+    double dummy = 0.0;
+    normalise(h, Renv[c - 1], (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, dummy);
   }
   Lenv[0] = dmalloc(1);
   fill(Lenv[0], 1, 1.0, h->st);
@@ -744,6 +753,8 @@ void variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
       phi[c].b = o.k;
       o.release();
       Lenv[c + 1] = update_L(X, c, Lenv[c], phi[c]);
+      double dummy = 0.0;
+      normalise(h, Lenv[c + 1], (long long)phi[c].b * X.col(c).nBR() * X.chr(c), dummy);
       // the next site's left bond is now o.k; its right bond is unchanged
       phi[c + 1].a = phi[c].b;
     }
@@ -751,6 +762,7 @@ void variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
   for (auto& p : Renv) dfree(p);
   double* Rc = dmalloc(1);
   fill(Rc, 1, 1.0, h->st);
+  double rc_log = 0.0;
   for (int c = C - 1; c >= 0; --c) {
     const Column& K_ = X.col(c);
     ThetaOp T = theta_op(X, c, Rc, phi[c].b);
@@ -770,11 +782,13 @@ void variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
       double* Rn = theta_right(X, c, T, phi[c]);
       dfree(Rc);
       Rc = Rn;
+      normalise(h, Rc, (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, rc_log);
       phi[c - 1].b = phi[c].a;
     }
   }
   dfree(Rc);
   for (auto& p : Lenv) dfree(p);
+  return rc_log;
 }
 
 // cut a right-canonical phi (centre 0) to bond chi; returns worst retained ratio
@@ -899,15 +913,15 @@ void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& wo
   }
   dfree(K);
   for (int s = 0; s < n_sweeps; ++s) {
-    variational_sweep(X, phi);
-    ln = A.lognorm;
+    double extra = variational_sweep(X, phi);
+    ln = A.lognorm + extra;
     normalise(h, phi[0].p, phi[0].n(), ln);
   }
   worst = std::max(worst, svd_cut(X, phi, chi));
   normalise(h, phi[C - 1].p, phi[C - 1].n(), ln);
   for (int s = 0; s < n_sweeps; ++s) {
-    variational_sweep(X, phi);
-    ln = A.lognorm;
+    double extra = variational_sweep(X, phi);
+    ln = A.lognorm + extra;
     normalise(h, phi[0].p, phi[0].n(), ln);
   }
   for (double* p : X.Ahat) cudaFree(p);
@@ -933,6 +947,7 @@ void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& wo
 
 // psi_{r-1} ~ T_r psi_r (sparse projector form)
 void row_step(sgtn_inst* h, int r, int chi, int n_sweeps, MPS& out, double& worst) {
+  if (std::getenv("SGTN_TRACE")) fprintf(stderr, "[sgtn] row step %d\n", r);
   RowCtx X;
   X.h = h;
   X.r = r;

@@ -110,7 +110,7 @@ def test_conditionals_match_oracle(Handle, case):
             # largest carry absolute, not relative, rounding: 1e-10 relative above 1e-8 x max
             big = po > 1e-8 * po.max()
             assert np.allclose(p[k][big], po[big], rtol=RTOL, atol=0)
-            assert np.abs(p[k] - po).max() < 1e-12
+            assert np.abs(p[k] - po).max() <= 1e-10 * po.max()
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0].name}_chi{c[2]}")
