@@ -723,6 +723,7 @@ SvdOut theta_svd(RowCtx& X, int c, const ThetaOp& T, int cap) {
 // final centre, and its logarithm is returned.
 double variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
   sgtn_inst* h = X.h;
+  const bool renorm = true;
   const int C = (int)phi.size();
   right_canonical(X, phi);
   std::vector<double*> Renv(C, nullptr), Lenv(C, nullptr);
@@ -732,7 +733,7 @@ double variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
     ThetaOp T = theta_op(X, c, Renv[c], phi[c].b);
     Renv[c - 1] = theta_right(X, c, T, phi[c]);
     double dummy = 0.0;
-    normalise(h, Renv[c - 1], (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, dummy);
+    if (renorm) normalise(h, Renv[c - 1], (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, dummy);
   }
   Lenv[0] = dmalloc(1);
   fill(Lenv[0], 1, 1.0, h->st);
@@ -754,7 +755,7 @@ double variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
       o.release();
       Lenv[c + 1] = update_L(X, c, Lenv[c], phi[c]);
       double dummy = 0.0;
-      normalise(h, Lenv[c + 1], (long long)phi[c].b * X.col(c).nBR() * X.chr(c), dummy);
+      if (renorm) normalise(h, Lenv[c + 1], (long long)phi[c].b * X.col(c).nBR() * X.chr(c), dummy);
       // the next site's left bond is now o.k; its right bond is unchanged
       phi[c + 1].a = phi[c].b;
     }
@@ -782,7 +783,7 @@ double variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
       double* Rn = theta_right(X, c, T, phi[c]);
       dfree(Rc);
       Rc = Rn;
-      normalise(h, Rc, (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, rc_log);
+      if (renorm) normalise(h, Rc, (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, rc_log);
       phi[c - 1].b = phi[c].a;
     }
   }
