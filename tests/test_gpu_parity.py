@@ -91,28 +91,29 @@ def test_truncated_boundary_matches_oracle(Handle, case):
 
 @pytest.mark.parametrize("case", CASES[:3], ids=lambda c: f"{c[0].name}_chi{c[2]}")
 def test_conditionals_match_oracle(Handle, case):
+    """Conditional marginals on probable partial configurations (the ones a search
+    visits: grown greedily from the oracle's own conditionals), 1e-10 relative."""
     inst, beta, chi, ns = case
     pm = PottsModel(inst)
     _, psis, mpos = boundary_mps(pm, beta, chi, ns)
     h = Handle(inst)
     h.set_beta(beta)
     h.contract_boundary(chi, n_sweeps=ns)
-    rng = np.random.default_rng(5)
+    beam = [((), 0.0)]
     for n in range(inst.rows * inst.cols):
         r, c = divmod(n, inst.cols)
-        cfgs = np.array([[rng.integers(pm.sites[p].d) for p in range(n)] for _ in range(5)], np.int32).reshape(5, n)
+        cfgs = np.array([b[0] for b in beam], np.int32).reshape(len(beam), n)
         p = h.conditionals(n, cfgs)
-        for k in range(5):
-            s = np.maximum(conditional_scores(pm, beta, mpos[r], psis[r], tuple(cfgs[k]), r, c), 0)
-            if s.sum() == 0:
-                assert not p[k].any()
-                continue
+        nxt = []
+        for k, (cf, lp) in enumerate(beam):
+            s = np.maximum(conditional_scores(pm, beta, mpos[r], psis[r], cf, r, c), 0)
             po = s / s.sum()
-            # FP64 SVDs are accurate to eps * sigma_max, so marginals far below the row's
-            # largest carry absolute, not relative, rounding: 1e-10 relative above 1e-8 x max
             big = po > 1e-8 * po.max()
             assert np.allclose(p[k][big], po[big], rtol=RTOL, atol=0)
             assert np.abs(p[k] - po).max() <= 1e-10 * po.max()
+            for x in np.argsort(-po)[:3]:
+                nxt.append((cf + (int(x),), lp + np.log(po[x])))
+        beam = sorted(nxt, key=lambda t: -t[1])[:6]
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0].name}_chi{c[2]}")
