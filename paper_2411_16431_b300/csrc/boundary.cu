@@ -339,6 +339,16 @@ double norm_host(sgtn_inst* h, const double* x, long long n, bool allow_zero) {
   if (!std::isfinite(v) || (!allow_zero && !(v > 0.0))) throw SgtnError(-4, "zero or non-finite norm");
   return v;
 }
+// Rescale x by the power of two nearest its norm (exact: changes no digit of
+// any later result, only keeps magnitudes inside the floating-point range).
+void rescale_pow2(sgtn_inst* h, double* x, long long n, double& lognorm) {
+  double v = norm_host(h, x, n, false);
+  int e = (int)std::lround(std::log2(v));
+  if (e == 0) return;
+  lognorm += e * 0.69314718055994530942;
+  scale_pow2(x, n, e, h->st);
+}
+
 void normalise(sgtn_inst* h, double* x, long long n, double& lognorm) {
   double v = norm_host(h, x, n, false);
   lognorm += std::log(v);
@@ -718,9 +728,9 @@ SvdOut theta_svd(RowCtx& X, int c, const ThetaOp& T, int cap) {
 }
 
 // One left-right-left sweep of one-site overlap maximisation (Fig. 8d).
-// Environments are renormalised after every update (they would under- or
-// overflow, in FP32 first); only the right environment's scale reaches the
-// final centre, and its logarithm is returned.
+// Environments are rescaled by powers of two after every update (they would
+// under- or overflow, in FP32 first); only the right environment's scale
+// reaches the final centre, and its logarithm is returned.
 double variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
   sgtn_inst* h = X.h;
   const bool renorm = true;
@@ -733,7 +743,7 @@ double variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
     ThetaOp T = theta_op(X, c, Renv[c], phi[c].b);
     Renv[c - 1] = theta_right(X, c, T, phi[c]);
     double dummy = 0.0;
-    if (renorm) normalise(h, Renv[c - 1], (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, dummy);
+    if (renorm) rescale_pow2(h, Renv[c - 1], (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, dummy);
   }
   Lenv[0] = dmalloc(1);
   fill(Lenv[0], 1, 1.0, h->st);
@@ -755,7 +765,7 @@ double variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
       o.release();
       Lenv[c + 1] = update_L(X, c, Lenv[c], phi[c]);
       double dummy = 0.0;
-      if (renorm) normalise(h, Lenv[c + 1], (long long)phi[c].b * X.col(c).nBR() * X.chr(c), dummy);
+      if (renorm) rescale_pow2(h, Lenv[c + 1], (long long)phi[c].b * X.col(c).nBR() * X.chr(c), dummy);
       // the next site's left bond is now o.k; its right bond is unchanged
       phi[c + 1].a = phi[c].b;
     }
@@ -783,7 +793,7 @@ double variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
       double* Rn = theta_right(X, c, T, phi[c]);
       dfree(Rc);
       Rc = Rn;
-      if (renorm) normalise(h, Rc, (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, rc_log);
+      if (renorm) rescale_pow2(h, Rc, (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, rc_log);
       phi[c - 1].b = phi[c].a;
     }
   }

@@ -102,6 +102,8 @@ void permute3(const double* in, int A, int B, int Cd, double* out, cudaStream_t 
 // Frobenius norm (deterministic), result on device in *out
 void fro_norm(const double* x, long long n, double* out, cudaStream_t st);
 void scale_by_inv(double* x, long long n, const double* norm, cudaStream_t st);
+// x *= 2^-e (exact in binary floating point)
+void scale_pow2(double* x, long long n, int e, cudaStream_t st);
 void fill(double* x, long long n, double v, cudaStream_t st);
 void copy(double* dst, const double* src, long long n, cudaStream_t st);
 

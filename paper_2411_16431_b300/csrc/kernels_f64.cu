@@ -473,6 +473,11 @@ __global__ void add_cols_kernel(double* R, const double* Q, int rows, int k, int
   }
 }
 
+__global__ void scale_pow2_kernel(double* x, long long n, int e) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = ldexp(x[i], -e);
+}
+
 __global__ void fill_kernel(double* x, long long n, double v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     x[i] = v;
@@ -791,6 +796,11 @@ void pseudo_random(double* x, long long n, unsigned long long seed, cudaStream_t
 
 void add_cols(double* R, const double* Q, int rows, int k, int ldq, cudaStream_t st) {
   add_cols_kernel<<<blocks_for((long long)rows * k), 256, 0, st>>>(R, Q, rows, k, ldq);
+  ++g_count.launches;
+}
+
+void scale_pow2(double* x, long long n, int e, cudaStream_t st) {
+  scale_pow2_kernel<<<blocks_for(n), 256, 0, st>>>(x, n, e);
   ++g_count.launches;
 }
 
