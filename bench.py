@@ -28,12 +28,34 @@ from paper_2411_16431_b300 import lattices as L  # noqa: E402
 
 # Workloads: sizes of the benchmark configurations.
 WORKLOADS = {
-    "chimera4x4": dict(desc="4x4 grid of K44 cells (128 spins), iid J,h in {+-1..+-7}/7, beta=1, chi=16, M=64, FP64",
-                       make=lambda seed: L.chimera_grid(4, 4, seed), beta=1.0, chi=16, M=64, sweeps=2),
+    "chimera4x4": dict(desc="4x4 grid of K44 cells (128 spins), iid J,h in {+-1..+-7}/7, beta=1, chi=16, M=64",
+                       make=lambda seed: L.chimera_grid(4, 4, seed), states=None, beta=1.0, chi=16, M=64, sweeps=2),
+    # Pegasus P6 nice cells (5x5 grid, 600 spins, 24-spin cells); every cell restricted to the
+    # 256 states nearest a seeded reference (stand-in for the local-dimension reduction of Sec. IV)
+    "pegasus5x5": dict(desc="Pegasus P6 nice, 5x5 cells of 24 spins (600 spins), d=256 states per cell "
+                            "(Hamming ball around a seeded reference), iid J,h in {+-1..+-7}/7, beta=1, chi=32, M=256",
+                       make=lambda seed: L.pegasus_nice(6, seed),
+                       states=lambda inst, seed: L.hamming_ball_states(inst, 256, seed=seed + 1),
+                       beta=1.0, chi=32, M=256, sweeps=2),
 }
 DEFAULT = "chimera4x4"
+PRECISIONS = {"fp64": (0, "f64"), "fp32": (3, "f32 (FP64 truncation)"),
+              "tf32": (1, "3xtf32 tensor cores + f32 (FP64 truncation)")}
 # FP64 peak of a B300 derived from unit counts: 148 SMs x 2 DFMA/clk/SM x 2 flop x 2032 MHz
 FP64_PEAK_GFLOPS = 148 * 2 * 2 * 2.032
+# FP32 SIMT peak from unit counts (148 SMs x 128 FMA/clk x 2 flop x 2032 MHz)
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e-3
+
+
+def _measured_bf16():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        return 1800.0
+
+
+# TF32 dense tensor peak = measured bf16 burst x 1/2 (nominal 1.1 / 2.25 PFLOP/s ratio)
+TF32_PEAK_TFLOPS = _measured_bf16() * 0.5
 
 
 def clocks_sampler(dev_index):
@@ -87,10 +109,11 @@ def cpu_oracle(wl, seed, budget_s=15.0, max_runs=5):
     except Exception:
         cores = os.cpu_count()
     inst = wl["make"](seed)
+    states = wl["states"](inst, seed) if wl["states"] else None
     runs, t_tot, evals = 0, 0.0, 0
     while runs < max_runs and (t_tot < budget_s or runs == 0):
         t0 = time.perf_counter()
-        res = oracle_search(inst, wl["beta"], chi=wl["chi"], M=wl["M"], n_sweeps=wl["sweeps"])
+        res = oracle_search(inst, wl["beta"], chi=wl["chi"], M=wl["M"], n_sweeps=wl["sweeps"], states=states)
         t_tot += time.perf_counter() - t0
         evals += res["evals"]
         runs += 1
@@ -104,12 +127,13 @@ def run_reference(args, wl):
         return
     from oracle.search import search as oracle_search
     inst = wl["make"](args.seed)
+    states = wl["states"](inst, args.seed) if wl["states"] else None
     for _ in range(args.warmup):
-        oracle_search(inst, wl["beta"], chi=wl["chi"], M=wl["M"], n_sweeps=wl["sweeps"])
+        oracle_search(inst, wl["beta"], chi=wl["chi"], M=wl["M"], n_sweeps=wl["sweeps"], states=states)
     t_tot, evals = 0.0, 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        res = oracle_search(inst, wl["beta"], chi=wl["chi"], M=wl["M"], n_sweeps=wl["sweeps"])
+        res = oracle_search(inst, wl["beta"], chi=wl["chi"], M=wl["M"], n_sweeps=wl["sweeps"], states=states)
         t_tot += time.perf_counter() - t0
         evals += res["evals"]
     try:
@@ -140,12 +164,14 @@ def run_native(args, wl):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
     inst = wl["make"](args.seed + rank)
-    h = sgtn.Handle(inst, stream=stream.cuda_stream)
+    states = wl["states"](inst, args.seed + rank) if wl["states"] else None
+    h = sgtn.Handle(inst, states, stream=stream.cuda_stream)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > 126 MB L2
+    prec, dtype_name = PRECISIONS[args.precision]
 
     def step():
         h.set_beta(wl["beta"])
-        h.contract_boundary(wl["chi"], n_sweeps=wl["sweeps"])
+        h.contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])
         return h.search(wl["M"])
 
     for _ in range(args.warmup):
@@ -165,7 +191,7 @@ def run_native(args, wl):
         a.record(stream)
         h.set_beta(wl["beta"])
         fa = sgtn.stats()[1]
-        h.contract_boundary(wl["chi"], n_sweeps=wl["sweeps"])
+        h.contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])
         bflops += sgtn.stats()[1] - fa
         res = h.search(wl["M"])
         b.record(stream)
@@ -184,26 +210,30 @@ def run_native(args, wl):
         t_ms, evals_all = float(tt.item()), float(ev.item())
     else:
         evals_all = evals
-    kt = {n: sgtn.kernel_time(n) for n in ("seg_gemm_f64", "jacobi_f64", "score_f64")}
+    kt = {n: sgtn.kernel_time(n) for n in ("seg_gemm_f64", "seg_gemm_f32", "tc_gemm_3xtf32", "jacobi_f64",
+                                           "score_f64", "score_f32")}
+    unconverged = h.boundary_info()[0]
     # boundary contraction timed alone for its TFLOP/s
     torch.cuda.synchronize()
     h.set_beta(wl["beta"])
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    h.contract_boundary(wl["chi"], n_sweeps=wl["sweeps"])
+    h.contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])
     b.record(stream)
     torch.cuda.synchronize()
     bound_ms = a.elapsed_time(b)
     # end to end through the public API from host buffers: build (H2D) .. results (D2H)
     e2e_times = []
     h2d = inst.ei.nbytes + inst.ej.nbytes + inst.j_num.nbytes + inst.h_num.nbytes + inst.site_of_spin.nbytes
+    if states is not None:
+        h2d += sum(np.asarray(x, np.int64).nbytes for x in states) + 8 * (len(states) + 1)
     d2h = 0
     for _ in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h2 = sgtn.Handle(inst, stream=stream.cuda_stream)
+        h2 = sgtn.Handle(inst, states, stream=stream.cuda_stream)
         h2.set_beta(wl["beta"])
-        h2.contract_boundary(wl["chi"], n_sweeps=wl["sweeps"])
+        h2.contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])
         r2 = h2.search(wl["M"])
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
@@ -215,15 +245,21 @@ def run_native(args, wl):
             dist.barrier()
             dist.destroy_process_group()
         return
-    # roofline of the dominant contraction kernel (FP64 ALU bound)
-    seg = kt["seg_gemm_f64"]
+    # roofline of the dominant contraction kernel among those with an algorithmic flop count
     roof = None
-    if seg and seg[1] > 0:
-        achieved = (seg[2] / seg[1]) / (seg[0] / seg[1] * 1e-3) / 1e12   # TFLOP/s per launch average
-        peak = FP64_PEAK_GFLOPS / 1e3
-        roof = {"kernel": "seg_gemm_f64", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2032 MHz (no measured FP64 peak)"}
+    peaks = {"seg_gemm_f64": (FP64_PEAK_GFLOPS / 1e3, "alu", "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2032 MHz "
+                                                               "(no measured FP64 peak)"),
+             "seg_gemm_f32": (FP32_PEAK_TFLOPS, "alu", "derived: 148 SMs x 128 FFMA/clk x 2 flop x 2032 MHz"),
+             "tc_gemm_3xtf32": (TF32_PEAK_TFLOPS / 3.0, "tensor",
+                                "measured bf16 burst peak x 1/2 (tf32 nominal ratio) / 3 (three products per 3xTF32)")}
+    cand = [(v[0], n) for n, v in kt.items() if v and n in peaks and v[1] > 0]
+    if cand:
+        _, kn = max(cand)
+        ms, nl, fl = kt[kn]
+        achieved = (fl / nl) / (ms / nl * 1e-3) / 1e12
+        pk, bound, src = peaks[kn]
+        roof = {"kernel": kn, "bound": bound, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                "frac": achieved / pk, "traffic": None, "peak_source": src}
     shares = {}
     tot_k = sum(v[0] for v in kt.values() if v)
     for n, v in kt.items():
@@ -231,9 +267,12 @@ def run_native(args, wl):
             shares[n] = {"ms": v[0], "launches": v[1], "share_of_timed_kernels": v[0] / tot_k if tot_k else None}
     line = {"metric": "marginal evals/s", "value": evals_all / (t_ms * 1e-3), "unit": "marginal evals/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype_name,
+            "data": "synthetic",
             "config": {"workload": args.workload, "description": wl["desc"], "instances_per_rank": 1,
-                       "parallelism": f"replicas{ws}", "l2": "flushed between timed steps (256 MB write)"},
+                       "precision": args.precision, "parallelism": f"replicas{ws}",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "unconverged_truncations": unconverged},
             "boundary_tflops": (bflops / args.steps) / (bound_ms * 1e-3) / 1e12,
             "boundary_ms": bound_ms,
             "roofline": roof, "kernel_times": shares,
@@ -258,6 +297,7 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp64")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]

@@ -270,7 +270,7 @@ SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, co
     copy(Z0, Q, (long long)n * s, st);
     orth(Z0, n, k_active, Q);
   }
-  const int maxit = 200;
+  const int maxit = 60;
   int it = 0;
   for (; it < maxit; ++it) {
     mul(Q, k_active, Y);                                                                     // Y = Theta Q
