@@ -22,11 +22,14 @@
 //  * MPS tensors are stored [phys][bond_l][bond_r]; the approximation being
 //    built (phi) is kept bond-major [bond_l][phys][bond_r].
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <functional>
 #include <cstdio>
 #include <cstdlib>
+#include <map>
 #include <numeric>
+#include <string>
 
 #include "handle.h"
 
@@ -49,6 +52,26 @@ struct F64Scope {
   }
 };
 
+// Optional per-call-site timing of the truncation linear algebra (SGTN_PROFILE
+// set): each svd() call is bracketed by stream synchronisations and its wall
+// time booked under the enclosing TagScope.
+struct SvdProf {
+  double ms = 0;
+  long long calls = 0, iters = 0;
+  int max_m = 0, max_n = 0;
+};
+static std::map<std::string, SvdProf> g_prof;
+static const char* g_tag = "other";
+static bool prof_on() {
+  static const bool on = std::getenv("SGTN_PROFILE") != nullptr;
+  return on;
+}
+struct TagScope {
+  const char* saved;
+  explicit TagScope(const char* t) : saved(g_tag) { g_tag = t; }
+  ~TagScope() { g_tag = saved; }
+};
+
 double* dmalloc(long long n) {
   double* p = nullptr;
   SGTN_CUDA(cudaMalloc(&p, size_t(n > 0 ? n : 1) * sizeof(double)));
@@ -69,24 +92,47 @@ SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, co
 // Truncated SVD of a dense row-major m x n matrix: exact one-sided Jacobi on
 // the shorter side when it is short, otherwise subspace iteration with a
 // Rayleigh-Ritz step (converged to the same top singular subspace).
-SvdOut svd(sgtn_inst* h, const double* Th, int m, int n, int cap) {
+SvdOut svd_impl(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   F64Scope f64;
   int p = std::min(m, n);
   if (p <= h->dense_svd_max || cap >= p) return svd_dense(h, Th, m, n, cap);
   return svd_subspace(h, Th, m, n, cap);
 }
 
+template <class F>
+auto profiled(sgtn_inst* h, const char* sub, int m, int n, F&& f) -> decltype(f()) {
+  if (!prof_on()) return f();
+  h->sync();
+  auto t0 = std::chrono::steady_clock::now();
+  auto o = f();
+  h->sync();
+  SvdProf& e = g_prof[std::string(g_tag) + sub];
+  e.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  e.calls += 1;
+  e.max_m = std::max(e.max_m, m);
+  e.max_n = std::max(e.max_n, n);
+  return o;
+}
+
+SvdOut svd(sgtn_inst* h, const double* Th, int m, int n, int cap) {
+  return profiled(h, "", m, n, [&] { return svd_impl(h, Th, m, n, cap); });
+}
+
 SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap);
+bool cqr_orth(sgtn_inst* h, const double* M, int len, int k, double* Q, bool first_f32);
 bool svd_tall_cqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o);
+bool svd_tall_cqr3(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o);
+bool svd_tall_rrcqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o);
 
 // Exact truncated SVD: for a tall-skinny (or short-fat) matrix with a short
-// side of at most 110, shifted CholeskyQR3 then a one-sided Jacobi SVD of the
+// side of at most 160 (the Cholesky factor is staged in one CTA's shared memory), shifted CholeskyQR3 then a one-sided Jacobi SVD of the
 // small triangular factor; otherwise (or if a Cholesky pivot fails, i.e. the
 // vectors are exactly dependent) one-sided Jacobi on the shorter side.
 SvdOut svd_dense(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   SvdOut o;
   int p = std::min(m, n), q = std::max(m, n);
-  if (p <= 110 && q >= 2 * p && q >= 256) {
+  if (p <= 160 && q >= 2 * p && q >= 256) {
+    if (prof_on()) g_prof[std::string(g_tag) + "/cqr_tries"].calls++;
     if (m >= n) {
       if (svd_tall_cqr(h, Th, m, n, cap, o)) return o;
     } else {
@@ -114,8 +160,9 @@ SvdOut svd_dense(sgtn_inst* h, const double* Th, int m, int n, int cap) {
 }
 
 // M (m x n, m >= n, row-major) = Q R by shifted CholeskyQR3, then R = U S V^T
-// by one-sided Jacobi.  Returns false (nothing allocated) if a pivot fails.
-bool svd_tall_cqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o) {
+// by one-sided Jacobi.  Returns false (nothing allocated) if a pivot fails
+// (numerically dependent columns).
+bool svd_tall_cqr3(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o) {
   cudaStream_t st = h->st;
   double* G = h->ws.get<double>("cq_G", size_t(n) * n);
   double* R = h->ws.get<double>("cq_R", size_t(n) * n);
@@ -167,6 +214,102 @@ bool svd_tall_cqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& 
   return true;
 }
 
+// Tall-skinny SVD: shifted CholeskyQR3 (the exact path), or, when its
+// Cholesky factor fails (numerically dependent columns), rank-revealing
+// CholeskyQR; false if both fail.
+bool svd_tall_cqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o) {
+  if (svd_tall_cqr3(h, M, m, n, cap, o)) return true;
+  if (prof_on()) g_prof[std::string(g_tag) + "/rrcqr"].calls++;
+  return svd_tall_rrcqr(h, M, m, n, cap, o);
+}
+
+// M (m x n, m >= n, row-major) = Q B with Q (m x r) orthonormal and r the
+// numerical rank, then B = U S V^T by one-sided Jacobi, so M = (Q U) S V^T.
+// Q is built in at most three rounds of rank-revealing CholeskyQR: pivoted
+// Cholesky of the Gram matrix of the current residual (stopped where the
+// remaining pivots fall below 1e-14 of the largest, i.e. residual columns
+// below 1e-7 of the largest norm), Q1 = M[:, piv] R^{-1} made orthogonal to the
+// earlier columns and orthonormalised by CholeskyQR2; B = Q^T M and the
+// residual M - Q B decide whether another round is needed (its Frobenius norm
+// above 1e-14 of ||M||_F).  Returns false (nothing allocated) if a round fails.
+// Used where shifted CholeskyQR3 fails; it is slightly less accurate there.
+bool svd_tall_rrcqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o) {
+  cudaStream_t st = h->st;
+  double* G = h->ws.get<double>("cq_G", size_t(n) * n);
+  double* R = h->ws.get<double>("cq_R", size_t(n) * n);
+  double* Ri = h->ws.get<double>("cq_Ri", size_t(n) * n);
+  double* Qt = h->ws.get<double>("cq_Qt", size_t(m) * n);     // Q total, leading dimension n
+  double* Mp = h->ws.get<double>("cq_Mp", size_t(m) * n);
+  double* Q1 = h->ws.get<double>("cq_Q1", size_t(m) * n);
+  double* Q2 = h->ws.get<double>("cq_Q2", size_t(m) * n);
+  double* E = h->ws.get<double>("cq_E", size_t(m) * n);
+  double* B = h->ws.get<double>("cq_B", size_t(n) * n);
+  double* C = h->ws.get<double>("cq_C", size_t(n) * n);
+  double* ones = h->ws.get<double>("cq_ones", n);
+  int32_t* perm = h->ws.get<int32_t>("cq_perm", n);
+  int* rank = h->ws.get<int>("cq_rank", 1);
+  fill(ones, n, 1.0, st);
+  const double normM = norm_host(h, M, (long long)m * n, true);
+  if (!(normM > 0.0)) return false;
+  double floor_abs = 0.0;
+  const double* cur = M;   // residual whose range is being added
+  int rt = 0;
+  for (int round = 0; round < 3 && rt < n; ++round) {
+    gemm(cur, true, n, cur, false, n, G, n, n, n, m, 1.0, 0, st);                       // G = cur^T cur
+    if (round == 0) {
+      // absolute floor for later rounds: pivots of (1e-13 max column norm)^2
+      std::vector<double> d(n);
+      SGTN_CUDA(cudaMemcpy2DAsync(d.data(), sizeof(double), G, size_t(n + 1) * sizeof(double), sizeof(double), n,
+                                  cudaMemcpyDeviceToHost, st));
+      h->sync();
+      double dm = 0;
+      for (double v : d) dm = std::max(dm, v);
+      floor_abs = 1e-26 * dm;
+    }
+    pchol_inv(G, n, 1e-14, floor_abs, R, Ri, perm, rank, st);
+    int r = 0;
+    SGTN_CUDA(cudaMemcpyAsync(&r, rank, sizeof(int), cudaMemcpyDeviceToHost, st));
+    h->sync();
+    r = std::min(r, n - rt);
+    if (r <= 0) break;
+    // Q1 = cur[:, perm] R^{-1}
+    gather_vecs(cur, m, n, 1, perm, ones, r, Mp, r, 1, st);
+    gemm(Mp, false, r, Ri, false, n, Q1, r, m, r, r, 1.0, 0, st);
+    if (rt > 0) {
+      // Q1 -= Qt (Qt^T Q1), twice (classical Gram-Schmidt with reorthogonalisation)
+      for (int pass = 0; pass < 2; ++pass) {
+        gemm(Qt, true, n, Q1, false, r, C, r, rt, r, m, 1.0, 0, st);
+        gemm(Qt, false, n, C, false, r, Q1, r, m, r, rt, -1.0, 1, st);
+      }
+    }
+    if (!cqr_orth(h, Q1, m, r, Q2, false)) return false;
+    gather_vecs(Q2, m, r, 1, h->iota, ones, r, Qt + rt, n, 1, st);                     // append columns
+    rt += r;
+    if (rt >= n) break;
+    // B = Qt^T M ; E = M - Qt B
+    gemm(Qt, true, n, M, false, n, B, n, rt, n, m, 1.0, 0, st);
+    gemm(Qt, false, n, B, false, n, E, n, m, n, rt, -1.0, 0, st);
+    add_cols(E, M, m, n, n, st);
+    const double ne = norm_host(h, E, (long long)m * n, true);
+    if (!(ne > 1e-14 * normM)) break;
+    cur = E;
+  }
+  if (rt <= 0) return false;
+  gemm(Qt, true, n, M, false, n, B, n, rt, n, m, 1.0, 0, st);                          // B = Qt^T M (rt x n)
+  SvdOut r = svd_jacobi(h, B, rt, n, cap);
+  // M = Qt B = (Qt U_B) S V^T :  US = Qt r.US ; Vt = r.Vt
+  o.k = r.k;
+  o.sig = r.sig;
+  o.dsig = r.dsig;
+  r.dsig = nullptr;
+  o.Vt = r.Vt;
+  r.Vt = nullptr;
+  o.US = dmalloc((long long)m * o.k);
+  gemm(Qt, false, n, r.US, false, o.k, o.US, o.k, m, o.k, rt, 1.0, 0, st);
+  r.release();
+  return true;
+}
+
 // Exact truncated SVD by one-sided Jacobi on the shorter side.
 SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   cudaStream_t st = h->st;
@@ -177,6 +320,8 @@ SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   int p = std::min(m, n);
   double* dsigall = h->ws.get<double>("svd_sig", p);
   double* V = nullptr;
+  if (prof_on()) h->sync();
+  auto t0 = std::chrono::steady_clock::now();
   if (m <= n) {
     jacobi(T2, n, m, 1, n, nullptr, 60, status, st);
     vec_norms(T2, n, m, 1, n, dsigall, st);
@@ -192,6 +337,14 @@ SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   SGTN_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
   h->sync();
   if (hs < 0) throw SgtnError(-4, "Jacobi SVD did not converge");
+  if (prof_on()) {
+    SvdProf& e = g_prof[std::string(g_tag) + (std::max(m, n) > 128 ? "/jacobi_long" : "/jacobi")];
+    e.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    e.calls++;
+    e.iters += hs;
+    e.max_m = std::max(e.max_m, p);
+    e.max_n = std::max(e.max_n, std::max(m, n));
+  }
   std::vector<int> idx(p);
   std::iota(idx.begin(), idx.end(), 0);
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return s[a] > s[b]; });
@@ -234,17 +387,81 @@ SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap) {
 }
 
 // Top-k right singular subspace of Theta (m x n) by block subspace iteration:
-// Q <- orth(Theta^T Theta Q) with a block of s = min(p, k + 32) vectors from a
-// fixed pseudo-random start, until the subspace moves by less than 1e-13
-// (largest principal-angle sine); then Rayleigh-Ritz: the SVD of Theta Q (s
-// columns, exact Jacobi) gives the singular values and Q V the vectors.
+// Q <- orth(Theta^T orth(Theta Q)) with a block of s = min(p, k + 32) vectors
+// from a fixed pseudo-random start, until the leading Ritz vectors move by
+// less than 1e-13 (largest principal-angle sine); the Rayleigh-Ritz step (SVD
+// of Theta Q, s columns, exact) gives the singular values and Q W the vectors.
 SvdOut svd_subspace(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   MatFn mul = [=](const double* Q, int s, double* Y) { gemm(Th, false, n, Q, false, s, Y, s, m, s, n, 1.0, 0, h->st); };
   MatFn tmul = [=](const double* Y, int s, double* Z) { gemm(Th, true, n, Y, false, s, Z, s, n, s, m, 1.0, 0, h->st); };
   return svd_subspace_op(h, m, n, cap, mul, tmul);
 }
 
-// Same, with Theta given only through Y = Theta Q and Z = Theta^T Y.
+// Orthonormal basis of the columns of M (len x k, row-major) into Q by
+// CholeskyQR passes (Gram matrix, Cholesky factor R, multiplication by R^{-1}),
+// repeated until the Gram matrix of a pass's input lies within 0.1 of the
+// identity: that pass leaves an orthogonality error of a few ulps
+// (CholeskyQR2; a shifted first factor when the unshifted one fails, as in
+// shifted CholeskyQR3).  first_f32: the first factor in FP32 arithmetic (the
+// FP64 passes after it remove its rounding).  Returns false if a pivot of a
+// later pass fails (numerically dependent columns); Q is then unspecified.
+// Q must not alias M.
+bool cqr_orth(sgtn_inst* h, const double* M, int len, int k, double* Q, bool first_f32) {
+  F64Scope f64;
+  cudaStream_t st = h->st;
+  if (k < 1 || len < k) return false;
+  double* G = h->ws.get<double>("cqo_G", size_t(k) * k);
+  double* R = h->ws.get<double>("cqo_R", size_t(k) * k);
+  double* Ri = h->ws.get<double>("cqo_Ri", size_t(k) * k);
+  double* T = h->ws.get<double>("cqo_T", size_t(len) * k);
+  double* T2 = h->ws.get<double>("cqo_T2", size_t(len) * k);
+  int* status = h->ws.get<int>("cqo_status", 1);
+  std::vector<double> hG(size_t(k) * k);
+  auto chol = [&](double shift, bool f32) {
+    cholesky_inv(G, k, shift, R, Ri, status, st, f32);
+    int hs = 0;
+    SGTN_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    h->sync();
+    return hs == 0;
+  };
+  const double* cur = M;
+  for (int pass = 0; pass < 4; ++pass) {
+    gemm(cur, true, k, cur, false, k, G, k, k, k, len, 1.0, 0, st);   // G = cur^T cur
+    SGTN_CUDA(cudaMemcpyAsync(hG.data(), G, hG.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    bool last = pass == 3;
+    if (pass == 0) {
+      bool ok = chol(0.0, first_f32);
+      if (!ok && first_f32) ok = chol(0.0, false);
+      if (!ok) {
+        double tr = 0;
+        for (int i = 0; i < k; ++i) tr += hG[size_t(i) * k + i];
+        if (!(tr > 0) || !std::isfinite(tr)) return false;
+        double shift = 11.0 * (double(len) * k + double(k) * (k + 1)) * 2.220446049250313e-16 * tr;
+        if (!chol(shift, false)) return false;
+      }
+    } else {
+      if (!chol(0.0, false)) return false;
+      double dev = 0;
+      for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) dev = std::max(dev, std::fabs(hG[size_t(i) * k + j] - (i == j ? 1.0 : 0.0)));
+      if (!std::isfinite(dev)) return false;
+      last = last || dev < 0.1;
+    }
+    double* out = last ? Q : (cur == T ? T2 : T);
+    gemm(cur, false, k, Ri, false, k, out, k, len, k, k, 1.0, 0, st);  // out = cur R^{-1}
+    cur = out;
+    if (last) break;
+  }
+  h->check();
+  return true;
+}
+
+// Same, with Theta given only through Y = Theta Q and Z = Theta^T Y.  Each
+// iteration orthonormalises both products by CholeskyQR (Y before it is
+// multiplied back, so that no condition number is squared); every second
+// iteration a Rayleigh-Ritz step (exact SVD of Theta Q) gives the Ritz
+// vectors, and the iteration stops when the leading min(cap, k) of them moved
+// by less than 1e-13 (largest principal-angle sine) since the previous check.
 SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, const MatFn& tmul) {
   F64Scope f64;
   cudaStream_t st = h->st;
@@ -253,62 +470,85 @@ SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, co
   double* Q = h->ws.get<double>("ss_Q", size_t(n) * s);
   double* Qn = h->ws.get<double>("ss_Qn", size_t(n) * s);
   double* Y = h->ws.get<double>("ss_Y", size_t(m) * s);
+  double* Yq = h->ws.get<double>("ss_Yq", size_t(m) * s);
+  double* Z = h->ws.get<double>("ss_Z", size_t(n) * s);
   double* G = h->ws.get<double>("ss_G", size_t(s) * s);
-  double* sig = h->ws.get<double>("ss_sig", s);
-  int* status = h->ws.get<int>("ss_status", 1);
-  pseudo_random(Q, (long long)n * s, 12345, st);
-  int k_active = s;
-  // orthonormal basis of the columns of Z (len x kk), ordered by singular value
-  auto orth = [&](double* Z, int len, int& kk, double* out) {
-    SvdOut o = svd_dense(h, Z, len, kk, kk);
+  double* Vp = h->ws.get<double>("ss_Vp", size_t(n) * s);
+  double* ones = h->ws.get<double>("ss_ones", s);
+  fill(ones, s, 1.0, st);
+  // orthonormal basis of the columns of A (len x kk) into out; dependent
+  // columns (a failed pivot) go through the rank-trimmed SVD basis instead
+  auto orth = [&](double* A, int len, int& kk, double* out) {
+    if (cqr_orth(h, A, len, kk, out, true)) return;
+    SvdOut o = svd_dense(h, A, len, kk, kk);
     gather_vecs(o.US, len, o.k, 1, h->iota, o.dsig + o.k, o.k, out, o.k, 1, st);
     kk = o.k;
     o.release();
   };
-  {
-    double* Z0 = h->ws.get<double>("ss_Z", size_t(n) * s);
-    copy(Z0, Q, (long long)n * s, st);
-    orth(Z0, n, k_active, Q);
-  }
+  int k = s;
+  pseudo_random(Z, (long long)n * s, 12345, st);
+  orth(Z, n, k, Q);
   const int maxit = 60;
-  int it = 0;
-  for (; it < maxit; ++it) {
-    mul(Q, k_active, Y);                                                                     // Y = Theta Q
-    double* Z = h->ws.get<double>("ss_Z", size_t(n) * k_active);
-    tmul(Y, k_active, Z);                                                                    // Z = Theta^T Y
-    int kn = k_active;
-    orth(Z, n, kn, Qn);
-    // subspace change of the leading min(cap, kn) directions: || Qk - Qn (Qn^T Qk) ||
-    int kc = std::min(cap, std::min(kn, k_active));
-    gemm(Qn, true, kn, Q, false, k_active, G, kc, kn, kc, n, 1.0, 0, st);                    // Qn^T Q[:, :kc]
-    double* Rr = h->ws.get<double>("ss_R", size_t(n) * kc);
-    // Rr = Q[:, :kc] - Qn G   (Q row-major n x k_active: first kc columns via ldx)
-    gemm(Qn, false, kn, G, false, kc, Rr, kc, n, kc, kn, -1.0, 0, st);   // Rr = -Qn G
-    add_cols(Rr, Q, n, kc, k_active, st);                                  // Rr += Q[:, :kc]
-    double ch = norm_host(h, Rr, (long long)n * kc, true);
-    std::swap(Q, Qn);
-    k_active = kn;
-    if (it >= 2 && ch < 1e-13 * std::sqrt(double(kc))) break;
+  int kc_prev = -1;
+  for (int it = 0;; ++it) {
+    mul(Q, k, Y);                                                                 // Y = Theta Q
+    const bool last = it + 1 >= maxit;
+    if (it % 2 == 1 || last) {
+      // Rayleigh-Ritz: Theta Q = U S W^T; Ritz vectors Q W, Ritz values S
+      SvdOut ob = svd_dense(h, Y, m, k, k);
+      const int kb = ob.k, kc = std::min(cap, kb);
+      gemm(Q, false, k, ob.Vt, true, k, Qn, kb, n, kb, k, 1.0, 0, st);           // Qn = Q W  (n x kb)
+      double ch = INFINITY;
+      if (kc == kc_prev) {
+        // || Vp - Qn_c (Qn_c^T Vp) ||  with Qn_c the leading kc Ritz vectors
+        double* Rr = h->ws.get<double>("ss_R", size_t(n) * kc);
+        gemm(Qn, true, kb, Vp, false, kc, G, kc, kc, kc, n, 1.0, 0, st);
+        gemm(Qn, false, kb, G, false, kc, Rr, kc, n, kc, kc, -1.0, 0, st);
+        add_cols(Rr, Vp, n, kc, kc, st);
+        ch = norm_host(h, Rr, (long long)n * kc, true);
+      }
+      const bool conv = ch < 1e-13 * std::sqrt(double(kc));
+      if (conv || last) {
+        // no gap at the cut: the truncation is ambiguous; keep the last
+        // Rayleigh-Ritz result and count the cut
+        if (!conv) ++h->unconverged_cuts;
+        if (prof_on()) {
+          SvdProf& e = g_prof[std::string(g_tag) + "/subspace"];
+          e.iters += it + 1;
+          e.calls++;
+          if (std::getenv("SGTN_TRACE"))
+            fprintf(stderr, "[sgtn] subspace m=%d n=%d cap=%d it=%d ch=%.2e s1=%.3e s_cap=%.3e s_cap+1=%.3e s_last=%.3e\n",
+                    m, n, cap, it + 1, ch, ob.sig[0], ob.sig[kc - 1], kc < kb ? ob.sig[kc] : 0.0, ob.sig[kb - 1]);
+        }
+        SvdOut o;
+        o.k = kc;
+        o.sig.assign(ob.sig.begin(), ob.sig.begin() + kc);
+        std::vector<double> sv(2 * kc);
+        for (int i = 0; i < kc; ++i) sv[i] = o.sig[i], sv[kc + i] = 1.0 / o.sig[i];
+        o.dsig = dmalloc(2 * kc);
+        SGTN_CUDA(cudaMemcpyAsync(o.dsig, sv.data(), 2 * kc * sizeof(double), cudaMemcpyHostToDevice, st));
+        o.US = dmalloc((long long)m * kc);
+        gather_vecs(ob.US, m, kb, 1, h->iota, ones, kc, o.US, kc, 1, st);
+        o.Vt = dmalloc((long long)kc * n);
+        gather_vecs(Qn, n, kb, 1, h->iota, ones, kc, o.Vt, 1, n, st);
+        ob.release();
+        h->sync();   // sv stays alive until the copy is done
+        return o;
+      }
+      gather_vecs(Qn, n, kb, 1, h->iota, ones, kc, Vp, kc, 1, st);                // Vp = leading kc Ritz vectors
+      kc_prev = kc;
+      // continue from the Ritz basis: Q = Q W, Theta Q = U S
+      std::swap(Q, Qn);
+      k = kb;
+      copy(Y, ob.US, (long long)m * k, st);
+      ob.release();
+    }
+    int ky = k;
+    orth(Y, m, ky, Yq);
+    tmul(Yq, ky, Z);                                                              // Z = Theta^T Yq
+    k = ky;
+    orth(Z, n, k, Q);
   }
-  // no gap at the cut: the truncation is ambiguous; keep the Rayleigh-Ritz
-  // result of the last subspace and count the cut
-  if (it >= maxit) ++h->unconverged_cuts;
-  // Rayleigh-Ritz: B = Theta Q (m x s), exact SVD of B
-  mul(Q, k_active, Y);
-  SvdOut ob = svd_dense(h, Y, m, k_active, cap);    // Y = U S W^T  (W: Vt rows, length k_active)
-  SvdOut o;
-  o.k = ob.k;
-  o.sig = ob.sig;
-  o.US = ob.US;
-  ob.US = nullptr;
-  o.dsig = ob.dsig;
-  ob.dsig = nullptr;
-  // right vectors of Theta: rows of (Q W)^T = W Q^T  -> Vt = ob.Vt (k x s) * Q^T (s x n)
-  o.Vt = dmalloc((long long)o.k * n);
-  gemm(ob.Vt, false, k_active, Q, true, k_active, o.Vt, n, o.k, n, k_active, 1.0, 0, st);
-  ob.release();
-  h->check();
-  return o;
 }
 
 void SvdOut::release() {
@@ -492,17 +732,21 @@ void right_canonical(RowCtx& X, std::vector<Ten>& phi) {
   for (int c = (int)phi.size() - 1; c > 0; --c) {
     Ten& t = phi[c];
     SvdOut o = svd(h, t.p, t.a, t.u * t.b, 1 << 30);
+    const int k = o.k;
+    double* Vt = o.Vt;
+    double* Lf = o.US;
+    o.Vt = o.US = nullptr;
+    o.release();
     Ten& l = phi[c - 1];
-    double* nl = dmalloc((long long)l.a * l.u * o.k);
-    gemm(l.p, false, l.b, o.US, false, o.k, nl, o.k, l.a * l.u, o.k, l.b, 1.0, 0, h->st);
+    double* nl = dmalloc((long long)l.a * l.u * k);
+    gemm(l.p, false, l.b, Lf, false, k, nl, k, l.a * l.u, k, l.b, 1.0, 0, h->st);
+    dfree(Lf);
     dfree(l.p);
     l.p = nl;
-    l.b = o.k;
+    l.b = k;
     dfree(t.p);
-    t.p = o.Vt;
-    o.Vt = nullptr;
-    t.a = o.k;
-    o.release();
+    t.p = Vt;
+    t.a = k;
   }
 }
 
@@ -724,7 +968,7 @@ SvdOut theta_svd(RowCtx& X, int c, const ThetaOp& T, int cap) {
   }
   MatFn mul = [&](const double* Q, int s, double* Y) { theta_mul(X, c, T, Q, s, Y); };
   MatFn tmul = [&](const double* Y, int s, double* Z) { theta_tmul(X, c, T, Y, s, Z); };
-  return svd_subspace_op(h, T.m, T.n, cap, mul, tmul);
+  return profiled(h, "", T.m, T.n, [&] { return svd_subspace_op(h, T.m, T.n, cap, mul, tmul); });
 }
 
 // One left-right-left sweep of one-site overlap maximisation (Fig. 8d).
@@ -733,6 +977,7 @@ SvdOut theta_svd(RowCtx& X, int c, const ThetaOp& T, int cap) {
 // reaches the final centre, and its logarithm is returned.
 double variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
   sgtn_inst* h = X.h;
+  TagScope tag("sweep");
   const bool renorm = true;
   const int C = (int)phi.size();
   right_canonical(X, phi);
@@ -805,6 +1050,7 @@ double variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
 // cut a right-canonical phi (centre 0) to bond chi; returns worst retained ratio
 double svd_cut(RowCtx& X, std::vector<Ten>& phi, int chi) {
   F64Scope f64;
+  TagScope tag("cut");
   sgtn_inst* h = X.h;
   double worst = 0.0;
   for (int c = 0; c + 1 < (int)phi.size(); ++c) {
@@ -831,6 +1077,7 @@ double svd_cut(RowCtx& X, std::vector<Ten>& phi, int chi) {
 
 void left_canonical(sgtn_inst* h, MPS& A) {
   F64Scope f64;
+  TagScope tag("left_canonical");
   const int C = A.C;
   for (int c = 0; c + 1 < C; ++c) {
     int s = A.phys[c], l = A.bond[c], r = A.bond[c + 1];
@@ -899,6 +1146,7 @@ void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& wo
     const Column& K_ = X.col(c);
     ThetaOp T = theta_op(X, c, K, kp);
     int m = K_.nBL() * X.chl(c);
+    TagScope tag("zipper");
     SvdOut o = theta_svd(X, c, T, 2 * chi);
     phi[c].p = o.Vt;
     o.Vt = nullptr;
@@ -1018,6 +1266,12 @@ void contract_boundary(sgtn_inst* h, int chi, int n_sweeps) {
   h->unconverged_cuts = 0;
   for (int r = R - 1; r >= 1; --r) row_step(h, r, chi, n_sweeps, h->psi[r - 1], worst);
   h->logz = h->log_offset + top_overlap(h);
+  if (prof_on()) {
+    for (auto& kv : g_prof)
+      fprintf(stderr, "[sgtn] svd %-22s calls %6lld  %9.1f ms  iters %6lld  max %d x %d\n", kv.first.c_str(),
+              kv.second.calls, kv.second.ms, kv.second.iters, kv.second.max_m, kv.second.max_n);
+    g_prof.clear();
+  }
   h->worst_sv = worst;
   h->chi = chi;
   h->n_sweeps = n_sweeps;

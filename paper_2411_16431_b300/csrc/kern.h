@@ -77,7 +77,15 @@ void jacobi(double* X, int len, int p, long long si, long long sj, double* V, in
             cudaStream_t st);
 // Upper Cholesky factor R of (G + shift I) (n x n, row-major; R^T R = G + shift I)
 // and R^{-1}, one CTA.  status[0] = 0 on success, j+1 if pivot j was not positive.
-void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv, int* status, cudaStream_t st);
+// f32: factor in FP32 arithmetic (inputs and outputs stay FP64).
+void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv, int* status, cudaStream_t st,
+                  bool f32 = false);
+// Cholesky with diagonal pivoting of a PSD G (n x n, n <= 160), stopped at the
+// numerical rank (largest remaining pivot <= max(tol_rel * max diag G, tol_abs)):
+// rank[0] = r, perm[0..r) the pivot order, R and R^{-1} (r x r upper triangular,
+// leading dimension n) with G[perm][perm] = R^T R on the leading block.  One CTA.
+void pchol_inv(const double* G, int n, double tol_rel, double tol_abs, double* R, double* Rinv, int32_t* perm,
+               int* rank, cudaStream_t st);
 double* trace_scratch();
 void vec_norms(const double* X, int len, int p, long long si, long long sj, double* out, cudaStream_t st);
 // out[i*oi + jj*oj] = scale[jj] * X[i*si + perm[jj]*sj]

@@ -227,6 +227,145 @@ __global__ void __launch_bounds__(1024) jacobi_smem_kernel(double* X, int len, i
     for (long long e = threadIdx.x; e < (long long)p * p; e += blockDim.x) V[e] = Vs[e];
 }
 
+// Thread-block-cluster variant: the p vectors are spread over the shared
+// memories of the cluster's P CTAs (vector j in CTA j % P, slot j / P, with
+// its column of V beside it).  In each round-robin step the warps of all CTAs
+// rotate disjoint pairs, reading and writing both vectors through distributed
+// shared memory, and a cluster barrier closes the step.  Pairs, rotations and
+// the stopping rule are those of jacobi_body; the FP64 work of a step is spread
+// over P SMs instead of one.
+// RV > 0: vectors of at most 32 RV elements stay in registers between the dot
+// products and the rotation (one distributed-shared-memory round trip a pair).
+template <int RV>
+__global__ void __launch_bounds__(512) jacobi_cluster_kernel(double* X, int len, int p, long long si, long long sj,
+                                                              double* V, int max_sweeps, double tol, int* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double csm[];
+  __shared__ double red[32];
+  __shared__ double fro_part;
+  __shared__ int flag[2];
+  const int P = int(cl.num_blocks()), rank = int(cl.block_rank());
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int slots = (p + P - 1) / P;
+  double* Xs = csm;                                   // slots x len
+  double* Vs = V ? csm + (long long)slots * len : nullptr;   // slots x p
+  double f = 0;
+  for (int l = 0; l < slots; ++l) {
+    const int j = l * P + rank;
+    if (j >= p) break;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      double v = X[i * si + j * sj];
+      Xs[(long long)l * len + i] = v;
+      f = fma(v, v, f);
+    }
+    if (Vs)
+      for (int i = threadIdx.x; i < p; i += blockDim.x) Vs[(long long)l * p + i] = (i == j) ? 1.0 : 0.0;
+  }
+  f = warp_sum(f);
+  if (lane == 0) red[warp] = f;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < nwarp; ++w) t += red[w];
+    fro_part = t;
+  }
+  cl.sync();
+  double fro = 0;
+  for (int r = 0; r < P; ++r) fro += *cl.map_shared_rank(&fro_part, r);
+  const double zero2 = fro * 1e-30;   // (1e-15 ||X||_F)^2
+  const int pp = p + (p & 1), npair = pp / 2;
+  int sweep = 0;
+  bool done = (p < 2);
+  while (!done && sweep < max_sweeps) {
+    int rot = 0;
+    for (int t = 0; t < pp - 1; ++t) {
+      for (int w = rank + P * warp; w < npair; w += P * nwarp) {
+        int pa = w, pb = pp - 1 - w;
+        int ca = pa == 0 ? 0 : 1 + (pa - 1 + t) % (pp - 1);
+        int cb = pb == 0 ? 0 : 1 + (pb - 1 + t) % (pp - 1);
+        if (ca >= p || cb >= p) continue;
+        double* xa = cl.map_shared_rank(Xs + (long long)(ca / P) * len, ca % P);
+        double* xb = cl.map_shared_rank(Xs + (long long)(cb / P) * len, cb % P);
+        double al = 0, be = 0, ga = 0;
+        double ur[RV > 0 ? RV : 1], vr[RV > 0 ? RV : 1];
+        if constexpr (RV > 0) {
+#pragma unroll
+          for (int q = 0; q < RV; ++q) {
+            const int i = lane + 32 * q;
+            ur[q] = i < len ? xa[i] : 0.0;
+            vr[q] = i < len ? xb[i] : 0.0;
+          }
+#pragma unroll
+          for (int q = 0; q < RV; ++q) {
+            al = fma(ur[q], ur[q], al);
+            be = fma(vr[q], vr[q], be);
+            ga = fma(ur[q], vr[q], ga);
+          }
+        } else {
+          for (int i = lane; i < len; i += 32) {
+            double u = xa[i], v = xb[i];
+            al = fma(u, u, al);
+            be = fma(v, v, be);
+            ga = fma(u, v, ga);
+          }
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (al > zero2 && be > zero2 && fabs(ga) > tol * sqrt(al * be)) {
+          double zeta = (be - al) / (2.0 * ga);
+          double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
+          if constexpr (RV > 0) {
+#pragma unroll
+            for (int q = 0; q < RV; ++q) {
+              const int i = lane + 32 * q;
+              if (i < len) {
+                xa[i] = c * ur[q] - s * vr[q];
+                xb[i] = s * ur[q] + c * vr[q];
+              }
+            }
+          } else {
+            for (int i = lane; i < len; i += 32) {
+              double u = xa[i], v = xb[i];
+              xa[i] = c * u - s * v;
+              xb[i] = s * u + c * v;
+            }
+          }
+          if (Vs) {
+            double* va = cl.map_shared_rank(Vs + (long long)(ca / P) * p, ca % P);
+            double* vb = cl.map_shared_rank(Vs + (long long)(cb / P) * p, cb % P);
+            for (int i = lane; i < p; i += 32) {
+              double u = va[i], v = vb[i];
+              va[i] = c * u - s * v;
+              vb[i] = s * u + c * v;
+            }
+          }
+          rot = 1;
+        }
+      }
+      cl.sync();
+    }
+    int any_local = __syncthreads_or(rot);
+    if (threadIdx.x == 0) flag[sweep & 1] = any_local;
+    cl.sync();
+    int any = 0;
+    for (int r = 0; r < P; ++r) any |= *cl.map_shared_rank(&flag[sweep & 1], r);
+    ++sweep;
+    done = (any == 0);
+  }
+  for (int l = 0; l < slots; ++l) {
+    const int j = l * P + rank;
+    if (j >= p) break;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) X[i * si + j * sj] = Xs[(long long)l * len + i];
+    if (V)
+      for (int i = threadIdx.x; i < p; i += blockDim.x) V[(long long)j * p + i] = Vs[(long long)l * p + i];
+  }
+  if (rank == 0 && threadIdx.x == 0) status[0] = done ? sweep : -1;
+  cl.sync();   // no CTA leaves while another may still read its flags
+}
+
 // Cooperative multi-CTA variant for many columns: one warp rotates one pair
 // per round, rounds are separated by grid-wide barriers (the launch is
 // cooperative, so all CTAs are resident).  flags[s] counts rotations in sweep
@@ -313,28 +452,32 @@ __global__ void __launch_bounds__(128) jacobi_coop_kernel(double* X, int len, in
 }
 
 // Right-looking upper Cholesky in shared memory, then R^{-1} column by column.
+// T is the arithmetic type (float: a cheap first factor whose rounding a later
+// FP64 pass removes); G, R and R^{-1} are FP64 in memory.
+template <class T>
 __global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* G, int n, double shift, double* R,
                                                             double* Rinv, int* status) {
-  extern __shared__ double A[];   // n x n
+  extern __shared__ __align__(16) unsigned char chol_smem[];
+  T* A = reinterpret_cast<T*>(chol_smem);   // n x n
   __shared__ int fail;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     int i = e / n, j = e % n;
-    A[e] = G[e] + (i == j ? shift : 0.0);
+    A[e] = T(G[e] + (i == j ? shift : 0.0));
   }
   if (threadIdx.x == 0) fail = 0;
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     if (threadIdx.x == 0) {
-      double d = A[j * n + j];
-      if (!(d > 0.0)) {
+      T d = A[j * n + j];
+      if (!(d > T(0))) {
         if (!fail) fail = j + 1;
-        A[j * n + j] = 1.0;
+        A[j * n + j] = T(1);
       } else {
         A[j * n + j] = sqrt(d);
       }
     }
     __syncthreads();
-    double r = A[j * n + j];
+    T r = A[j * n + j];
     for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[j * n + i] /= r;
     __syncthreads();
     int m = n - j - 1;
@@ -346,17 +489,102 @@ __global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* G, int
   }
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     int i = e / n, j = e % n;
-    R[e] = j >= i ? A[e] : 0.0;
+    R[e] = j >= i ? double(A[e]) : 0.0;
   }
   // R X = I, one column per thread, back substitution
   for (int c = threadIdx.x; c < n; c += blockDim.x) {
     for (int i = n - 1; i >= 0; --i) {
-      double v = (i == c) ? 1.0 : 0.0;
-      for (int k = i + 1; k <= c; ++k) v -= A[i * n + k] * Rinv[k * n + c];
-      Rinv[i * n + c] = (i <= c) ? v / A[i * n + i] : 0.0;
+      T v = (i == c) ? T(1) : T(0);
+      for (int k = i + 1; k <= c; ++k) v -= A[i * n + k] * T(Rinv[k * n + c]);
+      Rinv[i * n + c] = (i <= c) ? double(v / A[i * n + i]) : 0.0;
     }
   }
   if (threadIdx.x == 0) status[0] = fail;
+}
+
+// Cholesky with diagonal pivoting of a positive semidefinite G (n x n, FP64),
+// stopped at the numerical rank: step j takes the largest remaining diagonal
+// of the Schur complement and stops when it is <= max(tol_rel * max diag(G),
+// tol_abs).  Out: rank r, perm[0..r) (the pivot order), R (r x r upper, row-major
+// with leading dimension n) with G[perm][perm] ~ R^T R on the leading r x r
+// block, and R^{-1} (same layout).
+__global__ void __launch_bounds__(1024) pchol_inv_kernel(const double* G, int n, double tol_rel, double tol_abs,
+                                                         double* R, double* Rinv, int32_t* perm, int* rank) {
+  extern __shared__ double A[];   // n x n, original indexing
+  __shared__ int piv[256];
+  __shared__ double dmax0;
+  __shared__ int rk, qsel;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = G[e];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) piv[i] = i;
+  __syncthreads();
+  if (warp == 0) {
+    double m = 0;
+    for (int i = lane; i < n; i += 32) m = fmax(m, A[i * n + i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) {
+      dmax0 = m;
+      rk = n;
+    }
+  }
+  __syncthreads();
+  const double stop = fmax(tol_rel * dmax0, tol_abs);
+  for (int j = 0; j < n; ++j) {
+    if (warp == 0) {
+      // argmax of the remaining diagonal (ties: lowest position)
+      double bv = -1.0;
+      int bi = n;
+      for (int i = j + lane; i < n; i += 32) {
+        double v = A[piv[i] * n + piv[i]];
+        if (v > bv) bv = v, bi = i;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) bv = ov, bi = oi;
+      }
+      if (lane == 0) {
+        if (!(bv > stop)) {
+          rk = j;
+          qsel = -1;
+        } else {
+          int t = piv[j];
+          piv[j] = piv[bi];
+          piv[bi] = t;
+          A[piv[j] * n + piv[j]] = sqrt(bv);
+          qsel = bi;
+        }
+      }
+    }
+    __syncthreads();
+    if (qsel < 0) break;
+    const int pj = piv[j];
+    const double r = A[pj * n + pj];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[pj * n + piv[i]] /= r;
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int a = piv[j + 1 + e / m], b = piv[j + 1 + e % m];
+      A[a * n + b] -= A[pj * n + a] * A[pj * n + b];
+    }
+    __syncthreads();
+  }
+  const int r = rk;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e / r, k = e % r;
+    R[i * n + k] = k >= i ? A[piv[i] * n + piv[k]] : 0.0;
+  }
+  for (int i = threadIdx.x; i < r; i += blockDim.x) perm[i] = piv[i];
+  __syncthreads();
+  // R X = I by back substitution, one column per thread (R read from global)
+  for (int c = threadIdx.x; c < r; c += blockDim.x) {
+    for (int i = r - 1; i >= 0; --i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= c; ++k) v -= A[piv[i] * n + piv[k]] * Rinv[k * n + c];
+      Rinv[i * n + c] = (i <= c) ? v / A[piv[i] * n + piv[i]] : 0.0;
+    }
+  }
+  if (threadIdx.x == 0) rank[0] = r;
 }
 
 __global__ void vec_norms_kernel(const double* X, int len, int p, long long si, long long sj, double* out) {
@@ -701,9 +929,55 @@ void jacobi(double* X, int len, int p, long long si, long long sj, double* V, in
     cudaFuncSetAttribute(jacobi_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxSmem));
     attr_set = true;
   }
+  // cluster size: up to 16 CTAs (one pair per warp and step), if the vectors fit
+  static int max_cluster = 0;
+  if (!max_cluster) {
+    for (void* f : {(void*)jacobi_cluster_kernel<0>, (void*)jacobi_cluster_kernel<4>}) {
+      cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxSmem));
+    }
+    max_cluster = 8;
+    cudaLaunchConfig_t q = {};
+    cudaLaunchAttribute qa[1];
+    q.gridDim = dim3(16);
+    q.blockDim = dim3(512);
+    q.dynamicSmemBytes = 64 * 1024;
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = 16;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, (void*)jacobi_cluster_kernel<0>, &q) == cudaSuccess && ncl >= 1)
+      max_cluster = 16;
+    cudaGetLastError();
+  }
+  const int npair = (p + 1) / 2;
+  int P = std::max(1, std::min(max_cluster, npair));
+  const int slots = (p + P - 1) / P;
+  const size_t csmem = (size_t(slots) * len + (V ? size_t(slots) * p : 0)) * sizeof(double);
+  const int nw = std::min(16, (npair + P - 1) / P);
   {
     KTimer t("jacobi_f64", st);
-    if (smem <= kMaxSmem) {
+    if (p >= 8 && csmem <= kMaxSmem) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      cfg.gridDim = dim3(P);
+      cfg.blockDim = dim3(32 * nw);
+      cfg.dynamicSmemBytes = csmem;
+      cfg.stream = st;
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = P;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      if (len <= 128)
+        cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<4>, X, len, p, si, sj, V, max_sweeps, tol, status);
+      else
+        cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<0>, X, len, p, si, sj, V, max_sweeps, tol, status);
+    } else if (smem <= kMaxSmem) {
       jacobi_smem_kernel<<<1, 1024, smem, st>>>(X, len, p, si, sj, V, max_sweeps, tol, status);
     } else {
       // flags (one per sweep) and the Frobenius norm live in a small static scratch
@@ -731,13 +1005,33 @@ void jacobi(double* X, int len, int p, long long si, long long sj, double* V, in
   ++g_count.launches;
 }
 
-void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv, int* status, cudaStream_t st) {
+void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv, int* status, cudaStream_t st,
+                  bool f32) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(cholesky_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(cholesky_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(cholesky_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr = true;
   }
-  cholesky_inv_kernel<<<1, 1024, size_t(n) * n * sizeof(double), st>>>(G, n, shift, R, Rinv, status);
+  if (f32) {
+    KTimer t("cholesky_f32", st);
+    cholesky_inv_kernel<float><<<1, 1024, size_t(n) * n * sizeof(float), st>>>(G, n, shift, R, Rinv, status);
+  } else {
+    KTimer t("cholesky_f64", st);
+    cholesky_inv_kernel<double><<<1, 1024, size_t(n) * n * sizeof(double), st>>>(G, n, shift, R, Rinv, status);
+  }
+  ++g_count.launches;
+}
+
+void pchol_inv(const double* G, int n, double tol_rel, double tol_abs, double* R, double* Rinv, int32_t* perm,
+               int* rank, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(pchol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr = true;
+  }
+  KTimer t("pcholesky_f64", st);
+  pchol_inv_kernel<<<1, 1024, size_t(n) * n * sizeof(double), st>>>(G, n, tol_rel, tol_abs, R, Rinv, perm, rank);
   ++g_count.launches;
 }
 
