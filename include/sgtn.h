@@ -178,13 +178,18 @@ int sgtn_conditionals_noalloc(sgtn_h h, int32_t step, int32_t count, const int32
 void sgtn_stats(int64_t* launches, double* flops, int64_t* evals);
 
 /* Optional per-kernel timing (the paper has no counterpart): when enabled,
- * every launch of the named kernels ("seg_gemm_f64", "jacobi_f64",
- * "score_f64") is bracketed by CUDA events on its stream; reset clears the
- * totals.  sgtn_kernel_time returns the summed device time in ms, the number
- * of timed launches and their algorithmic flops (SGTN_ERR_ARG if the kernel
- * was not timed). */
+ * every launch of the library's kernels is bracketed by CUDA events on its
+ * stream, booked under a label naming the kernel and its role (for example
+ * "site_diagram_f64", "theta_mul_f64", "gemm_f32", "tc_gemm_3xtf32",
+ * "jacobi_f64", "cholesky_f64", "score_f32"); reset clears the totals.
+ * sgtn_kernel_time returns the summed device time in ms, the number of timed
+ * launches and their algorithmic flops (SGTN_ERR_ARG if the label was not
+ * seen).  sgtn_kernel_names writes the labels seen so far, comma-separated and
+ * NUL-terminated, into buf (at most cap bytes, truncated) and returns the
+ * length the full list needs (without the NUL). */
 void sgtn_kernel_timing(int32_t enable, int32_t reset);
 int sgtn_kernel_time(const char* name, double* ms, int64_t* launches, double* flops);
+int32_t sgtn_kernel_names(char* buf, int32_t cap);
 
 const char* sgtn_last_error(sgtn_h h);
 void sgtn_destroy(sgtn_h h);

@@ -236,6 +236,16 @@ int sgtn_kernel_time(const char* name, double* ms, int64_t* launches, double* fl
   return SGTN_OK;
 }
 
+int32_t sgtn_kernel_names(char* buf, int32_t cap) {
+  const std::string s = ktimer_names();
+  if (buf && cap > 0) {
+    const size_t n = std::min(s.size(), size_t(cap - 1));
+    std::memcpy(buf, s.data(), n);
+    buf[n] = '\0';
+  }
+  return int32_t(s.size());
+}
+
 const char* sgtn_last_error(sgtn_h h) { return h ? h->err.c_str() : "null handle"; }
 
 void sgtn_destroy(sgtn_h h) {

@@ -323,7 +323,11 @@ SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   if (prof_on()) h->sync();
   auto t0 = std::chrono::steady_clock::now();
   if (m <= n) {
-    jacobi(T2, n, m, 1, n, nullptr, 60, status, st);
+    // the rows are the vectors; V (m x m) accumulates the rotations, so the
+    // left factor comes out exactly orthogonal (U = V), also for directions
+    // with tiny singular values
+    V = h->ws.get<double>("svd_V", size_t(m) * m);
+    jacobi(T2, n, m, 1, n, V, 60, status, st);
     vec_norms(T2, n, m, 1, n, dsigall, st);
   } else {
     V = h->ws.get<double>("svd_V", size_t(n) * n);
@@ -373,7 +377,7 @@ SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   o.Vt = dmalloc((long long)k * n);
   if (m <= n) {
     gather_vecs(T2, n, 1, n, dperm, o.dsig + k, k, o.Vt, 1, n, st);        // rows / sigma
-    gemm(Th, false, n, o.Vt, true, n, o.US, k, m, k, n, 1.0, 0, st);      // Theta Vt^T = U S
+    gather_vecs(V, m, 1, m, dperm, o.dsig, k, o.US, k, 1, st);             // U S = V diag(sigma)
   } else {
     double* ones = h->ws.get<double>("svd_ones", k);
     fill(ones, k, 1.0, st);
@@ -611,6 +615,7 @@ void site_diagram(RowCtx& X, int c, const double* Kt, int kp, double* Th) {
   long long m = (long long)K_.nBL() * chl, n = (long long)K_.nU * kp;
   SGTN_CUDA(cudaMemsetAsync(Th, 0, size_t(m * n) * sizeof(double), X.h->st));
   SegGemm a;
+  a.name = "site_diagram";
   a.X = X.Ahat[c];
   a.Y = Kt;
   a.O = Th;
@@ -666,6 +671,7 @@ double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
   double* Lt = h->ws.get<double>("lupd_Lt", size_t(K_.nK()) * phi.b * chr);
   SGTN_CUDA(cudaMemsetAsync(Lt, 0, size_t(K_.nK()) * phi.b * chr * sizeof(double), h->st));
   SegGemm a;
+  a.name = "env_update";
   a.X = N;
   a.p = phi.b;
   a.q = chl;
@@ -697,6 +703,7 @@ double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
   // Lnext[b][br][chr] = sum_k Wk[k][br] Ltil[k][b][chr]   (batched over b)
   double* Ln = dmalloc((long long)phi.b * K_.nBR() * chr);
   SegGemm g;
+  g.name = "env_update";
   g.X = K_.Wk;
   g.p = K_.nBR();
   g.q = K_.nK();
@@ -779,6 +786,7 @@ ThetaOp theta_op(RowCtx& X, int c, const double* K, int kp) {
   double* Kt = absorb(X, c, K, kp, "ktil");
   T.blocks = h->ws.get<double>("theta_bs", size_t(T.nseg) * T.chl * kp);
   SegGemm a;
+  a.name = "site_diagram";
   a.X = X.Ahat[c];
   a.Y = Kt;
   a.O = T.blocks;
@@ -819,6 +827,7 @@ void theta_mul(RowCtx& X, int c, const ThetaOp& T, const double* Q, int s, doubl
   const TermTable& t = X.col(c).bs_rows;
   SGTN_CUDA(cudaMemsetAsync(Y, 0, size_t(T.m) * s * sizeof(double), X.h->st));
   SegGemm a;
+  a.name = "theta_mul";
   a.X = T.blocks;
   a.p = T.chl;
   a.q = T.kp;
@@ -855,6 +864,7 @@ void theta_tmul(RowCtx& X, int c, const ThetaOp& T, const double* Y, int s, doub
   const TermTable& t = X.col(c).bs_cols;
   SGTN_CUDA(cudaMemsetAsync(Z, 0, size_t(T.n) * s * sizeof(double), X.h->st));
   SegGemm a;
+  a.name = "theta_mul";
   a.X = T.blocks;
   a.p = T.kp;
   a.q = T.chl;
@@ -892,6 +902,7 @@ double* theta_left(RowCtx& X, int c, const ThetaOp& T, const double* L, int a_di
   const TermTable& tt = X.col(c).bs_cols;
   SGTN_CUDA(cudaMemsetAsync(t, 0, size_t(a_dim) * T.n * sizeof(double), X.h->st));
   SegGemm a;
+  a.name = "theta_env";
   a.X = L;
   a.p = a_dim;
   a.q = T.chl;
@@ -927,6 +938,7 @@ double* theta_right(RowCtx& X, int c, const ThetaOp& T, const Ten& phi) {
   const TermTable& tt = X.col(c).bs_rows;
   SGTN_CUDA(cudaMemsetAsync(Rp, 0, size_t(T.m) * phi.a * sizeof(double), X.h->st));
   SegGemm a;
+  a.name = "theta_env";
   a.X = T.blocks;
   a.p = T.chl;
   a.q = T.kp;
@@ -1090,6 +1102,7 @@ void left_canonical(sgtn_inst* h, MPS& A) {
     double* nn = dmalloc((long long)s2 * o.k * r2);
     // nn[s][k][r2] = sum_r Rm[k][r] A[s][r][r2]   (batched over s)
     SegGemm g;
+    g.name = "mps_absorb";
     g.X = Rm;
     g.p = o.k;
     g.q = r;

@@ -440,6 +440,7 @@ void prepare_scores(Step& S, const int32_t* hcfg) {
     double* Fn = S.alloc<double>(size_t(K_.nBL()) * chl * K);
     SGTN_CUDA(cudaMemsetAsync(Fn, 0, size_t(K_.nBL()) * chl * K * sizeof(double), st));
     SegGemm a;
+    a.name = "renv";
     a.X = S.Ahat[cc];
     a.p = chl;
     a.q = chr;

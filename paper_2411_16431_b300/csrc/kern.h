@@ -29,6 +29,7 @@ void ktimer_end(cudaStream_t st, double flops);
 void ktimer_enable(bool on);
 void ktimer_reset();
 bool ktimer_read(const char* name, double* ms, long long* n, double* flops);
+std::string ktimer_names();   // comma-separated names seen so far
 struct KTimer {
   cudaStream_t st;
   double flops;
@@ -62,6 +63,7 @@ struct SegGemm {
   long long nterm = 0;   // host-side term count for the FLOP counter (table mode)
   double alpha = 1.0;
   int accumulate = 0;
+  const char* name = nullptr;   // timing label (role of the call); "_f32" / "_f64" is appended
 };
 void seg_gemm(const SegGemm& a, cudaStream_t st);
 

@@ -852,11 +852,12 @@ void seg_gemm(const SegGemm& a_in, cudaStream_t st) {
   if (a.nseg <= 0 || a.p <= 0 || a.s <= 0) return;
   dim3 grid(a.nseg, (a.p + TM - 1) / TM, (a.s + TN - 1) / TN);
   double fl = 2.0 * a.p * a.q * a.s * double(a.seg_ptr ? a.nterm : (a.splitk ? 1 : a.nseg));
+  const std::string nm = std::string(a.name ? a.name : "seg_gemm") + (a.f32 ? "_f32" : "_f64");
   if (a.f32) {
-    KTimer t("seg_gemm_f32", st, fl);
+    KTimer t(nm.c_str(), st, fl);
     seg_gemm_kernel<float><<<grid, 256, 0, st>>>(a);
   } else {
-    KTimer t("seg_gemm_f64", st, fl);
+    KTimer t(nm.c_str(), st, fl);
     seg_gemm_kernel<double><<<grid, 256, 0, st>>>(a);
   }
   ++g_count.launches;
@@ -887,6 +888,7 @@ void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, lon
   a.nseg = 1;
   a.alpha = alpha;
   a.accumulate = accumulate;
+  a.name = "gemm";
   long long tiles = (long long)((m + TM - 1) / TM) * ((n + TN - 1) / TN);
   if (tiles < 148 && k >= 1024) {
     // few output tiles and a long reduction: split K over CTAs, then reduce
@@ -910,6 +912,7 @@ void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, lon
     b.splitk = chunk;
     b.alpha = 1.0;
     b.accumulate = 0;
+    b.name = "gemm_splitk";
     seg_gemm(b, st);
     splitk_reduce_kernel<<<blocks_for((long long)m * n), 256, 0, st>>>(part, nsplit, (long long)m * n, n, O, ldo, alpha,
                                                                         accumulate);

@@ -37,6 +37,8 @@ def load():
     L.sgtn_conditionals.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I32P, _F64P]
     L.sgtn_branch_step.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, _I32P, _F64P, _I32P, _F64P,
                                    _I32P, _F64P]
+    L.sgtn_kernel_names.argtypes = [ct.c_char_p, ct.c_int32]
+    L.sgtn_kernel_names.restype = ct.c_int32
     L.sgtn_search.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I8P, _I64P, _F64P, _F64P, _I32P]
     L.sgtn_conditionals_noalloc.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I32P, _F64P]
     L.sgtn_energies.argtypes = [ct.c_void_p, ct.c_int32, _I8P, _I64P]
@@ -80,6 +82,15 @@ def kernel_time(name):
     if load().sgtn_kernel_time(name.encode(), ct.byref(ms), ct.byref(n), ct.byref(fl)) != 0:
         return None
     return ms.value, n.value, fl.value
+
+
+def kernel_names():
+    """Labels of the timed kernels seen so far."""
+    L = load()
+    n = L.sgtn_kernel_names(None, 0)
+    buf = ct.create_string_buffer(n + 1)
+    L.sgtn_kernel_names(buf, n + 1)
+    return [x for x in buf.value.decode().split(",") if x]
 
 
 class SgtnError(RuntimeError):
