@@ -5,6 +5,8 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <string>
 #include <vector>
@@ -19,28 +21,34 @@ namespace {
 
 constexpr int TM = 64, TN = 64, TK = 16;
 
-struct SegDev {
-  SegGemm a;
-};
-
-template <class CT>
+// Segmented gathered GEMM.  One CTA (256 threads, a 16 x 16 grid) owns a
+// BM x BN tile of one output segment and runs over the flattened (term,
+// k-chunk) sequence of that segment: the operand tiles of the next step are
+// loaded into registers while the current ones are multiplied out of shared
+// memory (one barrier per step).  Thread (ty, tx) accumulates rows ty + 16u
+// and columns tx + 16v of the tile in the arithmetic type CT.  Term coefficients and column
+// scales are applied to the Y tile as it is stored.  Tile loads run along
+// whichever operand index has unit stride, so they coalesce.
+template <class CT, int BM, int BN>
 __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
-  __shared__ CT Xs[TK][TM + 1];
-  __shared__ CT Ys[TK][TN + 1];
+  constexpr int RM = BM / 16, RN = BN / 16;
+  constexpr int XL = (BM * TK + 255) / 256, YL = (TK * BN + 255) / 256;
+  __shared__ CT Xs[2][TK][BM + 1];
+  __shared__ CT Ys[2][TK][BN + 1];
   const int seg = blockIdx.x;
-  const int i0 = blockIdx.y * TM, j0 = blockIdx.z * TN;
+  const int i0 = blockIdx.y * BM, j0 = blockIdx.z * BN;
   const int tid = threadIdx.x;
   const int ty = tid / 16, tx = tid % 16;
-  CT acc[4][4];
+  CT acc[RM][RN];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < RM; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = CT(0);
+    for (int v = 0; v < RN; ++v) acc[u][v] = CT(0);
   int t0, t1;
   long long ooff;
   int qlen = a.q;
   if (a.splitk) {
-    int k_lo = seg * a.splitk;
+    const int k_lo = seg * a.splitk;
     qlen = min(a.splitk, a.q - k_lo);
   }
   if (a.seg_ptr) {
@@ -52,10 +60,13 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
     t1 = seg + 1;
     ooff = (long long)seg * a.ors;
   }
-  for (int t = t0; t < t1; ++t) {
-    long long xoff, yoff;
-    double cf = 1.0;
-    const double* cs = nullptr;
+  const int nk = (qlen + TK - 1) / TK;
+  const int nsteps = (t1 - t0) * nk;
+  const bool x_kfast = (a.xs_k == 1), y_jfast = (a.ys_j == 1);
+  // per-term operand offsets and scales
+  auto term = [&](int t, long long& xoff, long long& yoff, double& cf, const double*& cs) {
+    cf = 1.0;
+    cs = nullptr;
     if (a.seg_ptr) {
       xoff = (long long)a.xr[t] * a.xrs + (long long)a.xc[t] * a.xcs;
       yoff = (long long)a.yr[t] * a.yrs + (long long)a.yc[t] * a.ycs;
@@ -68,49 +79,91 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
       xoff = (long long)t * a.xrs;
       yoff = (long long)t * a.yrs;
     }
-    for (int k0 = 0; k0 < qlen; k0 += TK) {
-      // X tile: TM x TK ; Y tile: TK x TN
-      for (int e = tid; e < TM * TK; e += 256) {
-        int ii = e / TK, kk = e % TK;
-        int i = i0 + ii, k = k0 + kk;
-        Xs[kk][ii] = (i < a.p && k < qlen) ? CT(a.X[xoff + i * a.xs_i + k * a.xs_k]) : CT(0);
-      }
-      for (int e = tid; e < TK * TN; e += 256) {
-        int kk = e / TN, jj = e % TN;
-        int k = k0 + kk, j = j0 + jj;
-        double v = 0.0;
-        if (k < qlen && j < a.s) {
-          v = cf * a.Y[yoff + k * a.ys_k + j * a.ys_j];
-          if (cs) v *= cs[j];
-        }
-        Ys[kk][jj] = CT(v);
-      }
-      __syncthreads();
+  };
+  CT xr[XL], yr[YL];
+  auto load = [&](int step) {
+    const int t = t0 + step / nk, k0 = (step % nk) * TK;
+    long long xoff, yoff;
+    double cf;
+    const double* cs;
+    term(t, xoff, yoff, cf, cs);
 #pragma unroll
-      for (int kk = 0; kk < TK; ++kk) {
-        CT xv[4], yv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) xv[u] = Xs[kk][ty * 4 + u];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) yv[v] = Ys[kk][tx * 4 + v];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] = fma(xv[u], yv[v], acc[u][v]);
-      }
-      __syncthreads();
+    for (int l = 0; l < XL; ++l) {
+      const int e = tid + l * 256;
+      int ii, kk;
+      if (x_kfast) ii = e / TK, kk = e % TK;
+      else ii = e % BM, kk = e / BM;
+      const int i = i0 + ii, k = k0 + kk;
+      xr[l] = (e < BM * TK && i < a.p && k < qlen) ? CT(a.X[xoff + (long long)i * a.xs_i + (long long)k * a.xs_k]) : CT(0);
     }
+#pragma unroll
+    for (int l = 0; l < YL; ++l) {
+      const int e = tid + l * 256;
+      int kk, jj;
+      if (y_jfast) kk = e / BN, jj = e % BN;
+      else kk = e % TK, jj = e / TK;
+      const int k = k0 + kk, j = j0 + jj;
+      double v = 0.0;
+      if (e < TK * BN && k < qlen && j < a.s) {
+        v = cf * a.Y[yoff + (long long)k * a.ys_k + (long long)j * a.ys_j];
+        if (cs) v *= cs[j];
+      }
+      yr[l] = CT(v);
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int l = 0; l < XL; ++l) {
+      const int e = tid + l * 256;
+      if (e >= BM * TK) break;
+      int ii, kk;
+      if (x_kfast) ii = e / TK, kk = e % TK;
+      else ii = e % BM, kk = e / BM;
+      Xs[buf][kk][ii] = xr[l];
+    }
+#pragma unroll
+    for (int l = 0; l < YL; ++l) {
+      const int e = tid + l * 256;
+      if (e >= TK * BN) break;
+      int kk, jj;
+      if (y_jfast) kk = e / BN, jj = e % BN;
+      else kk = e % TK, jj = e / TK;
+      Ys[buf][kk][jj] = yr[l];
+    }
+  };
+  if (nsteps > 0) {
+    load(0);
+    store(0);
+  }
+  __syncthreads();
+  for (int step = 0; step < nsteps; ++step) {
+    const int buf = step & 1;
+    if (step + 1 < nsteps) load(step + 1);   // global loads in flight during the FMAs
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      CT xv[RM], yv[RN];
+#pragma unroll
+      for (int u = 0; u < RM; ++u) xv[u] = Xs[buf][kk][ty + 16 * u];
+#pragma unroll
+      for (int v = 0; v < RN; ++v) yv[v] = Ys[buf][kk][tx + 16 * v];
+#pragma unroll
+      for (int u = 0; u < RM; ++u)
+#pragma unroll
+        for (int v = 0; v < RN; ++v) acc[u][v] = fma(xv[u], yv[v], acc[u][v]);
+    }
+    if (step + 1 < nsteps) store(buf ^ 1);
+    __syncthreads();
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    int i = i0 + ty * 4 + u;
+  for (int u = 0; u < RM; ++u) {
+    const int i = i0 + ty + 16 * u;
     if (i >= a.p) continue;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      int j = j0 + tx * 4 + v;
+    for (int v = 0; v < RN; ++v) {
+      const int j = j0 + tx + 16 * v;
       if (j >= a.s) continue;
-      double* o = a.O + ooff + i * a.os_i + j * a.os_j;
-      double val = a.alpha * double(acc[u][v]);
+      double* o = a.O + ooff + (long long)i * a.os_i + (long long)j * a.os_j;
+      const double val = a.alpha * double(acc[u][v]);
       *o = a.accumulate ? *o + val : val;
     }
   }
@@ -850,15 +903,26 @@ void seg_gemm(const SegGemm& a_in, cudaStream_t st) {
   SegGemm a = a_in;
   if (g_compute_f32) a.f32 = 1;
   if (a.nseg <= 0 || a.p <= 0 || a.s <= 0) return;
-  dim3 grid(a.nseg, (a.p + TM - 1) / TM, (a.s + TN - 1) / TN);
+  // tile shape from the block shape: rows 16 / 32 / 64, columns 32 / 64
+  const int bm = a.p <= 16 ? 16 : a.p <= 32 ? 32 : 64;
+  const int bn = a.s <= 32 ? 32 : 64;
+  dim3 grid(a.nseg, (a.p + bm - 1) / bm, (a.s + bn - 1) / bn);
   double fl = 2.0 * a.p * a.q * a.s * double(a.seg_ptr ? a.nterm : (a.splitk ? 1 : a.nseg));
   const std::string nm = std::string(a.name ? a.name : "seg_gemm") + (a.f32 ? "_f32" : "_f64");
+  static const bool trace = std::getenv("SGTN_TRACE_GEMM") != nullptr;
+  if (trace)
+    fprintf(stderr, "[gemm] %s nseg %d nterm %lld p %d q %d s %d splitk %d grid %d x %d x %d\n", nm.c_str(), a.nseg,
+            a.seg_ptr ? a.nterm : (long long)a.nseg, a.p, a.q, a.s, a.splitk, grid.x, grid.y, grid.z);
+  KTimer t(nm.c_str(), st, fl);
+  auto go = [&](auto kern) { kern<<<grid, 256, 0, st>>>(a); };
   if (a.f32) {
-    KTimer t(nm.c_str(), st, fl);
-    seg_gemm_kernel<float><<<grid, 256, 0, st>>>(a);
+    if (bm == 16) bn == 32 ? go(seg_gemm_kernel<float, 16, 32>) : go(seg_gemm_kernel<float, 16, 64>);
+    else if (bm == 32) bn == 32 ? go(seg_gemm_kernel<float, 32, 32>) : go(seg_gemm_kernel<float, 32, 64>);
+    else bn == 32 ? go(seg_gemm_kernel<float, 64, 32>) : go(seg_gemm_kernel<float, 64, 64>);
   } else {
-    KTimer t(nm.c_str(), st, fl);
-    seg_gemm_kernel<double><<<grid, 256, 0, st>>>(a);
+    if (bm == 16) bn == 32 ? go(seg_gemm_kernel<double, 16, 32>) : go(seg_gemm_kernel<double, 16, 64>);
+    else if (bm == 32) bn == 32 ? go(seg_gemm_kernel<double, 32, 32>) : go(seg_gemm_kernel<double, 32, 64>);
+    else bn == 32 ? go(seg_gemm_kernel<double, 64, 32>) : go(seg_gemm_kernel<double, 64, 64>);
   }
   ++g_count.launches;
   g_count.flops += fl;

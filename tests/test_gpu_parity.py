@@ -68,6 +68,25 @@ def test_pegasus_boundary_and_search_match_oracle(Handle, case):
         assert res["energy_num"][0] >= inst.planted_energy_num
 
 
+def test_pegasus_large_state_sets_match_oracle(Handle):
+    """96 states per 24-spin cell: the tall CholeskyQR SVD path with nearly
+    rank-deficient site tensors in the variational sweeps (Fig. 8d).  Left
+    factors with tiny singular values must stay orthonormal, or log Z drifts
+    (it did, by 1e-7, before the short-side rotations were accumulated)."""
+    inst = L.pegasus_nice(4, 0)
+    states = L.hamming_ball_states(inst, 96, seed=1)
+    lz_o, psis, _ = boundary_mps(PottsModel(inst, states), 1.0, 12, 1)
+    h = Handle(inst, states)
+    h.set_beta(1.0)
+    lz, _ = h.contract_boundary(12, n_sweeps=1)
+    assert abs(lz - lz_o) < RTOL * abs(lz_o)
+    for r in range(inst.rows):
+        ts, _ = h.mps(r)
+        v, vo = mps_dense(ts), mps_dense(psis[r][0])
+        v, vo = v / np.linalg.norm(v), vo / np.linalg.norm(vo)
+        assert np.allclose(v, vo, rtol=1e-8, atol=1e-10)
+
+
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0].name}_chi{c[2]}")
 def test_truncated_boundary_matches_oracle(Handle, case):
     inst, beta, chi, ns = case
