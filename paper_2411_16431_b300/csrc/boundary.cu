@@ -633,6 +633,9 @@ void site_diagram(RowCtx& X, int c, const double* Kt, int kp, double* Th) {
   a.ors = (long long)chl * n;
   a.ocs = kp;
   a.seg_ptr = K_.theta.seg_ptr;
+  a.vseg_ptr = K_.theta.vseg_ptr;
+  a.vfirst = K_.theta.vfirst;
+  a.nvseg = K_.theta.nvseg;
   a.seg_or = K_.theta.seg_or;
   a.seg_oc = K_.theta.seg_oc;
   a.xr = K_.theta.xr;
@@ -689,6 +692,9 @@ double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
   a.os_j = 1;
   a.ors = (long long)phi.b * chr;
   a.seg_ptr = K_.lupd.seg_ptr;
+  a.vseg_ptr = K_.lupd.vseg_ptr;
+  a.vfirst = K_.lupd.vfirst;
+  a.nvseg = K_.lupd.nvseg;
   a.seg_or = K_.lupd.seg_or;
   a.seg_oc = K_.lupd.seg_oc;
   a.xr = K_.lupd.xr;
@@ -804,6 +810,9 @@ ThetaOp theta_op(RowCtx& X, int c, const double* K, int kp) {
   a.ors = (long long)T.chl * kp;
   a.out_by_seg = 1;
   a.seg_ptr = K_.theta.seg_ptr;
+  a.vseg_ptr = K_.theta.vseg_ptr;
+  a.vfirst = K_.theta.vfirst;
+  a.nvseg = K_.theta.nvseg;
   a.seg_or = K_.theta.seg_or;
   a.seg_oc = K_.theta.seg_oc;
   a.xr = K_.theta.xr;
@@ -844,6 +853,9 @@ void theta_mul(RowCtx& X, int c, const ThetaOp& T, const double* Q, int s, doubl
   a.os_j = 1;
   a.ors = (long long)T.chl * s;
   a.seg_ptr = t.seg_ptr;
+  a.vseg_ptr = t.vseg_ptr;
+  a.vfirst = t.vfirst;
+  a.nvseg = t.nvseg;
   a.seg_or = t.seg_or;
   a.seg_oc = t.seg_oc;
   a.xr = t.xr;
@@ -881,6 +893,9 @@ void theta_tmul(RowCtx& X, int c, const ThetaOp& T, const double* Y, int s, doub
   a.os_j = 1;
   a.ors = (long long)T.kp * s;
   a.seg_ptr = t.seg_ptr;
+  a.vseg_ptr = t.vseg_ptr;
+  a.vfirst = t.vfirst;
+  a.nvseg = t.nvseg;
   a.seg_or = t.seg_or;
   a.seg_oc = t.seg_oc;
   a.xr = t.xr;
@@ -919,6 +934,9 @@ double* theta_left(RowCtx& X, int c, const ThetaOp& T, const double* L, int a_di
   a.os_j = 1;
   a.ors = T.kp;
   a.seg_ptr = tt.seg_ptr;
+  a.vseg_ptr = tt.vseg_ptr;
+  a.vfirst = tt.vfirst;
+  a.nvseg = tt.nvseg;
   a.seg_or = tt.seg_or;
   a.seg_oc = tt.seg_oc;
   a.xr = tt.xr;
@@ -955,6 +973,9 @@ double* theta_right(RowCtx& X, int c, const ThetaOp& T, const Ten& phi) {
   a.os_j = 1;
   a.ors = (long long)T.chl * phi.a;
   a.seg_ptr = tt.seg_ptr;
+  a.vseg_ptr = tt.vseg_ptr;
+  a.vfirst = tt.vfirst;
+  a.nvseg = tt.nvseg;
   a.seg_or = tt.seg_or;
   a.seg_oc = tt.seg_oc;
   a.xr = tt.xr;

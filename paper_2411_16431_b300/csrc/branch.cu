@@ -457,6 +457,9 @@ void prepare_scores(Step& S, const int32_t* hcfg) {
     a.os_j = 1;
     a.ors = (long long)chl * K;
     a.seg_ptr = K_.renv.seg_ptr;
+    a.vseg_ptr = K_.renv.vseg_ptr;
+    a.vfirst = K_.renv.vfirst;
+    a.nvseg = K_.renv.nvseg;
     a.seg_or = K_.renv.seg_or;
     a.seg_oc = K_.renv.seg_oc;
     a.xr = K_.renv.xr;
@@ -579,6 +582,11 @@ void conditionals_arena(sgtn_inst* h, int step, int count, const int32_t* config
   S.K = count;
   S.arena = static_cast<char*>(arena);
   S.arena_cap = cap;
+  struct NoAlloc {
+    bool saved = g_no_alloc;
+    NoAlloc() { g_no_alloc = true; }
+    ~NoAlloc() { g_no_alloc = saved; }
+  } no_alloc;
   prepare_scores(S, configs);
   int d = h->M.sites[step].d;
   SGTN_CUDA(cudaMemcpyAsync(out_p, S.s, size_t(count) * d * sizeof(double), cudaMemcpyDeviceToHost, h->st));

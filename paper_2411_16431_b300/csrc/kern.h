@@ -21,6 +21,10 @@ extern bool g_compute_f32;
 // When set (with g_compute_f32), dense GEMMs large enough for 128 x 128 tiles
 // run on tcgen05 tensor cores (3xTF32).
 extern bool g_use_tc;
+// When set, the GEMM helpers allocate no device memory of their own (no
+// split-K or split-segment partial buffers): set by the allocation-free entry
+// point for the duration of its call.
+extern bool g_no_alloc;
 
 // Optional per-kernel timing with CUDA events on the launching stream.
 // KTimer brackets one launch; pairs are resolved when read.
@@ -64,6 +68,11 @@ struct SegGemm {
   double alpha = 1.0;
   int accumulate = 0;
   const char* name = nullptr;   // timing label (role of the call); "_f32" / "_f64" is appended
+  // optional balanced split of long segments (table mode): the virtual
+  // segments are multiplied into a scratch block each and summed per segment
+  // in a fixed order (deterministic)
+  const int32_t *vseg_ptr = nullptr, *vfirst = nullptr;
+  int nvseg = 0;
 };
 void seg_gemm(const SegGemm& a, cudaStream_t st);
 

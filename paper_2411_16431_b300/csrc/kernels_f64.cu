@@ -169,6 +169,24 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
   }
 }
 
+// Sum of the virtual-segment blocks P[v] (p x s, row-major) of each segment,
+// in virtual-segment order, into the segment's output block.
+__global__ void seg_reduce_kernel(const double* P, const int32_t* vfirst, int nseg, int p, int s, SegGemm a) {
+  const long long blk = (long long)p * s, total = (long long)nseg * blk;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int g = int(e / blk);
+    const long long r = e % blk;
+    const int i = int(r / s), j = int(r % s);
+    double v = 0.0;
+    for (int q = vfirst[g]; q < vfirst[g + 1]; ++q) v += P[q * blk + r];
+    const long long ooff =
+        a.out_by_seg ? (long long)g * a.ors : (long long)a.seg_or[g] * a.ors + (long long)a.seg_oc[g] * a.ocs;
+    double* o = a.O + ooff + (long long)i * a.os_i + (long long)j * a.os_j;
+    *o = a.accumulate ? *o + a.alpha * v : a.alpha * v;
+  }
+}
+
 __device__ inline double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -899,21 +917,12 @@ std::string ktimer_names() {
   return o;
 }
 
-void seg_gemm(const SegGemm& a_in, cudaStream_t st) {
-  SegGemm a = a_in;
-  if (g_compute_f32) a.f32 = 1;
-  if (a.nseg <= 0 || a.p <= 0 || a.s <= 0) return;
+namespace {
+void launch_seg(const SegGemm& a, cudaStream_t st) {
   // tile shape from the block shape: rows 16 / 32 / 64, columns 32 / 64
   const int bm = a.p <= 16 ? 16 : a.p <= 32 ? 32 : 64;
   const int bn = a.s <= 32 ? 32 : 64;
   dim3 grid(a.nseg, (a.p + bm - 1) / bm, (a.s + bn - 1) / bn);
-  double fl = 2.0 * a.p * a.q * a.s * double(a.seg_ptr ? a.nterm : (a.splitk ? 1 : a.nseg));
-  const std::string nm = std::string(a.name ? a.name : "seg_gemm") + (a.f32 ? "_f32" : "_f64");
-  static const bool trace = std::getenv("SGTN_TRACE_GEMM") != nullptr;
-  if (trace)
-    fprintf(stderr, "[gemm] %s nseg %d nterm %lld p %d q %d s %d splitk %d grid %d x %d x %d\n", nm.c_str(), a.nseg,
-            a.seg_ptr ? a.nterm : (long long)a.nseg, a.p, a.q, a.s, a.splitk, grid.x, grid.y, grid.z);
-  KTimer t(nm.c_str(), st, fl);
   auto go = [&](auto kern) { kern<<<grid, 256, 0, st>>>(a); };
   if (a.f32) {
     if (bm == 16) bn == 32 ? go(seg_gemm_kernel<float, 16, 32>) : go(seg_gemm_kernel<float, 16, 64>);
@@ -925,11 +934,54 @@ void seg_gemm(const SegGemm& a_in, cudaStream_t st) {
     else bn == 32 ? go(seg_gemm_kernel<double, 64, 32>) : go(seg_gemm_kernel<double, 64, 64>);
   }
   ++g_count.launches;
+}
+}  // namespace
+
+void seg_gemm(const SegGemm& a_in, cudaStream_t st) {
+  SegGemm a = a_in;
+  if (g_compute_f32) a.f32 = 1;
+  if (a.nseg <= 0 || a.p <= 0 || a.s <= 0) return;
+  double fl = 2.0 * a.p * a.q * a.s * double(a.seg_ptr ? a.nterm : (a.splitk ? 1 : a.nseg));
+  const std::string nm = std::string(a.name ? a.name : "seg_gemm") + (a.f32 ? "_f32" : "_f64");
+  const bool split = a.seg_ptr && a.vseg_ptr && a.nvseg > a.nseg && !g_no_alloc;
+  static const bool trace = std::getenv("SGTN_TRACE_GEMM") != nullptr;
+  if (trace)
+    fprintf(stderr, "[gemm] %s nseg %d nterm %lld p %d q %d s %d splitk %d vseg %d\n", nm.c_str(), a.nseg,
+            a.seg_ptr ? a.nterm : (long long)a.nseg, a.p, a.q, a.s, a.splitk, split ? a.nvseg : 0);
+  KTimer t(nm.c_str(), st, fl);
+  if (!split) {
+    launch_seg(a, st);
+  } else {
+    static double* part = nullptr;
+    static size_t part_n = 0;
+    const size_t need = size_t(a.nvseg) * a.p * a.s;
+    if (need > part_n) {
+      if (part) cudaFree(part);
+      cudaMalloc(&part, need * sizeof(double));
+      part_n = need;
+    }
+    SegGemm b = a;
+    b.seg_ptr = a.vseg_ptr;
+    b.nseg = a.nvseg;
+    b.out_by_seg = 1;
+    b.O = part;
+    b.os_i = a.s;
+    b.os_j = 1;
+    b.ors = (long long)a.p * a.s;
+    b.alpha = 1.0;
+    b.accumulate = 0;
+    launch_seg(b, st);
+    long long total = (long long)a.nseg * a.p * a.s;
+    int nb = int(std::min<long long>((total + 255) / 256, 148 * 16));
+    seg_reduce_kernel<<<nb, 256, 0, st>>>(part, a.vfirst, a.nseg, a.p, a.s, a);
+    ++g_count.launches;
+  }
   g_count.flops += fl;
 }
 
 bool g_compute_f32 = false;
 bool g_use_tc = false;
+bool g_no_alloc = false;
 
 void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, long long ldy, double* O, long long ldo,
           int m, int n, int k, double alpha, int accumulate, cudaStream_t st) {
@@ -954,7 +1006,7 @@ void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, lon
   a.accumulate = accumulate;
   a.name = "gemm";
   long long tiles = (long long)((m + TM - 1) / TM) * ((n + TN - 1) / TN);
-  if (tiles < 148 && k >= 1024) {
+  if (tiles < 148 && k >= 1024 && !g_no_alloc) {
     // few output tiles and a long reduction: split K over CTAs, then reduce
     int nsplit = int(std::min<long long>((k + 255) / 256, std::max<long long>(2, 592 / tiles)));
     int chunk = ((k + nsplit - 1) / nsplit + TK - 1) / TK * TK;

@@ -70,6 +70,11 @@ struct TermTable {
   std::vector<int32_t> h_xr, h_xc, h_yr, h_yc, h_cidx, h_csrow;
   int32_t *seg_ptr = nullptr, *seg_or = nullptr, *seg_oc = nullptr;
   int32_t *xr = nullptr, *xc = nullptr, *yr = nullptr, *yc = nullptr, *cidx = nullptr, *csrow = nullptr;
+  // balanced split for the GEMM (nvseg = 0: none): virtual segment v covers
+  // terms [vseg_ptr[v], vseg_ptr[v+1]); segment s owns virtual segments
+  // [vfirst[s], vfirst[s+1])
+  int nvseg = 0;
+  int32_t *vseg_ptr = nullptr, *vfirst = nullptr;
 };
 
 // Static description of MPO column c of row r (see the boundary code for the

@@ -48,6 +48,23 @@ struct TermBuilder {
     tt.yc = h->upload(tt.h_yc);
     tt.cidx = h->upload(tt.h_cidx);
     tt.csrow = h->upload(tt.h_csrow);
+    // segments much longer than nterm / (2 x 148) are cut into equal parts so
+    // that one GEMM launch has no straggler CTA
+    const int chunk = std::max(2, (tt.nterm + 295) / 296);
+    std::vector<int32_t> vptr, vfirst;
+    for (int g = 0; g < tt.nseg; ++g) {
+      const int b = tt.h_seg_ptr[g], e = tt.h_seg_ptr[g + 1], len = e - b;
+      const int parts = std::max(1, (len + chunk - 1) / chunk), step = (len + parts - 1) / parts;
+      vfirst.push_back(int32_t(vptr.size()));
+      for (int x = b; x < e; x += step) vptr.push_back(x);
+    }
+    vfirst.push_back(int32_t(vptr.size()));
+    vptr.push_back(tt.nterm);
+    if (int(vfirst.back()) > tt.nseg) {
+      tt.nvseg = vfirst.back();
+      tt.vseg_ptr = h->upload(vptr);
+      tt.vfirst = h->upload(vfirst);
+    }
     v.clear();
     v.shrink_to_fit();
   }

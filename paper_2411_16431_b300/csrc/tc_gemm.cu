@@ -266,6 +266,7 @@ bool tc_gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, 
   static size_t buf_n = 0;
   static int* err = nullptr;
   size_t need = 2 * (size_t(m) + n) * kpad;
+  if ((need > buf_n || !err) && g_no_alloc) return false;   // the SIMT path allocates nothing
   if (need > buf_n) {
     if (buf) cudaFree(buf);
     if (cudaMalloc(&buf, need * sizeof(float)) != cudaSuccess) return false;
