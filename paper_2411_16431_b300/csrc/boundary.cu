@@ -392,9 +392,9 @@ SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap) {
 
 // Top-k right singular subspace of Theta (m x n) by block subspace iteration:
 // Q <- orth(Theta^T orth(Theta Q)) with a block of s = min(p, k + 32) vectors
-// from a fixed pseudo-random start, until the leading Ritz vectors move by
-// less than 1e-13 (largest principal-angle sine); the Rayleigh-Ritz step (SVD
-// of Theta Q, s columns, exact) gives the singular values and Q W the vectors.
+// from a fixed pseudo-random start, until the leading Ritz vectors (weighted by
+// their singular values) settle; the Rayleigh-Ritz step (SVD of Theta Q, s
+// columns, exact) gives the singular values and Q W the vectors.
 SvdOut svd_subspace(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   MatFn mul = [=](const double* Q, int s, double* Y) { gemm(Th, false, n, Q, false, s, Y, s, m, s, n, 1.0, 0, h->st); };
   MatFn tmul = [=](const double* Y, int s, double* Z) { gemm(Th, true, n, Y, false, s, Z, s, n, s, m, 1.0, 0, h->st); };
@@ -464,8 +464,9 @@ bool cqr_orth(sgtn_inst* h, const double* M, int len, int k, double* Q, bool fir
 // iteration orthonormalises both products by CholeskyQR (Y before it is
 // multiplied back, so that no condition number is squared); every second
 // iteration a Rayleigh-Ritz step (exact SVD of Theta Q) gives the Ritz
-// vectors, and the iteration stops when the leading min(cap, k) of them moved
-// by less than 1e-13 (largest principal-angle sine) since the previous check.
+// vectors, and the iteration stops when the leading min(cap, k) of them,
+// weighted by sigma_j / sigma_1, moved by less than 1e-13 sqrt(k) (Frobenius)
+// since the previous check.
 SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, const MatFn& tmul) {
   F64Scope f64;
   cudaStream_t st = h->st;
@@ -479,6 +480,7 @@ SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, co
   double* G = h->ws.get<double>("ss_G", size_t(s) * s);
   double* Vp = h->ws.get<double>("ss_Vp", size_t(n) * s);
   double* ones = h->ws.get<double>("ss_ones", s);
+  double* wdev = h->ws.get<double>("ss_w", s);
   fill(ones, s, 1.0, st);
   // orthonormal basis of the columns of A (len x kk) into out; dependent
   // columns (a failed pivot) go through the rank-trimmed SVD basis instead
@@ -504,7 +506,10 @@ SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, co
       gemm(Q, false, k, ob.Vt, true, k, Qn, kb, n, kb, k, 1.0, 0, st);           // Qn = Q W  (n x kb)
       double ch = INFINITY;
       if (kc == kc_prev) {
-        // || Vp - Qn_c (Qn_c^T Vp) ||  with Qn_c the leading kc Ritz vectors
+        // || Vp - Qn_c (Qn_c^T Vp) ||  with Qn_c the leading kc Ritz vectors and
+        // the columns of Vp weighted by sigma_j / sigma_1: the change of the
+        // rank-kc approximation relative to its norm (a direction whose
+        // singular value sits at rounding level cannot settle, nor matters)
         double* Rr = h->ws.get<double>("ss_R", size_t(n) * kc);
         gemm(Qn, true, kb, Vp, false, kc, G, kc, kc, kc, n, 1.0, 0, st);
         gemm(Qn, false, kb, G, false, kc, Rr, kc, n, kc, kc, -1.0, 0, st);
@@ -539,7 +544,14 @@ SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, co
         h->sync();   // sv stays alive until the copy is done
         return o;
       }
-      gather_vecs(Qn, n, kb, 1, h->iota, ones, kc, Vp, kc, 1, st);                // Vp = leading kc Ritz vectors
+      {
+        // Vp = leading kc Ritz vectors, column j scaled by sigma_j / sigma_1
+        std::vector<double> w(kc);
+        for (int j = 0; j < kc; ++j) w[j] = ob.sig[j] / ob.sig[0];
+        SGTN_CUDA(cudaMemcpyAsync(wdev, w.data(), kc * sizeof(double), cudaMemcpyHostToDevice, st));
+        gather_vecs(Qn, n, kb, 1, h->iota, wdev, kc, Vp, kc, 1, st);
+        h->sync();
+      }
       kc_prev = kc;
       // continue from the Ritz basis: Q = Q W, Theta Q = U S
       std::swap(Q, Qn);

@@ -19,7 +19,7 @@ namespace sgtn {
 
 namespace {
 
-constexpr int TM = 64, TN = 64, TK = 16;
+constexpr int TK = 16;
 
 // Segmented gathered GEMM.  One CTA (256 threads, a 16 x 16 grid) owns a
 // BM x BN tile of one output segment and runs over the flattened (term,
@@ -1005,10 +1005,12 @@ void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, lon
   a.alpha = alpha;
   a.accumulate = accumulate;
   a.name = "gemm";
-  long long tiles = (long long)((m + TM - 1) / TM) * ((n + TN - 1) / TN);
-  if (tiles < 148 && k >= 1024 && !g_no_alloc) {
-    // few output tiles and a long reduction: split K over CTAs, then reduce
-    int nsplit = int(std::min<long long>((k + 255) / 256, std::max<long long>(2, 592 / tiles)));
+  const int bm = m <= 16 ? 16 : m <= 32 ? 32 : 64, bn = n <= 32 ? 32 : 64;   // as in launch_seg
+  long long tiles = (long long)((m + bm - 1) / bm) * ((n + bn - 1) / bn);
+  if (tiles < 148 && k >= 256 && !g_no_alloc) {
+    // few output tiles and a long reduction: split K over about two CTAs per
+    // SM (chunks of at least 32), then reduce the partial products
+    int nsplit = int(std::min<long long>((k + 31) / 32, std::max<long long>(2, (296 + tiles - 1) / tiles)));
     int chunk = ((k + nsplit - 1) / nsplit + TK - 1) / TK * TK;
     nsplit = (k + chunk - 1) / chunk;
     static double* part = nullptr;
