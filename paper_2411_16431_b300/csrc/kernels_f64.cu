@@ -522,53 +522,74 @@ __global__ void __launch_bounds__(128) jacobi_coop_kernel(double* X, int len, in
   if (blockIdx.x == 0 && threadIdx.x == 0) status[0] = done ? sweep : -1;
 }
 
-// Right-looking upper Cholesky in shared memory, then R^{-1} column by column.
-// T is the arithmetic type (float: a cheap first factor whose rounding a later
-// FP64 pass removes); G, R and R^{-1} are FP64 in memory.
+// Right-looking upper Cholesky of G + shift I in shared memory (two barriers a
+// column: the scaled pivot row is staged, then the trailing upper triangle is
+// updated by a 32 x 32 thread grid), then R^{-1} right-looking from the last
+// row (R X = I: finished row j of X is subtracted from every row above it),
+// with X kept transposed in the free lower triangle.  T is the arithmetic type
+// (float: a cheap first factor whose rounding a later FP64 pass removes); G,
+// R and R^{-1} are FP64 in memory.
 template <class T>
 __global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* G, int n, double shift, double* R,
                                                             double* Rinv, int* status) {
   extern __shared__ __align__(16) unsigned char chol_smem[];
   T* A = reinterpret_cast<T*>(chol_smem);   // n x n
+  T* row = A + n * n;                       // n: staged row / 1 / R_jj
   __shared__ int fail;
+  __shared__ T piv[2];   // sqrt of the current pivot and its reciprocal
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    int i = e / n, j = e % n;
-    A[e] = T(G[e] + (i == j ? shift : 0.0));
+    const int i = e / n, j = e % n;
+    A[e] = j >= i ? T(G[e] + (i == j ? shift : 0.0)) : T(0);
   }
-  if (threadIdx.x == 0) fail = 0;
+  // thread 0 takes each pivot (square root and reciprocal once, shared)
+  auto take_pivot = [&](int j) {
+    const T d = A[j * n + j];
+    const bool bad = !(d > T(0));
+    if (bad && !fail) fail = j + 1;
+    piv[0] = bad ? T(1) : T(sqrt(d));
+    piv[1] = T(1) / piv[0];
+  };
+  if (threadIdx.x == 0) {
+    fail = 0;
+    if (n > 0) take_pivot(0);   // A[0] was written by this thread above
+  }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) {
-      T d = A[j * n + j];
-      if (!(d > T(0))) {
-        if (!fail) fail = j + 1;
-        A[j * n + j] = T(1);
-      } else {
-        A[j * n + j] = sqrt(d);
+    const T r = piv[0], ri = piv[1];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) row[i] = A[j * n + i] * ri;
+    __syncthreads();
+    if (threadIdx.x == 0) A[j * n + j] = r;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[j * n + i] = row[i];
+    for (int k = j + 1 + ty; k < n; k += 32) {
+      const T rk = row[k];
+      for (int i = k + tx; i < n; i += 32) A[k * n + i] -= rk * row[i];
+    }
+    // element (j+1, j+1) was updated by thread 0 (k = j+1, i = k): next pivot
+    if (threadIdx.x == 0 && j + 1 < n) take_pivot(j + 1);
+    __syncthreads();
+  }
+  // R^{-1} = X (upper): X[i][c] (i < c) lives at A[c * n + i]; X[i][i] = 1 / R_ii
+  for (int i = threadIdx.x; i < n; i += blockDim.x) row[i] = T(1) / A[i * n + i];
+  __syncthreads();
+  for (int j = n - 1; j >= 0; --j) {
+    // row j of X is final once scaled by 1 / R_jj
+    for (int c = j + 1 + threadIdx.x; c < n; c += blockDim.x) A[c * n + j] *= row[j];
+    __syncthreads();
+    // rows k < j:  X[k][c] -= R[k][j] X[j][c]  for c >= j
+    for (int k = ty; k < j; k += 32) {
+      const T rkj = A[k * n + j];
+      for (int c = j + tx; c < n; c += 32) {
+        const T xjc = (c == j) ? row[j] : A[c * n + j];
+        A[c * n + k] -= rkj * xjc;
       }
     }
     __syncthreads();
-    T r = A[j * n + j];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[j * n + i] /= r;
-    __syncthreads();
-    int m = n - j - 1;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      int k = j + 1 + e / m, i = j + 1 + e % m;
-      if (i >= k) A[k * n + i] -= A[j * n + k] * A[j * n + i];
-    }
-    __syncthreads();
   }
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    int i = e / n, j = e % n;
-    R[e] = j >= i ? double(A[e]) : 0.0;
-  }
-  // R X = I, one column per thread, back substitution
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    for (int i = n - 1; i >= 0; --i) {
-      T v = (i == c) ? T(1) : T(0);
-      for (int k = i + 1; k <= c; ++k) v -= A[i * n + k] * T(Rinv[k * n + c]);
-      Rinv[i * n + c] = (i <= c) ? double(v / A[i * n + i]) : 0.0;
-    }
+    const int i = e / n, c = e % n;
+    R[e] = c >= i ? double(A[e]) : 0.0;
+    Rinv[e] = c > i ? double(A[c * n + i]) : (c == i ? double(row[i]) : 0.0);
   }
   if (threadIdx.x == 0) status[0] = fail;
 }
@@ -1136,10 +1157,10 @@ void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv,
   }
   if (f32) {
     KTimer t("cholesky_f32", st);
-    cholesky_inv_kernel<float><<<1, 1024, size_t(n) * n * sizeof(float), st>>>(G, n, shift, R, Rinv, status);
+    cholesky_inv_kernel<float><<<1, 1024, size_t(n) * (n + 1) * sizeof(float), st>>>(G, n, shift, R, Rinv, status);
   } else {
     KTimer t("cholesky_f64", st);
-    cholesky_inv_kernel<double><<<1, 1024, size_t(n) * n * sizeof(double), st>>>(G, n, shift, R, Rinv, status);
+    cholesky_inv_kernel<double><<<1, 1024, size_t(n) * (n + 1) * sizeof(double), st>>>(G, n, shift, R, Rinv, status);
   }
   ++g_count.launches;
 }
