@@ -159,43 +159,67 @@ SvdOut svd_dense(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   return svd_jacobi(h, Th, m, n, cap);
 }
 
-// M (m x n, m >= n, row-major) = Q R by shifted CholeskyQR3, then R = U S V^T
-// by one-sided Jacobi.  Returns false (nothing allocated) if a pivot fails
-// (numerically dependent columns).
+// M (m x n, m >= n, row-major) = Q R by CholeskyQR2 (well-conditioned M) or
+// shifted CholeskyQR3, then R = U S V^T by one-sided Jacobi.  Returns false
+// (nothing allocated) if a pivot fails (numerically dependent columns).
 bool svd_tall_cqr3(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o) {
   cudaStream_t st = h->st;
   double* G = h->ws.get<double>("cq_G", size_t(n) * n);
+  double* G0 = h->ws.get<double>("cq_G0", size_t(n) * n);
   double* R = h->ws.get<double>("cq_R", size_t(n) * n);
   double* Ri = h->ws.get<double>("cq_Ri", size_t(n) * n);
   double* Racc = h->ws.get<double>("cq_Racc", size_t(n) * n);
   double* Rtmp = h->ws.get<double>("cq_Rtmp", size_t(n) * n);
   double* Qa = h->ws.get<double>("cq_Qa", size_t(m) * n);
   double* Qb = h->ws.get<double>("cq_Qb", size_t(m) * n);
+  double* dmr = h->ws.get<double>("cq_minratio", 1);
   int* status = h->ws.get<int>("cq_status", 4);
-  const double* cur = M;
-  double* outQ[3] = {Qa, Qb, Qa};
-  // shift for the first pass: 11 (m n + n (n+1)) eps ||M||_2^2, with ||M||_2^2 <= trace(M^T M)
-  gemm(M, true, n, M, false, n, G, n, n, n, m, 1.0, 0, st);
-  std::vector<double> hG(size_t(n) * n);
-  SGTN_CUDA(cudaMemcpyAsync(hG.data(), G, hG.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-  h->sync();
-  double tr = 0;
-  for (int i = 0; i < n; ++i) tr += hG[size_t(i) * n + i];
-  if (!(tr > 0) || !std::isfinite(tr)) return false;
-  double shift = 11.0 * (double(m) * n + double(n) * (n + 1)) * 2.220446049250313e-16 * tr;
-  for (int pass = 0; pass < 3; ++pass) {
-    if (pass > 0) gemm(cur, true, n, cur, false, n, G, n, n, n, m, 1.0, 0, st);
-    cholesky_inv(G, n, pass == 0 ? shift : 0.0, R, Ri, status + pass, st);
-    gemm(cur, false, n, Ri, false, n, outQ[pass], n, m, n, n, 1.0, 0, st);
-    if (pass == 0) {
+  SGTN_CUDA(cudaMemsetAsync(status, 0, 3 * sizeof(int), st));
+  // one pass: G = cur^T cur, R = chol(G + shift I), out = cur R^{-1}, Racc = R Racc
+  auto pass = [&](const double* cur, double* out, double shift, int* stat, bool first, const double* Gin) {
+    if (!Gin) gemm(cur, true, n, cur, false, n, G, n, n, n, m, 1.0, 0, st);
+    cholesky_inv(Gin ? Gin : G, n, shift, R, Ri, stat, st);
+    gemm(cur, false, n, Ri, false, n, out, n, m, n, n, 1.0, 0, st);
+    if (first) {
       copy(Racc, R, (long long)n * n, st);
     } else {
       gemm(R, false, n, Racc, false, n, Rtmp, n, n, n, n, 1.0, 0, st);
       copy(Racc, Rtmp, (long long)n * n, st);
     }
-    cur = outQ[pass];
+  };
+  gemm(M, true, n, M, false, n, G0, n, n, n, m, 1.0, 0, st);
+  // CholeskyQR2 when the unshifted factor lost at most 10 of the 16 digits of
+  // any column (cond(M) below about 1e5): its orthogonality after two passes
+  // is at rounding level
+  cholesky_inv(G0, n, 0.0, R, Ri, status, st, false, dmr);
+  std::vector<double> hdiag(n);
+  double mr = 0;
+  int hs0 = 0;
+  SGTN_CUDA(cudaMemcpy2DAsync(hdiag.data(), sizeof(double), G0, size_t(n + 1) * sizeof(double), sizeof(double), n,
+                              cudaMemcpyDeviceToHost, st));
+  SGTN_CUDA(cudaMemcpyAsync(&mr, dmr, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SGTN_CUDA(cudaMemcpyAsync(&hs0, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  h->sync();
+  double tr = 0;
+  for (int i = 0; i < n; ++i) tr += hdiag[i];
+  if (!(tr > 0) || !std::isfinite(tr)) return false;
+  const double* cur = nullptr;
+  if (hs0 == 0 && mr > 1e-10) {
+    gemm(M, false, n, Ri, false, n, Qa, n, m, n, n, 1.0, 0, st);                 // Q1 = M R1^{-1}
+    copy(Racc, R, (long long)n * n, st);
+    pass(Qa, Qb, 0.0, status + 1, false, nullptr);
+    cur = Qb;
+  } else {
+    // shifted CholeskyQR3: first shift 11 (m n + n (n+1)) eps ||M||_2^2, with
+    // ||M||_2^2 <= trace(M^T M)
+    const double shift = 11.0 * (double(m) * n + double(n) * (n + 1)) * 2.220446049250313e-16 * tr;
+    SGTN_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+    pass(M, Qa, shift, status, true, G0);
+    pass(Qa, Qb, 0.0, status + 1, false, nullptr);
+    pass(Qb, Qa, 0.0, status + 2, false, nullptr);
+    cur = Qa;
   }
-  int hs[3];
+  int hs[3] = {0, 0, 0};
   SGTN_CUDA(cudaMemcpyAsync(hs, status, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
   h->sync();
   if (hs[0] || hs[1] || hs[2]) return false;

@@ -88,9 +88,11 @@ void jacobi(double* X, int len, int p, long long si, long long sj, double* V, in
             cudaStream_t st);
 // Upper Cholesky factor R of (G + shift I) (n x n, row-major; R^T R = G + shift I)
 // and R^{-1}, one CTA.  status[0] = 0 on success, j+1 if pivot j was not positive.
-// f32: factor in FP32 arithmetic (inputs and outputs stay FP64).
+// f32: factor in FP32 arithmetic (inputs and outputs stay FP64).  minratio
+// (optional): smallest pivot over the matching diagonal entry of G + shift I,
+// i.e. how much of a column survived the elimination (1: orthogonal columns).
 void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv, int* status, cudaStream_t st,
-                  bool f32 = false);
+                  bool f32 = false, double* minratio = nullptr);
 // Cholesky with diagonal pivoting of a PSD G (n x n, n <= 160), stopped at the
 // numerical rank (largest remaining pivot <= max(tol_rel * max diag G, tol_abs)):
 // rank[0] = r, perm[0..r) the pivot order, R and R^{-1} (r x r upper triangular,

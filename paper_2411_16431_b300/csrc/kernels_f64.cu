@@ -531,28 +531,34 @@ __global__ void __launch_bounds__(128) jacobi_coop_kernel(double* X, int len, in
 // R and R^{-1} are FP64 in memory.
 template <class T>
 __global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* G, int n, double shift, double* R,
-                                                            double* Rinv, int* status) {
+                                                            double* Rinv, int* status, double* minratio) {
   extern __shared__ __align__(16) unsigned char chol_smem[];
   T* A = reinterpret_cast<T*>(chol_smem);   // n x n
   T* row = A + n * n;                       // n: staged row / 1 / R_jj
+  T* gd = row + n;                          // n: diagonal of G + shift I
   __shared__ int fail;
   __shared__ T piv[2];   // sqrt of the current pivot and its reciprocal
+  __shared__ double mr;  // smallest pivot / (diagonal of G + shift)
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
     A[e] = j >= i ? T(G[e] + (i == j ? shift : 0.0)) : T(0);
   }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) gd[i] = T(G[i * n + i] + shift);
+  __syncthreads();
   // thread 0 takes each pivot (square root and reciprocal once, shared)
   auto take_pivot = [&](int j) {
     const T d = A[j * n + j];
     const bool bad = !(d > T(0));
     if (bad && !fail) fail = j + 1;
+    mr = fmin(mr, double(d / gd[j]));
     piv[0] = bad ? T(1) : T(sqrt(d));
     piv[1] = T(1) / piv[0];
   };
   if (threadIdx.x == 0) {
     fail = 0;
-    if (n > 0) take_pivot(0);   // A[0] was written by this thread above
+    mr = 1.0;
+    if (n > 0) take_pivot(0);
   }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
@@ -591,7 +597,10 @@ __global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* G, int
     R[e] = c >= i ? double(A[e]) : 0.0;
     Rinv[e] = c > i ? double(A[c * n + i]) : (c == i ? double(row[i]) : 0.0);
   }
-  if (threadIdx.x == 0) status[0] = fail;
+  if (threadIdx.x == 0) {
+    status[0] = fail;
+    if (minratio) minratio[0] = mr;
+  }
 }
 
 // Cholesky with diagonal pivoting of a positive semidefinite G (n x n, FP64),
@@ -1148,7 +1157,7 @@ void jacobi(double* X, int len, int p, long long si, long long sj, double* V, in
 }
 
 void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv, int* status, cudaStream_t st,
-                  bool f32) {
+                  bool f32, double* minratio) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(cholesky_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
@@ -1157,10 +1166,12 @@ void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv,
   }
   if (f32) {
     KTimer t("cholesky_f32", st);
-    cholesky_inv_kernel<float><<<1, 1024, size_t(n) * (n + 1) * sizeof(float), st>>>(G, n, shift, R, Rinv, status);
+    cholesky_inv_kernel<float><<<1, 1024, size_t(n) * (n + 2) * sizeof(float), st>>>(G, n, shift, R, Rinv, status,
+                                                                                    minratio);
   } else {
     KTimer t("cholesky_f64", st);
-    cholesky_inv_kernel<double><<<1, 1024, size_t(n) * (n + 1) * sizeof(double), st>>>(G, n, shift, R, Rinv, status);
+    cholesky_inv_kernel<double><<<1, 1024, size_t(n) * (n + 2) * sizeof(double), st>>>(G, n, shift, R, Rinv, status,
+                                                                                      minratio);
   }
   ++g_count.launches;
 }
