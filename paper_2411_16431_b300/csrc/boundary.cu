@@ -1044,12 +1044,15 @@ SvdOut theta_svd(RowCtx& X, int c, const ThetaOp& T, int cap) {
 // Environments are rescaled by powers of two after every update (they would
 // under- or overflow, in FP32 first); only the right environment's scale
 // reaches the final centre, and its logarithm is returned.
-double variational_sweep(RowCtx& X, std::vector<Ten>& phi) {
+double variational_sweep(RowCtx& X, std::vector<Ten>& phi, bool canonical) {
   sgtn_inst* h = X.h;
   TagScope tag("sweep");
   const bool renorm = true;
   const int C = (int)phi.size();
-  right_canonical(X, phi);
+  // phi coming from the zipper or from a previous sweep is already right-
+  // canonical (orthonormal rows right of a centre at column 0): bringing it
+  // there again would only change the gauge
+  if (!canonical) right_canonical(X, phi);
   std::vector<double*> Renv(C, nullptr), Lenv(C, nullptr);
   Renv[C - 1] = dmalloc(1);
   fill(Renv[C - 1], 1, 1.0, h->st);
@@ -1242,14 +1245,14 @@ void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& wo
   }
   dfree(K);
   for (int s = 0; s < n_sweeps; ++s) {
-    double extra = variational_sweep(X, phi);
+    double extra = variational_sweep(X, phi, true);
     ln = A.lognorm + extra;
     normalise(h, phi[0].p, phi[0].n(), ln);
   }
   worst = std::max(worst, svd_cut(X, phi, chi));
   normalise(h, phi[C - 1].p, phi[C - 1].n(), ln);
   for (int s = 0; s < n_sweeps; ++s) {
-    double extra = variational_sweep(X, phi);
+    double extra = variational_sweep(X, phi, s > 0);   // svd_cut leaves phi left-canonical
     ln = A.lognorm + extra;
     normalise(h, phi[0].p, phi[0].n(), ln);
   }
