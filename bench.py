@@ -26,26 +26,45 @@ sys.path.insert(0, ROOT)
 
 from paper_2411_16431_b300 import lattices as L  # noqa: E402
 
-# Workloads: sizes of the benchmark configurations.
+# Workloads: sizes of the benchmark configurations.  Pegasus cells keep the 256
+# states nearest a seeded reference configuration (Hamming ball): the stand-in
+# for the local-dimension reduction of Sec. IV (the full 2^24 states per cell
+# do not fit).
+_PEG_SAMPLE = dict(make=lambda seed: L.pegasus_nice(3, seed),
+                   states=lambda inst, seed: L.hamming_ball_states(inst, 32, seed=seed + 1),
+                   chi=8, M=64, desc="Pegasus P3 nice 2x2 cells, d=32, chi=8, M=64")
 WORKLOADS = {
     "chimera4x4": dict(desc="4x4 grid of K44 cells (128 spins), iid J,h in {+-1..+-7}/7, beta=1, chi=16, M=64",
-                       make=lambda seed: L.chimera_grid(4, 4, seed), states=None, beta=1.0, chi=16, M=64, sweeps=2),
-    # Pegasus P6 nice cells (5x5 grid, 600 spins, 24-spin cells); every cell restricted to the
-    # 256 states nearest a seeded reference (stand-in for the local-dimension reduction of Sec. IV)
+                       make=lambda seed: L.chimera_grid(4, 4, seed), states=None, beta=1.0, chi=16, M=64, sweeps=2,
+                       d=256),
     "pegasus5x5": dict(desc="Pegasus P6 nice, 5x5 cells of 24 spins (600 spins), d=256 states per cell "
                             "(Hamming ball around a seeded reference), iid J,h in {+-1..+-7}/7, beta=1, chi=32, M=256",
                        make=lambda seed: L.pegasus_nice(6, seed),
                        states=lambda inst, seed: L.hamming_ball_states(inst, 256, seed=seed + 1),
-                       beta=1.0, chi=32, M=256, sweeps=2,
+                       beta=1.0, chi=32, M=256, sweeps=2, d=256,
                        # the oracle's dense row MPOs cannot hold d=256 cells: its timed sample is a
                        # 2x2-cell Pegasus slice (P3 nice) with 32 states per cell
-                       oracle_sample=dict(make=lambda seed: L.pegasus_nice(3, seed),
-                                          states=lambda inst, seed: L.hamming_ball_states(inst, 32, seed=seed + 1),
-                                          chi=8, M=64, desc="Pegasus P3 nice 2x2 cells, d=32, chi=8, M=64")),
+                       oracle_sample=_PEG_SAMPLE),
+    "pegasus15x15": dict(desc="Pegasus P16 nice, 15x15 cells of 24 spins (5400 spins), d=256 states per cell "
+                              "(Hamming ball around a seeded reference), iid J,h in {+-1..+-7}/7, beta=2, chi=64, "
+                              "M=1024",
+                         make=lambda seed: L.pegasus_nice(16, seed),
+                         states=lambda inst, seed: L.hamming_ball_states(inst, 256, seed=seed + 1),
+                         beta=2.0, chi=64, M=1024, sweeps=2, d=256, oracle_sample=dict(_PEG_SAMPLE)),
+    "pegasus15x15_planted": dict(
+        desc="Pegasus P16 nice, 15x15 cells, planted frustrated 4-cycles (ground energy known), d=256 states per "
+             "cell around the planted state, beta=2, chi=64, M=1024",
+        make=lambda seed: L.planted(L.pegasus_nice(16, seed), seed + 7, loops_per_cell=6),
+        states=lambda inst, seed: L.hamming_ball_states(inst, 256, seed=seed + 1, reference=inst.planted),
+        beta=2.0, chi=64, M=1024, sweeps=2, d=256, oracle_sample=dict(_PEG_SAMPLE)),
 }
-DEFAULT = "chimera4x4"
-PRECISIONS = {"fp64": (0, "f64"), "fp32": (3, "f32 (FP64 truncation)"),
-              "tf32": (1, "3xtf32 tensor cores + f32 (FP64 truncation)")}
+DEFAULT = "pegasus15x15"
+# precision name -> (boundary precision, search precision or -1, dtype label)
+PRECISIONS = {"fp64": (0, -1, "f64"),
+              "fp32": (3, -1, "f32 contractions, f64 truncation"),
+              "tf32": (1, -1, "3xtf32 tensor cores + f32 contractions, f64 truncation"),
+              "fp64_tf32search": (0, 1, "f64 boundary, 3xtf32/f32 conditional scores")}
+DEFAULT_PRECISION = "tf32"
 # FP64 peak of a B300 derived from unit counts: 148 SMs x 2 DFMA/clk/SM x 2 flop x 2032 MHz
 FP64_PEAK_GFLOPS = 148 * 2 * 2 * 2.032
 # FP32 SIMT peak from unit counts (148 SMs x 128 FMA/clk x 2 flop x 2032 MHz)
@@ -135,6 +154,13 @@ def cpu_oracle(wl, seed, budget_s=15.0, max_runs=5):
             "sample": f"{runs} full oracle search(es) of {wl['sample_desc']} ({evals} evaluations, {t_tot:.1f} s)"}
 
 
+def bench_config(args, wl, ws=1):
+    return {"workload": args.workload, "description": wl["desc"], "instances_per_rank": 1,
+            "beta": wl["beta"], "chi": wl["chi"], "M": wl["M"], "states_per_cell": wl.get("d"),
+            "n_sweeps": wl["sweeps"], "precision": args.precision, "parallelism": f"replicas{ws}",
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
 def run_reference(args, wl):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -161,11 +187,38 @@ def run_reference(args, wl):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "description": wl["desc"], "instances_per_rank": 1},
+            "config": dict(bench_config(args, wl), oracle_sample=wl["sample_desc"]),
             "cpu_baseline": {"value": v, "unit": "marginal evals/s", "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} full oracle searches of {wl['sample_desc']} ({evals} evaluations)"},
             "e2e": {"value": v, "unit": "marginal evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def peak_of(name):
+    """(peak in TFLOP/s, bound, source) of a timed kernel label, from its arithmetic."""
+    if name.startswith("tc_gemm"):
+        return (TF32_PEAK_TFLOPS / 3.0, "tensor",
+                "measured bf16 burst peak x 1/2 (tf32 nominal ratio) / 3 (three products per 3xTF32)")
+    if name.endswith("_f32"):
+        return (FP32_PEAK_TFLOPS, "alu", "derived: 148 SMs x 128 FFMA/clk x 2 flop x 2032 MHz")
+    return (FP64_PEAK_GFLOPS / 1e3, "alu", "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2032 MHz (no measured FP64 peak)")
+
+
+def roofline_of(kt, names):
+    """Roofline entry of the kernel with the largest device time among ``names``."""
+    cand = [(kt[n][0], n) for n in names if kt.get(n) and kt[n][1] > 0 and kt[n][2] > 0]
+    if not cand:
+        return None
+    _, kn = max(cand)
+    ms, nl, fl = kt[kn]
+    achieved = (fl / nl) / (ms / nl * 1e-3) / 1e12
+    pk, bound, src = peak_of(kn)
+    return {"kernel": kn, "bound": bound, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+            "frac": achieved / pk, "traffic": None, "peak_source": src,
+            "launches": nl, "ms_per_launch": ms / nl, "flop_per_launch": fl / nl}
+
+
+CONTRACTION_KERNELS = ("site_diagram", "env_update", "theta_env", "theta_mul", "renv", "score", "tc_gemm", "gemm")
 
 
 def run_native(args, wl):
@@ -182,7 +235,8 @@ def run_native(args, wl):
     states = wl["states"](inst, args.seed + rank) if wl["states"] else None
     h = sgtn.Handle(inst, states, stream=stream.cuda_stream)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > 126 MB L2
-    prec, dtype_name = PRECISIONS[args.precision]
+    prec, sprec, dtype_name = PRECISIONS[args.precision]
+    h.set_search_precision(sprec)
 
     def step():
         h.set_beta(wl["beta"])
@@ -206,7 +260,7 @@ def run_native(args, wl):
         a.record(stream)
         h.set_beta(wl["beta"])
         fa = sgtn.stats()[1]
-        h.contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])
+        logz = h.contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])[0]
         bflops += sgtn.stats()[1] - fa
         res = h.search(wl["M"])
         b.record(stream)
@@ -225,8 +279,7 @@ def run_native(args, wl):
         t_ms, evals_all = float(tt.item()), float(ev.item())
     else:
         evals_all = evals
-    kt = {n: sgtn.kernel_time(n) for n in ("seg_gemm_f64", "seg_gemm_f32", "tc_gemm_3xtf32", "jacobi_f64",
-                                           "score_f64", "score_f32")}
+    kt = {n: sgtn.kernel_time(n) for n in sgtn.kernel_names()}
     unconverged = h.boundary_info()[0]
     # boundary contraction timed alone for its TFLOP/s
     torch.cuda.synchronize()
@@ -237,16 +290,22 @@ def run_native(args, wl):
     b.record(stream)
     torch.cuda.synchronize()
     bound_ms = a.elapsed_time(b)
+    # stated error of a mixed-precision boundary: log Z against the FP64 boundary (untimed)
+    logz_err = None
+    if prec != 0:
+        lz64 = h.contract_boundary(wl["chi"], precision=0, n_sweeps=wl["sweeps"])[0]
+        logz_err = {"logz": logz, "logz_fp64": lz64, "rel_err": abs(logz - lz64) / abs(lz64)}
     # end to end through the public API from host buffers: build (H2D) .. results (D2H)
     e2e_times = []
     h2d = inst.ei.nbytes + inst.ej.nbytes + inst.j_num.nbytes + inst.h_num.nbytes + inst.site_of_spin.nbytes
     if states is not None:
         h2d += sum(np.asarray(x, np.int64).nbytes for x in states) + 8 * (len(states) + 1)
     d2h = 0
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, min(args.steps, 2))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h2 = sgtn.Handle(inst, states, stream=stream.cuda_stream)
+        h2.set_search_precision(sprec)
         h2.set_beta(wl["beta"])
         h2.contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])
         r2 = h2.search(wl["M"])
@@ -260,42 +319,29 @@ def run_native(args, wl):
             dist.barrier()
             dist.destroy_process_group()
         return
-    # roofline of the dominant contraction kernel among those with an algorithmic flop count
-    roof = None
-    peaks = {"seg_gemm_f64": (FP64_PEAK_GFLOPS / 1e3, "alu", "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2032 MHz "
-                                                               "(no measured FP64 peak)"),
-             "seg_gemm_f32": (FP32_PEAK_TFLOPS, "alu", "derived: 148 SMs x 128 FFMA/clk x 2 flop x 2032 MHz"),
-             "tc_gemm_3xtf32": (TF32_PEAK_TFLOPS / 3.0, "tensor",
-                                "measured bf16 burst peak x 1/2 (tf32 nominal ratio) / 3 (three products per 3xTF32)")}
-    cand = [(v[0], n) for n, v in kt.items() if v and n in peaks and v[1] > 0]
-    if cand:
-        _, kn = max(cand)
-        ms, nl, fl = kt[kn]
-        achieved = (fl / nl) / (ms / nl * 1e-3) / 1e12
-        pk, bound, src = peaks[kn]
-        roof = {"kernel": kn, "bound": bound, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                "frac": achieved / pk, "traffic": None, "peak_source": src}
+    timed = [n for n, v in kt.items() if v]
+    roof = roofline_of(kt, timed)
+    roof_c = roofline_of(kt, [n for n in timed if n.startswith(CONTRACTION_KERNELS)])
     shares = {}
     tot_k = sum(v[0] for v in kt.values() if v)
-    for n, v in kt.items():
+    for n, v in sorted(kt.items(), key=lambda kv: -(kv[1][0] if kv[1] else 0)):
         if v:
             shares[n] = {"ms": v[0], "launches": v[1], "share_of_timed_kernels": v[0] / tot_k if tot_k else None}
     line = {"metric": "marginal evals/s", "value": evals_all / (t_ms * 1e-3), "unit": "marginal evals/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype_name,
             "data": "synthetic",
-            "config": {"workload": args.workload, "description": wl["desc"], "instances_per_rank": 1,
-                       "precision": args.precision, "parallelism": f"replicas{ws}",
-                       "l2": "flushed between timed steps (256 MB write)",
-                       "unconverged_truncations": unconverged},
+            "config": dict(bench_config(args, wl, ws), unconverged_truncations=unconverged),
             "boundary_tflops": (bflops / args.steps) / (bound_ms * 1e-3) / 1e12,
             "boundary_ms": bound_ms,
-            "roofline": roof, "kernel_times": shares,
+            "logz_check": logz_err,
+            "roofline": roof, "roofline_contraction": roof_c, "kernel_times": shares,
             "e2e": {"value": e2e_val, "unit": "marginal evals/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int((l1 - l0) / args.steps),
             "clocks": clocks,
-            "result": {"energy_num": int(res["energy_num"][0]), "logp": float(res["logp"][0])}}
+            "result": {"energy_num": int(res["energy_num"][0]), "logp": float(res["logp"][0]),
+                       "planted_energy_num": getattr(inst, "planted_energy_num", None)}}
     if ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle(wl, args.seed)
     print(json.dumps(line), flush=True)
@@ -307,12 +353,12 @@ def run_native(args, wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp64")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default=DEFAULT_PRECISION)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]

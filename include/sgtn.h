@@ -48,7 +48,9 @@ typedef enum {
  * and accumulates in FP32 while tensors are stored, truncated (SVD) and
  * normalised (log-norms) in FP64.  SGTN_TF32 (mixed, tensor cores): as FP32,
  * and dense GEMMs large enough for 128 x 128 tiles run on the tcgen05 tensor
- * cores with 3xTF32 splitting (about FP32 accuracy).  BF16 is reserved. */
+ * cores with 3xTF32 splitting (about FP32 accuracy).  BF16 is reserved.
+ * The conditionals, branch step and search run in the precision of the last
+ * sgtn_contract_boundary unless sgtn_set_search_precision chose another. */
 typedef enum { SGTN_FP64 = 0, SGTN_TF32 = 1, SGTN_BF16 = 2, SGTN_FP32 = 3 } sgtn_precision;
 
 /* Build the generalized Potts model of Sec. III, Eqs. (2)-(4): cluster
@@ -143,6 +145,14 @@ int sgtn_site_dims(sgtn_h h, int32_t site, int32_t* d);
  * their iteration cap because the singular values at the cut were not
  * separated (the truncation is then ambiguous; 0 for exact truncations), and
  * the precision the boundary was computed in. */
+/* Precision of sgtn_conditionals, sgtn_conditionals_noalloc, sgtn_branch_step
+ * and sgtn_search on this handle (the paper has no counterpart: its branch
+ * and bound runs in the precision of its contraction).  -1 (the default)
+ * follows the last sgtn_contract_boundary; SGTN_FP64, SGTN_FP32 or SGTN_TF32
+ * fix it, e.g. an FP64 boundary (exact log Z) with FP32 conditional scores.
+ * SGTN_ERR_ARG for any other value. */
+int sgtn_set_search_precision(sgtn_h h, int32_t precision);
+
 int sgtn_boundary_info(sgtn_h h, int32_t* unconverged_cuts, int32_t* precision);
 int sgtn_mps_shape(sgtn_h h, int32_t row, int32_t* phys, int32_t* bond, double* lognorm);
 int sgtn_mps_tensor(sgtn_h h, int32_t row, int32_t col, double* out);

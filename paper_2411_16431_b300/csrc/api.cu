@@ -78,20 +78,6 @@ int guarded(sgtn_h h, F&& f) {
 }
 }  // namespace
 
-// Contractions run in the handle's precision: FP32 arithmetic for SGTN_FP32,
-// plus tcgen05 tensor cores for large dense GEMMs for SGTN_TF32.  The branch
-// step and the search use the precision of the last contract_boundary.
-struct PrecisionScope {
-  explicit PrecisionScope(sgtn_h h) {
-    g_compute_f32 = h->precision == SGTN_FP32 || h->precision == SGTN_TF32;
-    g_use_tc = h->precision == SGTN_TF32;
-  }
-  ~PrecisionScope() {
-    g_compute_f32 = false;
-    g_use_tc = false;
-  }
-};
-
 extern "C" {
 
 int sgtn_build_instance(int32_t n_spins, int64_t n_edges, const int32_t* ei, const int32_t* ej, const int32_t* j_num,
@@ -135,7 +121,7 @@ int sgtn_contract_boundary(sgtn_h h, int32_t chi, int32_t precision, int32_t n_s
     if (precision != SGTN_FP64 && precision != SGTN_FP32 && precision != SGTN_TF32)
       throw SgtnError(SGTN_ERR_ARG, "precision must be SGTN_FP64, SGTN_FP32 or SGTN_TF32 in this build");
     h->precision = precision;
-    PrecisionScope ps(h);
+    PrecisionScope ps(h, false);
     contract_boundary(h, chi, n_sweeps);
     if (tc_gemm_take_error(h->st)) throw SgtnError(SGTN_ERR_TIMEOUT, "a tensor-core GEMM timed out");
     if (out_logz) *out_logz = h->logz;
@@ -145,7 +131,7 @@ int sgtn_contract_boundary(sgtn_h h, int32_t chi, int32_t precision, int32_t n_s
 
 int sgtn_conditionals(sgtn_h h, int32_t step, int32_t count, const int32_t* configs, double* out_p) {
   return guarded(h, [&] {
-    PrecisionScope ps(h);
+    PrecisionScope ps(h, true);
     conditionals(h, step, count, configs, out_p);
   });
 }
@@ -154,7 +140,7 @@ int sgtn_branch_step(sgtn_h h, int32_t step, int32_t M, int32_t in_count, const 
                      const double* in_logp, int32_t* out_configs, double* out_logp, int32_t* out_count,
                      double* io_pd) {
   return guarded(h, [&] {
-    PrecisionScope ps(h);
+    PrecisionScope ps(h, true);
     branch_step(h, step, M, in_count, in_configs, in_logp, out_configs, out_logp, out_count, io_pd);
   });
 }
@@ -162,7 +148,7 @@ int sgtn_branch_step(sgtn_h h, int32_t step, int32_t M, int32_t in_count, const 
 int sgtn_search(sgtn_h h, int32_t M, int32_t n_out, int8_t* out_spins, int64_t* out_energy_num, double* out_logp,
                 double* out_pd, int32_t* out_count) {
   return guarded(h, [&] {
-    PrecisionScope ps(h);
+    PrecisionScope ps(h, true);
     search(h, M, n_out, out_spins, out_energy_num, out_logp, out_pd, out_count);
   });
 }
@@ -178,6 +164,14 @@ int sgtn_energies(sgtn_h h, int32_t n, const int8_t* spins, int64_t* out) {
   return guarded(h, [&] {
     if (n < 0 || (n > 0 && (!spins || !out))) throw SgtnError(SGTN_ERR_ARG, "bad argument");
     energies(h, n, spins, out);
+  });
+}
+
+int sgtn_set_search_precision(sgtn_h h, int32_t precision) {
+  return guarded(h, [&] {
+    if (precision != -1 && precision != SGTN_FP64 && precision != SGTN_FP32 && precision != SGTN_TF32)
+      throw SgtnError(SGTN_ERR_ARG, "search precision must be -1, SGTN_FP64, SGTN_FP32 or SGTN_TF32");
+    h->search_precision = precision;
   });
 }
 

@@ -365,6 +365,12 @@ SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   SGTN_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
   h->sync();
   if (hs < 0) throw SgtnError(-4, "Jacobi SVD did not converge");
+  {
+    // per sweep and pair: three dot products and the rotation of both vectors
+    // (6 flop per element each) and of their columns of V
+    const double vl = std::max(m, n), np = p;
+    ktimer_add_flops("jacobi_f64", double(hs) * np * (np - 1) / 2 * (12.0 * vl + 6.0 * np));
+  }
   if (prof_on()) {
     SvdProf& e = g_prof[std::string(g_tag) + (std::max(m, n) > 128 ? "/jacobi_long" : "/jacobi")];
     e.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -437,7 +443,7 @@ SvdOut svd_subspace(sgtn_inst* h, const double* Th, int m, int n, int cap) {
 bool cqr_orth(sgtn_inst* h, const double* M, int len, int k, double* Q, bool first_f32) {
   F64Scope f64;
   cudaStream_t st = h->st;
-  if (k < 1 || len < k) return false;
+  if (k < 1 || len < k || k > 160) return false;   // the Cholesky factor is staged in one CTA's shared memory
   double* G = h->ws.get<double>("cqo_G", size_t(k) * k);
   double* R = h->ws.get<double>("cqo_R", size_t(k) * k);
   double* Ri = h->ws.get<double>("cqo_Ri", size_t(k) * k);

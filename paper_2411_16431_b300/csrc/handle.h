@@ -74,6 +74,7 @@ struct sgtn_inst {
   double log_offset = 0.0;
   std::vector<sgtn::MPS> psi;             // psi[r] covers rows r+1..R-1
   int chi = 0, precision = 0, n_sweeps = 0;
+  int search_precision = -1;              // conditionals / branch step / search; -1: as the boundary
   bool boundary_ok = false;
   double logz = 0.0, worst_sv = 0.0;
   sgtn::Scratch ws;
@@ -122,4 +123,23 @@ void logz_grad(sgtn_inst* h, double* dJ, double* dh, double* dbeta);
 size_t scores_scratch_bytes(sgtn_inst* h, int step, int K);
 void conditionals_arena(sgtn_inst* h, int step, int count, const int32_t* configs, double* out_p, void* arena,
                         size_t cap);
+}  // namespace sgtn
+
+namespace sgtn {
+// Arithmetic of the contractions issued inside one API call: FP32 (plus
+// tcgen05 tensor cores for large dense GEMMs with TF32) or FP64, from the
+// precision of the last contract_boundary, or, for the conditionals, branch
+// step and search, from the search precision when one was set.  Values:
+// 0 FP64, 1 TF32, 3 FP32 (sgtn_precision).
+struct PrecisionScope {
+  PrecisionScope(const sgtn_inst* h, bool search) {
+    const int p = (search && h->search_precision >= 0) ? h->search_precision : h->precision;
+    g_compute_f32 = p == 3 || p == 1;
+    g_use_tc = p == 1;
+  }
+  ~PrecisionScope() {
+    g_compute_f32 = false;
+    g_use_tc = false;
+  }
+};
 }  // namespace sgtn

@@ -31,6 +31,7 @@ extern bool g_no_alloc;
 void ktimer_begin(const char* name, cudaStream_t st);
 void ktimer_end(cudaStream_t st, double flops);
 void ktimer_enable(bool on);
+void ktimer_add_flops(const char* name, double flops);   // work known only after the launch
 void ktimer_reset();
 bool ktimer_read(const char* name, double* ms, long long* n, double* flops);
 std::string ktimer_names();   // comma-separated names seen so far

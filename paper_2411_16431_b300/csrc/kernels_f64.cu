@@ -923,6 +923,9 @@ void ktimer_end(cudaStream_t st, double flops) {
   g_timer.cur = nullptr;
   if (g_timer.pending.size() > 4096) g_timer.resolve();
 }
+void ktimer_add_flops(const char* name, double flops) {
+  if (g_timer.on) g_timer.acc[name][2] += flops;
+}
 void ktimer_enable(bool on) {
   g_timer.resolve();
   g_timer.on = on;
@@ -1164,12 +1167,13 @@ void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv,
     cudaFuncSetAttribute(cholesky_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr = true;
   }
+  const double fl = double(n) * n * n;   // n^3/3 FMA factor + n^3/6 FMA inverse, 2 flop each
   if (f32) {
-    KTimer t("cholesky_f32", st);
+    KTimer t("cholesky_f32", st, fl);
     cholesky_inv_kernel<float><<<1, 1024, size_t(n) * (n + 2) * sizeof(float), st>>>(G, n, shift, R, Rinv, status,
                                                                                     minratio);
   } else {
-    KTimer t("cholesky_f64", st);
+    KTimer t("cholesky_f64", st, fl);
     cholesky_inv_kernel<double><<<1, 1024, size_t(n) * (n + 2) * sizeof(double), st>>>(G, n, shift, R, Rinv, status,
                                                                                       minratio);
   }

@@ -49,6 +49,7 @@ extern "C" int sgtn_conditionals_noalloc(sgtn_h h, int32_t step, int32_t count, 
   try {
     SGTN_CUDA(cudaSetDevice(h->device));
     void* scratch = scratch_address(h->device);
+    sgtn::PrecisionScope ps(h, true);
     sgtn::conditionals_arena(h, step, count, configs, out_p, scratch, SGTN_NOALLOC_SCRATCH_BYTES);
     h->err.clear();
     return SGTN_OK;

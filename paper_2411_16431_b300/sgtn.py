@@ -37,6 +37,7 @@ def load():
     L.sgtn_conditionals.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I32P, _F64P]
     L.sgtn_branch_step.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, _I32P, _F64P, _I32P, _F64P,
                                    _I32P, _F64P]
+    L.sgtn_set_search_precision.argtypes = [ct.c_void_p, ct.c_int32]
     L.sgtn_kernel_names.argtypes = [ct.c_char_p, ct.c_int32]
     L.sgtn_kernel_names.restype = ct.c_int32
     L.sgtn_search.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I8P, _I64P, _F64P, _F64P, _I32P]
@@ -151,6 +152,10 @@ class Handle:
         ws = ct.c_double()
         self._ck(self.L.sgtn_contract_boundary(self.h, chi, precision, n_sweeps, ct.byref(lz), ct.byref(ws)))
         return lz.value, ws.value
+
+    def set_search_precision(self, precision):
+        """Precision of conditionals / branch_step / search (-1: as the last contract_boundary)."""
+        self._ck(self.L.sgtn_set_search_precision(self.h, precision))
 
     def boundary_info(self):
         """(iterative truncations stopped at their cap, precision of the boundary)."""

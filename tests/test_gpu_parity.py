@@ -310,6 +310,33 @@ def test_mixed_precision_error_is_small(Handle, case, prec):
     assert np.allclose(res["logp"], ref["logp"], rtol=1e-4)
 
 
+def test_fp64_boundary_with_fp32_search(Handle):
+    """FP64 boundary (log Z exact to 1e-10) with FP32 / TF32 conditional scores:
+    marginals within 1e-5 of the FP64 ones, same search result; -1 restores FP64."""
+    from paper_2411_16431_b300 import sgtn
+    inst, states, beta, chi, ns = PEGP, PEGP_STATES, 2.0, 8, 2
+    lz_o, _, _ = boundary_mps(PottsModel(inst, states), beta, chi, ns)
+    h = Handle(inst, states)
+    h.set_beta(beta)
+    lz, _ = h.contract_boundary(chi, n_sweeps=ns)
+    assert abs(lz - lz_o) < RTOL * abs(lz_o)
+    ref = h.search(16)
+    rng = np.random.default_rng(0)
+    cfg = np.array([[rng.integers(h.d[p]) for p in range(5)] for _ in range(8)], np.int32)
+    p64 = h.conditionals(5, cfg)
+    for prec in (sgtn.FP32, sgtn.TF32):
+        h.set_search_precision(prec)
+        p32 = h.conditionals(5, cfg)
+        assert np.abs(p32 - p64).max() <= 1e-5 * p64.max()
+        res = h.search(16)
+        assert np.array_equal(res["energy_num"], ref["energy_num"])
+        assert np.allclose(res["logp"], ref["logp"], rtol=1e-4)
+    h.set_search_precision(-1)
+    assert np.allclose(h.conditionals(5, cfg), p64, rtol=0, atol=0)
+    with pytest.raises(sgtn.SgtnError):
+        h.set_search_precision(7)
+
+
 def test_tall_skinny_svd_path_matches_oracle(Handle, monkeypatch):
     """Cases whose truncations are tall-skinny enough for the CholeskyQR route."""
     inst, beta, chi = L.chimera_grid(3, 8, 2), 1.2, 8
