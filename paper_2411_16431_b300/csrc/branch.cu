@@ -129,6 +129,16 @@ __global__ void colnorm_kernel(double* X, long long rows, int K) {
   for (long long i = threadIdx.x; i < rows; i += blockDim.x) X[i * K + k] *= s;
 }
 
+// out[i][k] = in[i][anc[k]]  (rows x K from rows x K0)
+__global__ void gather_cols_kernel(const double* in, long long rows, int K0, const int32_t* anc, int K, double* out) {
+  const long long n = rows * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / K;
+    const int k = int(e % K);
+    out[e] = in[i * K0 + anc[k]];
+  }
+}
+
 // s[k][x] for all branches k (threads) of one state x (block)
 template <class CT>
 __global__ void score_kernel(int K, int d, int chl, int chr, int nG, int nE, int nPdr, const double* E,
@@ -334,14 +344,19 @@ struct Step {
   // instead of calling cudaMalloc (256-byte aligned pieces)
   char* arena = nullptr;
   size_t arena_cap = 0, arena_used = 0;
+  bool spill = false;        // arena exhausted: cudaMalloc the rest (the search grows its arena next step)
+  size_t spilled = 0;
   template <class T>
   T* alloc(size_t n) {
     if (arena) {
       size_t b = ((n ? n : 1) * sizeof(T) + 255) / 256 * 256;
-      if (arena_used + b > arena_cap) throw SgtnError(-1, "scratch arena exhausted");
-      T* p = reinterpret_cast<T*>(arena + arena_used);
-      arena_used += b;
-      return p;
+      if (arena_used + b <= arena_cap) {
+        T* p = reinterpret_cast<T*>(arena + arena_used);
+        arena_used += b;
+        return p;
+      }
+      if (!spill) throw SgtnError(-1, "scratch arena exhausted");
+      spilled += b;
     }
     void* p = nullptr;
     SGTN_CUDA(cudaMalloc(&p, (n ? n : 1) * sizeof(T)));
@@ -354,11 +369,132 @@ struct Step {
   const Column& col(int cc) const { return h->cols[r * h->M.C + cc]; }
 };
 
-// everything up to the unnormalised scores s[k][x]
+// upper factors f[u][k] of column cc of row r for K branches (configs dcfg)
+void launch_upper_f(sgtn_inst* h, int r, int cc, int K, const int32_t* dcfg, int cfg_ld, double* f) {
+  const int C = h->M.C;
+  const Column& K_ = h->cols[r * C + cc];
+  const DSite* up = r > 0 ? &h->ds[(r - 1) * C + cc] : nullptr;
+  const DSite& me = h->ds[r * C + cc];
+  const int32_t *ul_pdr = nullptr, *ur_pdl = nullptr;
+  const double *Bv = nullptr, *Bdr = nullptr, *Bdl = nullptr;
+  int bv_nb = 1, bdr_nb = 1, bdl_nb = 1;
+  const int32_t* up_pd = nullptr;
+  if (r > 0) {
+    up_pd = up->cls[DD];
+    Bv = h->dB[size_t((r - 1) * C + cc) * 4 + 1];
+    bv_nb = h->M.tab[size_t((r - 1) * C + cc) * 4 + 1].nB;
+    if (cc - 1 >= 0) {
+      ul_pdr = h->ds[(r - 1) * C + cc - 1].cls[DDR];
+      Bdr = h->dB[size_t((r - 1) * C + cc - 1) * 4 + 2];
+      bdr_nb = h->M.tab[size_t((r - 1) * C + cc - 1) * 4 + 2].nB;
+    }
+    if (cc + 1 < C) {
+      ur_pdl = h->ds[(r - 1) * C + cc + 1].cls[DDL];
+      Bdl = h->dB[size_t((r - 1) * C + cc + 1) * 4 + 3];
+      bdl_nb = h->M.tab[size_t((r - 1) * C + cc + 1) * 4 + 3].nB;
+    }
+  }
+  upper_f_kernel<<<nblk((long long)K_.nU * K), 256, 0, h->st>>>(K, K_.nU, r, cc, C, dcfg, cfg_ld, up_pd, Bv, bv_nb,
+                                                               me.U_u, ul_pdr, Bdr, bdr_nb, me.U_ul, ur_pdl, Bdl,
+                                                               bdl_nb, me.U_ur, f);
+  ++g_count.launches;
+}
+
+// one step of the right environment: Fn [nBL][chl][K] from Ftl = Wk F [nK][chr][K]
+// of column cc (unplaced: summed over its states with weights w and factors f),
+// each branch's column normalised by its largest entry
+void renv_step(sgtn_inst* h, int r, int cc, const double* Ahat, const double* Ftl, const double* f, int K, int chl,
+               int chr, double* Fn) {
+  const int C = h->M.C;
+  const Column& K_ = h->cols[r * C + cc];
+  cudaStream_t st = h->st;
+  SGTN_CUDA(cudaMemsetAsync(Fn, 0, size_t(K_.nBL()) * chl * K * sizeof(double), st));
+  SegGemm a;
+  a.name = "renv";
+  a.X = Ahat;
+  a.p = chl;
+  a.q = chr;
+  a.xs_i = chr;
+  a.xs_k = 1;
+  a.xrs = (long long)chl * chr;
+  a.Y = Ftl;
+  a.s = K;
+  a.ys_k = K;
+  a.ys_j = 1;
+  a.yrs = (long long)chr * K;
+  a.O = Fn;
+  a.os_i = K;
+  a.os_j = 1;
+  a.ors = (long long)chl * K;
+  a.seg_ptr = K_.renv.seg_ptr;
+  a.vseg_ptr = K_.renv.vseg_ptr;
+  a.vfirst = K_.renv.vfirst;
+  a.nvseg = K_.renv.nvseg;
+  a.seg_or = K_.renv.seg_or;
+  a.seg_oc = K_.renv.seg_oc;
+  a.xr = K_.renv.xr;
+  a.xc = K_.renv.xc;
+  a.yr = K_.renv.yr;
+  a.yc = K_.renv.yc;
+  a.cidx = K_.renv.cidx;
+  a.csrow = K_.renv.csrow;
+  a.coef = h->ds[r * C + cc].w;
+  a.cs = f;
+  a.cs_ld = K;
+  a.nseg = K_.renv.nseg;
+  a.nterm = K_.renv.nterm;
+  seg_gemm(a, st);
+  colnorm_kernel<<<K, 256, 0, st>>>(Fn, (long long)K_.nBL() * chl, K);
+  ++g_count.launches;
+}
+
+// new left environment Eout [nBR(cc)][chr][Kout] after placing column cc:
+// branch kk extends branch par[kk] of Ein (Kin branches) with state xs[kk]
+void lenv_step(sgtn_inst* h, int r, int cc, const double* Ahat, const double* Ein, int Kin, int Kout,
+               const int32_t* par, const int32_t* xs, int chl, int chr, double* Eout) {
+  const int C = h->M.C;
+  const Column& K_ = h->cols[r * C + cc];
+  const DSite& D = h->ds[r * C + cc];
+  size_t smem = size_t(K_.nE) * chr * sizeof(double);
+  lenv_kernel<<<Kout, 128, smem, h->st>>>(Kin, Kout, par, xs, Ein, chl, chr, K_.nG, K_.nE, K_.nPdr, K_.nLR, K_.nGR,
+                                          Ahat, D.lam_x, D.cls[DD], D.cls[DR_], D.cls[DDR], K_.l_pl, K_.l_pdl,
+                                          h->dB[size_t(r * C + cc) * 4 + 0], K_.bh_nb,
+                                          h->dB[size_t(r * C + cc) * 4 + 2], K_.bdr_nb, Eout);
+  ++g_count.launches;
+}
+
+// scores S.s[k][x] of column S.c from S.E, S.Ahat[c], S.f[c] and Ft = Wk F
+void compute_scores(Step& S, const double* Ft) {
+  sgtn_inst* h = S.h;
+  cudaStream_t st = h->st;
+  const int r = S.r, c = S.c, K = S.K;
+  const Column& Kc = S.col(c);
+  const int chl = S.A->bond[c], chr = S.A->bond[c + 1];
+  const DSite& D = h->ds[r * h->M.C + c];
+  S.s = S.alloc<double>(size_t(K) * D.d);
+  int thr = std::min(256, std::max(32, ((K + 3) / 4 + 31) / 32 * 32));
+  if (K > 4 * thr) throw SgtnError(-1, "beam too large for the score kernel");
+  double sc_fl = 2.0 * K * D.d * (double)Kc.nG * Kc.nE * chl * (chr + 1);
+  if (g_compute_f32) {
+    KTimer tsc("score_f32", st, sc_fl);
+    score_kernel<float><<<D.d, thr, size_t(chl) * chr * sizeof(float), st>>>(
+        K, D.d, chl, chr, Kc.nG, Kc.nE, Kc.nPdr, S.E, S.Ahat[c], Ft, S.f[c], D.w, D.lam_x, D.u_x, D.cls[DD],
+        D.cls[DR_], D.cls[DDR], S.s);
+  } else {
+    KTimer tsc("score_f64", st, sc_fl);
+    score_kernel<double><<<D.d, thr, size_t(chl) * chr * sizeof(double), st>>>(
+        K, D.d, chl, chr, Kc.nG, Kc.nE, Kc.nPdr, S.E, S.Ahat[c], Ft, S.f[c], D.w, D.lam_x, D.u_x, D.cls[DD],
+        D.cls[DR_], D.cls[DDR], S.s);
+  }
+  ++g_count.launches;
+}
+
+// everything up to the unnormalised scores s[k][x], from scratch (stateless
+// entry points: conditionals, branch_step)
 void prepare_scores(Step& S, const int32_t* hcfg) {
   sgtn_inst* h = S.h;
   cudaStream_t st = h->st;
-  const int C = h->M.C, R = h->M.R;
+  const int C = h->M.C;
   const int r = S.r, c = S.c, K = S.K;
   if (!h->boundary_ok) throw SgtnError(-2, "contract_boundary must run first");
   S.A = &h->psi[r];
@@ -377,32 +513,8 @@ void prepare_scores(Step& S, const int32_t* hcfg) {
   // upper factors
   S.f.assign(C, nullptr);
   for (int cc = 0; cc < C; ++cc) {
-    const Column& K_ = S.col(cc);
-    S.f[cc] = S.alloc<double>(size_t(K_.nU) * K);
-    const DSite* up = r > 0 ? &h->ds[(r - 1) * C + cc] : nullptr;
-    const DSite& me = h->ds[r * C + cc];
-    const int32_t *ul_pdr = nullptr, *ur_pdl = nullptr;
-    const double *Bv = nullptr, *Bdr = nullptr, *Bdl = nullptr;
-    int bv_nb = 1, bdr_nb = 1, bdl_nb = 1;
-    const int32_t* up_pd = nullptr;
-    if (r > 0) {
-      up_pd = up->cls[DD];
-      Bv = h->dB[size_t((r - 1) * C + cc) * 4 + 1];
-      bv_nb = h->M.tab[size_t((r - 1) * C + cc) * 4 + 1].nB;
-      if (cc - 1 >= 0) {
-        ul_pdr = h->ds[(r - 1) * C + cc - 1].cls[DDR];
-        Bdr = h->dB[size_t((r - 1) * C + cc - 1) * 4 + 2];
-        bdr_nb = h->M.tab[size_t((r - 1) * C + cc - 1) * 4 + 2].nB;
-      }
-      if (cc + 1 < C) {
-        ur_pdl = h->ds[(r - 1) * C + cc + 1].cls[DDL];
-        Bdl = h->dB[size_t((r - 1) * C + cc + 1) * 4 + 3];
-        bdl_nb = h->M.tab[size_t((r - 1) * C + cc + 1) * 4 + 3].nB;
-      }
-    }
-    upper_f_kernel<<<nblk((long long)K_.nU * K), 256, 0, st>>>(K, K_.nU, r, cc, C, S.dcfg, S.cfg_ld, up_pd, Bv, bv_nb,
-                                                              me.U_u, ul_pdr, Bdr, bdr_nb, me.U_ul, ur_pdl, Bdl,
-                                                              bdl_nb, me.U_ur, S.f[cc]); ++g_count.launches;
+    S.f[cc] = S.alloc<double>(size_t(S.col(cc).nU) * K);
+    launch_upper_f(h, r, cc, K, S.dcfg, S.cfg_ld, S.f[cc]);
   }
   // left environment at column c
   {
@@ -418,12 +530,7 @@ void prepare_scores(Step& S, const int32_t* hcfg) {
       SGTN_CUDA(cudaMemcpyAsync(xs, hx.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice, st));
       int chl = S.A->bond[cc], chr = S.A->bond[cc + 1];
       double* En = S.alloc<double>(size_t(K_.nBR()) * chr * K);
-      const DSite& D = h->ds[r * C + cc];
-      size_t smem = size_t(K_.nE) * chr * sizeof(double);
-      lenv_kernel<<<K, 128, smem, st>>>(K, K, par, xs, S.E, chl, chr, K_.nG, K_.nE, K_.nPdr, K_.nLR, K_.nGR,
-                                        S.Ahat[cc], D.lam_x, D.cls[DD], D.cls[DR_], D.cls[DDR], K_.l_pl, K_.l_pdl,
-                                        h->dB[size_t(r * C + cc) * 4 + 0], K_.bh_nb, h->dB[size_t(r * C + cc) * 4 + 2],
-                                        K_.bdr_nb, En); ++g_count.launches;
+      lenv_step(h, r, cc, S.Ahat[cc], S.E, K, K, par, xs, chl, chr, En);
       S.E = En;
       h->sync();  // xs is reused
     }
@@ -438,69 +545,16 @@ void prepare_scores(Step& S, const int32_t* hcfg) {
     gemm(K_.Wk, false, K_.nBR(), F, false, (long long)chr * K, Ftl, (long long)chr * K, K_.nK(), chr * K, K_.nBR(), 1.0,
          0, st);
     double* Fn = S.alloc<double>(size_t(K_.nBL()) * chl * K);
-    SGTN_CUDA(cudaMemsetAsync(Fn, 0, size_t(K_.nBL()) * chl * K * sizeof(double), st));
-    SegGemm a;
-    a.name = "renv";
-    a.X = S.Ahat[cc];
-    a.p = chl;
-    a.q = chr;
-    a.xs_i = chr;
-    a.xs_k = 1;
-    a.xrs = (long long)chl * chr;
-    a.Y = Ftl;
-    a.s = K;
-    a.ys_k = K;
-    a.ys_j = 1;
-    a.yrs = (long long)chr * K;
-    a.O = Fn;
-    a.os_i = K;
-    a.os_j = 1;
-    a.ors = (long long)chl * K;
-    a.seg_ptr = K_.renv.seg_ptr;
-    a.vseg_ptr = K_.renv.vseg_ptr;
-    a.vfirst = K_.renv.vfirst;
-    a.nvseg = K_.renv.nvseg;
-    a.seg_or = K_.renv.seg_or;
-    a.seg_oc = K_.renv.seg_oc;
-    a.xr = K_.renv.xr;
-    a.xc = K_.renv.xc;
-    a.yr = K_.renv.yr;
-    a.yc = K_.renv.yc;
-    a.cidx = K_.renv.cidx;
-    a.csrow = K_.renv.csrow;
-    a.coef = h->ds[r * C + cc].w;
-    a.cs = S.f[cc];
-    a.cs_ld = K;
-    a.nseg = K_.renv.nseg;
-    a.nterm = K_.renv.nterm;
-    seg_gemm(a, st);
-    colnorm_kernel<<<K, 256, 0, st>>>(Fn, (long long)K_.nBL() * chl, K); ++g_count.launches;
+    renv_step(h, r, cc, S.Ahat[cc], Ftl, S.f[cc], K, chl, chr, Fn);
     F = Fn;
   }
   const Column& Kc = S.col(c);
-  int chl = S.A->bond[c], chr = S.A->bond[c + 1];
+  int chr = S.A->bond[c + 1];
   S.Ft = S.alloc<double>(size_t(Kc.nK()) * chr * K);
   gemm(Kc.Wk, false, Kc.nBR(), F, false, (long long)chr * K, S.Ft, (long long)chr * K, Kc.nK(), chr * K, Kc.nBR(), 1.0, 0,
        st);
-  const DSite& D = h->ds[r * C + c];
-  S.s = S.alloc<double>(size_t(K) * D.d);
-  int thr = std::min(256, std::max(32, ((K + 3) / 4 + 31) / 32 * 32));
-  if (K > 4 * thr) throw SgtnError(-1, "beam too large for the score kernel");
-  double sc_fl = 2.0 * K * D.d * (double)Kc.nG * Kc.nE * chl * (chr + 1);
-  if (g_compute_f32) {
-    KTimer tsc("score_f32", st, sc_fl);
-    score_kernel<float><<<D.d, thr, size_t(chl) * chr * sizeof(float), st>>>(
-        K, D.d, chl, chr, Kc.nG, Kc.nE, Kc.nPdr, S.E, S.Ahat[c], S.Ft, S.f[c], D.w, D.lam_x, D.u_x, D.cls[DD],
-        D.cls[DR_], D.cls[DDR], S.s);
-  } else {
-    KTimer tsc("score_f64", st, sc_fl);
-    score_kernel<double><<<D.d, thr, size_t(chl) * chr * sizeof(double), st>>>(
-        K, D.d, chl, chr, Kc.nG, Kc.nE, Kc.nPdr, S.E, S.Ahat[c], S.Ft, S.f[c], D.w, D.lam_x, D.u_x, D.cls[DD],
-        D.cls[DR_], D.cls[DDR], S.s);
-  }
-  ++g_count.launches;
+  compute_scores(S, S.Ft);
   h->check();
-  (void)R;
 }
 
 void check_configs(sgtn_inst* h, int step, int count, const int32_t* cfg) {
@@ -599,20 +653,14 @@ void conditionals_arena(sgtn_inst* h, int step, int count, const int32_t* config
   }
 }
 
-void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_configs, const double* in_logp,
-                 int32_t* out_configs, double* out_logp, int32_t* out_count, double* io_pd) {
-  check_configs(h, step, in_count, in_configs);
-  if (M <= 0 || !in_logp || !out_configs || !out_logp || !out_count || !io_pd) throw SgtnError(-1, "bad argument");
+// Steps 3-5 from the scores S.s of the K = S.K branches: log p, merge, top-M.
+// out_parent (optional) receives the branch index of every survivor.
+void select_step(Step& S, int step, int M, const int32_t* in_configs, const double* in_logp, int32_t* out_configs,
+                 double* out_logp, int32_t* out_count, double* io_pd, int32_t* out_parent) {
+  sgtn_inst* h = S.h;
   cudaStream_t st = h->st;
   const int C = h->M.C;
-  Step S;
-  S.h = h;
-  S.n = step;
-  S.r = step / C;
-  S.c = step % C;
-  S.K = in_count;
-  const int K = in_count;
-  prepare_scores(S, in_configs);
+  const int K = S.K;
   const HSite& site = h->M.sites[step];
   const int d = site.d;
   const long long ncand = (long long)K * d;
@@ -737,11 +785,28 @@ void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_
       for (int p = 0; p < step; ++p) out_configs[(long long)i * (step + 1) + p] = in_configs[(long long)k * step + p];
       out_configs[(long long)i * (step + 1) + step] = x;
       out_logp[i] = hlp[ci];
+      if (out_parent) out_parent[i] = k;
     }
     *out_count = outc;
     if (hlost) *io_pd = std::max(*io_pd, key_to_double(hlost));
   }
   h->check();
+  (void)C;
+}
+
+void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_configs, const double* in_logp,
+                 int32_t* out_configs, double* out_logp, int32_t* out_count, double* io_pd) {
+  check_configs(h, step, in_count, in_configs);
+  if (M <= 0 || !in_logp || !out_configs || !out_logp || !out_count || !io_pd) throw SgtnError(-1, "bad argument");
+  const int C = h->M.C;
+  Step S;
+  S.h = h;
+  S.n = step;
+  S.r = step / C;
+  S.c = step % C;
+  S.K = in_count;
+  prepare_scores(S, in_configs);
+  select_step(S, step, M, in_configs, in_logp, out_configs, out_logp, out_count, io_pd, nullptr);
 }
 
 void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_energy, double* out_logp, double* out_pd,
@@ -749,18 +814,116 @@ void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_ener
   if (!h->boundary_ok) throw SgtnError(-2, "contract_boundary must run first");
   if (M <= 0 || n_out <= 0 || !out_spins || !out_energy || !out_logp || !out_pd || !out_count)
     throw SgtnError(-1, "bad argument");
-  const int RC = h->M.R * h->M.C;
+  cudaStream_t st = h->st;
+  const int C = h->M.C, RC = h->M.R * h->M.C;
   std::vector<int32_t> cfg(1, 0), ncfg;
   std::vector<double> lp(1, 0.0), nlp;
   int count = 1;
   double pd = -INFINITY;
+  // Row cache: at the first column of row r everything that depends only on
+  // psi_r and on each branch's fixed row r-1 -- the projected MPS Ahat, the
+  // upper factors f and the right environments Ft = Wk F at every bond -- is
+  // computed once for the branches alive then (K0 of them).  A later branch
+  // inherits row r-1 from its ancestor anc[k] among those, so its f and Ft
+  // are gathered, not recomputed; the left environment grows by one column
+  // per step from the parent's.  Same values as the stateless branch step.
+  std::vector<double*> Ahat(C, nullptr), fr(C, nullptr), Ft(C, nullptr);
+  std::vector<int32_t> anc, par;
+  int K0 = 0, Kprev = 0;
+  double* E = nullptr;
+  int ebuf = 0;
+  size_t cap = size_t(64) << 20;   // per-step scratch; grows after a step that needed more
   for (int step = 0; step < RC; ++step) {
+    const int r = step / C, c = step % C, K = count;
+    Step S;
+    S.h = h;
+    S.n = step;
+    S.r = r;
+    S.c = c;
+    S.K = K;
+    S.A = &h->psi[r];
+    S.arena = h->ws.get<char>("search_arena", cap);
+    S.arena_cap = cap;
+    S.spill = true;
+    S.cfg_ld = std::max(step, 1);
+    S.dcfg = S.alloc<int32_t>(size_t(K) * S.cfg_ld);
+    if (step > 0)
+      SGTN_CUDA(cudaMemcpyAsync(S.dcfg, cfg.data(), size_t(K) * step * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (c == 0) {
+      K0 = K;
+      for (int cc = 0; cc < C; ++cc) {
+        const Column& K_ = S.col(cc);
+        const long long blk = (long long)S.A->bond[cc] * S.A->bond[cc + 1];
+        Ahat[cc] = h->ws.get<double>("srch_A" + std::to_string(cc), size_t(K_.nA() * blk));
+        gemm(K_.Wa, false, K_.nSig, S.A->t[cc], false, blk, Ahat[cc], blk, K_.nA(), int(blk), K_.nSig, 1.0, 0, st);
+        fr[cc] = h->ws.get<double>("srch_f" + std::to_string(cc), size_t(K_.nU) * K0);
+        launch_upper_f(h, r, cc, K0, S.dcfg, S.cfg_ld, fr[cc]);
+      }
+      double* F = h->ws.get<double>("srch_F1", size_t(K0));
+      fill(F, K0, 1.0, st);
+      int fb = 0;
+      for (int cc = C - 1; cc >= 0; --cc) {
+        const Column& K_ = S.col(cc);
+        const int chl = S.A->bond[cc], chr = S.A->bond[cc + 1];
+        Ft[cc] = h->ws.get<double>("srch_Ft" + std::to_string(cc), size_t(K_.nK()) * chr * K0);
+        gemm(K_.Wk, false, K_.nBR(), F, false, (long long)chr * K0, Ft[cc], (long long)chr * K0, K_.nK(), chr * K0,
+             K_.nBR(), 1.0, 0, st);
+        if (cc > 0) {
+          double* Fn = h->ws.get<double>(fb ? "srch_F1" : "srch_F0", size_t(K_.nBL()) * chl * K0);
+          fb ^= 1;
+          renv_step(h, r, cc, Ahat[cc], Ft[cc], fr[cc], K0, chl, chr, Fn);
+          F = Fn;
+        }
+      }
+      anc.resize(K);
+      std::iota(anc.begin(), anc.end(), 0);
+      E = h->ws.get<double>("srch_E" + std::to_string(ebuf), size_t(K));
+      fill(E, K, 1.0, st);
+    } else {
+      // place column c-1: E (Kprev branches) -> E for the K survivors
+      const int cc = c - 1, chl = S.A->bond[cc], chr = S.A->bond[cc + 1];
+      std::vector<int32_t> xs(K);
+      std::vector<int32_t> nanc(K);
+      for (int k = 0; k < K; ++k) {
+        xs[k] = cfg[size_t(k) * step + step - 1];
+        nanc[k] = anc[par[k]];
+      }
+      anc.swap(nanc);
+      int32_t* dpar = S.alloc<int32_t>(K);
+      int32_t* dxs = S.alloc<int32_t>(K);
+      SGTN_CUDA(cudaMemcpyAsync(dpar, par.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+      SGTN_CUDA(cudaMemcpyAsync(dxs, xs.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+      ebuf ^= 1;
+      double* En = h->ws.get<double>("srch_E" + std::to_string(ebuf), size_t(S.col(cc).nBR()) * chr * K);
+      lenv_step(h, r, cc, Ahat[cc], E, Kprev, K, dpar, dxs, chl, chr, En);
+      E = En;
+    }
+    // this column's f and Ft for the current branches
+    int32_t* danc = S.alloc<int32_t>(K);
+    SGTN_CUDA(cudaMemcpyAsync(danc, anc.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    const Column& Kc = S.col(c);
+    const int chr = S.A->bond[c + 1];
+    const long long frow = Kc.nU, trow = (long long)Kc.nK() * chr;
+    S.f.assign(C, nullptr);
+    S.f[c] = S.alloc<double>(size_t(frow) * K);
+    gather_cols_kernel<<<nblk(frow * K), 256, 0, st>>>(fr[c], frow, K0, danc, K, S.f[c]);
+    double* Ftc = S.alloc<double>(size_t(trow) * K);
+    gather_cols_kernel<<<nblk(trow * K), 256, 0, st>>>(Ft[c], trow, K0, danc, K, Ftc);
+    g_count.launches += 2;
+    S.E = E;
+    S.Ahat = Ahat;
+    compute_scores(S, Ftc);
     ncfg.assign(size_t(M) * (step + 1), 0);
     nlp.assign(M, 0.0);
+    par.assign(M, 0);
     int oc = 0;
-    branch_step(h, step, M, count, cfg.data(), lp.data(), ncfg.data(), nlp.data(), &oc, &pd);
+    select_step(S, step, M, cfg.data(), lp.data(), ncfg.data(), nlp.data(), &oc, &pd, par.data());
+    h->sync();   // the inputs of this step (host vectors) are replaced below
+    if (S.spilled) cap += 2 * S.spilled;
     cfg.assign(ncfg.begin(), ncfg.begin() + size_t(oc) * (step + 1));
     lp.assign(nlp.begin(), nlp.begin() + oc);
+    par.resize(oc);
+    Kprev = K;
     count = oc;
   }
   int nw = std::min(n_out, count);
