@@ -219,38 +219,6 @@ __global__ void logp_kernel(int K, int d, const double* s, const double* logp_in
   }
 }
 
-// parent class: smallest branch index with the same vector of remaining boundary classes;
-// parent rank: position of the configuration in lexicographic order
-__global__ void parent_kernel(int K, int n, const int32_t* cfg, int cfg_ld, int npairs, const int32_t* pair_site,
-                              const int32_t* const* pair_cls, int32_t* pc, int32_t* prank) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  const int32_t* a = cfg + (long long)k * cfg_ld;
-  int cls = k;
-  for (int k2 = 0; k2 < k; ++k2) {
-    const int32_t* b = cfg + (long long)k2 * cfg_ld;
-    bool eq = true;
-    for (int j = 0; j < npairs && eq; ++j) {
-      int p = pair_site[j];
-      eq = pair_cls[j][a[p]] == pair_cls[j][b[p]];
-    }
-    if (eq) {
-      cls = k2;
-      break;
-    }
-  }
-  pc[k] = cls;
-  int rank = 0;
-  for (int k2 = 0; k2 < K; ++k2) {
-    if (k2 == k) continue;
-    const int32_t* b = cfg + (long long)k2 * cfg_ld;
-    int cmp = 0;
-    for (int j = 0; j < n && cmp == 0; ++j) cmp = (b[j] < a[j]) ? -1 : (b[j] > a[j]) ? 1 : 0;
-    if (cmp < 0 || (cmp == 0 && k2 < k)) ++rank;
-  }
-  prank[k] = rank;
-}
-
 __global__ void merge1_kernel(int K, int d, int nX, const unsigned long long* key, const int32_t* pc,
                               const int32_t* xk, unsigned long long* best) {
   long long n = (long long)K * d;
@@ -394,9 +362,12 @@ void launch_upper_f(sgtn_inst* h, int r, int cc, int K, const int32_t* dcfg, int
       bdl_nb = h->M.tab[size_t((r - 1) * C + cc + 1) * 4 + 3].nB;
     }
   }
-  upper_f_kernel<<<nblk((long long)K_.nU * K), 256, 0, h->st>>>(K, K_.nU, r, cc, C, dcfg, cfg_ld, up_pd, Bv, bv_nb,
+  {
+    KTimer kt("upper_f", h->st);
+    upper_f_kernel<<<nblk((long long)K_.nU * K), 256, 0, h->st>>>(K, K_.nU, r, cc, C, dcfg, cfg_ld, up_pd, Bv, bv_nb,
                                                                me.U_u, ul_pdr, Bdr, bdr_nb, me.U_ul, ur_pdl, Bdl,
                                                                bdl_nb, me.U_ur, f);
+  }
   ++g_count.launches;
 }
 
@@ -456,10 +427,13 @@ void lenv_step(sgtn_inst* h, int r, int cc, const double* Ahat, const double* Ei
   const Column& K_ = h->cols[r * C + cc];
   const DSite& D = h->ds[r * C + cc];
   size_t smem = size_t(K_.nE) * chr * sizeof(double);
-  lenv_kernel<<<Kout, 128, smem, h->st>>>(Kin, Kout, par, xs, Ein, chl, chr, K_.nG, K_.nE, K_.nPdr, K_.nLR, K_.nGR,
+  {
+    KTimer kt("lenv", h->st);
+    lenv_kernel<<<Kout, 128, smem, h->st>>>(Kin, Kout, par, xs, Ein, chl, chr, K_.nG, K_.nE, K_.nPdr, K_.nLR, K_.nGR,
                                           Ahat, D.lam_x, D.cls[DD], D.cls[DR_], D.cls[DDR], K_.l_pl, K_.l_pdl,
                                           h->dB[size_t(r * C + cc) * 4 + 0], K_.bh_nb,
                                           h->dB[size_t(r * C + cc) * 4 + 2], K_.bdr_nb, Eout);
+  }
   ++g_count.launches;
 }
 
@@ -670,11 +644,17 @@ void select_step(Step& S, int step, int M, const int32_t* in_configs, const doub
   unsigned long long* key = S.alloc<unsigned long long>(ncand);
   int* clamps = S.alloc<int>(1);
   SGTN_CUDA(cudaMemsetAsync(clamps, 0, sizeof(int), st));
-  logp_kernel<<<K, 256, 0, st>>>(K, d, S.s, dlp_in, lp, key, clamps);
+  {
+    KTimer kt("logp", h->st);
+    logp_kernel<<<K, 256, 0, st>>>(K, d, S.s, dlp_in, lp, key, clamps);
+  }
   g_count.evals += ncand; ++g_count.launches;
-  // parent classes from the boundary pairs (p, dir) with p < step < l (Eq. 7)
+  // parent classes from the boundary pairs (p, dir) with p < step < l (Eq. 7):
+  // pc[k] = smallest branch with the same vector of boundary classes, prank[k]
+  // = position of branch k's configuration in lexicographic order (ties by
+  // index).  Both come from two sorts on the host, which holds the configs.
   std::vector<int32_t> psite;
-  std::vector<const int32_t*> pcls;
+  std::vector<const int32_t*> hcls;
   for (int p = 0; p < step; ++p) {
     const HSite& P = h->M.sites[p];
     for (int dd = 0; dd < 8; ++dd) {
@@ -683,20 +663,46 @@ void select_step(Step& S, int step, int M, const int32_t* in_configs, const doub
       int l = rr * C + cc;
       if (l > step && !P.coupled[dd].empty()) {
         psite.push_back(p);
-        pcls.push_back(h->ds[p].cls[dd]);
+        hcls.push_back(P.proj[dd].of_state.data());
       }
     }
   }
-  int npairs = int(psite.size());
-  int32_t* dps = S.alloc<int32_t>(npairs);
-  const int32_t** dpc = S.alloc<const int32_t*>(npairs);
-  if (npairs) {
-    SGTN_CUDA(cudaMemcpyAsync(dps, psite.data(), npairs * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    SGTN_CUDA(cudaMemcpyAsync(dpc, pcls.data(), npairs * sizeof(int32_t*), cudaMemcpyHostToDevice, st));
+  const int npairs = int(psite.size());
+  std::vector<int32_t> hpc(K), hprank(K), order(K);
+  {
+    auto cfgp = [&](int k) { return in_configs + (long long)k * step; };
+    auto same_classes = [&](int a, int b) {
+      const int32_t *ca = cfgp(a), *cb = cfgp(b);
+      for (int j = 0; j < npairs; ++j)
+        if (hcls[j][ca[psite[j]]] != hcls[j][cb[psite[j]]]) return false;
+      return true;
+    };
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+      const int32_t *ca = cfgp(a), *cb = cfgp(b);
+      for (int j = 0; j < npairs; ++j) {
+        const int32_t x = hcls[j][ca[psite[j]]], y = hcls[j][cb[psite[j]]];
+        if (x != y) return x < y;
+      }
+      return a < b;
+    });
+    for (int i = 0; i < K; ++i) {
+      const int k = order[i];
+      hpc[k] = (i > 0 && same_classes(k, order[i - 1])) ? hpc[order[i - 1]] : k;
+    }
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+      const int32_t *ca = cfgp(a), *cb = cfgp(b);
+      for (int j = 0; j < step; ++j)
+        if (ca[j] != cb[j]) return ca[j] < cb[j];
+      return a < b;
+    });
+    for (int i = 0; i < K; ++i) hprank[order[i]] = i;
   }
   int32_t* pc = S.alloc<int32_t>(K);
   int32_t* prank = S.alloc<int32_t>(K);
-  parent_kernel<<<(K + 127) / 128, 128, 0, st>>>(K, step, S.dcfg, S.cfg_ld, npairs, dps, dpc, pc, prank); ++g_count.launches;
+  SGTN_CUDA(cudaMemcpyAsync(pc, hpc.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  SGTN_CUDA(cudaMemcpyAsync(prank, hprank.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   const int nX = site.Xk.n;
   long long nslot = (long long)K * nX;
   unsigned long long* best = S.alloc<unsigned long long>(nslot);
@@ -705,9 +711,18 @@ void select_step(Step& S, int step, int M, const int32_t* in_configs, const doub
   SGTN_CUDA(cudaMemsetAsync(mn, 0x7f, nslot * sizeof(int), st));
   unsigned long long* lost = S.alloc<unsigned long long>(1);
   SGTN_CUDA(cudaMemsetAsync(lost, 0, sizeof(unsigned long long), st));
-  merge1_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, pc, h->ds[step].xk_x, best); ++g_count.launches;
-  merge2_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, lp, pc, prank, h->ds[step].xk_x, best, mn); ++g_count.launches;
-  merge3_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, pc, prank, h->ds[step].xk_x, mn, lost); ++g_count.launches;
+  {
+    KTimer kt("merge1", h->st);
+    merge1_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, pc, h->ds[step].xk_x, best);
+  } ++g_count.launches;
+  {
+    KTimer kt("merge2", h->st);
+    merge2_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, lp, pc, prank, h->ds[step].xk_x, best, mn);
+  } ++g_count.launches;
+  {
+    KTimer kt("merge3", h->st);
+    merge3_kernel<<<nblk(ncand), 256, 0, st>>>(K, d, nX, key, pc, prank, h->ds[step].xk_x, mn, lost);
+  } ++g_count.launches;
   // radix select of the M-th largest key
   unsigned int* hist = S.alloc<unsigned int>(256);
   unsigned long long prefix = 0, pmask = 0;
@@ -747,8 +762,11 @@ void select_step(Step& S, int step, int M, const int32_t* in_configs, const doub
     int cap_sel = M + 1, cap_tie = 4 * M + 4096;
     long long* sel = S.alloc<long long>(cap_sel);
     long long* tie = S.alloc<long long>(cap_tie);
-    select_kernel<<<nblk(ncand), 256, 0, st>>>(ncand, key, lp, T, tol, nsel, sel, nsel + 1, tie, lost, cap_sel,
-                                               cap_tie); ++g_count.launches;
+    {
+      KTimer kt("select", h->st);
+      select_kernel<<<nblk(ncand), 256, 0, st>>>(ncand, key, lp, T, tol, nsel, sel, nsel + 1, tie, lost, cap_sel,
+                                               cap_tie);
+    } ++g_count.launches;
     int hn[2];
     SGTN_CUDA(cudaMemcpyAsync(hn, nsel, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     h->sync();
@@ -757,8 +775,6 @@ void select_step(Step& S, int step, int M, const int32_t* in_configs, const doub
     std::vector<long long> hsel(n_above), htie(n_tie);
     if (n_above) SGTN_CUDA(cudaMemcpyAsync(hsel.data(), sel, n_above * sizeof(long long), cudaMemcpyDeviceToHost, st));
     if (n_tie) SGTN_CUDA(cudaMemcpyAsync(htie.data(), tie, n_tie * sizeof(long long), cudaMemcpyDeviceToHost, st));
-    std::vector<int32_t> hprank(K);
-    SGTN_CUDA(cudaMemcpyAsync(hprank.data(), prank, K * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     std::vector<double> hlp(ncand);
     SGTN_CUDA(cudaMemcpyAsync(hlp.data(), lp, ncand * sizeof(double), cudaMemcpyDeviceToHost, st));
     unsigned long long hlost = 0;
@@ -906,9 +922,15 @@ void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_ener
     const long long frow = Kc.nU, trow = (long long)Kc.nK() * chr;
     S.f.assign(C, nullptr);
     S.f[c] = S.alloc<double>(size_t(frow) * K);
-    gather_cols_kernel<<<nblk(frow * K), 256, 0, st>>>(fr[c], frow, K0, danc, K, S.f[c]);
+    {
+      KTimer kt("gather", h->st);
+      gather_cols_kernel<<<nblk(frow * K), 256, 0, st>>>(fr[c], frow, K0, danc, K, S.f[c]);
+    }
     double* Ftc = S.alloc<double>(size_t(trow) * K);
-    gather_cols_kernel<<<nblk(trow * K), 256, 0, st>>>(Ft[c], trow, K0, danc, K, Ftc);
+    {
+      KTimer kt("gather", h->st);
+      gather_cols_kernel<<<nblk(trow * K), 256, 0, st>>>(Ft[c], trow, K0, danc, K, Ftc);
+    }
     g_count.launches += 2;
     S.E = E;
     S.Ahat = Ahat;
