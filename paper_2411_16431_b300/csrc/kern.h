@@ -69,6 +69,7 @@ struct SegGemm {
   double alpha = 1.0;
   int accumulate = 0;
   const char* name = nullptr;   // timing label (role of the call); "_f32" / "_f64" is appended
+  int tile_m = 0, tile_n = 0;   // CTA tile (16/32/64 x 32/64); 0: from the block shape
   // optional balanced split of long segments (table mode): the virtual
   // segments are multiplied into a scratch block each and summed per segment
   // in a fixed order (deterministic)

@@ -522,16 +522,23 @@ __global__ void __launch_bounds__(128) jacobi_coop_kernel(double* X, int len, in
   if (blockIdx.x == 0 && threadIdx.x == 0) status[0] = done ? sweep : -1;
 }
 
-// Right-looking upper Cholesky of G + shift I in shared memory (two barriers a
-// column: the scaled pivot row is staged, then the trailing upper triangle is
-// updated by a 32 x 32 thread grid), then R^{-1} right-looking from the last
-// row (R X = I: finished row j of X is subtracted from every row above it),
-// with X kept transposed in the free lower triangle.  T is the arithmetic type
-// (float: a cheap first factor whose rounding a later FP64 pass removes); G,
-// R and R^{-1} are FP64 in memory.
+// Right-looking upper Cholesky of the n x n block W + shift I in shared memory
+// (two barriers a column: the scaled pivot row is staged, then the trailing
+// upper triangle is updated by a 32 x 32 thread grid), then R^{-1}
+// right-looking from the last row (R X = I: finished row j of X is subtracted
+// from every row above it), with X kept transposed in the free lower
+// triangle.  W, R and Rinv are blocks of row-major matrices with leading
+// dimension ld; Rinv may alias W (all of W is read before anything is
+// written).  Gd points at the matching diagonal block of the original G (for
+// the pivot ratios).  On a non-positive pivot j the first failure is recorded
+// as status[0] = status_off + j + 1; status is not written otherwise.
+// minratio[0] = min(minratio[0], smallest pivot / (G_jj + shift)).  T is the
+// arithmetic type (float: a cheap factor whose rounding a later FP64 pass
+// removes); memory stays FP64.
 template <class T>
-__global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* G, int n, double shift, double* R,
-                                                            double* Rinv, int* status, double* minratio) {
+__global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* W, int n, int ld, double shift, double* R,
+                                                            double* Rinv, const double* Gd, int* status,
+                                                            int status_off, double* minratio) {
   extern __shared__ __align__(16) unsigned char chol_smem[];
   T* A = reinterpret_cast<T*>(chol_smem);   // n x n
   T* row = A + n * n;                       // n: staged row / 1 / R_jj
@@ -542,9 +549,9 @@ __global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* G, int
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
-    A[e] = j >= i ? T(G[e] + (i == j ? shift : 0.0)) : T(0);
+    A[e] = j >= i ? T(W[(long long)i * ld + j] + (i == j ? shift : 0.0)) : T(0);
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) gd[i] = T(G[i * n + i] + shift);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) gd[i] = T(Gd[(long long)i * (ld + 1)] + shift);
   __syncthreads();
   // thread 0 takes each pivot (square root and reciprocal once, shared)
   auto take_pivot = [&](int j) {
@@ -594,13 +601,20 @@ __global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* G, int
   }
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, c = e % n;
-    R[e] = c >= i ? double(A[e]) : 0.0;
-    Rinv[e] = c > i ? double(A[c * n + i]) : (c == i ? double(row[i]) : 0.0);
+    R[(long long)i * ld + c] = c >= i ? double(A[e]) : 0.0;
+    Rinv[(long long)i * ld + c] = c > i ? double(A[c * n + i]) : (c == i ? double(row[i]) : 0.0);
   }
   if (threadIdx.x == 0) {
-    status[0] = fail;
-    if (minratio) minratio[0] = mr;
+    if (fail && status[0] == 0) status[0] = status_off + fail;
+    if (minratio) minratio[0] = fmin(minratio[0], mr);
   }
+}
+
+// X[i][j] = 0 for a rows x cols block with leading dimension ld
+__global__ void zero_block_kernel(double* X, int rows, int cols, int ld) {
+  const long long n = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    X[(e / cols) * ld + e % cols] = 0.0;
 }
 
 // Cholesky with diagonal pivoting of a positive semidefinite G (n x n, FP64),
@@ -909,14 +923,20 @@ struct TimerState {
 TimerState g_timer;
 }  // namespace
 
+// Timers nest: only the outermost one records (a Cholesky's time includes its
+// GEMMs, which are then not booked a second time).
+static int g_timer_depth = 0;
 void ktimer_begin(const char* name, cudaStream_t st) {
   if (!g_timer.on) return;
+  if (g_timer_depth++ > 0) return;
   g_timer.cur = name;
   g_timer.cur_a = g_timer.get();
   cudaEventRecord(g_timer.cur_a, st);
 }
 void ktimer_end(cudaStream_t st, double flops) {
-  if (!g_timer.on || !g_timer.cur) return;
+  if (!g_timer.on) return;
+  if (g_timer_depth > 0 && --g_timer_depth > 0) return;
+  if (!g_timer.cur) return;
   cudaEvent_t b = g_timer.get();
   cudaEventRecord(b, st);
   g_timer.pending.push_back({g_timer.cur, g_timer.cur_a, b, flops});
@@ -929,6 +949,7 @@ void ktimer_add_flops(const char* name, double flops) {
 void ktimer_enable(bool on) {
   g_timer.resolve();
   g_timer.on = on;
+  g_timer_depth = 0;
 }
 void ktimer_reset() {
   g_timer.resolve();
@@ -953,8 +974,8 @@ std::string ktimer_names() {
 namespace {
 void launch_seg(const SegGemm& a, cudaStream_t st) {
   // tile shape from the block shape: rows 16 / 32 / 64, columns 32 / 64
-  const int bm = a.p <= 16 ? 16 : a.p <= 32 ? 32 : 64;
-  const int bn = a.s <= 32 ? 32 : 64;
+  const int bm = a.tile_m ? a.tile_m : a.p <= 16 ? 16 : a.p <= 32 ? 32 : 64;
+  const int bn = a.tile_n ? a.tile_n : a.s <= 32 ? 32 : 64;
   dim3 grid(a.nseg, (a.p + bm - 1) / bm, (a.s + bn - 1) / bn);
   auto go = [&](auto kern) { kern<<<grid, 256, 0, st>>>(a); };
   if (a.f32) {
@@ -1038,9 +1059,14 @@ void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, lon
   a.alpha = alpha;
   a.accumulate = accumulate;
   a.name = "gemm";
-  const int bm = m <= 16 ? 16 : m <= 32 ? 32 : 64, bn = n <= 32 ? 32 : 64;   // as in launch_seg
+  // small outputs (Gram matrices, blocks of a Cholesky factor) take 16 x 32
+  // tiles, so that more CTAs share the work and less of each tile is padding
+  const bool small = (long long)m * n <= 160 * 160;
+  const int bm = small ? 16 : m <= 16 ? 16 : m <= 32 ? 32 : 64, bn = small ? 32 : n <= 32 ? 32 : 64;
+  a.tile_m = bm;
+  a.tile_n = bn;
   long long tiles = (long long)((m + bm - 1) / bm) * ((n + bn - 1) / bn);
-  if (tiles < 148 && k >= 256 && !g_no_alloc) {
+  if (tiles < 148 && k >= (small ? 64 : 256) && !g_no_alloc) {
     // few output tiles and a long reduction: split K over about two CTAs per
     // SM (chunks of at least 32), then reduce the partial products
     int nsplit = int(std::min<long long>((k + 31) / 32, std::max<long long>(2, (296 + tiles - 1) / tiles)));
@@ -1159,25 +1185,76 @@ void jacobi(double* X, int len, int p, long long si, long long sj, double* V, in
   ++g_count.launches;
 }
 
-void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv, int* status, cudaStream_t st,
-                  bool f32, double* minratio) {
+namespace {
+constexpr int kCholBlock = 48;   // blocks up to this size are factored by one CTA
+
+void chol_base(double* W, int n, int ld, double shift, double* R, const double* Gd, int* status, int off,
+               double* minratio, cudaStream_t st, bool f32) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(cholesky_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     cudaFuncSetAttribute(cholesky_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr = true;
   }
-  const double fl = double(n) * n * n;   // n^3/3 FMA factor + n^3/6 FMA inverse, 2 flop each
-  if (f32) {
-    KTimer t("cholesky_f32", st, fl);
-    cholesky_inv_kernel<float><<<1, 1024, size_t(n) * (n + 2) * sizeof(float), st>>>(G, n, shift, R, Rinv, status,
-                                                                                    minratio);
-  } else {
-    KTimer t("cholesky_f64", st, fl);
-    cholesky_inv_kernel<double><<<1, 1024, size_t(n) * (n + 2) * sizeof(double), st>>>(G, n, shift, R, Rinv, status,
-                                                                                      minratio);
-  }
+  if (f32)
+    cholesky_inv_kernel<float><<<1, 1024, size_t(n) * (n + 2) * sizeof(float), st>>>(W, n, ld, shift, R, W, Gd,
+                                                                                    status, off, minratio);
+  else
+    cholesky_inv_kernel<double><<<1, 1024, size_t(n) * (n + 2) * sizeof(double), st>>>(W, n, ld, shift, R, W, Gd,
+                                                                                      status, off, minratio);
   ++g_count.launches;
+}
+
+// Recursive blocked Cholesky and inverse, in place: on entry W (n x n block,
+// leading dimension ld) holds the upper triangle of G; on return R holds the
+// factor of G + shift I and W its inverse.  With n = n1 + n2:
+//   R11 = chol(G11), R12 = R11^{-T} G12, S = G22 - R12^T R12, R22 = chol(S),
+//   R^{-1}_12 = -R11^{-1} R12 R22^{-1};
+// the off-diagonal products are GEMMs over many CTAs, only the diagonal
+// blocks of at most kCholBlock rows are factored by one CTA.
+void chol_rec(double* W, int n, int ld, double shift, double* R, const double* Gd, int* status, int off,
+              double* minratio, double* T, cudaStream_t st, bool f32) {
+  if (n <= kCholBlock) {
+    chol_base(W, n, ld, shift, R, Gd, status, off, minratio, st, f32);
+    return;
+  }
+  const int n1 = std::min(n - 16, (n / 2 + 15) / 16 * 16), n2 = n - n1;
+  double *W12 = W + n1, *W21 = W + (long long)n1 * ld, *W22 = W21 + n1;
+  double *R12 = R + n1, *R21 = R + (long long)n1 * ld, *R22 = R21 + n1;
+  chol_rec(W, n1, ld, shift, R, Gd, status, off, minratio, T, st, f32);
+  gemm(W, true, ld, W12, false, ld, R12, ld, n1, n2, n1, 1.0, 0, st);        // R12 = R11^{-T} G12
+  gemm(R12, true, ld, R12, false, ld, W22, ld, n2, n2, n1, -1.0, 1, st);     // W22 = G22 - R12^T R12
+  chol_rec(W22, n2, ld, shift, R22, Gd + (long long)n1 * (ld + 1), status, off + n1, minratio, T, st, f32);
+  gemm(R12, false, ld, W22, false, ld, T, n2, n1, n2, n2, 1.0, 0, st);        // T = R12 R22^{-1}
+  gemm(W, false, ld, T, false, n2, W12, ld, n1, n2, n1, -1.0, 0, st);         // (R^{-1})_12 = -R11^{-1} T
+  const long long nz = (long long)n2 * n1;
+  zero_block_kernel<<<blocks_for(nz), 256, 0, st>>>(W21, n2, n1, ld);
+  zero_block_kernel<<<blocks_for(nz), 256, 0, st>>>(R21, n2, n1, ld);
+  g_count.launches += 2;
+}
+}  // namespace
+
+void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv, int* status, cudaStream_t st,
+                  bool f32, double* minratio) {
+  const double fl = double(n) * n * n;   // n^3/3 FMA factor + n^3/6 FMA inverse, 2 flop each
+  KTimer t(f32 ? "cholesky_f32" : "cholesky_f64", st, fl);
+  // the off-diagonal GEMMs run in FP64 whatever the caller's contraction precision
+  const bool sf = g_compute_f32, su = g_use_tc;
+  g_compute_f32 = g_use_tc = false;
+  static double* T = nullptr;
+  static double one = 1.0;
+  static size_t T_n = 0;
+  if (size_t(n) * n > T_n) {
+    if (T) cudaFree(T);
+    cudaMalloc(&T, size_t(n) * n * sizeof(double));
+    T_n = size_t(n) * n;
+  }
+  cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (minratio) cudaMemcpyAsync(minratio, &one, sizeof(double), cudaMemcpyHostToDevice, st);
+  if (Rinv != G) cudaMemcpyAsync(Rinv, G, size_t(n) * n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  chol_rec(Rinv, n, n, shift, R, G, status, 0, minratio, T, st, f32);
+  g_compute_f32 = sf;
+  g_use_tc = su;
 }
 
 void pchol_inv(const double* G, int n, double tol_rel, double tol_abs, double* R, double* Rinv, int32_t* perm,
