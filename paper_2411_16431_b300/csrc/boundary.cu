@@ -125,13 +125,13 @@ bool svd_tall_cqr3(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut&
 bool svd_tall_rrcqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o);
 
 // Exact truncated SVD: for a tall-skinny (or short-fat) matrix with a short
-// side of at most 160 (the Cholesky factor is staged in one CTA's shared memory), shifted CholeskyQR3 then a one-sided Jacobi SVD of the
+// side of at most 320, CholeskyQR2 or shifted CholeskyQR3 then a one-sided Jacobi SVD of the
 // small triangular factor; otherwise (or if a Cholesky pivot fails, i.e. the
 // vectors are exactly dependent) one-sided Jacobi on the shorter side.
 SvdOut svd_dense(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   SvdOut o;
   int p = std::min(m, n), q = std::max(m, n);
-  if (p <= 160 && q >= 2 * p && q >= 256) {
+  if (p <= 320 && q >= 2 * p && q >= 256) {
     if (prof_on()) g_prof[std::string(g_tag) + "/cqr_tries"].calls++;
     if (m >= n) {
       if (svd_tall_cqr(h, Th, m, n, cap, o)) return o;
@@ -243,6 +243,7 @@ bool svd_tall_cqr3(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut&
 // CholeskyQR; false if both fail.
 bool svd_tall_cqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o) {
   if (svd_tall_cqr3(h, M, m, n, cap, o)) return true;
+  if (n > 160) return false;   // the pivoted Cholesky is staged in one CTA's shared memory
   if (prof_on()) g_prof[std::string(g_tag) + "/rrcqr"].calls++;
   return svd_tall_rrcqr(h, M, m, n, cap, o);
 }
@@ -384,7 +385,9 @@ SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return s[a] > s[b]; });
   double smax = p ? s[idx[0]] : 0.0;
   if (std::getenv("SGTN_TRACE"))
-    fprintf(stderr, "[sgtn] svd_jacobi m=%d n=%d cap=%d smax=%.3e smin=%.3e\n", m, n, cap, smax, p ? s[idx[p - 1]] : 0.0);
+    fprintf(stderr, "[sgtn] svd_jacobi m=%d n=%d cap=%d smax=%.3e smin=%.3e sweeps=%d ms=%.3f\n", m, n, cap, smax,
+            p ? s[idx[p - 1]] : 0.0, hs,
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
   if (!(smax > 0.0) || !std::isfinite(smax)) throw SgtnError(-4, "zero or non-finite tensor in truncation");
   int cnt = 0;
   for (int i = 0; i < p; ++i)
@@ -443,7 +446,7 @@ SvdOut svd_subspace(sgtn_inst* h, const double* Th, int m, int n, int cap) {
 bool cqr_orth(sgtn_inst* h, const double* M, int len, int k, double* Q, bool first_f32) {
   F64Scope f64;
   cudaStream_t st = h->st;
-  if (k < 1 || len < k || k > 160) return false;   // the Cholesky factor is staged in one CTA's shared memory
+  if (k < 1 || len < k) return false;
   double* G = h->ws.get<double>("cqo_G", size_t(k) * k);
   double* R = h->ws.get<double>("cqo_R", size_t(k) * k);
   double* Ri = h->ws.get<double>("cqo_Ri", size_t(k) * k);
