@@ -759,7 +759,8 @@ void select_step(Step& S, int step, int M, const int32_t* in_configs, const doub
     }
     int* nsel = S.alloc<int>(2);
     SGTN_CUDA(cudaMemsetAsync(nsel, 0, 2 * sizeof(int), st));
-    int cap_sel = M + 1, cap_tie = 4 * M + 4096;
+    // a tie class may be as large as the candidate set (degenerate instances)
+    int cap_sel = M + 1, cap_tie = int(std::min<long long>(ncand, INT_MAX));
     long long* sel = S.alloc<long long>(cap_sel);
     long long* tie = S.alloc<long long>(cap_tie);
     {

@@ -152,6 +152,25 @@ def test_search_matches_oracle(Handle, case):
         assert res["energy_num"][0] >= inst.planted_energy_num
 
 
+def test_search_with_fully_degenerate_scores(Handle):
+    """All couplings and fields zero: every candidate of every step is tied;
+    merges and the top-M cut then decide by configuration order alone, as in
+    the oracle."""
+    import dataclasses
+    base = L.chimera_grid(2, 3, 5)
+    inst = dataclasses.replace(base, j_num=np.zeros_like(base.j_num), h_num=np.zeros_like(base.h_num),
+                               name=base.name + "_free")
+    M = 40
+    ref = oracle_search(inst, 1.0, chi=4, M=M, n_sweeps=1)
+    h = Handle(inst)
+    h.set_beta(1.0)
+    h.contract_boundary(4, n_sweeps=1)
+    res = h.search(M)
+    assert np.array_equal(res["spins"], ref["spins"])
+    assert np.array_equal(res["energy_num"], ref["energy_num"])
+    assert np.allclose(res["logp"], ref["logp"], rtol=RTOL)
+
+
 @pytest.mark.parametrize("case", [(L.chimera_grid(4, 4, 0), 1.0, 16, 64, 2), (L.chimera_grid(3, 4, 7), 2.0, 4, 16, 1),
                                   (L.kings_grid(4, 5, 2), 2.0, 3, 8, 1)], ids=lambda c: c[0].name)
 def test_branch_steps_match_oracle(Handle, case):
