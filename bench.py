@@ -218,7 +218,9 @@ def roofline_of(kt, names):
             "launches": nl, "ms_per_launch": ms / nl, "flop_per_launch": fl / nl}
 
 
-CONTRACTION_KERNELS = ("site_diagram", "env_update", "theta_env", "theta_mul", "renv", "score", "tc_gemm", "gemm")
+# the sparse / batched contractions of the method (site diagram, environments, scores); the
+# dense GEMMs ("gemm", "gemm_splitk") serve both contractions and the truncation and are left out
+CONTRACTION_KERNELS = ("site_diagram", "env_update", "theta_env", "theta_mul", "renv", "score", "tc_gemm")
 
 
 def run_native(args, wl):
