@@ -64,6 +64,7 @@ int guarded(sgtn_h h, F&& f) {
   if (!h) return SGTN_ERR_ARG;
   try {
     SGTN_CUDA(cudaSetDevice(h->device));
+    pool_set_stream(h->st);
     f();
     h->err.clear();
     return SGTN_OK;
@@ -246,7 +247,9 @@ void sgtn_destroy(sgtn_h h) {
   if (!h) return;
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->st);
+  pool_set_stream(h->st);
   for (auto& m : h->psi) free_mps(m);
+  pool_trim(h->st);
   h->ws.release();
   for (void* p : h->allocs) cudaFree(p);
   delete h;

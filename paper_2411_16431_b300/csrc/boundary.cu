@@ -36,6 +36,84 @@
 #include "rowstep.h"
 
 namespace sgtn {
+
+namespace {
+struct PoolKey {
+  cudaStream_t st;
+  size_t bytes;
+  bool operator<(const PoolKey& o) const { return st != o.st ? st < o.st : bytes < o.bytes; }
+};
+std::map<PoolKey, std::vector<void*>> g_pool_free;
+std::map<void*, PoolKey> g_pool_live;
+size_t g_pool_cached = 0;
+cudaStream_t g_pool_stream = nullptr;
+constexpr size_t kPoolCap = size_t(16) << 30;   // cached bytes kept at most
+size_t pool_round(size_t b) {
+  if (b <= 256) return 256;
+  if (b <= (size_t(1) << 20)) {
+    size_t r = 256;
+    while (r < b) r <<= 1;
+    return r;
+  }
+  const size_t mb = size_t(1) << 20;
+  return (b + mb - 1) / mb * mb;
+}
+void pool_release_all() {
+  for (auto& kv : g_pool_free)
+    for (void* p : kv.second) cudaFree(p);
+  g_pool_free.clear();
+  g_pool_cached = 0;
+}
+}  // namespace
+
+void pool_set_stream(cudaStream_t st) { g_pool_stream = st; }
+
+void* pool_alloc(size_t bytes) {
+  const PoolKey key{g_pool_stream, pool_round(bytes)};
+  void* p = nullptr;
+  auto it = g_pool_free.find(key);
+  if (it != g_pool_free.end() && !it->second.empty()) {
+    p = it->second.back();
+    it->second.pop_back();
+    g_pool_cached -= key.bytes;
+  } else if (cudaMalloc(&p, key.bytes) != cudaSuccess) {
+    cudaGetLastError();
+    pool_release_all();   // cudaFree synchronises: no cached block is still in use
+    SGTN_CUDA(cudaMalloc(&p, key.bytes));
+  }
+  g_pool_live[p] = key;
+  return p;
+}
+
+void pool_free(void* p) {
+  if (!p) return;
+  auto it = g_pool_live.find(p);
+  if (it == g_pool_live.end()) {
+    cudaFree(p);
+    return;
+  }
+  const PoolKey key = it->second;
+  g_pool_live.erase(it);
+  if (g_pool_cached + key.bytes > kPoolCap) {
+    cudaFree(p);
+    return;
+  }
+  g_pool_free[key].push_back(p);
+  g_pool_cached += key.bytes;
+}
+
+void pool_trim(cudaStream_t st) {
+  for (auto it = g_pool_free.begin(); it != g_pool_free.end();) {
+    if (it->first.st == st) {
+      for (void* p : it->second) cudaFree(p);
+      g_pool_cached -= it->first.bytes * it->second.size();
+      it = g_pool_free.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
 namespace detail {
 
 // Linear algebra of the truncation (SVDs, orthonormalisations, canonical forms)
@@ -72,13 +150,9 @@ struct TagScope {
   ~TagScope() { g_tag = saved; }
 };
 
-double* dmalloc(long long n) {
-  double* p = nullptr;
-  SGTN_CUDA(cudaMalloc(&p, size_t(n > 0 ? n : 1) * sizeof(double)));
-  return p;
-}
+double* dmalloc(long long n) { return static_cast<double*>(pool_alloc(size_t(n > 0 ? n : 1) * sizeof(double))); }
 void dfree(double*& p) {
-  if (p) cudaFree(p);
+  pool_free(p);
   p = nullptr;
 }
 
@@ -1165,7 +1239,7 @@ void left_canonical(sgtn_inst* h, MPS& A) {
     SvdOut o = svd(h, A.t[c], s * l, r, 1 << 30);
     double* Q = left_factor(h, o, s * l);
     double* Rm = right_factor(h, o, r);
-    cudaFree(A.t[c]);
+    dfree(A.t[c]);
     A.t[c] = Q;
     int s2 = A.phys[c + 1], r2 = A.bond[c + 2];
     double* nn = dmalloc((long long)s2 * o.k * r2);
@@ -1190,7 +1264,7 @@ void left_canonical(sgtn_inst* h, MPS& A) {
     g.nseg = s2;
     seg_gemm(g, h->st);
     dfree(Rm);
-    cudaFree(A.t[c + 1]);
+    dfree(A.t[c + 1]);
     A.t[c + 1] = nn;
     A.bond[c + 1] = o.k;
     o.release();
@@ -1265,7 +1339,7 @@ void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& wo
     ln = A.lognorm + extra;
     normalise(h, phi[0].p, phi[0].n(), ln);
   }
-  for (double* p : X.Ahat) cudaFree(p);
+  for (double*& p : X.Ahat) dfree(p);
   X.Ahat.clear();
   // store as [phys][bond_l][bond_r]
   free_mps(out);
@@ -1320,7 +1394,7 @@ double top_overlap(sgtn_inst* h) {
   SGTN_CUDA(cudaMemcpyAsync(&v, Rc, sizeof(double), cudaMemcpyDeviceToHost, h->st));
   h->sync();
   dfree(Rc);
-  for (double* p : X.Ahat) cudaFree(p);
+  for (double*& p : X.Ahat) dfree(p);
   if (!(v > 0.0) || !std::isfinite(v)) throw SgtnError(-4, "non-positive partition function");
   return ln + std::log(v);
 }

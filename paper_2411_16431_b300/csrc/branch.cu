@@ -326,13 +326,12 @@ struct Step {
       if (!spill) throw SgtnError(-1, "scratch arena exhausted");
       spilled += b;
     }
-    void* p = nullptr;
-    SGTN_CUDA(cudaMalloc(&p, (n ? n : 1) * sizeof(T)));
+    void* p = pool_alloc((n ? n : 1) * sizeof(T));
     owned.push_back(p);
     return static_cast<T*>(p);
   }
   ~Step() {
-    for (void* p : owned) cudaFree(p);
+    for (void* p : owned) pool_free(p);
   }
   const Column& col(int cc) const { return h->cols[r * h->M.C + cc]; }
 };

@@ -126,6 +126,18 @@ void conditionals_arena(sgtn_inst* h, int step, int count, const int32_t* config
 }  // namespace sgtn
 
 namespace sgtn {
+// Device tensors of the contraction (MPS sites, SVD factors, environments) come
+// from a cache: a freed block is kept, keyed by its stream and rounded size,
+// and handed to the next request of that size on the same stream (stream
+// order makes the reuse safe), so a row step does not call cudaMalloc /
+// cudaFree -- which synchronises the device -- per tensor.  pool_set_stream
+// names the stream of the calling handle; pool_trim returns a stream's cached
+// blocks to the driver (at sgtn_destroy).
+void pool_set_stream(cudaStream_t st);
+void* pool_alloc(size_t bytes);
+void pool_free(void* p);
+void pool_trim(cudaStream_t st);
+
 // Arithmetic of the contractions issued inside one API call: FP32 (plus
 // tcgen05 tensor cores for large dense GEMMs with TF32) or FP64, from the
 // precision of the last contract_boundary, or, for the conditionals, branch

@@ -246,8 +246,7 @@ void set_beta_device(sgtn_inst* h, double beta) {
 }
 
 void free_mps(MPS& m) {
-  for (double* p : m.t)
-    if (p) cudaFree(p);
+  for (double* p : m.t) pool_free(p);
   m.t.clear();
   m.valid = false;
 }
