@@ -229,3 +229,60 @@ class Handle:
             self._ck(self.L.sgtn_mps_tensor(self.h, row, c, _p(t, _F64P)))
             ts.append(t)
         return ts, ln.value
+
+
+def logz(inst, J, h, beta, chi, n_sweeps=2, states_per_site=None, precision=FP64):
+    """log Z (Eq. 9) as a differentiable torch function of the couplings J
+    (float64 tensor, one per edge of ``inst`` in its ei/ej order), the fields h
+    (one per spin) and beta (0-d tensor).  J and h must be multiples of
+    1/inst.denom (the library works on integer numerators).  The forward pass
+    contracts the boundary MPSs; the backward pass asks the library for
+    dlogZ/dJ, dlogZ/dh and dlogZ/dbeta (environment correlators of the same
+    boundary, upper boundary recomputed on the device)."""
+    return _logz_function().apply(J, h, beta, inst, chi, n_sweeps, states_per_site, precision)
+
+
+_LOGZ_FN = None
+
+
+def _logz_function():
+    global _LOGZ_FN
+    if _LOGZ_FN is not None:
+        return _LOGZ_FN
+    import dataclasses
+
+    import torch
+
+    def numerators(x, denom, what):
+        v = x.detach().to("cpu", torch.float64).numpy() * denom
+        r = np.rint(v)
+        if np.max(np.abs(v - r), initial=0.0) > 1e-9:
+            raise ValueError(f"{what} must be multiples of 1/{denom}")
+        return r.astype(np.int32)
+
+    class _LogZ(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, J, hf, beta, inst, chi, n_sweeps, states, precision):
+            inst2 = dataclasses.replace(inst, j_num=numerators(J, inst.denom, "J"),
+                                        h_num=numerators(hf, inst.denom, "h"))
+            H = Handle(inst2, states)
+            H.set_beta(float(beta))
+            lz, _ = H.contract_boundary(chi, precision=precision, n_sweeps=n_sweeps)
+            ctx.handle = H
+            ctx.like = (J, hf, beta)
+            return torch.tensor(lz, dtype=torch.float64, device=J.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            H = ctx.handle
+            dJ, dh, db = H.logz_grad()
+            H.close()
+            ctx.handle = None
+            J, hf, beta = ctx.like
+            return (g * torch.as_tensor(dJ, dtype=J.dtype, device=J.device),
+                    g * torch.as_tensor(dh, dtype=hf.dtype, device=hf.device),
+                    g * torch.as_tensor(db, dtype=beta.dtype, device=beta.device),
+                    None, None, None, None, None)
+
+    _LOGZ_FN = _LogZ
+    return _LOGZ_FN

@@ -282,6 +282,27 @@ def test_logz_grad_exact_equals_brute_force(Handle):
     assert abs(db + H) < 1e-10 * abs(H)
 
 
+def test_logz_autograd_function(Handle):
+    """torch.autograd on sgtn.logz: gradients w.r.t. J, h and beta are the
+    library's dlogZ (brute-force correlators on an exact slice), and log Z
+    itself is the brute-force value."""
+    import torch
+    from paper_2411_16431_b300 import sgtn
+    inst, beta = L.slice_cells(L.chimera_grid(4, 4, 2), 2, 1), 1.3
+    J = torch.tensor(inst.j_num / inst.denom, dtype=torch.float64, requires_grad=True)
+    hf = torch.tensor(inst.h_num / inst.denom, dtype=torch.float64, requires_grad=True)
+    b = torch.tensor(beta, dtype=torch.float64, requires_grad=True)
+    lz = sgtn.logz(inst, J, hf, b, chi=64, n_sweeps=1)
+    lz.backward()
+    assert abs(lz.item() - brute.log_z(inst, beta)) < RTOL * abs(lz.item())
+    ss, m, H = brute.correlators(inst, beta)
+    assert np.allclose(J.grad.numpy(), -beta * ss, atol=1e-11)
+    assert np.allclose(hf.grad.numpy(), -beta * m, atol=1e-11)
+    assert abs(b.grad.item() + H) < 1e-10 * abs(H)
+    with pytest.raises(ValueError):
+        sgtn.logz(inst, J.detach() + 0.01, hf.detach(), b.detach(), chi=64)
+
+
 @pytest.mark.parametrize("svd_max", ["320", "8"])
 @pytest.mark.parametrize("case", [CASES[0], CASES[2], PEG_CASES[0], PEG_CASES[1]], ids=lambda c: c[0].name)
 def test_block_sparse_theta_matches_oracle(Handle, case, svd_max, monkeypatch):
