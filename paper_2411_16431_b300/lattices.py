@@ -324,6 +324,47 @@ def slice_cells(inst: Instance, rows: int, cols: int) -> Instance:
                     inst.name + f"_slice{rows}x{cols}")
 
 
+# The eight symmetries of the rectangular grid of clusters (the paper runs
+# every instance in all of its contraction orientations, Sec. V): cluster
+# (r, c) of an R x C grid goes to the returned cell of the transformed grid.
+TRANSFORMS = ("identity", "rot90", "rot180", "rot270", "flip_lr", "flip_ud", "transpose", "antitranspose")
+
+
+def transformed_cell(k: int, r: int, c: int, rows: int, cols: int) -> Tuple[int, int, int, int]:
+    """(r', c', rows', cols') of cluster (r, c) under grid symmetry k (see TRANSFORMS)."""
+    R, C = rows, cols
+    return [(r, c, R, C), (c, R - 1 - r, C, R), (R - 1 - r, C - 1 - c, R, C), (C - 1 - c, r, C, R),
+            (r, C - 1 - c, R, C), (R - 1 - r, c, R, C), (c, r, C, R), (C - 1 - c, R - 1 - r, C, R)][k]
+
+
+def transform(inst: Instance, k: int) -> Instance:
+    """The same spins, couplings and fields with the cluster grid mapped by symmetry k.
+
+    Only the placement of the clusters changes (spins keep their indices and
+    their order inside a cluster), so H, Z and the ground states are the same;
+    the boundary-MPS contraction and the exploration order run along
+    different directions of the lattice.
+    """
+    site = np.empty_like(inst.site_of_spin)
+    rows2 = cols2 = 0
+    for i, s in enumerate(inst.site_of_spin.tolist()):
+        r2, c2, rows2, cols2 = transformed_cell(k, s // inst.cols, s % inst.cols, inst.rows, inst.cols)
+        site[i] = r2 * cols2 + c2
+    out = Instance(inst.n_spins, inst.ei.copy(), inst.ej.copy(), inst.j_num.copy(), inst.h_num.copy(), inst.denom,
+                   site, rows2, cols2, inst.name + ("" if k == 0 else "_" + TRANSFORMS[k]), inst.planted,
+                   inst.planted_energy_num, dict(inst.meta))
+    return out
+
+
+def transform_states(inst: Instance, states_per_site, k: int):
+    """Per-cluster state lists of ``inst`` reordered for ``transform(inst, k)``."""
+    out = [None] * (inst.rows * inst.cols)
+    for s, lst in enumerate(states_per_site):
+        r2, c2, _, cols2 = transformed_cell(k, s // inst.cols, s % inst.cols, inst.rows, inst.cols)
+        out[r2 * cols2 + c2] = lst
+    return out
+
+
 def hamming_ball_states(inst: Instance, d: int, seed: int = 0, reference: Optional[np.ndarray] = None):
     """Per-cluster state lists of (at most) d states nearest to a reference configuration.
 

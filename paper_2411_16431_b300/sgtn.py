@@ -286,3 +286,26 @@ def _logz_function():
 
     _LOGZ_FN = _LogZ
     return _LOGZ_FN
+
+
+def search_transforms(inst, beta, chi, M, states_per_site=None, precision=FP64, n_sweeps=2, transforms=range(8)):
+    """Boundary contraction + search of the instance in each of the grid
+    symmetries ``transforms`` (lattices.TRANSFORMS), one handle after the
+    other: the paper runs every instance in all of its orientations and keeps
+    the best state (Sec. V).  Spins keep their indices, so the returned states
+    and energies are comparable.  Returns (index of the best, list of
+    (transform, log Z, search result))."""
+    from . import lattices as L
+    out = []
+    for k in transforms:
+        t = L.transform(inst, k)
+        st = None if states_per_site is None else L.transform_states(inst, states_per_site, k)
+        h = Handle(t, st)
+        try:
+            h.set_beta(beta)
+            lz, _ = h.contract_boundary(chi, precision=precision, n_sweeps=n_sweeps)
+            out.append((k, lz, h.search(M)))
+        finally:
+            h.close()
+    best = min(range(len(out)), key=lambda i: (int(out[i][2]["energy_num"][0]), i))
+    return best, out

@@ -282,6 +282,26 @@ def test_logz_grad_exact_equals_brute_force(Handle):
     assert abs(db + H) < 1e-10 * abs(H)
 
 
+def test_grid_symmetries_on_the_gpu(Handle):
+    """Exact log Z is the same in all eight grid orientations (brute force), and
+    the search over all of them returns a state whose energy is the best one."""
+    from paper_2411_16431_b300 import sgtn
+    inst, beta = L.kings_grid(3, 4, 5), 0.8
+    ref = brute.log_z(inst, beta)
+    for k in range(8):
+        h = Handle(L.transform(inst, k))
+        h.set_beta(beta)
+        lz, _ = h.contract_boundary(64, n_sweeps=1)
+        assert abs(lz - ref) < RTOL * abs(ref)
+        h.close()
+    best, runs = sgtn.search_transforms(inst, beta, chi=4, M=8, n_sweeps=1)
+    energies = [int(r[2]["energy_num"][0]) for r in runs]
+    assert energies[best] == min(energies)
+    assert energies[best] >= brute.ground_state(inst)[1]
+    for _, _, r in runs:
+        assert inst.energy_num(r["spins"][0]) == int(r["energy_num"][0])
+
+
 def test_logz_autograd_function(Handle):
     """torch.autograd on sgtn.logz: gradients w.r.t. J, h and beta are the
     library's dlogZ (brute-force correlators on an exact slice), and log Z

@@ -302,3 +302,21 @@ def test_truncated_gradient_close_to_finite_differences():
         fd = (vals[0] - vals[1]) / (2.0 / (7 * K))
         got = dJ[e] if kind == "J" else dh[e]
         assert abs(got - fd) < 1e-2 * max(1.0, abs(fd)), (kind, e, got, fd)
+
+
+def test_grid_symmetries_keep_log_z_and_ground_state():
+    """The eight symmetries of the cluster grid change only the direction of the
+    contraction: exact log Z and the exact-DP ground state are unchanged (king's
+    lattice: both diagonals trade places; Chimera: vertical and horizontal
+    couplings trade places)."""
+    for inst, beta in ((L.kings_grid(2, 3, 4), 0.7), (L.slice_cells(L.chimera_grid(3, 3, 6), 2, 1), 1.1)):
+        ref = brute.log_z(inst, beta)
+        e0 = brute.ground_state(inst)[1]
+        for k in range(8):
+            t = L.transform(inst, k)
+            assert t.rows * t.cols == inst.rows * inst.cols
+            assert len(set(t.site_of_spin.tolist())) == t.rows * t.cols
+            lz, _, _ = boundary_mps(PottsModel(t), beta, 256, 1)
+            assert abs(lz - ref) < 1e-12 * abs(ref)
+            res = search(t, beta, chi=256, M=10 ** 6, n_sweeps=1)
+            assert res["energy_num"][0] == e0
