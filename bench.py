@@ -57,6 +57,13 @@ WORKLOADS = {
         make=lambda seed: L.planted(L.pegasus_nice(16, seed), seed + 7, loops_per_cell=6),
         states=lambda inst, seed: L.hamming_ball_states(inst, 256, seed=seed + 1, reference=inst.planted),
         beta=2.0, chi=64, M=1024, sweeps=2, d=256, oracle_sample=dict(_PEG_SAMPLE)),
+    # single-spin sites with both diagonals (the mediating path with trivial d)
+    "kings50x50": dict(desc="King's lattice 50x50 (2500 spins, nearest and diagonal bonds), one spin per site, "
+                            "iid J,h in {+-1..+-7}/7, beta=4, chi=16, M=256",
+                       make=lambda seed: L.kings_grid(50, 50, seed), states=None, beta=4.0, chi=16, M=256,
+                       sweeps=2, d=2,
+                       oracle_sample=dict(make=lambda seed: L.kings_grid(8, 8, seed), states=lambda inst, seed: None,
+                                          chi=8, M=64, desc="King's lattice 8x8, chi=8, M=64")),
 }
 DEFAULT = "pegasus15x15"
 # precision name -> (boundary precision, search precision or -1, dtype label)
