@@ -441,10 +441,11 @@ SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   h->sync();
   if (hs < 0) throw SgtnError(-4, "Jacobi SVD did not converge");
   {
-    // per sweep and pair: three dot products and the rotation of both vectors
-    // (6 flop per element each) and of their columns of V
+    // per sweep: the squared norms (2 flop per element), and per pair the
+    // product (2 flop per element), the rotation of both vectors (6) and of
+    // their columns of V (6 per element of V)
     const double vl = std::max(m, n), np = p;
-    ktimer_add_flops("jacobi_f64", double(hs) * np * (np - 1) / 2 * (12.0 * vl + 6.0 * np));
+    ktimer_add_flops("jacobi_f64", double(hs) * (2.0 * np * vl + np * (np - 1) / 2 * (8.0 * vl + 6.0 * np)));
   }
   if (prof_on()) {
     SvdProf& e = g_prof[std::string(g_tag) + (std::max(m, n) > 128 ? "/jacobi_long" : "/jacobi")];

@@ -321,6 +321,7 @@ __global__ void __launch_bounds__(512) jacobi_cluster_kernel(double* X, int len,
   const int slots = (p + P - 1) / P;
   double* Xs = csm;                                   // slots x len
   double* Vs = V ? csm + (long long)slots * len : nullptr;   // slots x p
+  double* Ns = csm + (long long)slots * len + (V ? (long long)slots * p : 0);   // slots: squared norms
   double f = 0;
   for (int l = 0; l < slots; ++l) {
     const int j = l * P + rank;
@@ -348,8 +349,19 @@ __global__ void __launch_bounds__(512) jacobi_cluster_kernel(double* X, int len,
   const int pp = p + (p & 1), npair = pp / 2;
   int sweep = 0;
   bool done = (p < 2);
+  const double tol2 = tol * tol;
   while (!done && sweep < max_sweeps) {
     int rot = 0;
+    // exact squared norms at the start of every sweep; within the sweep they
+    // follow the rotations (a' = a - t g, b' = b + t g, t = tan of the angle)
+    for (int l = warp; l < slots; l += nwarp) {
+      if (l * P + rank >= p) continue;
+      double q = 0;
+      for (int i = lane; i < len; i += 32) q = fma(Xs[(long long)l * len + i], Xs[(long long)l * len + i], q);
+      q = warp_sum(q);
+      if (lane == 0) Ns[l] = q;
+    }
+    cl.sync();
     for (int t = 0; t < pp - 1; ++t) {
       for (int w = rank + P * warp; w < npair; w += P * nwarp) {
         int pa = w, pb = pp - 1 - w;
@@ -358,7 +370,10 @@ __global__ void __launch_bounds__(512) jacobi_cluster_kernel(double* X, int len,
         if (ca >= p || cb >= p) continue;
         double* xa = cl.map_shared_rank(Xs + (long long)(ca / P) * len, ca % P);
         double* xb = cl.map_shared_rank(Xs + (long long)(cb / P) * len, cb % P);
-        double al = 0, be = 0, ga = 0;
+        double* na = cl.map_shared_rank(Ns + ca / P, ca % P);
+        double* nb = cl.map_shared_rank(Ns + cb / P, cb % P);
+        const double al = *na, be = *nb;
+        double ga = 0;
         double ur[RV > 0 ? RV : 1], vr[RV > 0 ? RV : 1];
         if constexpr (RV > 0) {
 #pragma unroll
@@ -368,41 +383,63 @@ __global__ void __launch_bounds__(512) jacobi_cluster_kernel(double* X, int len,
             vr[q] = i < len ? xb[i] : 0.0;
           }
 #pragma unroll
-          for (int q = 0; q < RV; ++q) {
-            al = fma(ur[q], ur[q], al);
-            be = fma(vr[q], vr[q], be);
-            ga = fma(ur[q], vr[q], ga);
-          }
+          for (int q = 0; q < RV; ++q) ga = fma(ur[q], vr[q], ga);
         } else {
-          for (int i = lane; i < len; i += 32) {
-            double u = xa[i], v = xb[i];
-            al = fma(u, u, al);
-            be = fma(v, v, be);
-            ga = fma(u, v, ga);
-          }
+          for (int i = lane; i < len; i += 32) ga = fma(xa[i], xb[i], ga);
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
         ga = warp_sum(ga);
-        if (al > zero2 && be > zero2 && fabs(ga) > tol * sqrt(al * be)) {
-          double zeta = (be - al) / (2.0 * ga);
-          double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
+        if (al > zero2 && be > zero2 && ga * ga > tol2 * al * be) {
+          // angle that zeroes the pair's product: with d = b - a and
+          // r = sqrt(d^2 + 4 g^2), cos^2 = (1 + |d| / r) / 2 and
+          // sin = sign(d) g / (r cos); tan = sin / cos
+          const double d = be - al;
+          const double rinv = rsqrt(fma(d, d, 4.0 * ga * ga));
+          const double c2 = fma(0.5 * fabs(d), rinv, 0.5);
+          const double rc = rsqrt(c2);
+          const double c = c2 * rc, s = (d >= 0 ? 1.0 : -1.0) * ga * rinv * rc;
+          const double tg = s * rc;
+          double an = al - tg * ga, bn = be + tg * ga;
           if constexpr (RV > 0) {
 #pragma unroll
             for (int q = 0; q < RV; ++q) {
               const int i = lane + 32 * q;
+              const double u = ur[q], v = vr[q];
+              ur[q] = c * u - s * v;
+              vr[q] = s * u + c * v;
               if (i < len) {
-                xa[i] = c * ur[q] - s * vr[q];
-                xb[i] = s * ur[q] + c * vr[q];
+                xa[i] = ur[q];
+                xb[i] = vr[q];
               }
             }
-          } else {
-            for (int i = lane; i < len; i += 32) {
-              double u = xa[i], v = xb[i];
-              xa[i] = c * u - s * v;
-              xb[i] = s * u + c * v;
+            if (an < 1e-4 * al || bn < 1e-4 * be) {
+              // cancellation in the update: recompute both norms
+              double qa = 0, qb = 0;
+#pragma unroll
+              for (int q = 0; q < RV; ++q) {
+                qa = fma(ur[q], ur[q], qa);
+                qb = fma(vr[q], vr[q], qb);
+              }
+              an = warp_sum(qa);
+              bn = warp_sum(qb);
             }
+          } else {
+            double qa = 0, qb = 0;
+            for (int i = lane; i < len; i += 32) {
+              const double u = xa[i], v = xb[i];
+              const double u2 = c * u - s * v, v2 = s * u + c * v;
+              xa[i] = u2;
+              xb[i] = v2;
+              qa = fma(u2, u2, qa);
+              qb = fma(v2, v2, qb);
+            }
+            if (an < 1e-4 * al || bn < 1e-4 * be) {
+              an = warp_sum(qa);
+              bn = warp_sum(qb);
+            }
+          }
+          if (lane == 0) {
+            *na = an;
+            *nb = bn;
           }
           if (Vs) {
             double* va = cl.map_shared_rank(Vs + (long long)(ca / P) * p, ca % P);
@@ -1136,7 +1173,7 @@ void jacobi(double* X, int len, int p, long long si, long long sj, double* V, in
   const int npair = (p + 1) / 2;
   int P = std::max(1, std::min(max_cluster, npair));
   const int slots = (p + P - 1) / P;
-  const size_t csmem = (size_t(slots) * len + (V ? size_t(slots) * p : 0)) * sizeof(double);
+  const size_t csmem = (size_t(slots) * len + (V ? size_t(slots) * p : 0) + size_t(slots)) * sizeof(double);
   const int nw = std::min(16, (npair + P - 1) / P);
   {
     KTimer t("jacobi_f64", st);
