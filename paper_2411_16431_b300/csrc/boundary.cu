@@ -251,17 +251,17 @@ bool svd_tall_cqr3(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut&
   SGTN_CUDA(cudaMemsetAsync(status, 0, 3 * sizeof(int), st));
   // one pass: G = cur^T cur, R = chol(G + shift I), out = cur R^{-1}, Racc = R Racc
   auto pass = [&](const double* cur, double* out, double shift, int* stat, bool first, const double* Gin) {
-    if (!Gin) gemm(cur, true, n, cur, false, n, G, n, n, n, m, 1.0, 0, st);
+    if (!Gin) gram_upper(cur, n, G, n, m, st);
     cholesky_inv(Gin ? Gin : G, n, shift, R, Ri, stat, st);
-    gemm(cur, false, n, Ri, false, n, out, n, m, n, n, 1.0, 0, st);
+    gemm(cur, false, n, Ri, false, n, out, n, m, n, n, 1.0, 0, st, 2);
     if (first) {
       copy(Racc, R, (long long)n * n, st);
     } else {
-      gemm(R, false, n, Racc, false, n, Rtmp, n, n, n, n, 1.0, 0, st);
+      gemm(R, false, n, Racc, false, n, Rtmp, n, n, n, n, 1.0, 0, st, 2);
       copy(Racc, Rtmp, (long long)n * n, st);
     }
   };
-  gemm(M, true, n, M, false, n, G0, n, n, n, m, 1.0, 0, st);
+  gram_upper(M, n, G0, n, m, st);
   // CholeskyQR2 when the unshifted factor lost at most 10 of the 16 digits of
   // any column (cond(M) below about 1e5): its orthogonality after two passes
   // is at rounding level
@@ -279,7 +279,7 @@ bool svd_tall_cqr3(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut&
   if (!(tr > 0) || !std::isfinite(tr)) return false;
   const double* cur = nullptr;
   if (hs0 == 0 && mr > 1e-10) {
-    gemm(M, false, n, Ri, false, n, Qa, n, m, n, n, 1.0, 0, st);                 // Q1 = M R1^{-1}
+    gemm(M, false, n, Ri, false, n, Qa, n, m, n, n, 1.0, 0, st, 2);              // Q1 = M R1^{-1}
     copy(Racc, R, (long long)n * n, st);
     pass(Qa, Qb, 0.0, status + 1, false, nullptr);
     cur = Qb;
@@ -373,7 +373,7 @@ bool svd_tall_rrcqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut
     if (r <= 0) break;
     // Q1 = cur[:, perm] R^{-1}
     gather_vecs(cur, m, n, 1, perm, ones, r, Mp, r, 1, st);
-    gemm(Mp, false, r, Ri, false, n, Q1, r, m, r, r, 1.0, 0, st);
+    gemm(Mp, false, r, Ri, false, n, Q1, r, m, r, r, 1.0, 0, st, 2);
     if (rt > 0) {
       // Q1 -= Qt (Qt^T Q1), twice (classical Gram-Schmidt with reorthogonalisation)
       for (int pass = 0; pass < 2; ++pass) {
@@ -538,7 +538,7 @@ bool cqr_orth(sgtn_inst* h, const double* M, int len, int k, double* Q, bool fir
   };
   const double* cur = M;
   for (int pass = 0; pass < 4; ++pass) {
-    gemm(cur, true, k, cur, false, k, G, k, k, k, len, 1.0, 0, st);   // G = cur^T cur
+    gram_upper(cur, k, G, k, len, st);                                 // G = cur^T cur (upper)
     SGTN_CUDA(cudaMemcpyAsync(hG.data(), G, hG.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     bool last = pass == 3;
     if (pass == 0) {
@@ -555,12 +555,12 @@ bool cqr_orth(sgtn_inst* h, const double* M, int len, int k, double* Q, bool fir
       if (!chol(0.0, false)) return false;
       double dev = 0;
       for (int i = 0; i < k; ++i)
-        for (int j = 0; j < k; ++j) dev = std::max(dev, std::fabs(hG[size_t(i) * k + j] - (i == j ? 1.0 : 0.0)));
+        for (int j = i; j < k; ++j) dev = std::max(dev, std::fabs(hG[size_t(i) * k + j] - (i == j ? 1.0 : 0.0)));
       if (!std::isfinite(dev)) return false;
       last = last || dev < 0.1;
     }
     double* out = last ? Q : (cur == T ? T2 : T);
-    gemm(cur, false, k, Ri, false, k, out, k, len, k, k, 1.0, 0, st);  // out = cur R^{-1}
+    gemm(cur, false, k, Ri, false, k, out, k, len, k, k, 1.0, 0, st, 2);   // out = cur R^{-1}
     cur = out;
     if (last) break;
   }

@@ -70,6 +70,11 @@ struct SegGemm {
   int accumulate = 0;
   const char* name = nullptr;   // timing label (role of the call); "_f32" / "_f64" is appended
   int tile_m = 0, tile_n = 0;   // CTA tile (16/32/64 x 32/64); 0: from the block shape
+  // uniform mode, structure of one product: tri & 1 -- only the upper triangle
+  // of the (square) output is needed (tiles wholly below the diagonal are
+  // skipped and left unwritten); tri & 2 -- Y is upper triangular (the
+  // reduction of output column j stops at k = j)
+  int tri = 0;
   // optional balanced split of long segments (table mode): the virtual
   // segments are multiplied into a scratch block each and summed per segment
   // in a fixed order (deterministic)
@@ -80,7 +85,11 @@ void seg_gemm(const SegGemm& a, cudaStream_t st);
 
 // Plain row-major GEMM helper on top of seg_gemm: O[m x n] = alpha * op(X) op(Y)
 void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, long long ldy, double* O,
-          long long ldo, int m, int n, int k, double alpha, int accumulate, cudaStream_t st);
+          long long ldo, int m, int n, int k, double alpha, int accumulate, cudaStream_t st, int tri = 0);
+// G (n x n) = X^T X for X (m x n, leading dimension ldx): upper triangle only
+inline void gram_upper(const double* X, long long ldx, double* G, int n, int m, cudaStream_t st) {
+  gemm(X, true, ldx, X, false, ldx, G, n, n, n, m, 1.0, 0, st, 1);
+}
 
 // One-sided Jacobi (Hestenes) on the p vectors of a matrix: vector j has
 // element i at X[i*si + j*sj], i < len.  On return the vectors are mutually

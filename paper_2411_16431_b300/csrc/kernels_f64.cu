@@ -60,6 +60,9 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
     t1 = seg + 1;
     ooff = (long long)seg * a.ors;
   }
+  if ((a.tri & 1) && i0 >= j0 + BN) return;   // wholly below the diagonal: not needed
+  int k_base = a.splitk ? seg * a.splitk : 0;
+  if (a.tri & 2) qlen = max(0, min(qlen, j0 + BN - k_base));   // Y[k][j] = 0 for k > j
   const int nk = (qlen + TK - 1) / TK;
   const int nsteps = (t1 - t0) * nk;
   const bool x_kfast = (a.xs_k == 1), y_jfast = (a.ys_j == 1);
@@ -1075,8 +1078,8 @@ bool g_use_tc = false;
 bool g_no_alloc = false;
 
 void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, long long ldy, double* O, long long ldo,
-          int m, int n, int k, double alpha, int accumulate, cudaStream_t st) {
-  if (g_use_tc && g_compute_f32 && m >= 128 && n >= 64 && k >= 32 &&
+          int m, int n, int k, double alpha, int accumulate, cudaStream_t st, int tri) {
+  if (!tri && g_use_tc && g_compute_f32 && m >= 128 && n >= 64 && k >= 32 &&
       tc_gemm(X, tx, ldx, Y, ty, ldy, O, ldo, m, n, k, alpha, accumulate, st))
     return;
   SegGemm a;
@@ -1096,6 +1099,7 @@ void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, lon
   a.alpha = alpha;
   a.accumulate = accumulate;
   a.name = "gemm";
+  a.tri = tri;
   // small outputs (Gram matrices, blocks of a Cholesky factor) take 16 x 32
   // tiles, so that more CTAs share the work and less of each tile is padding
   const bool small = (long long)m * n <= 160 * 160;
@@ -1262,7 +1266,7 @@ void chol_rec(double* W, int n, int ld, double shift, double* R, const double* G
   gemm(W, true, ld, W12, false, ld, R12, ld, n1, n2, n1, 1.0, 0, st);        // R12 = R11^{-T} G12
   gemm(R12, true, ld, R12, false, ld, W22, ld, n2, n2, n1, -1.0, 1, st);     // W22 = G22 - R12^T R12
   chol_rec(W22, n2, ld, shift, R22, Gd + (long long)n1 * (ld + 1), status, off + n1, minratio, T, st, f32);
-  gemm(R12, false, ld, W22, false, ld, T, n2, n1, n2, n2, 1.0, 0, st);        // T = R12 R22^{-1}
+  gemm(R12, false, ld, W22, false, ld, T, n2, n1, n2, n2, 1.0, 0, st, 2);     // T = R12 R22^{-1}
   gemm(W, false, ld, T, false, n2, W12, ld, n1, n2, n1, -1.0, 0, st);         // (R^{-1})_12 = -R11^{-1} T
   const long long nz = (long long)n2 * n1;
   zero_block_kernel<<<blocks_for(nz), 256, 0, st>>>(W21, n2, n1, ld);
