@@ -303,7 +303,9 @@ def run_native(args, wl):
     logz_err = None
     if prec != 0:
         lz64 = h.contract_boundary(wl["chi"], precision=0, n_sweeps=wl["sweeps"])[0]
-        logz_err = {"logz": logz, "logz_fp64": lz64, "rel_err": abs(logz - lz64) / abs(lz64)}
+        ok = np.isfinite(logz) and np.isfinite(lz64)
+        logz_err = {"logz": logz if np.isfinite(logz) else None, "logz_fp64": lz64 if np.isfinite(lz64) else None,
+                    "rel_err": abs(logz - lz64) / abs(lz64) if ok else None}
     # end to end through the public API from host buffers: build (H2D) .. results (D2H)
     e2e_times = []
     h2d = inst.ei.nbytes + inst.ej.nbytes + inst.j_num.nbytes + inst.h_num.nbytes + inst.site_of_spin.nbytes

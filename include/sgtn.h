@@ -86,7 +86,10 @@ int sgtn_set_beta(sgtn_h h, double beta);
  * more sweeps.  All boundary MPSs stay resident on the device for the
  * branch step.  precision: SGTN_FP64 (everything in double) or a mixed mode
  * (contractions on tensor cores, truncation and log-norms in double).
- *   out_logz            log Z of Eq. (9) (may be NULL)
+ *   out_logz            log Z of Eq. (9) (may be NULL); NaN when the
+ *                       approximate psi_0 has a non-positive overlap with the
+ *                       top row (log Z undefined; the call still succeeds and
+ *                       the boundary MPSs serve the branch step)
  *   out_worst_trunc_sv  largest, over all cuts, of the smallest retained
  *                       singular value relative to the largest (may be NULL) */
 int sgtn_contract_boundary(sgtn_h h, int32_t chi, int32_t precision, int32_t n_sweeps,

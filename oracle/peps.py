@@ -353,7 +353,10 @@ def top_row_log_overlap(mpo0: RowMPO, A, lognorm):
         E = np.einsum("ai,abs,sij->bj", E, W[:, :, 0, :], A[c], optimize=True)
     val = float(E.reshape(()))
     if not val > 0:
-        raise FloatingPointError("non-positive partition function")
+        # an approximate psi_0 (negative entries, Sec. V) can give a
+        # non-positive overlap: log Z is undefined, the boundary MPSs remain
+        # usable for the branch and bound (its scores are clamped at 0)
+        return float("nan")
     return lognorm + np.log(val)
 
 

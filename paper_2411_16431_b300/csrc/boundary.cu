@@ -1396,7 +1396,11 @@ double top_overlap(sgtn_inst* h) {
   h->sync();
   dfree(Rc);
   for (double*& p : X.Ahat) dfree(p);
-  if (!(v > 0.0) || !std::isfinite(v)) throw SgtnError(-4, "non-positive partition function");
+  if (!std::isfinite(v)) throw SgtnError(-4, "non-finite top-row overlap");
+  // an approximate psi_0 (negative entries, Sec. V) can give a non-positive
+  // overlap: log Z is then undefined (NaN); the boundary MPSs stay usable for
+  // the branch step, whose scores are clamped at 0
+  if (!(v > 0.0)) return std::nan("");
   return ln + std::log(v);
 }
 
