@@ -1,7 +1,9 @@
 """Benchmark of the hot path: boundary-MPS contraction + branch-and-bound search.
 
 One step = set_beta + contract_boundary + search on one instance resident in
-HBM (every kernel of the path).  ``value`` = conditional marginals evaluated
+HBM (every kernel of the path); the "_x8" workloads run the instance in all
+eight grid symmetries at once (one stream and host thread each, through
+sgtn_batch_search), as the paper runs every instance from every corner.  ``value`` = conditional marginals evaluated
 per second over the whole job (all ranks); the boundary contraction's
 algorithmic TFLOP/s is reported beside it.  Multi-GPU runs are independent
 replicas (one instance per rank, different seeds): the method has no data
@@ -59,12 +61,19 @@ WORKLOADS = {
         beta=2.0, chi=64, M=1024, sweeps=2, d=256, oracle_sample=dict(_PEG_SAMPLE)),
     # single-spin sites with both diagonals (the mediating path with trivial d)
     "kings50x50": dict(desc="King's lattice 50x50 (2500 spins, nearest and diagonal bonds), one spin per site, "
-                            "iid J,h in {+-1..+-7}/7, beta=4, chi=16, M=256",
-                       make=lambda seed: L.kings_grid(50, 50, seed), states=None, beta=4.0, chi=16, M=256,
-                       sweeps=2, d=2,
-                       oracle_sample=dict(make=lambda seed: L.kings_grid(8, 8, seed), states=lambda inst, seed: None,
-                                          chi=8, M=64, desc="King's lattice 8x8, chi=8, M=64")),
+                            "class I couplings (J uniform in [-1, 1] on a 1/1000 grid, h = 0), beta=4, chi=16, M=256",
+                       make=lambda seed: L.kings_grid(50, 50, seed, couplings="uniform"), states=None, beta=4.0,
+                       chi=16, M=256, sweeps=2, d=2,
+                       # beta = 4 is past the beta < 3 where the paper finds FP32 contractions adequate (Sec. VI)
+                       precision="fp64",
+                       oracle_sample=dict(make=lambda seed: L.kings_grid(8, 8, seed, couplings="uniform"),
+                                          states=lambda inst, seed: None, chi=8, M=64,
+                                          desc="King's lattice 8x8 (class I), chi=8, M=64")),
 }
+# the same instances in all eight grid symmetries per step (Sec. IV: every instance is run from every corner)
+for _name in ("pegasus15x15", "kings50x50"):
+    WORKLOADS[_name + "_x8"] = dict(WORKLOADS[_name], transforms=8,
+                                    desc=WORKLOADS[_name]["desc"] + "; all 8 grid symmetries per step, concurrently")
 DEFAULT = "pegasus15x15"
 # precision name -> (boundary precision, search precision or -1, dtype label)
 PRECISIONS = {"fp64": (0, -1, "f64"),
@@ -163,6 +172,7 @@ def cpu_oracle(wl, seed, budget_s=15.0, max_runs=5):
 
 def bench_config(args, wl, ws=1):
     return {"workload": args.workload, "description": wl["desc"], "instances_per_rank": 1,
+            "grid_symmetries_per_step": wl.get("transforms", 1),
             "beta": wl["beta"], "chi": wl["chi"], "M": wl["M"], "states_per_cell": wl.get("d"),
             "n_sweeps": wl["sweeps"], "precision": args.precision, "parallelism": f"replicas{ws}",
             "l2": "flushed between timed steps (256 MB write)"}
@@ -242,15 +252,44 @@ def run_native(args, wl):
     stream = torch.cuda.current_stream()
     inst = wl["make"](args.seed + rank)
     states = wl["states"](inst, args.seed + rank) if wl["states"] else None
-    h = sgtn.Handle(inst, states, stream=stream.cuda_stream)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > 126 MB L2
     prec, sprec, dtype_name = PRECISIONS[args.precision]
-    h.set_search_precision(sprec)
+    n_tr = wl.get("transforms", 1)
+    # the instance in each of its first n_tr grid symmetries, every one on its own stream
+    t_streams = [stream] if n_tr == 1 else [torch.cuda.Stream() for _ in range(n_tr)]
+
+    def make_handles():
+        hs = []
+        for k in range(n_tr):
+            ti = inst if k == 0 else L.transform(inst, k)
+            tst = states if (k == 0 or states is None) else L.transform_states(inst, states, k)
+            hk = sgtn.Handle(ti, tst, stream=t_streams[k].cuda_stream)
+            hk.set_search_precision(sprec)
+            hs.append(hk)
+        return hs
+
+    handles = make_handles()
+    h = handles[0]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > 126 MB L2
+
+    failed_transforms = [0]   # grid symmetries whose search stopped (no candidate with a positive score)
+
+    def run_all(hs):
+        """One step on every handle: (log Z of the first, best search result over all)."""
+        if len(hs) == 1:
+            hs[0].set_beta(wl["beta"])
+            lz = hs[0].contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])[0]
+            return lz, hs[0].search(wl["M"])
+        out = sgtn.batch_search(hs, wl["beta"], wl["chi"], wl["M"], precision=prec, n_sweeps=wl["sweeps"],
+                                raise_on_error=False)
+        ok = [i for i in range(len(out)) if out[i][1] is not None]
+        failed_transforms[0] = len(out) - len(ok)
+        if not ok:
+            raise RuntimeError("every grid symmetry failed: " + hs[0].L.sgtn_last_error(hs[0].h).decode())
+        best = min(ok, key=lambda i: (int(out[i][1]["energy_num"][0]), i))
+        return out[0][0], out[best][1]
 
     def step():
-        h.set_beta(wl["beta"])
-        h.contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])
-        return h.search(wl["M"])
+        return run_all(handles)[1]
 
     for _ in range(args.warmup):
         res = step()
@@ -267,11 +306,14 @@ def run_native(args, wl):
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        h.set_beta(wl["beta"])
-        fa = sgtn.stats()[1]
-        logz = h.contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])[0]
-        bflops += sgtn.stats()[1] - fa
-        res = h.search(wl["M"])
+        if n_tr == 1:
+            h.set_beta(wl["beta"])
+            fa = sgtn.stats()[1]
+            logz = h.contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])[0]
+            bflops += sgtn.stats()[1] - fa
+            res = h.search(wl["M"])
+        else:
+            logz, res = run_all(handles)   # every stream has finished when the call returns
         b.record(stream)
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
@@ -295,10 +337,13 @@ def run_native(args, wl):
     h.set_beta(wl["beta"])
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
+    fa = sgtn.stats()[1]
     h.contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])
     b.record(stream)
     torch.cuda.synchronize()
     bound_ms = a.elapsed_time(b)
+    if n_tr > 1:
+        bflops = (sgtn.stats()[1] - fa) * args.steps   # one instance's boundary, timed alone
     # stated error of a mixed-precision boundary: log Z against the FP64 boundary (untimed)
     logz_err = None
     if prec != 0:
@@ -311,19 +356,18 @@ def run_native(args, wl):
     h2d = inst.ei.nbytes + inst.ej.nbytes + inst.j_num.nbytes + inst.h_num.nbytes + inst.site_of_spin.nbytes
     if states is not None:
         h2d += sum(np.asarray(x, np.int64).nbytes for x in states) + 8 * (len(states) + 1)
+    h2d *= n_tr
     d2h = 0
     for _ in range(max(1, min(args.steps, 2))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h2 = sgtn.Handle(inst, states, stream=stream.cuda_stream)
-        h2.set_search_precision(sprec)
-        h2.set_beta(wl["beta"])
-        h2.contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])
-        r2 = h2.search(wl["M"])
+        hs2 = make_handles()
+        _, r2 = run_all(hs2)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
-        d2h = r2["spins"].nbytes + r2["energy_num"].nbytes + r2["logp"].nbytes + 8
-        h2.close()
+        d2h = n_tr * (r2["spins"].nbytes + r2["energy_num"].nbytes + r2["logp"].nbytes + 16)
+        for h2 in hs2:
+            h2.close()
     e2e_val = (evals / args.steps) / statistics.median(e2e_times) * ws
     if rank != 0:
         if ws > 1:
@@ -342,7 +386,8 @@ def run_native(args, wl):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype_name,
             "data": "synthetic",
-            "config": dict(bench_config(args, wl, ws), unconverged_truncations=unconverged),
+            "config": dict(bench_config(args, wl, ws), unconverged_truncations=unconverged,
+                           failed_grid_symmetries=failed_transforms[0] if n_tr > 1 else None),
             "boundary_tflops": (bflops / args.steps) / (bound_ms * 1e-3) / 1e12,
             "boundary_ms": bound_ms,
             "logz_check": logz_err,
@@ -369,10 +414,13 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--precision", choices=sorted(PRECISIONS), default=DEFAULT_PRECISION)
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default=None,
+                    help=f"default: the workload's own, else {DEFAULT_PRECISION}")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
+    if args.precision is None:
+        args.precision = wl.get("precision", DEFAULT_PRECISION)
     if args.impl == "reference":
         run_reference(args, wl)
     else:

@@ -7,7 +7,10 @@
  * sgtn_last_error() returns a text description.  Calls out of order (a
  * search before set_beta, ...) return SGTN_ERR_STATE.  A handle is bound to
  * the CUDA device that was current at sgtn_build_instance and to the stream
- * given there; handles are not thread-safe.
+ * given there.  One handle must not be used by two threads at once; distinct
+ * handles on distinct streams may be driven by concurrent host threads (the
+ * library's mode flags are per thread, its device scratch per stream and its
+ * allocator cache is locked) -- sgtn_batch_search does exactly that.
  *
  * Conventions shared by every entry point
  *  - H(s) = sum_{<ij>} J_ij s_i s_j + sum_i h_i s_i        (Sec. II, Eq. 1)
@@ -123,6 +126,25 @@ int sgtn_branch_step(sgtn_h h, int32_t step, int32_t M, int32_t in_count, const 
 int sgtn_search(sgtn_h h, int32_t M, int32_t n_out, int8_t* out_spins, int64_t* out_energy_num,
                 double* out_logp, double* out_pd, int32_t* out_count);
 
+/* Many independent searches at once (instances of different sizes, or the
+ * eight grid symmetries of one instance, Sec. IV): for every handle i,
+ * set_beta(beta), contract_boundary(chi, precision, n_sweeps) and
+ * search(M, n_out), exactly as the three calls would do one after another.
+ * Handles that share a CUDA stream run in order on one host thread; handles
+ * on different streams run concurrently on up to n_threads host threads
+ * (0: one per stream), so their kernels overlap on the device.  Each handle
+ * must appear once.
+ *   out_spins[i], out_energy_num[i], out_logp[i]: host buffers of handle i as
+ *     in sgtn_search (n_out x n_spins_i, n_out, n_out)
+ *   out_logz[i]  log Z of handle i (NaN if undefined or if it failed first)
+ *   out_pd[i], out_count[i]  as in sgtn_search
+ *   status[i]    that handle's return code (its sgtn_last_error has the text)
+ * Returns SGTN_OK if every handle succeeded, else the first failing handle's
+ * code; SGTN_ERR_ARG for null arrays or a repeated handle (nothing runs). */
+int sgtn_batch_search(sgtn_h* hs, int32_t n, double beta, int32_t chi, int32_t precision, int32_t n_sweeps,
+                      int32_t M, int32_t n_out, int8_t** out_spins, int64_t** out_energy_num, double** out_logp,
+                      double* out_logz, double* out_pd, int32_t* out_count, int32_t n_threads, int32_t* status);
+
 /* Gradient of log Z (Eq. 9): dJ[k] = d log Z / dJ_k = -beta <s_i s_j> for edge
  * k, dh[i] = -beta <s_i>, *dbeta = -<H>, evaluated as environment
  * correlators: row r is averaged in the sandwich <E_r| T_r |psi_r> of the
@@ -187,7 +209,7 @@ int sgtn_conditionals_noalloc(sgtn_h h, int32_t step, int32_t count, const int32
  * floating-point operations of its contractions (2 m n k per gathered
  * matrix product, no padding; SVD work excluded) and number of conditional
  * marginals evaluated (one per branch x cluster state).  Any pointer may be
- * NULL.  Not synchronised: read it from the thread that issues the work. */
+ * NULL.  The counters are atomic and summed over all threads. */
 void sgtn_stats(int64_t* launches, double* flops, int64_t* evals);
 
 /* Optional per-kernel timing (the paper has no counterpart): when enabled,

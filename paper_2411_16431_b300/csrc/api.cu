@@ -1,7 +1,14 @@
 // C ABI of the sgtn library: argument checks, error capture, dispatch.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
 
 #include "../../include/sgtn.h"
 #include "handle.h"
@@ -59,6 +66,10 @@ void energies(sgtn_inst* h, int n, const int8_t* spins, int64_t* out) {
 using namespace sgtn;
 
 namespace {
+// live handles per stream: a stream's scratch is released with its last handle
+std::mutex g_streams_mu;
+std::map<cudaStream_t, int> g_stream_users;
+
 template <class F>
 int guarded(sgtn_h h, F&& f) {
   if (!h) return SGTN_ERR_ARG;
@@ -89,12 +100,16 @@ int sgtn_build_instance(int32_t n_spins, int64_t n_edges, const int32_t* ei, con
   sgtn_inst* h = new sgtn_inst();
   cudaGetDevice(&h->device);
   h->st = static_cast<cudaStream_t>(stream);
+  {
+    std::lock_guard<std::mutex> lk(g_streams_mu);
+    ++g_stream_users[h->st];
+  }
   if (const char* e = std::getenv("SGTN_DENSE_SVD_MAX")) h->dense_svd_max = std::max(1, std::atoi(e));
   if (const char* e = std::getenv("SGTN_BS_MIN_ENTRIES")) h->bs_min_entries = std::max(0ll, std::atoll(e));
   std::string e = h->M.build(n_spins, n_edges, ei, ej, j_num, h_num, denom, site_of_spin, rows, cols, state_offsets,
                              states);
   if (!e.empty()) {
-    delete h;
+    sgtn_destroy(h);
     return SGTN_ERR_ARG;
   }
   int rc = guarded(h, [&] { setup_device(h); });
@@ -247,12 +262,83 @@ void sgtn_destroy(sgtn_h h) {
   if (!h) return;
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->st);
+  if (std::getenv("SGTN_TRACE_MEM")) {
+    std::vector<std::pair<size_t, std::string>> v;
+    for (auto& kv : h->ws.bufs) v.push_back({kv.second.second, kv.first});
+    std::sort(v.rbegin(), v.rend());
+    fprintf(stderr, "[sgtn] workspace %.1f MB in %zu buffers:", h->ws.total() / 1048576.0, v.size());
+    for (size_t i = 0; i < v.size() && i < 12; ++i) fprintf(stderr, " %s %.1f", v[i].second.c_str(), v[i].first / 1048576.0);
+    fprintf(stderr, "\n");
+  }
   pool_set_stream(h->st);
   for (auto& m : h->psi) free_mps(m);
   pool_trim(h->st);
   h->ws.release();
   for (void* p : h->allocs) cudaFree(p);
+  bool last = false;
+  {
+    std::lock_guard<std::mutex> lk(g_streams_mu);
+    auto it = g_stream_users.find(h->st);
+    if (it != g_stream_users.end() && --it->second <= 0) {
+      g_stream_users.erase(it);
+      last = true;
+    }
+  }
+  if (last) stream_scratch_release(h->st);
   delete h;
+}
+
+int sgtn_batch_search(sgtn_h* hs, int32_t n, double beta, int32_t chi, int32_t precision, int32_t n_sweeps,
+                      int32_t M, int32_t n_out, int8_t** out_spins, int64_t** out_energy_num, double** out_logp,
+                      double* out_logz, double* out_pd, int32_t* out_count, int32_t n_threads, int32_t* status) {
+  if (n < 0 || n_threads < 0) return SGTN_ERR_ARG;
+  if (n == 0) return SGTN_OK;
+  if (!hs || !status || !out_spins || !out_energy_num || !out_logp || !out_logz || !out_pd || !out_count)
+    return SGTN_ERR_ARG;
+  // handles that share a stream form one group, run in order by one thread
+  std::vector<std::vector<int>> groups;
+  std::map<cudaStream_t, int> gid;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return SGTN_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return SGTN_ERR_ARG;   // one handle twice would race with itself
+    auto it = gid.find(hs[i]->st);
+    if (it == gid.end()) {
+      gid[hs[i]->st] = int(groups.size());
+      groups.push_back({i});
+    } else {
+      groups[it->second].push_back(i);
+    }
+  }
+  auto run_one = [&](int i) {
+    sgtn_h h = hs[i];
+    double lz = std::nan("");
+    int rc = sgtn_set_beta(h, beta);
+    if (rc == SGTN_OK) rc = sgtn_contract_boundary(h, chi, precision, n_sweeps, &lz, nullptr);
+    out_logz[i] = lz;
+    out_count[i] = 0;
+    if (rc == SGTN_OK)
+      rc = sgtn_search(h, M, n_out, out_spins[i], out_energy_num[i], out_logp[i], &out_pd[i], &out_count[i]);
+    status[i] = rc;
+  };
+  const int ng = int(groups.size());
+  const int nt = std::max(1, n_threads > 0 ? std::min(int(n_threads), ng) : ng);
+  std::atomic<int> next{0};
+  auto worker = [&] {
+    for (int g; (g = next.fetch_add(1)) < ng;)
+      for (int i : groups[g]) run_one(i);
+  };
+  std::vector<std::thread> pool;
+  try {
+    for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  } catch (const std::exception&) {
+    // no more threads: the ones started and this one take the remaining groups
+  }
+  worker();
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < n; ++i)
+    if (status[i] != SGTN_OK) return status[i];
+  return SGTN_OK;
 }
 
 }  // extern "C"

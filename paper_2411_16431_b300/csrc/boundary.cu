@@ -28,6 +28,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 
@@ -43,10 +44,13 @@ struct PoolKey {
   size_t bytes;
   bool operator<(const PoolKey& o) const { return st != o.st ? st < o.st : bytes < o.bytes; }
 };
+// One cache for all streams, guarded by g_pool_mu; the stream a block is
+// handed out for belongs to the calling thread.
+std::recursive_mutex g_pool_mu;
 std::map<PoolKey, std::vector<void*>> g_pool_free;
 std::map<void*, PoolKey> g_pool_live;
 size_t g_pool_cached = 0;
-cudaStream_t g_pool_stream = nullptr;
+thread_local cudaStream_t g_pool_stream = nullptr;
 constexpr size_t kPoolCap = size_t(16) << 30;   // cached bytes kept at most
 size_t pool_round(size_t b) {
   if (b <= 256) return 256;
@@ -69,6 +73,7 @@ void pool_release_all() {
 void pool_set_stream(cudaStream_t st) { g_pool_stream = st; }
 
 void* pool_alloc(size_t bytes) {
+  std::lock_guard<std::recursive_mutex> lk(g_pool_mu);
   const PoolKey key{g_pool_stream, pool_round(bytes)};
   void* p = nullptr;
   auto it = g_pool_free.find(key);
@@ -87,6 +92,7 @@ void* pool_alloc(size_t bytes) {
 
 void pool_free(void* p) {
   if (!p) return;
+  std::lock_guard<std::recursive_mutex> lk(g_pool_mu);
   auto it = g_pool_live.find(p);
   if (it == g_pool_live.end()) {
     cudaFree(p);
@@ -103,6 +109,7 @@ void pool_free(void* p) {
 }
 
 void pool_trim(cudaStream_t st) {
+  std::lock_guard<std::recursive_mutex> lk(g_pool_mu);
   for (auto it = g_pool_free.begin(); it != g_pool_free.end();) {
     if (it->first.st == st) {
       for (void* p : it->second) cudaFree(p);
@@ -138,8 +145,14 @@ struct SvdProf {
   long long calls = 0, iters = 0;
   int max_m = 0, max_n = 0;
 };
+// (profiling is meant for one handle at a time; the map is still guarded)
 static std::map<std::string, SvdProf> g_prof;
-static const char* g_tag = "other";
+static std::mutex g_prof_mu;
+static thread_local const char* g_tag = "other";
+static SvdProf& prof_entry(const std::string& key) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  return g_prof[key];
+}
 static bool prof_on() {
   static const bool on = std::getenv("SGTN_PROFILE") != nullptr;
   return on;
@@ -180,7 +193,7 @@ auto profiled(sgtn_inst* h, const char* sub, int m, int n, F&& f) -> decltype(f(
   auto t0 = std::chrono::steady_clock::now();
   auto o = f();
   h->sync();
-  SvdProf& e = g_prof[std::string(g_tag) + sub];
+  SvdProf& e = prof_entry(std::string(g_tag) + sub);
   e.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   e.calls += 1;
   e.max_m = std::max(e.max_m, m);
@@ -198,15 +211,22 @@ bool svd_tall_cqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& 
 bool svd_tall_cqr3(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o);
 bool svd_tall_rrcqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o);
 
-// Exact truncated SVD: for a tall-skinny (or short-fat) matrix with a short
-// side of at most 320, CholeskyQR2 or shifted CholeskyQR3 then a one-sided Jacobi SVD of the
-// small triangular factor; otherwise (or if a Cholesky pivot fails, i.e. the
-// vectors are exactly dependent) one-sided Jacobi on the shorter side.
+// Exact truncated SVD: for a matrix with a short side of at most 320 (and a
+// long side of at least 256, or a short side of at least 64), CholeskyQR2 or
+// shifted CholeskyQR3 then a one-sided Jacobi SVD of the rows of the small
+// triangular factor (rank-revealing CholeskyQR for dependent vectors,
+// up to 160 of them); a truncation well below the short side of dependent
+// vectors goes to subspace iteration; otherwise one-sided Jacobi on the
+// shorter side.
 SvdOut svd_dense(sgtn_inst* h, const double* Th, int m, int n, int cap) {
   SvdOut o;
   int p = std::min(m, n), q = std::max(m, n);
-  if (p <= 320 && q >= 2 * p && q >= 256) {
-    if (prof_on()) g_prof[std::string(g_tag) + "/cqr_tries"].calls++;
+  // CholeskyQR first also for squarish matrices of 64 or more vectors: the
+  // one-sided Jacobi then rotates the rows of the triangular factor, which
+  // converges in about a third of the sweeps that the vectors of a matrix
+  // with graded singular values take
+  if (p <= 320 && (q >= 256 || p >= 64)) {
+    if (prof_on()) prof_entry(std::string(g_tag) + "/cqr_tries").calls++;
     if (m >= n) {
       if (svd_tall_cqr(h, Th, m, n, cap, o)) return o;
     } else {
@@ -228,6 +248,14 @@ SvdOut svd_dense(sgtn_inst* h, const double* Th, int m, int n, int cap) {
         t.release();
         return o;
       }
+    }
+    // numerically dependent vectors, too many for the pivoted Cholesky: a
+    // truncation to well below the short side takes the leading subspace by
+    // subspace iteration (a few products with Theta) instead of rotating all
+    // p long vectors to convergence
+    if (cap + 32 < p) {
+      if (prof_on()) prof_entry(std::string(g_tag) + "/dependent_subspace").calls++;
+      return svd_subspace(h, Th, m, n, cap);
     }
   }
   return svd_jacobi(h, Th, m, n, cap);
@@ -318,7 +346,7 @@ bool svd_tall_cqr3(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut&
 bool svd_tall_cqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o) {
   if (svd_tall_cqr3(h, M, m, n, cap, o)) return true;
   if (n > 160) return false;   // the pivoted Cholesky is staged in one CTA's shared memory
-  if (prof_on()) g_prof[std::string(g_tag) + "/rrcqr"].calls++;
+  if (prof_on()) prof_entry(std::string(g_tag) + "/rrcqr").calls++;
   return svd_tall_rrcqr(h, M, m, n, cap, o);
 }
 
@@ -448,7 +476,7 @@ SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap) {
     ktimer_add_flops("jacobi_f64", double(hs) * (2.0 * np * vl + np * (np - 1) / 2 * (8.0 * vl + 6.0 * np)));
   }
   if (prof_on()) {
-    SvdProf& e = g_prof[std::string(g_tag) + (std::max(m, n) > 128 ? "/jacobi_long" : "/jacobi")];
+    SvdProf& e = prof_entry(std::string(g_tag) + (std::max(m, n) > 128 ? "/jacobi_long" : "/jacobi"));
     e.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     e.calls++;
     e.iters += hs;
@@ -630,7 +658,7 @@ SvdOut svd_subspace_op(sgtn_inst* h, int m, int n, int cap, const MatFn& mul, co
         // Rayleigh-Ritz result and count the cut
         if (!conv) ++h->unconverged_cuts;
         if (prof_on()) {
-          SvdProf& e = g_prof[std::string(g_tag) + "/subspace"];
+          SvdProf& e = prof_entry(std::string(g_tag) + "/subspace");
           e.iters += it + 1;
           e.calls++;
           if (std::getenv("SGTN_TRACE"))
@@ -786,11 +814,40 @@ double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
   const Column& K_ = X.col(c);
   int chl = X.chl(c), chr = X.chr(c);
   long long nbl = K_.nBL();
-  // N[(u,b), (bl,chl)] = sum_a phi[a][(u,b)] L[a][(bl,chl)]
-  long long nub = (long long)phi.u * phi.b;
-  double* N = h->ws.get<double>("lupd_N", size_t(nub * nbl * chl));
-  gemm(phi.p, true, nub, L, false, nbl * chl, N, nbl * chl, int(nub), int(nbl * chl), phi.a, 1.0, 0, h->st);
-  // Ltil[(pr,e,pdr)][b][chr] = sum_terms w_x N[(u_x, bl)] Ahat[(pd,e,g)]
+  // N[p][b][chl] = sum_a phi[a][u_p][b] L[a][bl_p][chl] for the (u, bl) pairs
+  // p that some state reads (far fewer than all u x bl pairs when both the
+  // physical and the left bond index are large)
+  const int np = K_.lpairs.nseg;
+  double* N = h->ws.get<double>("lupd_N", size_t(np) * phi.b * chl);
+  {
+    SegGemm n;
+    n.name = "env_update";
+    n.X = phi.p;
+    n.p = phi.b;
+    n.q = phi.a;
+    n.xs_i = 1;
+    n.xs_k = (long long)phi.u * phi.b;
+    n.xrs = phi.b;
+    n.Y = L;
+    n.s = chl;
+    n.ys_k = nbl * chl;
+    n.ys_j = 1;
+    n.yrs = chl;
+    n.O = N;
+    n.os_i = chl;
+    n.os_j = 1;
+    n.ors = (long long)phi.b * chl;
+    n.out_by_seg = 1;
+    n.seg_ptr = K_.lpairs.seg_ptr;
+    n.xr = K_.lpairs.xr;
+    n.xc = K_.lpairs.xc;
+    n.yr = K_.lpairs.yr;
+    n.yc = K_.lpairs.yc;
+    n.nseg = np;
+    n.nterm = np;
+    seg_gemm(n, h->st);
+  }
+  // Ltil[(pr,e,pdr)][b][chr] = sum_terms w_x N[pair(u_x, bl)] Ahat[(pd,e,g)]
   double* Lt = h->ws.get<double>("lupd_Lt", size_t(K_.nK()) * phi.b * chr);
   SGTN_CUDA(cudaMemsetAsync(Lt, 0, size_t(K_.nK()) * phi.b * chr * sizeof(double), h->st));
   SegGemm a;
@@ -798,10 +855,10 @@ double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
   a.X = N;
   a.p = phi.b;
   a.q = chl;
-  a.xs_i = nbl * chl;
+  a.xs_i = chl;
   a.xs_k = 1;
-  a.xrs = (long long)phi.b * nbl * chl;
-  a.xcs = chl;
+  a.xrs = (long long)phi.b * chl;
+  a.xcs = 0;
   a.Y = X.Ahat[c];
   a.s = chr;
   a.ys_k = chr;
@@ -817,7 +874,7 @@ double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
   a.nvseg = K_.lupd.nvseg;
   a.seg_or = K_.lupd.seg_or;
   a.seg_oc = K_.lupd.seg_oc;
-  a.xr = K_.lupd.xr;
+  a.xr = K_.lupd_pair;
   a.xc = K_.lupd.xc;
   a.yr = K_.lupd.yr;
   a.yc = K_.lupd.yc;
@@ -1428,6 +1485,7 @@ void contract_boundary(sgtn_inst* h, int chi, int n_sweeps) {
   for (int r = R - 1; r >= 1; --r) row_step(h, r, chi, n_sweeps, h->psi[r - 1], worst);
   h->logz = h->log_offset + top_overlap(h);
   if (prof_on()) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
     for (auto& kv : g_prof)
       fprintf(stderr, "[sgtn] svd %-22s calls %6lld  %9.1f ms  iters %6lld  max %d x %d\n", kv.first.c_str(),
               kv.second.calls, kv.second.ms, kv.second.iters, kv.second.max_m, kv.second.max_n);

@@ -2,29 +2,59 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
+#include <stdexcept>
 #include <string>
+
+// The library's error: a status code of include/sgtn.h and a message.
+struct SgtnError : std::runtime_error {
+  int code;
+  SgtnError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
 
 namespace sgtn {
 
+// A double that several host threads add to.
+struct AtomicSum {
+  std::atomic<double> v{0.0};
+  void operator+=(double x) {
+    double o = v.load(std::memory_order_relaxed);
+    while (!v.compare_exchange_weak(o, o + x, std::memory_order_relaxed)) {
+    }
+  }
+  operator double() const { return v.load(std::memory_order_relaxed); }
+};
 // Process-wide diagnostics: kernel launches issued by this library and the
-// algorithmic floating-point operations of its contractions.
+// algorithmic floating-point operations of its contractions (summed over all
+// host threads driving handles).
 struct Counters {
-  long long launches = 0;
-  double flops = 0.0;
-  long long evals = 0;
+  std::atomic<long long> launches{0};
+  AtomicSum flops;
+  std::atomic<long long> evals{0};
 };
 extern Counters g_count;
+// The three mode flags below belong to the calling host thread: a handle's
+// call sets them for its own duration, so handles driven by different threads
+// (one stream each) do not see each other's modes.
 // When set, every contraction (seg_gemm / gemm) multiplies and accumulates in
 // FP32; the SVDs, norms and log-norms stay FP64.  Set per call from the handle.
-extern bool g_compute_f32;
+extern thread_local bool g_compute_f32;
 // When set (with g_compute_f32), dense GEMMs large enough for 128 x 128 tiles
 // run on tcgen05 tensor cores (3xTF32).
-extern bool g_use_tc;
+extern thread_local bool g_use_tc;
 // When set, the GEMM helpers allocate no device memory of their own (no
 // split-K or split-segment partial buffers): set by the allocation-free entry
 // point for the duration of its call.
-extern bool g_no_alloc;
+extern thread_local bool g_no_alloc;
+
+// Device scratch private to one stream: slot `slot` of stream `st`, at least
+// `bytes` long, reused by every later call on that stream (stream order keeps
+// the uses apart).  Growing it waits for the stream.  nullptr if it would have
+// to grow while g_no_alloc is set.
+enum ScratchSlot { SC_SEG_PART, SC_SPLITK_PART, SC_CHOL_T, SC_JAC_FLAGS, SC_JAC_FRO, SC_TC_BUF, SC_NSLOT };
+void* stream_scratch(cudaStream_t st, int slot, size_t bytes);
+void stream_scratch_release(cudaStream_t st);
 
 // Optional per-kernel timing with CUDA events on the launching stream.
 // KTimer brackets one launch; pairs are resolved when read.

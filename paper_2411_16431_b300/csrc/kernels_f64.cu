@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -923,18 +924,53 @@ inline int blocks_for(long long n, int t = 256) {
 Counters g_count;
 
 namespace {
+std::mutex g_scratch_mu;
+std::map<std::pair<cudaStream_t, int>, std::pair<void*, size_t>> g_scratch;
+}  // namespace
+
+void* stream_scratch(cudaStream_t st, int slot, size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  auto& e = g_scratch[{st, slot}];
+  if (bytes <= e.second) return e.first;
+  if (g_no_alloc) return nullptr;
+  if (e.first) {
+    cudaStreamSynchronize(st);
+    cudaFree(e.first);
+    e = {nullptr, 0};
+  }
+  if (cudaMalloc(&e.first, bytes) != cudaSuccess) {
+    e = {nullptr, 0};
+    throw SgtnError(-3, "out of device memory for " + std::to_string(bytes) + " bytes of scratch");
+  }
+  e.second = bytes;
+  return e.first;
+}
+
+void stream_scratch_release(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  for (auto it = g_scratch.begin(); it != g_scratch.end();) {
+    if (it->first.first == st) {
+      cudaStreamSynchronize(st);
+      cudaFree(it->second.first);
+      it = g_scratch.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+namespace {
 struct Pending {
   std::string name;
   cudaEvent_t a, b;
   double flops;
 };
 struct TimerState {
-  bool on = false;
+  std::atomic<bool> on{false};
+  std::mutex mu;                                       // guards the members below
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
   std::map<std::string, std::array<double, 3>> acc;   // ms, launches, flops
-  const char* cur = nullptr;
-  cudaEvent_t cur_a = nullptr;
   cudaEvent_t get() {
     if (!pool.empty()) {
       cudaEvent_t e = pool.back();
@@ -961,41 +997,51 @@ struct TimerState {
   }
 };
 TimerState g_timer;
+// Timers nest per host thread: only the outermost one records (a Cholesky's
+// time includes its GEMMs, which are then not booked a second time).
+thread_local int t_timer_depth = 0;
+thread_local const char* t_timer_cur = nullptr;
+thread_local cudaEvent_t t_timer_a = nullptr;
 }  // namespace
 
-// Timers nest: only the outermost one records (a Cholesky's time includes its
-// GEMMs, which are then not booked a second time).
-static int g_timer_depth = 0;
 void ktimer_begin(const char* name, cudaStream_t st) {
   if (!g_timer.on) return;
-  if (g_timer_depth++ > 0) return;
-  g_timer.cur = name;
-  g_timer.cur_a = g_timer.get();
-  cudaEventRecord(g_timer.cur_a, st);
+  if (t_timer_depth++ > 0) return;
+  std::lock_guard<std::mutex> lk(g_timer.mu);
+  t_timer_cur = name;
+  t_timer_a = g_timer.get();
+  cudaEventRecord(t_timer_a, st);
 }
 void ktimer_end(cudaStream_t st, double flops) {
   if (!g_timer.on) return;
-  if (g_timer_depth > 0 && --g_timer_depth > 0) return;
-  if (!g_timer.cur) return;
+  if (t_timer_depth > 0 && --t_timer_depth > 0) return;
+  if (!t_timer_cur) return;
+  std::lock_guard<std::mutex> lk(g_timer.mu);
   cudaEvent_t b = g_timer.get();
   cudaEventRecord(b, st);
-  g_timer.pending.push_back({g_timer.cur, g_timer.cur_a, b, flops});
-  g_timer.cur = nullptr;
+  g_timer.pending.push_back({t_timer_cur, t_timer_a, b, flops});
+  t_timer_cur = nullptr;
   if (g_timer.pending.size() > 4096) g_timer.resolve();
 }
 void ktimer_add_flops(const char* name, double flops) {
-  if (g_timer.on) g_timer.acc[name][2] += flops;
+  if (!g_timer.on) return;
+  std::lock_guard<std::mutex> lk(g_timer.mu);
+  g_timer.acc[name][2] += flops;
 }
 void ktimer_enable(bool on) {
+  std::lock_guard<std::mutex> lk(g_timer.mu);
   g_timer.resolve();
   g_timer.on = on;
-  g_timer_depth = 0;
+  t_timer_depth = 0;
+  t_timer_cur = nullptr;
 }
 void ktimer_reset() {
+  std::lock_guard<std::mutex> lk(g_timer.mu);
   g_timer.resolve();
   g_timer.acc.clear();
 }
 bool ktimer_read(const char* name, double* ms, long long* n, double* flops) {
+  std::lock_guard<std::mutex> lk(g_timer.mu);
   g_timer.resolve();
   auto it = g_timer.acc.find(name);
   if (it == g_timer.acc.end()) return false;
@@ -1005,6 +1051,7 @@ bool ktimer_read(const char* name, double* ms, long long* n, double* flops) {
   return true;
 }
 std::string ktimer_names() {
+  std::lock_guard<std::mutex> lk(g_timer.mu);
   g_timer.resolve();
   std::string o;
   for (auto& kv : g_timer.acc) o += kv.first + ",";
@@ -1046,14 +1093,8 @@ void seg_gemm(const SegGemm& a_in, cudaStream_t st) {
   if (!split) {
     launch_seg(a, st);
   } else {
-    static double* part = nullptr;
-    static size_t part_n = 0;
-    const size_t need = size_t(a.nvseg) * a.p * a.s;
-    if (need > part_n) {
-      if (part) cudaFree(part);
-      cudaMalloc(&part, need * sizeof(double));
-      part_n = need;
-    }
+    double* part = static_cast<double*>(
+        stream_scratch(st, SC_SEG_PART, size_t(a.nvseg) * a.p * a.s * sizeof(double)));
     SegGemm b = a;
     b.seg_ptr = a.vseg_ptr;
     b.nseg = a.nvseg;
@@ -1073,9 +1114,9 @@ void seg_gemm(const SegGemm& a_in, cudaStream_t st) {
   g_count.flops += fl;
 }
 
-bool g_compute_f32 = false;
-bool g_use_tc = false;
-bool g_no_alloc = false;
+thread_local bool g_compute_f32 = false;
+thread_local bool g_use_tc = false;
+thread_local bool g_no_alloc = false;
 
 void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, long long ldy, double* O, long long ldo,
           int m, int n, int k, double alpha, int accumulate, cudaStream_t st, int tri) {
@@ -1113,14 +1154,8 @@ void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, lon
     int nsplit = int(std::min<long long>((k + 31) / 32, std::max<long long>(2, (296 + tiles - 1) / tiles)));
     int chunk = ((k + nsplit - 1) / nsplit + TK - 1) / TK * TK;
     nsplit = (k + chunk - 1) / chunk;
-    static double* part = nullptr;
-    static size_t part_n = 0;
-    size_t need = size_t(nsplit) * m * n;
-    if (need > part_n) {
-      if (part) cudaFree(part);
-      cudaMalloc(&part, need * sizeof(double));
-      part_n = need;
-    }
+    double* part =
+        static_cast<double*>(stream_scratch(st, SC_SPLITK_PART, size_t(nsplit) * m * n * sizeof(double)));
     SegGemm b = a;
     b.O = part;
     b.os_i = n;
@@ -1144,20 +1179,17 @@ void jacobi(double* X, int len, int p, long long si, long long sj, double* V, in
             cudaStream_t st) {
   double tol = 1e-15 * sqrt(double(len > 1 ? len : 1));
   size_t smem = (size_t(len) * p + (V ? size_t(p) * p : 0)) * sizeof(double);
-  static bool attr_set = false;
   const size_t kMaxSmem = 220 * 1024;
-  if (!attr_set) {
+  // once per process (thread-safe initialisation of a local static): kernel
+  // attributes, and the cluster size, up to 16 CTAs (one pair per warp and
+  // step) if the device takes it
+  static const int max_cluster = [kMaxSmem] {
     cudaFuncSetAttribute(jacobi_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxSmem));
-    attr_set = true;
-  }
-  // cluster size: up to 16 CTAs (one pair per warp and step), if the vectors fit
-  static int max_cluster = 0;
-  if (!max_cluster) {
     for (void* f : {(void*)jacobi_cluster_kernel<0>, (void*)jacobi_cluster_kernel<4>}) {
       cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxSmem));
     }
-    max_cluster = 8;
+    int mc = 8;
     cudaLaunchConfig_t q = {};
     cudaLaunchAttribute qa[1];
     q.gridDim = dim3(16);
@@ -1171,9 +1203,10 @@ void jacobi(double* X, int len, int p, long long si, long long sj, double* V, in
     q.numAttrs = 1;
     int ncl = 0;
     if (cudaOccupancyMaxActiveClusters(&ncl, (void*)jacobi_cluster_kernel<0>, &q) == cudaSuccess && ncl >= 1)
-      max_cluster = 16;
+      mc = 16;
     cudaGetLastError();
-  }
+    return mc;
+  }();
   const int npair = (p + 1) / 2;
   int P = std::max(1, std::min(max_cluster, npair));
   const int slots = (p + P - 1) / P;
@@ -1201,13 +1234,10 @@ void jacobi(double* X, int len, int p, long long si, long long sj, double* V, in
     } else if (smem <= kMaxSmem) {
       jacobi_smem_kernel<<<1, 1024, smem, st>>>(X, len, p, si, sj, V, max_sweeps, tol, status);
     } else {
-      // flags (one per sweep) and the Frobenius norm live in a small static scratch
-      static int* flags = nullptr;
-      static double* fro = nullptr;
-      if (!flags) {
-        cudaMalloc(&flags, 256 * sizeof(int));
-        cudaMalloc(&fro, sizeof(double));
-      }
+      // flags (one per sweep) and the Frobenius norm live in the stream's scratch
+      int* flags = static_cast<int*>(stream_scratch(st, SC_JAC_FLAGS, 256 * sizeof(int)));
+      double* fro = static_cast<double*>(stream_scratch(st, SC_JAC_FRO, sizeof(double)));
+      if (!flags || !fro) throw SgtnError(-3, "Jacobi scratch needs an allocation in an allocation-free call");
       cudaMemsetAsync(flags, 0, 256 * sizeof(int), st);
       int ms = max_sweeps > 256 ? 256 : max_sweeps;
       int nblk = ((p + 1) / 2 + 3) / 4;   // 4 warps (pairs) per CTA
@@ -1231,12 +1261,12 @@ constexpr int kCholBlock = 48;   // blocks up to this size are factored by one C
 
 void chol_base(double* W, int n, int ld, double shift, double* R, const double* Gd, int* status, int off,
                double* minratio, cudaStream_t st, bool f32) {
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {
     cudaFuncSetAttribute(cholesky_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     cudaFuncSetAttribute(cholesky_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   if (f32)
     cholesky_inv_kernel<float><<<1, 1024, size_t(n) * (n + 2) * sizeof(float), st>>>(W, n, ld, shift, R, W, Gd,
                                                                                     status, off, minratio);
@@ -1282,14 +1312,9 @@ void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv,
   // the off-diagonal GEMMs run in FP64 whatever the caller's contraction precision
   const bool sf = g_compute_f32, su = g_use_tc;
   g_compute_f32 = g_use_tc = false;
-  static double* T = nullptr;
-  static double one = 1.0;
-  static size_t T_n = 0;
-  if (size_t(n) * n > T_n) {
-    if (T) cudaFree(T);
-    cudaMalloc(&T, size_t(n) * n * sizeof(double));
-    T_n = size_t(n) * n;
-  }
+  static const double one = 1.0;
+  double* T = static_cast<double*>(stream_scratch(st, SC_CHOL_T, size_t(n) * n * sizeof(double)));
+  if (!T) throw SgtnError(-3, "Cholesky scratch needs an allocation in an allocation-free call");
   cudaMemsetAsync(status, 0, sizeof(int), st);
   if (minratio) cudaMemcpyAsync(minratio, &one, sizeof(double), cudaMemcpyHostToDevice, st);
   if (Rinv != G) cudaMemcpyAsync(Rinv, G, size_t(n) * n * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -1300,11 +1325,11 @@ void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv,
 
 void pchol_inv(const double* G, int n, double tol_rel, double tol_abs, double* R, double* Rinv, int32_t* perm,
                int* rank, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {
     cudaFuncSetAttribute(pchol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   KTimer t("pcholesky_f64", st);
   pchol_inv_kernel<<<1, 1024, size_t(n) * n * sizeof(double), st>>>(G, n, tol_rel, tol_abs, R, Rinv, perm, rank);
   ++g_count.launches;

@@ -101,6 +101,10 @@ struct Column {
   TermTable bs_rows; // block-sparse Theta grouped by row block bl: terms (xr = seg, yr = u)
   TermTable bs_cols; // grouped by column block u: terms (xr = seg, xc = bl, yr = bl, yc = seg)
   TermTable renv;    // segments bl, terms (x, e), column scale row = u
+  // the (u, bl) pairs that lupd terms read, one segment each (xr = u, yr = bl),
+  // and per lupd term the index of its pair
+  TermTable lpairs;
+  int32_t* lupd_pair = nullptr;
   // per-beta dense weight matrices (device, double)
   double* Wa = nullptr;   // [nA][nSig]
   double* Wk = nullptr;   // [nK][nBR]

@@ -1,6 +1,7 @@
 // Device-side set-up: per-site index tables, per-column term tables of the
 // sparse site diagrams (Fig. 7), and the per-beta Boltzmann factors (Eq. 5).
 #include <algorithm>
+#include <map>
 #include <numeric>
 #include <tuple>
 
@@ -183,6 +184,21 @@ void setup_device(sgtn_inst* h) {
             tb.add(kblk, kblk, 0, u[x], bl, ablk, 0, x, u[x]);
           }
       tb.finish(h, K.lupd);
+      {
+        // distinct (u, bl) pairs read by the lupd terms: the left-environment
+        // update forms its intermediate only for these
+        std::map<std::pair<int32_t, int32_t>, int32_t> pid;
+        std::vector<int32_t> tp(K.lupd.nterm);
+        for (int t = 0; t < K.lupd.nterm; ++t) {
+          auto key = std::make_pair(K.lupd.h_xr[t], K.lupd.h_xc[t]);
+          auto it = pid.find(key);
+          if (it == pid.end()) it = pid.emplace(key, int32_t(pid.size())).first;
+          tp[t] = it->second;
+        }
+        for (auto& kv : pid) tb.add(kv.second, kv.second, 0, kv.first.first, 0, kv.first.second, 0, 0, 0);
+        tb.finish(h, K.lpairs);
+        K.lupd_pair = h->upload(tp);
+      }
       // groupings of the site-diagram output blocks (one block per theta segment)
       for (int sg = 0; sg < K.theta.nseg; ++sg) {
         int bl = K.theta.h_seg_or[sg], uu = K.theta.h_seg_oc[sg];

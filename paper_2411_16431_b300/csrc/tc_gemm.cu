@@ -262,21 +262,18 @@ bool tc_gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, 
              int m, int n, int k, double alpha, int accumulate, cudaStream_t st) {
   if (m <= 0 || n <= 0 || k <= 0) return true;
   int kpad = (k + 3) / 4 * 4;   // 16-byte row pitch for TMA
-  static float* buf = nullptr;
-  static size_t buf_n = 0;
-  static int* err = nullptr;
-  size_t need = 2 * (size_t(m) + n) * kpad;
-  if ((need > buf_n || !err) && g_no_alloc) return false;   // the SIMT path allocates nothing
-  if (need > buf_n) {
-    if (buf) cudaFree(buf);
-    if (cudaMalloc(&buf, need * sizeof(float)) != cudaSuccess) return false;
-    buf_n = need;
-  }
-  if (!err) {
-    cudaMalloc(&err, sizeof(int));
-    cudaMemset(err, 0, sizeof(int));
-  }
+  // the timeout flag is shared by all streams (it only ever goes 0 -> 1)
+  static int* const err = [] {
+    int* e = nullptr;
+    if (cudaMalloc(&e, sizeof(int)) != cudaSuccess) return (int*)nullptr;
+    cudaMemset(e, 0, sizeof(int));
+    return e;
+  }();
+  if (!err) return false;
   tc_err_ptr() = err;
+  size_t need = 2 * (size_t(m) + n) * kpad;
+  float* buf = static_cast<float*>(stream_scratch(st, SC_TC_BUF, need * sizeof(float)));
+  if (!buf) return false;   // would allocate in an allocation-free call: the SIMT path allocates nothing
   float* ahi = buf;
   float* alo = ahi + size_t(m) * kpad;
   float* bhi = alo + size_t(m) * kpad;
@@ -292,11 +289,11 @@ bool tc_gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, 
   if (!make_map(&mA1, ahi, m, kpad) || !make_map(&mA2, alo, m, kpad) || !make_map(&mB1, bhi, n, kpad) ||
       !make_map(&mB2, blo, n, kpad))
     return false;
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {
     cudaFuncSetAttribute(tc_gemm_3xtf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM);
   double fl = 2.0 * m * n * k;
   {
@@ -309,7 +306,7 @@ bool tc_gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, 
 }
 
 int*& tc_err_ptr() {
-  static int* e = nullptr;
+  static int* e = nullptr;   // written once, with the same value, by every caller
   return e;
 }
 

@@ -9,7 +9,9 @@ from it.
 Random numbers come from SplitMix64 (Steele, Lea, Flood, "Fast splittable
 pseudorandom number generators", OOPSLA 2014), seeded per instance.  A draw
 of a coupling or field picks one of the 14 values {+-1, ..., +-7} uniformly
-(value/7), matching the i.i.d. workloads used for benchmarking.
+(value/7), matching the i.i.d. workloads used for benchmarking; the square and
+king's lattices can instead draw class I couplings (uniform in [-1, 1] on a
+grid of step 1/1000, no fields; paper Sec. IV and App. B).
 
 Lattices
 --------
@@ -97,10 +99,23 @@ class Instance:
         return int(np.sum(self.j_num * s[self.ei] * s[self.ej]) + np.sum(self.h_num * s))
 
 
-def _finish(n, edges, site_of_spin, rows, cols, rng, name, fields=True):
+UNIFORM_DENOM = 1000
+
+
+def _finish(n, edges, site_of_spin, rows, cols, rng, name, fields=True, couplings="pm7"):
+    """``couplings``: "pm7" draws J and h from {+-1..+-7}/7; "uniform" draws J
+    uniformly from the grid {-1000..1000}/1000 of [-1, 1] with no fields (the
+    paper's class I, Sec. IV) -- ``fields`` is then ignored."""
     edges = sorted(set((min(a, b), max(a, b)) for a, b in edges if a != b))
     ei = np.array([a for a, _ in edges], dtype=np.int32)
     ej = np.array([b for _, b in edges], dtype=np.int32)
+    if couplings == "uniform":
+        jn = np.array([rng.below(2 * UNIFORM_DENOM + 1) - UNIFORM_DENOM for _ in edges], dtype=np.int32)
+        hn = np.zeros(n, dtype=np.int32)
+        return Instance(n, ei, ej, jn, hn, UNIFORM_DENOM, np.asarray(site_of_spin, dtype=np.int32), rows, cols,
+                        name + "_classI")
+    if couplings != "pm7":
+        raise ValueError(f"unknown coupling distribution {couplings!r}")
     jn = np.array([rng.pm7() for _ in edges], dtype=np.int32)
     hn = np.array([rng.pm7() if fields else 0 for _ in range(n)], dtype=np.int32)
     return Instance(n, ei, ej, jn, hn, 7, np.asarray(site_of_spin, dtype=np.int32), rows, cols, name)
@@ -131,7 +146,8 @@ def chimera_grid(rows: int, cols: int, seed: int, fields: bool = True) -> Instan
     return _finish(n, edges, site, rows, cols, rng, f"chimera{rows}x{cols}_s{seed}", fields)
 
 
-def square_grid(rows: int, cols: int, seed: int, fields: bool = True, kings: bool = False) -> Instance:
+def square_grid(rows: int, cols: int, seed: int, fields: bool = True, kings: bool = False,
+                couplings: str = "pm7") -> Instance:
     """One spin per site with nearest-neighbour bonds (and both diagonals if ``kings``)."""
     rng = SplitMix64(seed)
     n = rows * cols
@@ -148,11 +164,11 @@ def square_grid(rows: int, cols: int, seed: int, fields: bool = True, kings: boo
                 if kings and c >= 1:
                     edges.append((i, i + cols - 1))
     kind = "kings" if kings else "square"
-    return _finish(n, edges, list(range(n)), rows, cols, rng, f"{kind}{rows}x{cols}_s{seed}", fields)
+    return _finish(n, edges, list(range(n)), rows, cols, rng, f"{kind}{rows}x{cols}_s{seed}", fields, couplings)
 
 
-def kings_grid(rows: int, cols: int, seed: int, fields: bool = True) -> Instance:
-    return square_grid(rows, cols, seed, fields, kings=True)
+def kings_grid(rows: int, cols: int, seed: int, fields: bool = True, couplings: str = "pm7") -> Instance:
+    return square_grid(rows, cols, seed, fields, kings=True, couplings=couplings)
 
 
 # --- Pegasus ---------------------------------------------------------------

@@ -44,6 +44,9 @@ def load():
     L.sgtn_conditionals_noalloc.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I32P, _F64P]
     L.sgtn_energies.argtypes = [ct.c_void_p, ct.c_int32, _I8P, _I64P]
     L.sgtn_logz_grad.argtypes = [ct.c_void_p, _F64P, _F64P, _F64P]
+    L.sgtn_batch_search.argtypes = [ct.POINTER(ct.c_void_p), ct.c_int32, ct.c_double, ct.c_int32, ct.c_int32,
+                                    ct.c_int32, ct.c_int32, ct.c_int32, ct.POINTER(_I8P), ct.POINTER(_I64P),
+                                    ct.POINTER(_F64P), _F64P, _F64P, _I32P, ct.c_int32, _I32P]
     L.sgtn_site_dims.argtypes = [ct.c_void_p, ct.c_int32, _I32P]
     L.sgtn_boundary_info.argtypes = [ct.c_void_p, _I32P, _I32P]
     L.sgtn_mps_shape.argtypes = [ct.c_void_p, ct.c_int32, _I32P, _I32P, _F64P]
@@ -288,24 +291,58 @@ def _logz_function():
     return _LOGZ_FN
 
 
-def search_transforms(inst, beta, chi, M, states_per_site=None, precision=FP64, n_sweeps=2, transforms=range(8)):
+def batch_search(handles, beta, chi, M, precision=FP64, n_sweeps=2, n_out=1, threads=0, raise_on_error=True):
+    """sgtn_batch_search: set_beta, contract_boundary and search on every
+    handle, handles on distinct streams concurrently.  Returns a list of
+    (log Z, search result) in handle order; raises if any handle failed, or,
+    with raise_on_error=False, gives (NaN, None) for a failed handle (its
+    error text stays in the handle)."""
+    L = load()
+    n = len(handles)
+    hs = (ct.c_void_p * n)(*[h.h for h in handles])
+    sps = [np.zeros((n_out, h.inst.n_spins), np.int8) for h in handles]
+    ens = [np.zeros(n_out, np.int64) for _ in handles]
+    lps = [np.zeros(n_out) for _ in handles]
+    sp_p = (_I8P * n)(*[_p(a, _I8P) for a in sps])
+    en_p = (_I64P * n)(*[_p(a, _I64P) for a in ens])
+    lp_p = (_F64P * n)(*[_p(a, _F64P) for a in lps])
+    lz = np.zeros(n)
+    pd = np.zeros(n)
+    cnt = np.zeros(n, np.int32)
+    status = np.zeros(n, np.int32)
+    rc = L.sgtn_batch_search(hs, n, float(beta), chi, precision, n_sweeps, M, n_out, sp_p, en_p, lp_p,
+                             _p(lz, _F64P), _p(pd, _F64P), _p(cnt, _I32P), threads, _p(status, _I32P))
+    bad = [i for i in range(n) if status[i] != 0]
+    if rc != 0 and (raise_on_error or not bad):
+        i = bad[0] if bad else 0
+        raise SgtnError(f"sgtn_batch_search failed ({rc}); handle {i}: {L.sgtn_last_error(hs[i]).decode()}")
+    return [(float(lz[i]), dict(spins=sps[i][:cnt[i]], energy_num=ens[i][:cnt[i]], logp=lps[i][:cnt[i]],
+                                pd=float(pd[i]))) if status[i] == 0 else (float("nan"), None) for i in range(n)]
+
+
+def search_transforms(inst, beta, chi, M, states_per_site=None, precision=FP64, n_sweeps=2, transforms=range(8),
+                      streams=None):
     """Boundary contraction + search of the instance in each of the grid
-    symmetries ``transforms`` (lattices.TRANSFORMS), one handle after the
-    other: the paper runs every instance in all of its orientations and keeps
-    the best state (Sec. V).  Spins keep their indices, so the returned states
+    symmetries ``transforms`` (lattices.TRANSFORMS): the paper runs every
+    instance in all of its orientations and keeps the best state (Sec. V).
+    ``streams``: one CUDA stream (raw pointer) per transform, to run them
+    concurrently through sgtn_batch_search; None runs them one after another
+    on the default stream.  Spins keep their indices, so the returned states
     and energies are comparable.  Returns (index of the best, list of
     (transform, log Z, search result))."""
     from . import lattices as L
-    out = []
-    for k in transforms:
-        t = L.transform(inst, k)
-        st = None if states_per_site is None else L.transform_states(inst, states_per_site, k)
-        h = Handle(t, st)
-        try:
-            h.set_beta(beta)
-            lz, _ = h.contract_boundary(chi, precision=precision, n_sweeps=n_sweeps)
-            out.append((k, lz, h.search(M)))
-        finally:
+    ks = list(transforms)
+    if streams is not None and len(streams) != len(ks):
+        raise ValueError("one stream per transform")
+    hs = []
+    try:
+        for j, k in enumerate(ks):
+            st = None if states_per_site is None else L.transform_states(inst, states_per_site, k)
+            hs.append(Handle(L.transform(inst, k), st, stream=None if streams is None else streams[j]))
+        res = batch_search(hs, beta, chi, M, precision=precision, n_sweeps=n_sweeps)
+    finally:
+        for h in hs:
             h.close()
+    out = [(k, lz, r) for k, (lz, r) in zip(ks, res)]
     best = min(range(len(out)), key=lambda i: (int(out[i][2]["energy_num"][0]), i))
     return best, out

@@ -25,7 +25,8 @@ def Handle():
 
 
 EXACT = [L.square_grid(3, 3, 1), L.kings_grid(4, 4, 3), L.slice_cells(L.chimera_grid(4, 4, 0), 2, 1),
-         L.kings_grid(2, 5, 9), L.square_grid(1, 6, 2), L.square_grid(5, 1, 3)]
+         L.kings_grid(2, 5, 9), L.square_grid(1, 6, 2), L.square_grid(5, 1, 3),
+         L.kings_grid(3, 4, 6, couplings="uniform")]
 
 
 @pytest.mark.parametrize("inst", EXACT, ids=lambda i: i.name)
@@ -39,7 +40,9 @@ def test_exact_logz_matches_brute_force(Handle, inst):
 
 CASES = [(L.chimera_grid(4, 4, 0), 1.0, 16, 2), (L.chimera_grid(3, 4, 7), 2.0, 4, 1),
          (L.kings_grid(5, 6, 4), 1.0, 3, 2), (L.square_grid(6, 5, 8), 3.0, 2, 2),
-         (L.planted(L.chimera_grid(3, 3, 5), 2), 1.5, 6, 1)]
+         (L.planted(L.chimera_grid(3, 3, 5), 2), 1.5, 6, 1),
+         # class I (Sec. IV): reflection-symmetric, exactly tied first marginals; beta and chi of App. B
+         (L.kings_grid(7, 8, 5, couplings="uniform"), 4.0, 16, 2)]
 
 
 PEG = L.pegasus_nice(4, 11)
@@ -172,7 +175,9 @@ def test_search_with_fully_degenerate_scores(Handle):
 
 
 @pytest.mark.parametrize("case", [(L.chimera_grid(4, 4, 0), 1.0, 16, 64, 2), (L.chimera_grid(3, 4, 7), 2.0, 4, 16, 1),
-                                  (L.kings_grid(4, 5, 2), 2.0, 3, 8, 1)], ids=lambda c: c[0].name)
+                                  (L.kings_grid(4, 5, 2), 2.0, 3, 8, 1),
+                                  (L.kings_grid(4, 5, 3, couplings="uniform"), 4.0, 4, 8, 1)],
+                         ids=lambda c: c[0].name)
 def test_branch_steps_match_oracle(Handle, case):
     """Every intermediate beam of the search, step by step (configurations, log p, p_d)."""
     inst, beta, chi, M, ns = case
@@ -294,12 +299,51 @@ def test_grid_symmetries_on_the_gpu(Handle):
         lz, _ = h.contract_boundary(64, n_sweeps=1)
         assert abs(lz - ref) < RTOL * abs(ref)
         h.close()
-    best, runs = sgtn.search_transforms(inst, beta, chi=4, M=8, n_sweeps=1)
+    import torch
+    ss = [torch.cuda.Stream() for _ in range(8)]
+    best, runs = sgtn.search_transforms(inst, beta, chi=4, M=8, n_sweeps=1, streams=[s.cuda_stream for s in ss])
     energies = [int(r[2]["energy_num"][0]) for r in runs]
     assert energies[best] == min(energies)
     assert energies[best] >= brute.ground_state(inst)[1]
     for _, _, r in runs:
         assert inst.energy_num(r["spins"][0]) == int(r["energy_num"][0])
+
+
+def test_batch_search_matches_one_by_one(Handle):
+    """sgtn_batch_search on instances of uneven size and kind, each on its own
+    stream and host thread (kernels overlapping on the device), gives the
+    results of the same calls made one handle at a time; handles that share a
+    stream run in order."""
+    import torch
+    from paper_2411_16431_b300 import sgtn
+    insts = [(L.chimera_grid(3, 3, 1), None), (L.kings_grid(6, 7, 2, couplings="uniform"), None), (PEG, PEG_STATES),
+             (L.planted(L.chimera_grid(3, 4, 5), 2), None), (L.square_grid(5, 9, 3), None), (PEGP, PEGP_STATES)]
+    beta, chi, M, ns = 1.2, 8, 16, 2
+    for prec in (sgtn.FP64, sgtn.TF32):
+        seq = []
+        for inst, st in insts:
+            h = Handle(inst, st)
+            h.set_beta(beta)
+            lz, _ = h.contract_boundary(chi, precision=prec, n_sweeps=ns)
+            seq.append((lz, h.search(M)))
+            h.close()
+        streams = [torch.cuda.Stream() for _ in insts]
+        for stream_of in (lambda i: streams[i].cuda_stream, lambda i: streams[i % 2].cuda_stream):
+            hs = [Handle(inst, st, stream=stream_of(i)) for i, (inst, st) in enumerate(insts)]
+            try:
+                res = sgtn.batch_search(hs, beta, chi, M, precision=prec, n_sweeps=ns)
+            finally:
+                for h in hs:
+                    h.close()
+            for (lz0, r0), (lz1, r1) in zip(seq, res):
+                assert abs(lz1 - lz0) <= 1e-13 * abs(lz0)
+                assert np.array_equal(r0["spins"], r1["spins"])
+                assert np.array_equal(r0["energy_num"], r1["energy_num"])
+                assert np.allclose(r0["logp"], r1["logp"], rtol=1e-12, atol=0)
+    h = Handle(insts[0][0])
+    with pytest.raises(sgtn.SgtnError):
+        sgtn.batch_search([h, h], beta, chi, M)
+    h.close()
 
 
 def test_logz_autograd_function(Handle):

@@ -25,6 +25,16 @@ def test_chimera_counts():
     assert set(np.abs(inst.j_num)) <= set(range(1, 8))
 
 
+def test_class_one_couplings():
+    """Class I (Sec. IV): J uniform in [-1, 1], h = 0, hence a global reflection symmetry."""
+    inst = L.kings_grid(6, 7, 2, couplings="uniform")
+    assert inst.denom == 1000 and not inst.h_num.any()
+    assert np.abs(inst.j_num).max() <= 1000 and len(set(inst.j_num.tolist())) > inst.n_edges // 2
+    assert inst.n_edges == 6 * 6 + 5 * 7 + 2 * 5 * 6
+    s = np.where(np.arange(inst.n_spins) % 3 == 0, 1, -1)
+    assert inst.energy_num(s) == inst.energy_num(-s)
+
+
 def test_pegasus_counts_and_degree():
     # nice subgraph of P_M has 24 (M-1)^2 nodes; max degree 15 (Sec. II)
     for m, n in ((4, 216), (6, 600), (16, 5400)):
@@ -101,7 +111,7 @@ def test_projector_classes_by_enumeration():
 
 SMALL = [L.square_grid(3, 3, 1), L.kings_grid(4, 4, 3), L.square_grid(4, 4, 4, fields=False),
          L.slice_cells(L.chimera_grid(4, 4, 0), 2, 1), L.slice_cells(L.chimera_grid(4, 4, 0), 1, 2),
-         L.kings_grid(2, 5, 9)]
+         L.kings_grid(2, 5, 9), L.kings_grid(3, 4, 6, couplings="uniform")]
 
 
 @pytest.mark.parametrize("inst", SMALL, ids=lambda i: i.name)
@@ -211,7 +221,8 @@ def test_exact_conditionals_match_brute_force(inst):
 
 @pytest.mark.parametrize("inst", [L.kings_grid(4, 4, 3), L.square_grid(4, 4, 12),
                                   L.slice_cells(L.chimera_grid(4, 4, 0), 2, 1),
-                                  L.planted(L.slice_cells(L.chimera_grid(2, 2, 5), 1, 2), 4)], ids=lambda i: i.name)
+                                  L.planted(L.slice_cells(L.chimera_grid(2, 2, 5), 1, 2), 4),
+                                  L.kings_grid(3, 4, 6, couplings="uniform")], ids=lambda i: i.name)
 def test_exact_search_is_dynamic_programming(inst):
     """With exact marginals and no top-M cut, merging keeps the best completion of each boundary,
     so the search returns the brute-force ground state and log p = -beta E - log Z."""
