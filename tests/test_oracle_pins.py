@@ -331,3 +331,56 @@ def test_grid_symmetries_keep_log_z_and_ground_state():
             assert abs(lz - ref) < 1e-12 * abs(ref)
             res = search(t, beta, chi=256, M=10 ** 6, n_sweeps=1)
             assert res["energy_num"][0] == e0
+
+
+# --- loopy belief propagation (Sec. IV) -------------------------------------------
+
+def _exact_cluster_marginals(inst, beta):
+    """p(x_n) by enumeration: x_n = bits of the cluster's spins (bit j = j-th spin, 1 = down)."""
+    S = brute.all_spins(inst.n_spins)
+    E = brute.energies_num(inst, S) / inst.denom
+    p = np.exp(-beta * (E - E.min()))
+    p /= p.sum()
+    out = []
+    for site in range(inst.rows * inst.cols):
+        spins = np.nonzero(inst.site_of_spin == site)[0]
+        x = np.zeros(len(p), np.int64)
+        for j, g in enumerate(spins):
+            x |= ((1 - S[:, g].astype(np.int64)) // 2) << j
+        out.append(np.bincount(x, weights=p, minlength=1 << len(spins)))
+    return out
+
+
+@pytest.mark.parametrize("inst", [L.slice_cells(L.chimera_grid(4, 4, 0), 1, 2), L.slice_cells(L.chimera_grid(4, 4, 3), 2, 1),
+                                  L.kings_grid(1, 7, 4), L.square_grid(5, 1, 2, couplings="uniform")],
+                         ids=lambda i: i.name)
+def test_lbp_is_exact_on_a_chain_of_clusters(inst):
+    """On a tree of clusters (a single row or column) belief propagation is exact once
+    messages have crossed it: the marginals are the enumerated cluster marginals."""
+    from oracle.lbp import lbp
+    beta = 0.9
+    marg, change = lbp(PottsModel(inst), beta, n_iter=inst.rows * inst.cols + 1)
+    exact = _exact_cluster_marginals(inst, beta)
+    for m, e in zip(marg, exact):
+        assert np.allclose(m, e, rtol=1e-10, atol=1e-14)
+    assert change < 1e-12
+
+
+def test_lbp_limits():
+    """beta = 0 gives uniform marginals; couplings of zero between clusters give the
+    local Boltzmann weights of each cluster; marginals sum to one on a loopy grid."""
+    from oracle.lbp import lbp, top_states
+    inst = L.chimera_grid(3, 3, 5)
+    marg, _ = lbp(PottsModel(inst), 0.0, n_iter=3)
+    assert all(np.allclose(m, 1.0 / len(m), rtol=1e-13) for m in marg)
+    dec = L.chimera_grid(2, 3, 6)
+    inter = dec.site_of_spin[dec.ei] != dec.site_of_spin[dec.ej]
+    dec.j_num = np.where(inter, 0, dec.j_num).astype(np.int32)
+    pm = PottsModel(dec)
+    marg, _ = lbp(pm, 1.3, n_iter=4)
+    for S, m in zip(pm.sites, marg):
+        w = np.exp(-1.3 * (S.E - S.E.min()) / dec.denom)
+        assert np.allclose(m, w / w.sum(), rtol=1e-12)
+    marg, change = lbp(PottsModel(L.kings_grid(4, 4, 3)), 1.0, n_iter=6)
+    assert all(abs(m.sum() - 1) < 1e-12 and (m >= 0).all() for m in marg) and change > 0
+    assert list(top_states(np.array([0.1, 0.3, 0.3, 0.05, 0.25]), 3)) == [1, 2, 4]
