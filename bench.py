@@ -70,6 +70,21 @@ WORKLOADS = {
                                           states=lambda inst, seed: None, chi=8, M=64,
                                           desc="King's lattice 8x8 (class I), chi=8, M=64")),
 }
+# many independent Pegasus instances of uneven size per step, each on its own stream: P3..P7 nice
+# (2x2 .. 6x6 cells of 24 spins, 13/13/13/13/12 of each), 256 states per cell, beta 1, chi 32, M 128
+def _batch64(seed):
+    out = []
+    for i in range(64):
+        inst = L.pegasus_nice(3 + i % 5, seed * 1000 + i)
+        out.append((inst, L.hamming_ball_states(inst, 256, seed=seed * 1000 + i + 1)))
+    return out
+
+
+WORKLOADS["batch64_pegasus"] = dict(
+    desc="64 independent Pegasus instances of uneven size (P3..P7 nice: 2x2 to 6x6 cells, 96 to 864 spins), "
+         "d=256 states per cell, iid J,h in {+-1..+-7}/7, beta=1, chi=32, M=128, one stream each",
+    make=lambda seed: _batch64(seed)[0][0], states=lambda inst, seed: _batch64(seed)[0][1], batch=_batch64,
+    n_batch=64, threads=16, beta=1.0, chi=32, M=128, sweeps=2, d=256, oracle_sample=dict(_PEG_SAMPLE))
 # the same instances in all eight grid symmetries per step (Sec. IV: every instance is run from every corner)
 for _name in ("pegasus15x15", "kings50x50"):
     WORKLOADS[_name + "_x8"] = dict(WORKLOADS[_name], transforms=8,
@@ -171,8 +186,8 @@ def cpu_oracle(wl, seed, budget_s=15.0, max_runs=5):
 
 
 def bench_config(args, wl, ws=1):
-    return {"workload": args.workload, "description": wl["desc"], "instances_per_rank": 1,
-            "grid_symmetries_per_step": wl.get("transforms", 1),
+    return {"workload": args.workload, "description": wl["desc"],
+            "instances_per_rank": wl.get("n_batch", 1), "grid_symmetries_per_step": wl.get("transforms", 1),
             "beta": wl["beta"], "chi": wl["chi"], "M": wl["M"], "states_per_cell": wl.get("d"),
             "n_sweeps": wl["sweeps"], "precision": args.precision, "parallelism": f"replicas{ws}",
             "l2": "flushed between timed steps (256 MB write)"}
@@ -253,15 +268,23 @@ def run_native(args, wl):
     inst = wl["make"](args.seed + rank)
     states = wl["states"](inst, args.seed + rank) if wl["states"] else None
     prec, sprec, dtype_name = PRECISIONS[args.precision]
-    n_tr = wl.get("transforms", 1)
-    # the instance in each of its first n_tr grid symmetries, every one on its own stream
+    # the units of one step: the instance, or its first n grid symmetries, or a batch of
+    # independent instances; every unit on its own stream when there are several
+    if "batch" in wl:
+        units = wl["batch"](args.seed + rank)
+        inst, states = units[0]
+    elif wl.get("transforms", 1) > 1:
+        units = [(inst if k == 0 else L.transform(inst, k),
+                  states if (k == 0 or states is None) else L.transform_states(inst, states, k))
+                 for k in range(wl["transforms"])]
+    else:
+        units = [(inst, states)]
+    n_tr = len(units)
     t_streams = [stream] if n_tr == 1 else [torch.cuda.Stream() for _ in range(n_tr)]
 
     def make_handles():
         hs = []
-        for k in range(n_tr):
-            ti = inst if k == 0 else L.transform(inst, k)
-            tst = states if (k == 0 or states is None) else L.transform_states(inst, states, k)
+        for k, (ti, tst) in enumerate(units):
             hk = sgtn.Handle(ti, tst, stream=t_streams[k].cuda_stream)
             hk.set_search_precision(sprec)
             hs.append(hk)
@@ -280,11 +303,13 @@ def run_native(args, wl):
             lz = hs[0].contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])[0]
             return lz, hs[0].search(wl["M"])
         out = sgtn.batch_search(hs, wl["beta"], wl["chi"], wl["M"], precision=prec, n_sweeps=wl["sweeps"],
-                                raise_on_error=False)
+                                threads=wl.get("threads", 0), raise_on_error=False)
         ok = [i for i in range(len(out)) if out[i][1] is not None]
         failed_transforms[0] = len(out) - len(ok)
         if not ok:
-            raise RuntimeError("every grid symmetry failed: " + hs[0].L.sgtn_last_error(hs[0].h).decode())
+            raise RuntimeError("every unit failed: " + hs[0].L.sgtn_last_error(hs[0].h).decode())
+        if "batch" in wl:   # independent instances: report the first one's result
+            return out[0][0], out[0][1] if out[0][1] is not None else out[ok[0]][1]
         best = min(ok, key=lambda i: (int(out[i][1]["energy_num"][0]), i))
         return out[0][0], out[best][1]
 
@@ -353,10 +378,11 @@ def run_native(args, wl):
                     "rel_err": abs(logz - lz64) / abs(lz64) if ok else None}
     # end to end through the public API from host buffers: build (H2D) .. results (D2H)
     e2e_times = []
-    h2d = inst.ei.nbytes + inst.ej.nbytes + inst.j_num.nbytes + inst.h_num.nbytes + inst.site_of_spin.nbytes
-    if states is not None:
-        h2d += sum(np.asarray(x, np.int64).nbytes for x in states) + 8 * (len(states) + 1)
-    h2d *= n_tr
+    h2d = 0
+    for ui, us in units:
+        h2d += ui.ei.nbytes + ui.ej.nbytes + ui.j_num.nbytes + ui.h_num.nbytes + ui.site_of_spin.nbytes
+        if us is not None:
+            h2d += sum(np.asarray(x, np.int64).nbytes for x in us) + 8 * (len(us) + 1)
     d2h = 0
     for _ in range(max(1, min(args.steps, 2))):
         torch.cuda.synchronize()
@@ -365,7 +391,7 @@ def run_native(args, wl):
         _, r2 = run_all(hs2)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
-        d2h = n_tr * (r2["spins"].nbytes + r2["energy_num"].nbytes + r2["logp"].nbytes + 16)
+        d2h = sum(ui.n_spins + 8 + 8 + 8 + 8 for ui, _ in units)   # spins, energy, log p, log Z, p_d
         for h2 in hs2:
             h2.close()
     e2e_val = (evals / args.steps) / statistics.median(e2e_times) * ws
@@ -387,7 +413,7 @@ def run_native(args, wl):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype_name,
             "data": "synthetic",
             "config": dict(bench_config(args, wl, ws), unconverged_truncations=unconverged,
-                           failed_grid_symmetries=failed_transforms[0] if n_tr > 1 else None),
+                           failed_units=failed_transforms[0] if n_tr > 1 else None),
             "boundary_tflops": (bflops / args.steps) / (bound_ms * 1e-3) / 1e12,
             "boundary_ms": bound_ms,
             "logz_check": logz_err,

@@ -145,6 +145,27 @@ int sgtn_batch_search(sgtn_h* hs, int32_t n, double beta, int32_t chi, int32_t p
                       int32_t M, int32_t n_out, int8_t** out_spins, int64_t** out_energy_num, double** out_logp,
                       double* out_logz, double* out_pd, int32_t* out_count, int32_t n_threads, int32_t* status);
 
+/* Loopy belief propagation over the clusters (Sec. IV) at the current beta,
+ * for the local dimensional reduction: approximate marginals of every
+ * cluster's states from messages indexed by the projected classes of Eq. (4)
+ *   mu_{s->t}(a) = sum_{x: P^{st}(x)=a} exp(-beta E_x) prod_{t'!=t} nu_{t'->s}(P^{st'}(x))
+ *   nu_{s->t}(b) = sum_a exp(-beta Ebar^{st}[a,b]) mu_{s->t}(a)
+ *   p(x_s) ~ exp(-beta E_x) prod_t nu_{t->s}(P^{st}(x)),
+ * t running over the sites that share a coupling with s.  n_iter synchronous
+ * iterations from nu = 1, every nu scaled to sum 1 after its update.
+ *   out_index[R*C][k]   positions (in the site's state list) of the k most
+ *                       probable states of every site, most probable first,
+ *                       ties to the smaller position; -1 past out_count
+ *   out_marginal[R*C][k] their marginals (a site's marginals sum to 1 over
+ *                       all of its states)
+ *   out_count[R*C]      min(k, states of the site)
+ *   *out_change         largest |nu_new - nu_old| of the last iteration (may
+ *                       be NULL; 0 when n_iter = 0)
+ * Host buffers.  Requires set_beta; sites of at most 2^20 states (the
+ * ranking is quadratic in the states of a site). */
+int sgtn_lbp(sgtn_h h, int32_t n_iter, int32_t k, int32_t* out_index, double* out_marginal, int32_t* out_count,
+             double* out_change);
+
 /* Gradient of log Z (Eq. 9): dJ[k] = d log Z / dJ_k = -beta <s_i s_j> for edge
  * k, dh[i] = -beta <s_i>, *dbeta = -<H>, evaluated as environment
  * correlators: row r is averaged in the sandwich <E_r| T_r |psi_r> of the

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsgtn.so")
-SOURCES = ["model.cpp", "kernels_f64.cu", "setup.cu", "boundary.cu", "branch.cu", "api.cu", "noalloc.cu", "grad.cu", "tc_gemm.cu"]
+SOURCES = ["model.cpp", "kernels_f64.cu", "setup.cu", "boundary.cu", "branch.cu", "api.cu", "noalloc.cu", "grad.cu", "tc_gemm.cu", "lbp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

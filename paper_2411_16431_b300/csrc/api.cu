@@ -169,6 +169,18 @@ int sgtn_search(sgtn_h h, int32_t M, int32_t n_out, int8_t* out_spins, int64_t* 
   });
 }
 
+int sgtn_lbp(sgtn_h h, int32_t n_iter, int32_t k, int32_t* out_index, double* out_marginal, int32_t* out_count,
+             double* out_change) {
+  return guarded(h, [&] {
+    if (!h->beta_set) throw SgtnError(SGTN_ERR_STATE, "set_beta must run first");
+    if (n_iter < 0 || k < 1 || !out_index || !out_marginal || !out_count)
+      throw SgtnError(SGTN_ERR_ARG, "bad n_iter, k or null output");
+    for (const auto& S : h->M.sites)
+      if (S.d > (1 << 20)) throw SgtnError(SGTN_ERR_ARG, "a site has more than 2^20 states");
+    lbp(h, n_iter, k, out_index, out_marginal, out_count, out_change);
+  });
+}
+
 int sgtn_logz_grad(sgtn_h h, double* dJ, double* dh, double* dbeta) {
   return guarded(h, [&] {
     if (!dh || !dbeta || (!dJ && !h->M.ei.empty())) throw SgtnError(SGTN_ERR_ARG, "null output");

@@ -130,6 +130,8 @@ void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_
 void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_energy, double* out_logp, double* out_pd,
             int32_t* out_count);
 void energies(sgtn_inst* h, int n, const int8_t* spins, int64_t* out);
+void lbp(sgtn_inst* h, int n_iter, int k, int32_t* out_index, double* out_marginal, int32_t* out_count,
+         double* out_change);
 void logz_grad(sgtn_inst* h, double* dJ, double* dh, double* dbeta);
 size_t scores_scratch_bytes(sgtn_inst* h, int step, int K);
 void conditionals_arena(sgtn_inst* h, int step, int count, const int32_t* configs, double* out_p, void* arena,

@@ -44,6 +44,7 @@ def load():
     L.sgtn_conditionals_noalloc.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I32P, _F64P]
     L.sgtn_energies.argtypes = [ct.c_void_p, ct.c_int32, _I8P, _I64P]
     L.sgtn_logz_grad.argtypes = [ct.c_void_p, _F64P, _F64P, _F64P]
+    L.sgtn_lbp.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I32P, _F64P, _I32P, _F64P]
     L.sgtn_batch_search.argtypes = [ct.POINTER(ct.c_void_p), ct.c_int32, ct.c_double, ct.c_int32, ct.c_int32,
                                     ct.c_int32, ct.c_int32, ct.c_int32, ct.POINTER(_I8P), ct.POINTER(_I64P),
                                     ct.POINTER(_F64P), _F64P, _F64P, _I32P, ct.c_int32, _I32P]
@@ -206,6 +207,18 @@ class Handle:
         k = cnt.value
         return dict(spins=sp[:k], energy_num=en[:k], logp=lp[:k], pd=pd.value)
 
+    def lbp(self, n_iter, k):
+        """Loopy belief propagation (sgtn_lbp): per site the positions of its k most
+        probable states and their marginals, and the last iteration's message change."""
+        ns = self.inst.rows * self.inst.cols
+        idx = np.zeros((ns, k), np.int32)
+        marg = np.zeros((ns, k))
+        cnt = np.zeros(ns, np.int32)
+        chg = ct.c_double()
+        self._ck(self.L.sgtn_lbp(self.h, n_iter, k, _p(idx, _I32P), _p(marg, _F64P), _p(cnt, _I32P),
+                                 ct.byref(chg)))
+        return [idx[s, :cnt[s]] for s in range(ns)], [marg[s, :cnt[s]] for s in range(ns)], chg.value
+
     def logz_grad(self):
         """(dlogZ/dJ[n_edges], dlogZ/dh[n_spins], dlogZ/dbeta) for the current beta and boundary."""
         dJ = np.zeros(max(self.inst.n_edges, 1))
@@ -289,6 +302,26 @@ def _logz_function():
 
     _LOGZ_FN = _LogZ
     return _LOGZ_FN
+
+
+def lbp_reduce(inst, beta, n_iter, k, states_per_site=None, stream=None):
+    """Local dimensional reduction (Sec. IV): the k most probable states of every
+    cluster by loopy belief propagation at beta, as state lists (bit patterns) for
+    a new Handle.  ``states_per_site`` is the pool to choose from (None: every
+    state of each cluster).  Returns (state lists, marginals, last message change)."""
+    h = Handle(inst, states_per_site, stream=stream)
+    try:
+        h.set_beta(beta)
+        idx, marg, chg = h.lbp(n_iter, k)
+    finally:
+        h.close()
+    out = []
+    for s, ix in enumerate(idx):
+        if states_per_site is None:
+            out.append(np.asarray(ix, np.int64))   # full enumeration: position == bit pattern
+        else:
+            out.append(np.asarray(states_per_site[s], np.int64)[ix])
+    return out, marg, chg
 
 
 def batch_search(handles, beta, chi, M, precision=FP64, n_sweeps=2, n_out=1, threads=0, raise_on_error=True):

@@ -455,3 +455,45 @@ def test_tall_skinny_svd_path_matches_oracle(Handle, monkeypatch):
     h2.set_beta(beta)
     lz2, _ = h2.contract_boundary(chi, n_sweeps=2)
     assert abs(lz2 - lz_o) < RTOL * abs(lz_o)
+
+
+LBP_CASES = [(L.chimera_grid(4, 4, 0), None, 1.0, 8), (L.kings_grid(5, 6, 4, couplings="uniform"), None, 2.0, 10),
+             (PEG, PEG_STATES, 0.8, 6), (L.slice_cells(L.chimera_grid(4, 4, 3), 1, 3), None, 0.7, 4),
+             (L.kings_grid(1, 7, 4), None, 1.5, 8), (L.chimera_grid(3, 3, 2), None, 1.0, 0)]
+
+
+@pytest.mark.parametrize("case", LBP_CASES, ids=lambda c: f"{c[0].name}_it{c[3]}")
+def test_lbp_matches_oracle(Handle, case):
+    """sgtn_lbp: marginals of the kept states, the kept set (up to ties within 1e-10)
+    and the last message change agree with the oracle's belief propagation."""
+    from oracle.lbp import lbp as oracle_lbp, top_states
+    inst, states, beta, n_iter = case
+    marg_o, chg_o = oracle_lbp(PottsModel(inst, states), beta, n_iter)
+    h = Handle(inst, states)
+    h.set_beta(beta)
+    k = 12
+    idx, marg, chg = h.lbp(n_iter, k)
+    assert abs(chg - chg_o) <= 1e-12
+    for s, mo in enumerate(marg_o):
+        kk = min(k, len(mo))
+        assert len(idx[s]) == kk
+        assert np.allclose(marg[s], mo[idx[s]], rtol=1e-10, atol=0)
+        thr = mo[top_states(mo, kk)[-1]]
+        assert set(np.nonzero(mo > thr * (1 + 1e-10))[0]) <= set(idx[s].tolist())
+        assert all(mo[i] >= thr * (1 - 1e-10) for i in idx[s])
+        assert np.all(np.diff(marg[s]) <= 0)
+    h.close()
+
+
+def test_lbp_reduction_feeds_the_search(Handle):
+    """Reduce the 12-state pool of every cell to its 8 most probable states by belief
+    propagation, then contract and search on the reduced model: exact energies."""
+    from paper_2411_16431_b300 import sgtn
+    red, marg, chg = sgtn.lbp_reduce(PEG, 0.8, 6, 8, states_per_site=PEG_STATES)
+    assert all(len(r) == 8 and set(r.tolist()) <= set(np.asarray(p).tolist()) for r, p in zip(red, PEG_STATES))
+    h = Handle(PEG, red)
+    h.set_beta(0.8)
+    h.contract_boundary(6, n_sweeps=1)
+    res = h.search(16)
+    assert PEG.energy_num(res["spins"][0]) == int(res["energy_num"][0])
+    h.close()
