@@ -353,6 +353,16 @@ def batch_search(handles, beta, chi, M, precision=FP64, n_sweeps=2, n_out=1, thr
                                 pd=float(pd[i]))) if status[i] == 0 else (float("nan"), None) for i in range(n)]
 
 
+def logz_spread(runs):
+    """Standard deviation of log Z over the grid symmetries of one instance (the
+    stability test of App. C compares Z from the eight contraction corners; the
+    spread of log Z is its relative spread, and stays finite where Z overflows).
+    NaN entries (undefined log Z) are left out; NaN if fewer than two remain."""
+    v = np.array([r[1] for r in runs], dtype=np.float64)
+    v = v[np.isfinite(v)]
+    return float(np.std(v)) if len(v) >= 2 else float("nan")
+
+
 def search_transforms(inst, beta, chi, M, states_per_site=None, precision=FP64, n_sweeps=2, transforms=range(8),
                       streams=None):
     """Boundary contraction + search of the instance in each of the grid
@@ -362,7 +372,8 @@ def search_transforms(inst, beta, chi, M, states_per_site=None, precision=FP64, 
     concurrently through sgtn_batch_search; None runs them one after another
     on the default stream.  Spins keep their indices, so the returned states
     and energies are comparable.  Returns (index of the best, list of
-    (transform, log Z, search result))."""
+    (transform, log Z, search result)); ``logz_spread(runs)`` gives the
+    contraction-stability measure of App. C over them."""
     from . import lattices as L
     ks = list(transforms)
     if streams is not None and len(streams) != len(ks):

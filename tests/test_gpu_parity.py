@@ -307,6 +307,10 @@ def test_grid_symmetries_on_the_gpu(Handle):
     assert energies[best] >= brute.ground_state(inst)[1]
     for _, _, r in runs:
         assert inst.energy_num(r["spins"][0]) == int(r["energy_num"][0])
+    assert sgtn.logz_spread(runs) >= 0
+    # untruncated: every corner gives the exact log Z, so the spread vanishes
+    _, runs64 = sgtn.search_transforms(inst, beta, chi=64, M=8, n_sweeps=1, streams=[s.cuda_stream for s in ss])
+    assert sgtn.logz_spread(runs64) < 1e-10 * abs(ref)
 
 
 def test_batch_search_matches_one_by_one(Handle):
