@@ -384,3 +384,44 @@ def test_lbp_limits():
     marg, change = lbp(PottsModel(L.kings_grid(4, 4, 3)), 1.0, n_iter=6)
     assert all(abs(m.sum() - 1) < 1e-12 and (m >= 0).all() for m in marg) and change > 0
     assert list(top_states(np.array([0.1, 0.3, 0.3, 0.05, 0.25]), 3)) == [1, 2, 4]
+
+
+# --- droplets (Fig. 4) ----------------------------------------------------------------
+
+@pytest.mark.parametrize("inst", [L.kings_grid(4, 4, 3), L.slice_cells(L.chimera_grid(4, 4, 0), 2, 1),
+                                  L.kings_grid(3, 5, 6, couplings="uniform")], ids=lambda i: i.name)
+def test_droplets_are_exact_excitations(inst):
+    """Every droplet of the best configuration is an excitation whose energy, recomputed
+    from scratch on the flipped configuration, is E_best + dE; it is connected, within the
+    energy window and farther than the Hamming threshold from the others.  With exact
+    marginals and no cut the main branch of a merge has the lowest interior energy, so
+    every dE >= 0."""
+    from oracle.droplets import adjacency, connected, search_droplets
+    max_dE, hmin = 6 * inst.denom, 1
+    res = search_droplets(inst, 1.2, chi=256, M=10 ** 6, max_dE=max_dE, min_hamming=hmin, n_sweeps=1)
+    s = res["pm"].spins_of_config(res["config"])
+    E0 = inst.energy_num(s)
+    assert E0 == brute.ground_state(inst)[1]
+    adj = adjacency(inst)
+    assert res["droplets"]
+    for dE, F in res["droplets"]:
+        t = s.copy()
+        t[F] *= -1
+        assert inst.energy_num(t) == E0 + dE
+        assert 0 <= dE <= max_dE and connected(F, adj)
+    Fs = [set(F) for _, F in res["droplets"]]
+    assert all(len(a ^ b) > hmin for i, a in enumerate(Fs) for b in Fs[i + 1:])
+
+
+def test_droplet_filters():
+    """The Fig. 4 filters on hand-made droplets: energy window, connectivity, and the
+    Hamming rule (a closer, lower droplet replaces every droplet it clashes with)."""
+    from oracle.droplets import try_insert
+    adj = [[1], [0, 2], [1, 3], [2], []]          # path 0-1-2-3, isolated 4
+    d = try_insert([], (5, frozenset({0, 1})), 10, 1, adj)
+    assert d == [(5, frozenset({0, 1}))]
+    assert try_insert(d, (11, frozenset({3})), 10, 1, adj) == d          # above the window
+    assert try_insert(d, (1, frozenset({0, 2})), 10, 1, adj) == d        # not connected
+    assert try_insert(d, (7, frozenset({1})), 10, 1, adj) == d           # clashes, not lower
+    assert try_insert(d, (3, frozenset({1})), 10, 1, adj) == [(3, frozenset({1}))]
+    assert try_insert(d, (3, frozenset({2, 3})), 10, 1, adj) == d + [(3, frozenset({2, 3}))]
