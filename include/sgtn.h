@@ -126,6 +126,27 @@ int sgtn_branch_step(sgtn_h h, int32_t step, int32_t M, int32_t in_count, const 
 int sgtn_search(sgtn_h h, int32_t M, int32_t n_out, int8_t* out_spins, int64_t* out_energy_num,
                 double* out_logp, double* out_pd, int32_t* out_count);
 
+/* Search with the excitation bookkeeping of Fig. 4: as sgtn_search (n_out =
+ * 1), and the droplets of the best configuration -- low-energy excitations
+ * found where the bounding merged candidates with the same boundary (Eq. 7).
+ * A merged-away candidate gives the main branch a droplet (the spins where it
+ * differs, and the exact energy change dE, numerator over denom); its own
+ * droplets are carried over too.  Kept: dE <= max_dE_num, spins connected in
+ * the interaction graph (couplings J != 0), and pairwise more than
+ * min_hamming flips apart (a closer droplet replaces the ones it clashes
+ * with only if its dE is lower than theirs).
+ *   out_spins[n_spins], *out_energy_num, *out_logp, *out_pd: the best
+ *     configuration, as sgtn_search
+ *   *out_ndrop   number of droplets (may exceed cap)
+ *   out_dE[cap], out_offsets[cap+1], out_flips[cap * n_spins]: the first
+ *     min(cap, ndrop) droplets in order of (dE, flipped spins); the spins of
+ *     droplet i are out_flips[out_offsets[i] .. out_offsets[i+1]), increasing.
+ * Flipping them in out_spins gives a configuration of energy
+ * out_energy_num + out_dE[i].  Host buffers. */
+int sgtn_search_droplets(sgtn_h h, int32_t M, int64_t max_dE_num, int32_t min_hamming, int32_t cap,
+                         int8_t* out_spins, int64_t* out_energy_num, double* out_logp, double* out_pd,
+                         int32_t* out_ndrop, int64_t* out_dE, int32_t* out_offsets, int32_t* out_flips);
+
 /* Many independent searches at once (instances of different sizes, or the
  * eight grid symmetries of one instance, Sec. IV): for every handle i,
  * set_beta(beta), contract_boundary(chi, precision, n_sweeps) and

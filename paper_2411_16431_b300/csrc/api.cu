@@ -181,6 +181,30 @@ int sgtn_lbp(sgtn_h h, int32_t n_iter, int32_t k, int32_t* out_index, double* ou
   });
 }
 
+int sgtn_search_droplets(sgtn_h h, int32_t M, int64_t max_dE_num, int32_t min_hamming, int32_t cap,
+                         int8_t* out_spins, int64_t* out_energy_num, double* out_logp, double* out_pd,
+                         int32_t* out_ndrop, int64_t* out_dE, int32_t* out_offsets, int32_t* out_flips) {
+  return guarded(h, [&] {
+    if (cap < 0 || min_hamming < 0 || !out_ndrop || (cap > 0 && (!out_dE || !out_offsets || !out_flips)))
+      throw SgtnError(SGTN_ERR_ARG, "bad cap, min_hamming or null output");
+    PrecisionScope ps(h, true);
+    DropletOpts o;
+    o.max_dE = max_dE_num;
+    o.min_hamming = min_hamming;
+    std::vector<Drop> drops;
+    int32_t cnt = 0;
+    search(h, M, 1, out_spins, out_energy_num, out_logp, out_pd, &cnt, &o, &drops);
+    *out_ndrop = int32_t(drops.size());
+    const int nw = std::min<int>(cap, int(drops.size()));
+    if (cap > 0) out_offsets[0] = 0;
+    for (int i = 0; i < nw; ++i) {
+      out_dE[i] = drops[i].dE;
+      std::copy(drops[i].flips.begin(), drops[i].flips.end(), out_flips + out_offsets[i]);
+      out_offsets[i + 1] = out_offsets[i] + int32_t(drops[i].flips.size());
+    }
+  });
+}
+
 int sgtn_logz_grad(sgtn_h h, double* dJ, double* dh, double* dbeta) {
   return guarded(h, [&] {
     if (!dh || !dbeta || (!dJ && !h->M.ei.empty())) throw SgtnError(SGTN_ERR_ARG, "null output");

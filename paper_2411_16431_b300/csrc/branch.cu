@@ -21,8 +21,12 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <deque>
+#include <iterator>
+#include <memory>
 #include <numeric>
 #include <string>
+#include <unordered_map>
 
 #include "handle.h"
 
@@ -628,8 +632,17 @@ void conditionals_arena(sgtn_inst* h, int step, int count, const int32_t* config
 
 // Steps 3-5 from the scores S.s of the K = S.K branches: log p, merge, top-M.
 // out_parent (optional) receives the branch index of every survivor.
+// One step's merges seen from the host, for the droplet bookkeeping of
+// Fig. 4: every valid candidate that was merged away while its group's winner
+// survived the top-M cut, with that winner's position in the kept list.
+struct MergeLosers {
+  std::vector<long long> cand;   // candidate index k * d + x
+  std::vector<int> winner;
+};
+
 void select_step(Step& S, int step, int M, const int32_t* in_configs, const double* in_logp, int32_t* out_configs,
-                 double* out_logp, int32_t* out_count, double* io_pd, int32_t* out_parent) {
+                 double* out_logp, int32_t* out_count, double* io_pd, int32_t* out_parent,
+                 MergeLosers* losers = nullptr) {
   sgtn_inst* h = S.h;
   cudaStream_t st = h->st;
   const int C = h->M.C;
@@ -805,6 +818,22 @@ void select_step(Step& S, int step, int M, const int32_t* in_configs, const doub
     }
     *out_count = outc;
     if (hlost) *io_pd = std::max(*io_pd, key_to_double(hlost));
+    if (losers) {
+      // merge groups are (parent class, class of x toward the unplaced sites)
+      const std::vector<int32_t>& xkc = site.Xk.of_state;
+      std::unordered_map<long long, int> win_of;
+      for (int i = 0; i < outc; ++i) {
+        const long long ci = keep[i];
+        win_of[(long long)hpc[ci / d] * nX + xkc[ci % d]] = i;
+      }
+      for (long long ci = 0; ci < ncand; ++ci) {
+        if (!(hlp[ci] > -INFINITY)) continue;
+        auto it = win_of.find((long long)hpc[ci / d] * nX + xkc[ci % d]);
+        if (it == win_of.end() || keep[it->second] == ci) continue;
+        losers->cand.push_back(ci);
+        losers->winner.push_back(it->second);
+      }
+    }
   }
   h->check();
   (void)C;
@@ -825,8 +854,174 @@ void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_
   select_step(S, step, M, in_configs, in_logp, out_configs, out_logp, out_count, io_pd, nullptr);
 }
 
+namespace {
+// Host-side droplet bookkeeping (Fig. 4).  A main branch keeps its parent's
+// droplets, then takes its merged-away candidates in order of (dE,
+// configuration): each one's own droplet (the spins where it differs from the
+// main branch, with the exact energy change) and its parent's droplets
+// carried over (F xor F', dE + dE').  A droplet is kept if dE <= max_dE, its
+// spins are connected in the interaction graph (J != 0), and it replaces
+// every kept droplet within min_hamming flips only if its dE is lower than
+// all of theirs.  Energies are exact int64 numerators: the energy of the
+// placed clusters changes by E_x plus the compressed couplings to the placed
+// neighbours (Eq. 2), and spins coupled to unplaced clusters are equal across
+// a merge group, so dE holds for every completion.
+struct DropletBook {
+  sgtn_inst* h;
+  DropletOpts opt;
+  std::vector<std::vector<int32_t>> adj;
+  std::vector<std::vector<Drop>> drops{std::vector<Drop>()};
+  std::vector<long long> ep{0};          // energy of the placed clusters, per beam entry
+  std::vector<char> mark;
+
+  DropletBook(sgtn_inst* hh, const DropletOpts& o) : h(hh), opt(o) {
+    const Model& M = h->M;
+    adj.assign(M.N, {});
+    for (size_t e = 0; e < M.ei.size(); ++e)
+      if (M.jn[e] != 0) {
+        adj[M.ei[e]].push_back(M.ej[e]);
+        adj[M.ej[e]].push_back(M.ei[e]);
+      }
+    mark.assign(M.N, 0);
+  }
+  // energy added by placing state x at `step` after the parent configuration pc
+  long long inc(int step, const int32_t* pc, int x) const {
+    const Model& M = h->M;
+    const int C = M.C, r = step / C, c = step % C;
+    const HSite& S = M.sites[step];
+    long long e = S.E[x];
+    auto add = [&](int q, int slot, Dir dq, Dir ds) {
+      const HTable& T = M.tab[size_t(q) * 4 + slot];
+      const int a = M.sites[q].proj[dq].of_state[pc[q]], b = S.proj[ds].of_state[x];
+      e += T.E[size_t(a) * T.nB + b];
+    };
+    if (c > 0) add(step - 1, 0, DR_, DL_);
+    if (r > 0) add(step - C, 1, DD, DU);
+    if (r > 0 && c > 0) add(step - C - 1, 2, DDR, DUL);
+    if (r > 0 && c + 1 < C) add(step - C + 1, 3, DDL, DUR);
+    return e;
+  }
+  bool connected(const std::vector<int32_t>& F) {
+    if (F.empty()) return false;
+    for (int v : F) mark[v] = 1;
+    std::vector<int32_t> todo{F[0]};
+    mark[F[0]] = 2;
+    size_t seen = 1;
+    while (!todo.empty()) {
+      const int u = todo.back();
+      todo.pop_back();
+      for (int v : adj[u])
+        if (mark[v] == 1) {
+          mark[v] = 2;
+          ++seen;
+          todo.push_back(v);
+        }
+    }
+    for (int v : F) mark[v] = 0;
+    return seen == F.size();
+  }
+  static std::vector<int32_t> symdiff(const std::vector<int32_t>& a, const std::vector<int32_t>& b) {
+    std::vector<int32_t> o;
+    std::set_symmetric_difference(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(o));
+    return o;
+  }
+  static size_t hamming(const std::vector<int32_t>& a, const std::vector<int32_t>& b) {
+    size_t i = 0, j = 0, n = 0;
+    while (i < a.size() && j < b.size()) {
+      if (a[i] == b[j]) ++i, ++j;
+      else if (a[i] < b[j]) ++i, ++n;
+      else ++j, ++n;
+    }
+    return n + (a.size() - i) + (b.size() - j);
+  }
+  void insert(std::vector<Drop>& lst, Drop&& cand) {
+    if (cand.dE > opt.max_dE || !connected(cand.flips)) return;
+    std::vector<size_t> clash;
+    long long lo = LLONG_MAX;
+    for (size_t i = 0; i < lst.size(); ++i)
+      if (hamming(lst[i].flips, cand.flips) <= size_t(opt.min_hamming)) {
+        clash.push_back(i);
+        lo = std::min(lo, lst[i].dE);
+      }
+    if (clash.empty()) {
+      lst.push_back(std::move(cand));
+    } else if (cand.dE < lo) {
+      std::vector<Drop> keep;
+      size_t q = 0;
+      for (size_t i = 0; i < lst.size(); ++i) {
+        if (q < clash.size() && clash[q] == i) {
+          ++q;
+          continue;
+        }
+        keep.push_back(std::move(lst[i]));
+      }
+      keep.push_back(std::move(cand));
+      lst.swap(keep);
+    }
+  }
+  // spins where configuration (row a of A + xa) and (row b of B + xb) differ
+  std::vector<int32_t> flips(int step, const int32_t* pa, int xa, const int32_t* pb, int xb) const {
+    const Model& M = h->M;
+    std::vector<int32_t> F;
+    for (int p = 0; p <= step; ++p) {
+      const int sa = p < step ? pa[p] : xa, sb = p < step ? pb[p] : xb;
+      if (sa == sb) continue;
+      const HSite& P = M.sites[p];
+      const int64_t z = P.states[sa] ^ P.states[sb];
+      for (size_t j = 0; j < P.spins.size(); ++j)
+        if ((z >> j) & 1) F.push_back(P.spins[j]);
+    }
+    std::sort(F.begin(), F.end());
+    return F;
+  }
+  // after select_step: cfg (stride step) the old beam, ncfg (stride step+1) the kept one
+  void step(int step, const std::vector<int32_t>& cfg, const std::vector<int32_t>& ncfg, int oc,
+            const std::vector<int32_t>& par, const MergeLosers& ml) {
+    const int d = h->M.sites[step].d, w1 = step + 1;
+    auto prow = [&](int k) { return cfg.data() + (size_t)k * step; };
+    std::vector<long long> nep(oc);
+    for (int i = 0; i < oc; ++i) nep[i] = ep[par[i]] + inc(step, prow(par[i]), ncfg[(size_t)i * w1 + step]);
+    std::vector<std::vector<std::pair<long long, long long>>> byw(oc);
+    for (size_t j = 0; j < ml.cand.size(); ++j) {
+      const long long ci = ml.cand[j];
+      const int k = int(ci / d), x = int(ci % d), w = ml.winner[j];
+      byw[w].push_back({ep[k] + inc(step, prow(k), x) - nep[w], ci});
+    }
+    std::vector<std::vector<Drop>> nd(oc);
+    for (int i = 0; i < oc; ++i) {
+      std::vector<Drop> lst = drops[par[i]];
+      auto& L = byw[i];
+      std::sort(L.begin(), L.end(), [&](const std::pair<long long, long long>& a, const std::pair<long long, long long>& b) {
+        if (a.first != b.first) return a.first < b.first;
+        const int ka = int(a.second / d), kb = int(b.second / d);
+        const int32_t *ra = prow(ka), *rb = prow(kb);
+        for (int p = 0; p < step; ++p)
+          if (ra[p] != rb[p]) return ra[p] < rb[p];
+        return a.second % d < b.second % d;
+      });
+      const int32_t* wrow = prow(par[i]);
+      const int wx = ncfg[(size_t)i * w1 + step];
+      for (const auto& lc : L) {
+        const long long dE = lc.first;
+        const int k = int(lc.second / d), x = int(lc.second % d);
+        const std::vector<Drop>& pl = drops[k];
+        long long lo = dE;
+        for (const Drop& q : pl) lo = std::min(lo, dE + q.dE);
+        if (lo > opt.max_dE) continue;   // nothing from this candidate fits the window
+        const std::vector<int32_t> F = flips(step, wrow, wx, prow(k), x);
+        insert(lst, Drop{dE, F});
+        for (const Drop& q : pl) insert(lst, Drop{dE + q.dE, symdiff(F, q.flips)});
+      }
+      nd[i] = std::move(lst);
+    }
+    drops.swap(nd);
+    ep.swap(nep);
+  }
+};
+}  // namespace
+
 void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_energy, double* out_logp, double* out_pd,
-            int32_t* out_count) {
+            int32_t* out_count, const DropletOpts* dopt, std::vector<Drop>* dout) {
   if (!h->boundary_ok) throw SgtnError(-2, "contract_boundary must run first");
   if (M <= 0 || n_out <= 0 || !out_spins || !out_energy || !out_logp || !out_pd || !out_count)
     throw SgtnError(-1, "bad argument");
@@ -849,6 +1044,8 @@ void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_ener
   double* E = nullptr;
   int ebuf = 0;
   size_t cap = size_t(64) << 20;   // per-step scratch; grows after a step that needed more
+  std::unique_ptr<DropletBook> book;
+  if (dopt) book.reset(new DropletBook(h, *dopt));
   for (int step = 0; step < RC; ++step) {
     const int r = step / C, c = step % C, K = count;
     Step S;
@@ -939,8 +1136,11 @@ void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_ener
     nlp.assign(M, 0.0);
     par.assign(M, 0);
     int oc = 0;
-    select_step(S, step, M, cfg.data(), lp.data(), ncfg.data(), nlp.data(), &oc, &pd, par.data());
+    MergeLosers ml;
+    select_step(S, step, M, cfg.data(), lp.data(), ncfg.data(), nlp.data(), &oc, &pd, par.data(),
+                book ? &ml : nullptr);
     h->sync();   // the inputs of this step (host vectors) are replaced below
+    if (book) book->step(step, cfg, ncfg, oc, par, ml);
     if (S.spilled) cap += 2 * S.spilled;
     cfg.assign(ncfg.begin(), ncfg.begin() + size_t(oc) * (step + 1));
     lp.assign(nlp.begin(), nlp.begin() + oc);
@@ -961,6 +1161,12 @@ void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_ener
   for (int i = 0; i < nw; ++i) out_logp[i] = lp[i];
   *out_pd = pd;
   *out_count = nw;
+  if (book && dout) {
+    *dout = book->drops[0];
+    std::sort(dout->begin(), dout->end(), [](const Drop& a, const Drop& b) {
+      return a.dE != b.dE ? a.dE < b.dE : a.flips < b.flips;
+    });
+  }
 }
 
 }  // namespace sgtn

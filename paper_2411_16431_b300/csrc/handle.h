@@ -127,8 +127,18 @@ void contract_boundary(sgtn_inst* h, int chi, int n_sweeps);
 void conditionals(sgtn_inst* h, int step, int count, const int32_t* configs, double* out_p);
 void branch_step(sgtn_inst* h, int step, int M, int in_count, const int32_t* in_configs, const double* in_logp,
                  int32_t* out_configs, double* out_logp, int32_t* out_count, double* io_pd);
+// Droplets of Fig. 4 (the excitation bookkeeping of the merges)
+struct DropletOpts {
+  long long max_dE = 0;   // energy window (numerator over denom)
+  int min_hamming = 0;    // kept droplets differ pairwise in more flips than this
+};
+struct Drop {
+  long long dE = 0;
+  std::vector<int32_t> flips;   // spin ids, increasing
+};
 void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_energy, double* out_logp, double* out_pd,
-            int32_t* out_count);
+            int32_t* out_count,
+            const DropletOpts* dopt = nullptr, std::vector<Drop>* dout = nullptr);
 void energies(sgtn_inst* h, int n, const int8_t* spins, int64_t* out);
 void lbp(sgtn_inst* h, int n_iter, int k, int32_t* out_index, double* out_marginal, int32_t* out_count,
          double* out_change);

@@ -45,6 +45,8 @@ def load():
     L.sgtn_energies.argtypes = [ct.c_void_p, ct.c_int32, _I8P, _I64P]
     L.sgtn_logz_grad.argtypes = [ct.c_void_p, _F64P, _F64P, _F64P]
     L.sgtn_lbp.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I32P, _F64P, _I32P, _F64P]
+    L.sgtn_search_droplets.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_int32, ct.c_int32, _I8P, _I64P,
+                                       _F64P, _F64P, _I32P, _I64P, _I32P, _I32P]
     L.sgtn_batch_search.argtypes = [ct.POINTER(ct.c_void_p), ct.c_int32, ct.c_double, ct.c_int32, ct.c_int32,
                                     ct.c_int32, ct.c_int32, ct.c_int32, ct.POINTER(_I8P), ct.POINTER(_I64P),
                                     ct.POINTER(_F64P), _F64P, _F64P, _I32P, ct.c_int32, _I32P]
@@ -218,6 +220,25 @@ class Handle:
         self._ck(self.L.sgtn_lbp(self.h, n_iter, k, _p(idx, _I32P), _p(marg, _F64P), _p(cnt, _I32P),
                                  ct.byref(chg)))
         return [idx[s, :cnt[s]] for s in range(ns)], [marg[s, :cnt[s]] for s in range(ns)], chg.value
+
+    def search_droplets(self, M, max_dE_num, min_hamming, cap=4096):
+        """sgtn_search_droplets: the best configuration and its droplets (Fig. 4) as a
+        list of (dE numerator, flipped spin ids), in order of (dE, spins)."""
+        N = self.inst.n_spins
+        sp = np.zeros(N, np.int8)
+        en = ct.c_int64()
+        lp = ct.c_double()
+        pd = ct.c_double()
+        nd = ct.c_int32()
+        dE = np.zeros(max(cap, 1), np.int64)
+        off = np.zeros(max(cap, 1) + 1, np.int32)
+        fl = np.zeros(max(cap, 1) * N, np.int32)
+        self._ck(self.L.sgtn_search_droplets(self.h, M, int(max_dE_num), min_hamming, cap, _p(sp, _I8P),
+                                             ct.byref(en), ct.byref(lp), ct.byref(pd), ct.byref(nd), _p(dE, _I64P),
+                                             _p(off, _I32P), _p(fl, _I32P)))
+        k = min(cap, nd.value)
+        drops = [(int(dE[i]), fl[off[i]:off[i + 1]].copy()) for i in range(k)]
+        return dict(spins=sp, energy_num=en.value, logp=lp.value, pd=pd.value, droplets=drops, n_droplets=nd.value)
 
     def logz_grad(self):
         """(dlogZ/dJ[n_edges], dlogZ/dh[n_spins], dlogZ/dbeta) for the current beta and boundary."""

@@ -501,3 +501,31 @@ def test_lbp_reduction_feeds_the_search(Handle):
     res = h.search(16)
     assert PEG.energy_num(res["spins"][0]) == int(res["energy_num"][0])
     h.close()
+
+
+DROP_CASES = [(L.chimera_grid(4, 4, 0), None, 1.0, 16, 64, 2, 8 * 7, 1),
+              (L.kings_grid(5, 6, 4, couplings="uniform"), None, 2.0, 4, 16, 1, 3000, 2),
+              (PEGP, PEGP_STATES, 2.0, 8, 16, 2, 10 * 7, 1),
+              (L.kings_grid(4, 4, 3), None, 1.2, 256, 10 ** 6, 1, 6 * 7, 1)]
+
+
+@pytest.mark.parametrize("case", DROP_CASES, ids=lambda c: c[0].name)
+def test_droplets_match_oracle(Handle, case):
+    """sgtn_search_droplets: the best configuration and every droplet (exact dE and the
+    same flipped spins) equal the oracle's bookkeeping of the same search, and each
+    droplet's flipped configuration has energy E + dE."""
+    from oracle.droplets import search_droplets
+    inst, states, beta, chi, M, ns, max_dE, hmin = case
+    ref = search_droplets(inst, beta, chi, M, max_dE, hmin, n_sweeps=ns, states=states)
+    h = Handle(inst, states)
+    h.set_beta(beta)
+    h.contract_boundary(chi, n_sweeps=ns)
+    res = h.search_droplets(M, max_dE, hmin)
+    assert res["energy_num"] == ref["energy_num"]
+    assert res["n_droplets"] == len(ref["droplets"]) > 0
+    for (dE, F), (rE, rF) in zip(res["droplets"], ref["droplets"]):
+        assert dE == rE and F.tolist() == list(rF)
+        t = res["spins"].astype(np.int64)
+        t[F] *= -1
+        assert inst.energy_num(t) == res["energy_num"] + dE
+    h.close()
