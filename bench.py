@@ -297,12 +297,23 @@ def run_native(args, wl):
     failed_transforms = [0]   # grid symmetries whose search stopped (no candidate with a positive score)
     spread = [None]           # std of log Z over the grid symmetries (App. C stability test)
 
+    def one_search(hk):
+        if args.droplets is None:
+            return hk.search(wl["M"])
+        # search with the excitation bookkeeping of Fig. 4 (energy window in energy units)
+        r = hk.search_droplets(wl["M"], int(round(args.droplets * hk.inst.denom)), args.min_hamming, cap=0)
+        drop_count[0] = r["n_droplets"]
+        return dict(spins=r["spins"][None], energy_num=np.array([r["energy_num"]]), logp=np.array([r["logp"]]),
+                    pd=r["pd"])
+
+    drop_count = [None]
+
     def run_all(hs):
         """One step on every handle: (log Z of the first, best search result over all)."""
         if len(hs) == 1:
             hs[0].set_beta(wl["beta"])
             lz = hs[0].contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])[0]
-            return lz, hs[0].search(wl["M"])
+            return lz, one_search(hs[0])
         out = sgtn.batch_search(hs, wl["beta"], wl["chi"], wl["M"], precision=prec, n_sweeps=wl["sweeps"],
                                 threads=wl.get("threads", 0), raise_on_error=False)
         ok = [i for i in range(len(out)) if out[i][1] is not None]
@@ -338,7 +349,7 @@ def run_native(args, wl):
             fa = sgtn.stats()[1]
             logz = h.contract_boundary(wl["chi"], precision=prec, n_sweeps=wl["sweeps"])[0]
             bflops += sgtn.stats()[1] - fa
-            res = h.search(wl["M"])
+            res = one_search(h)
         else:
             logz, res = run_all(handles)   # every stream has finished when the call returns
         b.record(stream)
@@ -417,6 +428,8 @@ def run_native(args, wl):
             "config": dict(bench_config(args, wl, ws), unconverged_truncations=unconverged,
                            failed_units=failed_transforms[0] if n_tr > 1 else None),
             "logz_spread_over_grid_symmetries": spread[0] if wl.get("transforms", 1) > 1 else None,
+            "droplets": None if args.droplets is None else {"max_dE": args.droplets, "min_hamming": args.min_hamming,
+                                                            "count_of_best": drop_count[0]},
             "boundary_tflops": (bflops / args.steps) / (bound_ms * 1e-3) / 1e12,
             "boundary_ms": bound_ms,
             "logz_check": logz_err,
@@ -446,6 +459,9 @@ def main():
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default=None,
                     help=f"default: the workload's own, else {DEFAULT_PRECISION}")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--droplets", type=float, default=None,
+                    help="search with droplet bookkeeping (Fig. 4) in this energy window (single-instance workloads)")
+    ap.add_argument("--min-hamming", type=int, default=2, help="Hamming threshold of the droplet filter")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.precision is None:
