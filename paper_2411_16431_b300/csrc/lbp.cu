@@ -82,20 +82,44 @@ __global__ void lbp_mu_kernel(const LbpEdge* E, const int32_t* site_ptr, const i
   if (lane == 0) mu[ed.off + a] = acc;
 }
 
-// nu_{s->t} = B^T mu_{s->t}, scaled to sum 1, into the partner edge's slot;
-// chg[e] = largest change against the previous message.  One CTA per edge.
-__global__ void lbp_nu_kernel(const LbpEdge* E, const double* mu, const double* nu_old, double* nu_new, double* chg) {
-  __shared__ double red[32];
+// nu_{s->t} = B^T mu_{s->t} (unscaled) into the partner edge's slot.  Grid
+// (edge, chunk of 64 b).  B is read along its contiguous index: with
+// B(a, b) = B[a sa + b sb], sb == 1 puts consecutive b in consecutive threads
+// (one thread per b, loop over a); sa == 1 gives one warp per b whose lanes
+// run over a.
+__global__ void lbp_nu_kernel(const LbpEdge* E, const double* mu, double* nu_new) {
   const LbpEdge& ed = E[blockIdx.x];
   const LbpEdge& pt = E[ed.partner];
+  const int nb = pt.na, b0 = blockIdx.y * 64;
+  if (b0 >= nb) return;
+  const double* m = mu + ed.off;
+  if (ed.sb == 1) {
+    const int b = b0 + threadIdx.x;
+    if (threadIdx.x < 64 && b < nb) {
+      double v = 0.0;
+      for (int a = 0; a < ed.na; ++a) v = fma(ed.B[a * ed.sa + b], m[a], v);
+      nu_new[pt.off + b] = v;
+    }
+  } else {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int b = b0 + warp; b < min(nb, b0 + 64); b += nw) {
+      const double* Bb = ed.B + (long long)b * ed.sb;
+      double v = 0.0;
+      for (int a = lane; a < ed.na; a += 32) v = fma(Bb[a], m[a], v);
+      v = lbp_warp_sum(v);
+      if (lane == 0) nu_new[pt.off + b] = v;
+    }
+  }
+}
+
+// scale every new message to sum 1; chg[e] = largest change against the
+// previous one (one CTA per edge, the message indexed like edge e's partner)
+__global__ void lbp_norm_kernel(const LbpEdge* E, const double* nu_old, double* nu_new, double* chg) {
+  __shared__ double red[32];
+  const LbpEdge& pt = E[E[blockIdx.x].partner];
   const int nb = pt.na;
   double part = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    double v = 0.0;
-    for (int a = 0; a < ed.na; ++a) v = fma(ed.B[a * ed.sa + b * ed.sb], mu[ed.off + a], v);
-    nu_new[pt.off + b] = v;
-    part += v;
-  }
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) part += nu_new[pt.off + b];
   const double tot = lbp_block_sum(part, red);
   double mx = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
@@ -108,9 +132,9 @@ __global__ void lbp_nu_kernel(const LbpEdge* E, const double* mu, const double* 
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = 0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-    chg[blockIdx.x] = m;
+    double mm = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) mm = fmax(mm, red[w]);
+    chg[blockIdx.x] = mm;
   }
 }
 
@@ -138,27 +162,30 @@ __global__ void lbp_marginal_kernel(const LbpEdge* E, const int32_t* site_ptr, c
 
 // rank of every state of a site (larger marginal first, ties to the smaller
 // index) and the k first written out; one CTA per site, marginals staged in
-// shared memory when they fit
+// shared memory when they fit.  Marginals are non-negative, so their bit
+// patterns order like their values: the comparisons run on the integer pipe
+// (B300 issues FP64 comparisons at its low FP64 rate).
 __global__ void lbp_rank_kernel(const int32_t* dsite, const long long* moff, const double* marg, int k,
                                 int32_t* out_idx, double* out_p, int smem_cap) {
-  extern __shared__ double sm[];
+  extern __shared__ long long sk[];
   const int s = blockIdx.x, d = dsite[s];
   const double* m = marg + moff[s];
+  const long long* mk = reinterpret_cast<const long long*>(m);
   const bool staged = d <= smem_cap;
   if (staged)
-    for (int x = threadIdx.x; x < d; x += blockDim.x) sm[x] = m[x];
+    for (int x = threadIdx.x; x < d; x += blockDim.x) sk[x] = __double_as_longlong(m[x]);
   __syncthreads();
-  const double* b = staged ? sm : m;
+  const long long* b = staged ? sk : mk;
   for (int x = threadIdx.x; x < d; x += blockDim.x) {
-    const double bx = b[x];
+    const long long bx = b[x];
     int rank = 0;
     for (int y = 0; y < d; ++y) {
-      const double by = b[y];
-      rank += (by > bx) || (by == bx && y < x);
+      const long long by = b[y];
+      rank += (by > bx) | ((by == bx) & (y < x));
     }
     if (rank < k) {
       out_idx[(long long)s * k + rank] = x;
-      out_p[(long long)s * k + rank] = bx;
+      out_p[(long long)s * k + rank] = __longlong_as_double(bx);
     }
   }
 }
@@ -264,6 +291,8 @@ void lbp(sgtn_inst* h, int n_iter, int k, int32_t* out_index, double* out_margin
   fill(nu, (long long)nmsg, 1.0, st);
   SGTN_CUDA(cudaMemsetAsync(chg, 0, std::max(ne, 1) * 8, st));
   const int nitems = int(item_e.size());
+  int max_na = 1;
+  for (const auto& ed : E) max_na = std::max(max_na, ed.na);
   for (int it = 0; it < n_iter && ne > 0; ++it) {
     {
       KTimer kt("lbp_mu", st);
@@ -271,9 +300,10 @@ void lbp(sgtn_inst* h, int n_iter, int k, int32_t* out_index, double* out_margin
     }
     {
       KTimer kt("lbp_nu", st);
-      lbp_nu_kernel<<<ne, 256, 0, st>>>(dE, mu, nu, nu2, chg);
+      lbp_nu_kernel<<<dim3(ne, (max_na + 63) / 64), 256, 0, st>>>(dE, mu, nu2);
+      lbp_norm_kernel<<<ne, 256, 0, st>>>(dE, nu, nu2, chg);
     }
-    g_count.launches += 2;
+    g_count.launches += 3;
     std::swap(nu, nu2);
   }
   {
@@ -289,7 +319,7 @@ void lbp(sgtn_inst* h, int n_iter, int k, int32_t* out_index, double* out_margin
   SGTN_CUDA(cudaMemsetAsync(oidx, 0xff, size_t(ns) * k * 4, st));
   {
     KTimer kt("lbp_rank", st);
-    lbp_rank_kernel<<<ns, 256, size_t(std::min(dmax, smem_cap)) * 8, st>>>(dds, dmo, marg, k, oidx, op, smem_cap);
+    lbp_rank_kernel<<<ns, 1024, size_t(std::min(dmax, smem_cap)) * 8, st>>>(dds, dmo, marg, k, oidx, op, smem_cap);
   }
   g_count.launches += 2;
   h->check();
