@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(128) jacobi_coop_kernel(double* X, int len, in
 template <class T>
 __global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* W, int n, int ld, double shift, double* R,
                                                             double* Rinv, const double* Gd, int* status,
-                                                            int status_off, double* minratio) {
+                                                            int status_off, double* minratio, int init) {
   extern __shared__ __align__(16) unsigned char chol_smem[];
   T* A = reinterpret_cast<T*>(chol_smem);   // n x n
   T* row = A + n * n;                       // n: staged row / 1 / R_jj
@@ -646,17 +646,23 @@ __global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* W, int
     Rinv[(long long)i * ld + c] = c > i ? double(A[c * n + i]) : (c == i ? double(row[i]) : 0.0);
   }
   if (threadIdx.x == 0) {
-    if (fail && status[0] == 0) status[0] = status_off + fail;
-    if (minratio) minratio[0] = fmin(minratio[0], mr);
+    // the first diagonal block of a factorisation starts both outputs afresh
+    if (init) status[0] = fail ? status_off + fail : 0;
+    else if (fail && status[0] == 0) status[0] = status_off + fail;
+    if (minratio) minratio[0] = init ? mr : fmin(minratio[0], mr);
   }
 }
 
-// X[i][j] = 0 for a rows x cols block with leading dimension ld
-__global__ void zero_block_kernel(double* X, int rows, int cols, int ld) {
+// X[i][j] = 0 and Y[i][j] = 0 for two rows x cols blocks with leading dimension ld
+__global__ void zero_blocks2_kernel(double* X, double* Y, int rows, int cols, int ld) {
   const long long n = (long long)rows * cols;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    X[(e / cols) * ld + e % cols] = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long o = (e / cols) * ld + e % cols;
+    X[o] = 0.0;
+    Y[o] = 0.0;
+  }
 }
+
 
 // Cholesky with diagonal pivoting of a positive semidefinite G (n x n, FP64),
 // stopped at the numerical rank: step j takes the largest remaining diagonal
@@ -1269,10 +1275,10 @@ void chol_base(double* W, int n, int ld, double shift, double* R, const double* 
   (void)attr;
   if (f32)
     cholesky_inv_kernel<float><<<1, 1024, size_t(n) * (n + 2) * sizeof(float), st>>>(W, n, ld, shift, R, W, Gd,
-                                                                                    status, off, minratio);
+                                                                                    status, off, minratio, off == 0);
   else
     cholesky_inv_kernel<double><<<1, 1024, size_t(n) * (n + 2) * sizeof(double), st>>>(W, n, ld, shift, R, W, Gd,
-                                                                                      status, off, minratio);
+                                                                                      status, off, minratio, off == 0);
   ++g_count.launches;
 }
 
@@ -1299,9 +1305,8 @@ void chol_rec(double* W, int n, int ld, double shift, double* R, const double* G
   gemm(R12, false, ld, W22, false, ld, T, n2, n1, n2, n2, 1.0, 0, st, 2);     // T = R12 R22^{-1}
   gemm(W, false, ld, T, false, n2, W12, ld, n1, n2, n1, -1.0, 0, st);         // (R^{-1})_12 = -R11^{-1} T
   const long long nz = (long long)n2 * n1;
-  zero_block_kernel<<<blocks_for(nz), 256, 0, st>>>(W21, n2, n1, ld);
-  zero_block_kernel<<<blocks_for(nz), 256, 0, st>>>(R21, n2, n1, ld);
-  g_count.launches += 2;
+  zero_blocks2_kernel<<<blocks_for(nz), 256, 0, st>>>(W21, R21, n2, n1, ld);
+  ++g_count.launches;
 }
 }  // namespace
 
@@ -1312,11 +1317,10 @@ void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv,
   // the off-diagonal GEMMs run in FP64 whatever the caller's contraction precision
   const bool sf = g_compute_f32, su = g_use_tc;
   g_compute_f32 = g_use_tc = false;
-  static const double one = 1.0;
   double* T = static_cast<double*>(stream_scratch(st, SC_CHOL_T, size_t(n) * n * sizeof(double)));
   if (!T) throw SgtnError(-3, "Cholesky scratch needs an allocation in an allocation-free call");
-  cudaMemsetAsync(status, 0, sizeof(int), st);
-  if (minratio) cudaMemcpyAsync(minratio, &one, sizeof(double), cudaMemcpyHostToDevice, st);
+  // status and minratio are set by the first diagonal block (offset 0), which
+  // runs before every other block of this factorisation in stream order
   if (Rinv != G) cudaMemcpyAsync(Rinv, G, size_t(n) * n * sizeof(double), cudaMemcpyDeviceToDevice, st);
   chol_rec(Rinv, n, n, shift, R, G, status, 0, minratio, T, st, f32);
   g_compute_f32 = sf;
