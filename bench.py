@@ -148,6 +148,17 @@ def clocks_summary(proc):
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def combine_ranks(t_ms, evals, device):
+    """Whole-job figures of a replicas run: the slowest rank's time, every rank's evaluations."""
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ev = torch.tensor([float(evals)], device=device, dtype=torch.float64)
+    dist.all_reduce(ev, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(ev.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -361,11 +372,7 @@ def run_native(args, wl):
     t_ms = sum(times)
     evals = e1 - e0
     if ws > 1:
-        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ev = torch.tensor([evals], device="cuda", dtype=torch.float64)
-        dist.all_reduce(ev, op=dist.ReduceOp.SUM)
-        t_ms, evals_all = float(tt.item()), float(ev.item())
+        t_ms, evals_all = combine_ranks(t_ms, evals, "cuda")
     else:
         evals_all = evals
     kt = {n: sgtn.kernel_time(n) for n in sgtn.kernel_names()}

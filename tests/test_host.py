@@ -44,3 +44,35 @@ def test_bench_workload_tables():
         assert wl["chi"] >= 1 and wl["M"] >= 1 and "desc" in wl
     k = bench.WORKLOADS["kings50x50"]["make"](0)
     assert k.denom == 1000 and not np.any(k.h_num)
+
+
+def _ranks_worker(rank, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE="2")
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=2)
+    ws, r, _ = bench.dist_env()
+    t, ev = bench.combine_ranks(100.0 + 50 * rank, 1000 + rank, "cpu")
+    dist.barrier()
+    dist.destroy_process_group()
+    out.put((ws, r, t, ev))
+
+
+def test_replicas_combine_over_two_gloo_ranks():
+    """The N > 1 bench path on CPU: two gloo ranks, max of the times, sum of the evaluations."""
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_ranks_worker, args=(r, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+    assert [r[:2] for r in res] == [(2, 0), (2, 1)]
+    assert all(r[2] == 150.0 and r[3] == 2001.0 for r in res)
