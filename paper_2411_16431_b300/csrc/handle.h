@@ -50,17 +50,6 @@ struct Scratch {
       if (kv.second.first) cudaFree(kv.second.first);
     bufs.clear();
   }
-  // buffers whose name starts with `prefix`: freed (the next get allocates again)
-  void release_prefix(const std::string& prefix) {
-    for (auto it = bufs.begin(); it != bufs.end();) {
-      if (it->first.compare(0, prefix.size(), prefix) == 0) {
-        if (it->second.first) cudaFree(it->second.first);
-        it = bufs.erase(it);
-      } else {
-        ++it;
-      }
-    }
-  }
   size_t total() const {
     size_t t = 0;
     for (auto& kv : bufs) t += kv.second.second;
