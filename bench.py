@@ -95,7 +95,9 @@ PRECISIONS = {"fp64": (0, -1, "f64"),
               "fp32": (3, -1, "f32 contractions, f64 truncation"),
               "tf32": (1, -1, "3xtf32 tensor cores + f32 contractions, f64 truncation"),
               "fp64_tf32search": (0, 1, "f64 boundary, 3xtf32/f32 conditional scores")}
-DEFAULT_PRECISION = "tf32"
+# the default meets the log Z <= 1e-6 bound of the mixed-vs-FP64 comparison exactly (FP64
+# boundary); "tf32" is faster with a log Z error of a few 1e-6 at beta = 2
+DEFAULT_PRECISION = "fp64_tf32search"
 # FP64 peak of a B300 derived from unit counts: 148 SMs x 2 DFMA/clk/SM x 2 flop x 2032 MHz
 FP64_PEAK_GFLOPS = 148 * 2 * 2 * 2.032
 # FP32 SIMT peak from unit counts (148 SMs x 128 FMA/clk x 2 flop x 2032 MHz)
@@ -146,6 +148,25 @@ def clocks_summary(proc):
     if not sm:
         return None
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def marginal_check(h, inst, states, spins, mixed, n_steps=8):
+    """Largest |p_mixed - p_fp64| / max p_fp64 of the conditionals along one configuration."""
+    R, C = inst.rows, inst.cols
+    cfg = []
+    for site in range(R * C):
+        sp = np.nonzero(inst.site_of_spin == site)[0]
+        pat = int(sum(((1 - int(spins[g])) // 2) << j for j, g in enumerate(sp)))
+        cfg.append(pat if states is None else int(np.nonzero(np.asarray(states[site]) == pat)[0][0]))
+    steps = sorted(set(np.linspace(1, R * C - 1, n_steps).astype(int).tolist()))
+    worst = 0.0
+    for n in steps:
+        h.set_search_precision(0)
+        p64 = h.conditionals(n, np.array(cfg[:n], np.int32)[None])[0]
+        h.set_search_precision(mixed)
+        pm = h.conditionals(n, np.array(cfg[:n], np.int32)[None])[0]
+        worst = max(worst, float(np.max(np.abs(pm - p64)) / np.max(p64)))
+    return {"steps": steps, "max_abs_err_rel_to_max": worst, "search_precision": mixed}
 
 
 def combine_ranks(t_ms, evals, device):
@@ -390,12 +411,20 @@ def run_native(args, wl):
     if n_tr > 1:
         bflops = (sgtn.stats()[1] - fa) * args.steps   # one instance's boundary, timed alone
     # stated error of a mixed-precision boundary: log Z against the FP64 boundary (untimed)
-    logz_err = None
+    logz_err = {"logz": logz, "logz_fp64": logz, "rel_err": 0.0, "boundary": "fp64"} if prec == 0 else None
     if prec != 0:
         lz64 = h.contract_boundary(wl["chi"], precision=0, n_sweeps=wl["sweeps"])[0]
         ok = np.isfinite(logz) and np.isfinite(lz64)
         logz_err = {"logz": logz if np.isfinite(logz) else None, "logz_fp64": lz64 if np.isfinite(lz64) else None,
                     "rel_err": abs(logz - lz64) / abs(lz64) if ok else None}
+    # stated marginal error of the mixed search arithmetic: conditionals along the best
+    # configuration at 8 steps, mixed against FP64 scores on the same (FP64) boundary (untimed)
+    marg_err = None
+    if (sprec != -1 or prec != 0) and n_tr == 1 and wl.get("transforms", 1) == 1:
+        if prec != 0:
+            h.contract_boundary(wl["chi"], precision=0, n_sweeps=wl["sweeps"])   # (already FP64 after logz_check)
+        marg_err = marginal_check(h, inst, states, res["spins"][0], sprec if sprec != -1 else prec)
+        h.set_search_precision(sprec)
     # end to end through the public API from host buffers: build (H2D) .. results (D2H)
     e2e_times = []
     h2d = 0
@@ -440,6 +469,7 @@ def run_native(args, wl):
             "boundary_tflops": (bflops / args.steps) / (bound_ms * 1e-3) / 1e12,
             "boundary_ms": bound_ms,
             "logz_check": logz_err,
+            "marginal_check": marg_err,
             "roofline": roof, "roofline_contraction": roof_c, "kernel_times": shares,
             "e2e": {"value": e2e_val, "unit": "marginal evals/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
