@@ -254,7 +254,17 @@ bool make_map(CUtensorMap* map, const float* base, int rows, int kpad) {
 
 }  // namespace
 
-int*& tc_err_ptr();
+// The timeout flag of the tensor-core GEMM, shared by all streams (it only ever
+// goes 0 -> 1 on the device); allocated once, on first use.
+static int* tc_err_flag() {
+  static int* const e = [] {
+    int* p = nullptr;
+    if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return (int*)nullptr;
+    cudaMemset(p, 0, sizeof(int));
+    return p;
+  }();
+  return e;
+}
 
 // C[m x n] (+)= alpha * op(X) op(Y), operands FP64 in memory, 3xTF32 tensor cores.
 // Returns false (nothing launched) if the tensor map cannot be built.
@@ -262,15 +272,8 @@ bool tc_gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, 
              int m, int n, int k, double alpha, int accumulate, cudaStream_t st) {
   if (m <= 0 || n <= 0 || k <= 0) return true;
   int kpad = (k + 3) / 4 * 4;   // 16-byte row pitch for TMA
-  // the timeout flag is shared by all streams (it only ever goes 0 -> 1)
-  static int* const err = [] {
-    int* e = nullptr;
-    if (cudaMalloc(&e, sizeof(int)) != cudaSuccess) return (int*)nullptr;
-    cudaMemset(e, 0, sizeof(int));
-    return e;
-  }();
+  int* const err = tc_err_flag();
   if (!err) return false;
-  tc_err_ptr() = err;
   size_t need = 2 * (size_t(m) + n) * kpad;
   float* buf = static_cast<float*>(stream_scratch(st, SC_TC_BUF, need * sizeof(float)));
   if (!buf) return false;   // would allocate in an allocation-free call: the SIMT path allocates nothing
@@ -305,14 +308,11 @@ bool tc_gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, 
   return true;
 }
 
-int*& tc_err_ptr() {
-  static int* e = nullptr;   // written once, with the same value, by every caller
-  return e;
-}
+
 
 // 1 if any tensor-core GEMM timed out since the last call (then cleared)
 int tc_gemm_take_error(cudaStream_t st) {
-  int* e = tc_err_ptr();
+  int* e = tc_err_flag();
   if (!e) return 0;
   int v = 0;
   cudaMemcpyAsync(&v, e, sizeof(int), cudaMemcpyDeviceToHost, st);
