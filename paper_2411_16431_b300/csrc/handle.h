@@ -143,8 +143,8 @@ namespace sgtn {
 // and handed to the next request of that size on the same stream (stream
 // order makes the reuse safe), so a row step does not call cudaMalloc /
 // cudaFree -- which synchronises the device -- per tensor.  pool_set_stream
-// names the stream of the calling handle; pool_trim returns a stream's cached
-// blocks to the driver (at sgtn_destroy).
+// names the stream of the calling thread's handle; pool_trim frees a stream's
+// cached blocks with cudaFree (at sgtn_destroy).
 void pool_set_stream(cudaStream_t st);
 void* pool_alloc(size_t bytes);
 void pool_free(void* p);
