@@ -556,34 +556,35 @@ bool cqr_orth(sgtn_inst* h, const double* M, int len, int k, double* Q, bool fir
   double* T = h->ws.get<double>("cqo_T", size_t(len) * k);
   double* T2 = h->ws.get<double>("cqo_T2", size_t(len) * k);
   int* status = h->ws.get<int>("cqo_status", 1);
-  std::vector<double> hG(size_t(k) * k);
+  // deviation of the Gram matrix from the identity and its trace, computed on
+  // the device and read with the Cholesky status (one transfer of 16 bytes)
+  double* dstat = h->ws.get<double>("cqo_stat", 2);
+  double hstat[2] = {0.0, 0.0};
   auto chol = [&](double shift, bool f32) {
     cholesky_inv(G, k, shift, R, Ri, status, st, f32);
     int hs = 0;
     SGTN_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SGTN_CUDA(cudaMemcpyAsync(hstat, dstat, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     h->sync();
     return hs == 0;
   };
   const double* cur = M;
   for (int pass = 0; pass < 4; ++pass) {
     gram_upper(cur, k, G, k, len, st);                                 // G = cur^T cur (upper)
-    SGTN_CUDA(cudaMemcpyAsync(hG.data(), G, hG.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    gram_stats(G, k, dstat, st);
     bool last = pass == 3;
     if (pass == 0) {
       bool ok = chol(0.0, first_f32);
       if (!ok && first_f32) ok = chol(0.0, false);
       if (!ok) {
-        double tr = 0;
-        for (int i = 0; i < k; ++i) tr += hG[size_t(i) * k + i];
+        const double tr = hstat[1];
         if (!(tr > 0) || !std::isfinite(tr)) return false;
         double shift = 11.0 * (double(len) * k + double(k) * (k + 1)) * 2.220446049250313e-16 * tr;
         if (!chol(shift, false)) return false;
       }
     } else {
       if (!chol(0.0, false)) return false;
-      double dev = 0;
-      for (int i = 0; i < k; ++i)
-        for (int j = i; j < k; ++j) dev = std::max(dev, std::fabs(hG[size_t(i) * k + j] - (i == j ? 1.0 : 0.0)));
+      const double dev = hstat[0];
       if (!std::isfinite(dev)) return false;
       last = last || dev < 0.1;
     }

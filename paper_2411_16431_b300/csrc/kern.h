@@ -117,6 +117,9 @@ void seg_gemm(const SegGemm& a, cudaStream_t st);
 void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, long long ldy, double* O,
           long long ldo, int m, int n, int k, double alpha, int accumulate, cudaStream_t st, int tri = 0);
 // G (n x n) = X^T X for X (m x n, leading dimension ldx): upper triangle only
+// out[0] = max |G_ij - delta_ij| over the upper triangle (NaN if any entry is
+// not finite), out[1] = trace of G (k x k); device outputs
+void gram_stats(const double* G, int k, double* out, cudaStream_t st);
 inline void gram_upper(const double* X, long long ldx, double* G, int n, int m, cudaStream_t st) {
   gemm(X, true, ldx, X, false, ldx, G, n, n, n, m, 1.0, 0, st, 1);
 }

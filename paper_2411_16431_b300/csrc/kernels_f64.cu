@@ -653,6 +653,47 @@ __global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* W, int
   }
 }
 
+// Statistics of the upper triangle of a k x k Gram matrix, one CTA:
+// out[0] = max |G_ij - delta_ij| over j >= i (NaN if an entry is not finite),
+// out[1] = trace.  Fixed-order reductions.
+__global__ void __launch_bounds__(1024) gram_stats_kernel(const double* G, int k, double* out) {
+  __shared__ double rmax[32], rsum[32];
+  __shared__ int rbad[32];
+  double mx = 0.0, tr = 0.0;
+  int bad = 0;
+  for (long long e = threadIdx.x; e < (long long)k * k; e += blockDim.x) {
+    const int i = int(e / k), j = int(e % k);
+    if (j < i) continue;
+    const double g = G[e];
+    if (!isfinite(g)) bad = 1;
+    mx = fmax(mx, fabs(g - (i == j ? 1.0 : 0.0)));
+    if (i == j) tr += g;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    rmax[warp] = mx;
+    rsum[warp] = tr;
+    rbad[warp] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0, t = 0.0;
+    int b = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+      m = fmax(m, rmax[w]);
+      t += rsum[w];
+      b |= rbad[w];
+    }
+    out[0] = b ? nan("") : m;
+    out[1] = t;
+  }
+}
+
 // X[i][j] = 0 and Y[i][j] = 0 for two rows x cols blocks with leading dimension ld
 __global__ void zero_blocks2_kernel(double* X, double* Y, int rows, int cols, int ld) {
   const long long n = (long long)rows * cols;
@@ -1325,6 +1366,11 @@ void cholesky_inv(const double* G, int n, double shift, double* R, double* Rinv,
   chol_rec(Rinv, n, n, shift, R, G, status, 0, minratio, T, st, f32);
   g_compute_f32 = sf;
   g_use_tc = su;
+}
+
+void gram_stats(const double* G, int k, double* out, cudaStream_t st) {
+  gram_stats_kernel<<<1, 1024, 0, st>>>(G, k, out);
+  ++g_count.launches;
 }
 
 void pchol_inv(const double* G, int n, double tol_rel, double tol_abs, double* R, double* Rinv, int32_t* perm,
