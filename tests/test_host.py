@@ -76,3 +76,40 @@ def test_replicas_combine_over_two_gloo_ranks():
         p.join(timeout=60)
     assert [r[:2] for r in res] == [(2, 0), (2, 1)]
     assert all(r[2] == 150.0 and r[3] == 2001.0 for r in res)
+
+
+def test_hamming_ball_states():
+    """Distinct patterns per cell, the reference first, ordered by Hamming distance."""
+    from paper_2411_16431_b300 import lattices as L
+    inst = L.pegasus_nice(4, 2)
+    states = L.hamming_ball_states(inst, 40, seed=5)
+    for site, st in enumerate(states):
+        assert len(st) == 40 and len(set(st.tolist())) == 40
+        dist = [bin(int(x) ^ int(st[0])).count("1") for x in st]
+        assert dist[0] == 0 and dist == sorted(dist) and max(dist) <= 2
+    pl = L.planted(L.chimera_grid(2, 3, 1), 3)
+    ref = L.hamming_ball_states(pl, 5)
+    for site, st in enumerate(ref):
+        sp = np.nonzero(pl.site_of_spin == site)[0]
+        assert int(st[0]) == sum(1 << j for j, g in enumerate(sp) if pl.planted[g] < 0)
+
+
+def test_grid_transform_keeps_energies():
+    """A grid symmetry relabels the cell grid only: the same spin configuration has the
+    same energy, every coupling stays between king's-graph neighbours, and the state
+    lists of a cell follow it to its new position."""
+    from paper_2411_16431_b300 import lattices as L
+    inst = L.pegasus_nice(4, 1)
+    states = L.hamming_ball_states(inst, 6, seed=2)
+    rng = np.random.default_rng(0)
+    s = rng.choice([-1, 1], inst.n_spins).astype(np.int8)
+    for k in range(8):
+        t = L.transform(inst, k)
+        assert t.energy_num(s) == inst.energy_num(s)
+        r, c = t.site_of_spin // t.cols, t.site_of_spin % t.cols
+        assert np.all(np.abs(r[t.ei] - r[t.ej]) <= 1) and np.all(np.abs(c[t.ei] - c[t.ej]) <= 1)
+        ts = L.transform_states(inst, states, k)
+        for site in range(inst.rows * inst.cols):
+            spins = np.nonzero(inst.site_of_spin == site)[0]
+            new_site = int(t.site_of_spin[spins[0]])
+            assert np.array_equal(ts[new_site], states[site])
