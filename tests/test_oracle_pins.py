@@ -435,3 +435,17 @@ def test_droplet_filters():
     assert try_insert(d, (7, frozenset({1})), 10, 1, adj) == d           # clashes, not lower
     assert try_insert(d, (3, frozenset({1})), 10, 1, adj) == [(3, frozenset({1}))]
     assert try_insert(d, (3, frozenset({2, 3})), 10, 1, adj) == d + [(3, frozenset({2, 3}))]
+
+
+def test_search_tie_rule_on_a_flat_landscape():
+    """With every coupling and field zero all configurations are equally probable:
+    every merge and the top-M cut are ties, which go to the lexicographically
+    smallest configuration, so the search returns all-zero state indices
+    (all spins up) with energy 0 and log p = -N log 2."""
+    inst = L.kings_grid(3, 4, 2)
+    inst.j_num = np.zeros_like(inst.j_num)
+    inst.h_num = np.zeros_like(inst.h_num)
+    res = search(inst, 1.0, chi=4, M=3, n_sweeps=1)
+    assert res["configs"][0] == (0,) * (inst.rows * inst.cols)
+    assert int(res["energy_num"][0]) == 0
+    assert abs(res["logp"][0] + inst.n_spins * np.log(2)) < 1e-10
