@@ -113,3 +113,21 @@ def test_grid_transform_keeps_energies():
             spins = np.nonzero(inst.site_of_spin == site)[0]
             new_site = int(t.site_of_spin[spins[0]])
             assert np.array_equal(ts[new_site], states[site])
+
+
+def test_bench_roofline_helpers():
+    """The bench's roofline entry: the kernel with the most device time, achieved =
+    algorithmic flop per launch / time per launch, frac = achieved / peak."""
+    sys.path.insert(0, ROOT)
+    import bench
+    kt = {"cholesky_f64": (500.0, 100, 2e9), "score_f32": (100.0, 10, 5e11), "tc_gemm_3xtf32": (50.0, 5, 1e12),
+          "select": (1.0, 10, 0.0)}
+    r = bench.roofline_of(kt, list(kt))
+    assert r["kernel"] == "cholesky_f64" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - (2e9 / 100) / (5e-3) / 1e12) < 1e-12
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15 and r["traffic"] is None
+    assert abs(r["peak"] - bench.FP64_PEAK_GFLOPS / 1e3) < 1e-12
+    t = bench.roofline_of(kt, ["tc_gemm_3xtf32"])
+    assert t["bound"] == "tensor" and t["peak"] == bench.peak_of("tc_gemm_3xtf32")[0]
+    assert bench.peak_of("score_f32")[0] == bench.FP32_PEAK_TFLOPS
+    assert bench.roofline_of(kt, ["select"]) is None          # no flop count: no roofline entry
