@@ -411,7 +411,8 @@ def run_native(args, wl):
     if n_tr > 1:
         bflops = (sgtn.stats()[1] - fa) * args.steps   # one instance's boundary, timed alone
     # stated error of a mixed-precision boundary: log Z against the FP64 boundary (untimed)
-    logz_err = {"logz": logz, "logz_fp64": logz, "rel_err": 0.0, "boundary": "fp64"} if prec == 0 else None
+    fin = (lambda v: float(v) if np.isfinite(v) else None)   # JSON has no NaN: an undefined log Z is null
+    logz_err = {"logz": fin(logz), "logz_fp64": fin(logz), "rel_err": 0.0, "boundary": "fp64"} if prec == 0 else None
     if prec != 0:
         lz64 = h.contract_boundary(wl["chi"], precision=0, n_sweeps=wl["sweeps"])[0]
         ok = np.isfinite(logz) and np.isfinite(lz64)
@@ -463,7 +464,8 @@ def run_native(args, wl):
             "data": "synthetic",
             "config": dict(bench_config(args, wl, ws), unconverged_truncations=unconverged,
                            failed_units=failed_transforms[0] if n_tr > 1 else None),
-            "logz_spread_over_grid_symmetries": spread[0] if wl.get("transforms", 1) > 1 else None,
+            "logz_spread_over_grid_symmetries": (spread[0] if spread[0] is not None and np.isfinite(spread[0])
+                                                 else None) if wl.get("transforms", 1) > 1 else None,
             "droplets": None if args.droplets is None else {"max_dE": args.droplets, "min_hamming": args.min_hamming,
                                                             "count_of_best": drop_count[0]},
             "boundary_tflops": (bflops / args.steps) / (bound_ms * 1e-3) / 1e12,
