@@ -105,6 +105,12 @@ int sgtn_contract_boundary(sgtn_h h, int32_t chi, int32_t precision, int32_t n_s
  * d the number of states of cluster `step`.  Requires contract_boundary. */
 int sgtn_conditionals(sgtn_h h, int32_t step, int32_t count, const int32_t* configs, double* out_p);
 
+/* Largest number of partial configurations one call scores together: `count`
+ * of sgtn_conditionals(_noalloc), `in_count` of sgtn_branch_step and the beam
+ * width M of sgtn_search / sgtn_batch_search / sgtn_search_droplets.  Larger
+ * values return SGTN_ERR_ARG before anything is copied or launched. */
+#define SGTN_MAX_BEAM 1024
+
 /* One branch-and-bound step (Sec. III.A, Fig. 3): branch every input
  * configuration over all states of cluster `step`, score candidates with the
  * chain rule (Eq. 6), keep the most probable candidate of every boundary
@@ -233,9 +239,11 @@ int sgtn_mps_tensor(sgtn_h h, int32_t row, int32_t col, double* out);
  * every device temporary is taken from one static device array of
  * SGTN_NOALLOC_SCRATCH_BYTES bytes that each GPU loading the library reserves
  * until the process exits; the call performs no device allocation.
- *  - Set-up: the first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture is started.
+ *  - Set-up: every call looks up the array's device address
+ *    (cudaGetSymbolAddress) with the handle's device current, so the address
+ *    stays right after a cudaDeviceReset; the first call on a device loads
+ *    the library's device code there, so make it before any stream capture
+ *    is started.
  *  - A call whose temporaries (about 8 bytes x count x states, plus the
  *    projected boundary MPS of the row) exceed the array returns SGTN_ERR_ARG
  *    and sgtn_last_error() states the bytes needed; nothing is launched.
@@ -253,6 +261,11 @@ int sgtn_conditionals_noalloc(sgtn_h h, int32_t step, int32_t count, const int32
  * marginals evaluated (one per branch x cluster state).  Any pointer may be
  * NULL.  The counters are atomic and summed over all threads. */
 void sgtn_stats(int64_t* launches, double* flops, int64_t* evals);
+
+/* Number of device allocations (cudaMalloc calls) the library has made so far
+ * in this process, over all handles and threads (the paper has no
+ * counterpart; it lets a caller check that a call allocated nothing). */
+int64_t sgtn_device_allocations(void);
 
 /* Optional per-kernel timing (the paper has no counterpart): when enabled,
  * every launch of the library's kernels is bracketed by CUDA events on its

@@ -42,8 +42,8 @@ void energies(sgtn_inst* h, int n, const int8_t* spins, int64_t* out) {
   static_assert(sizeof(long long) == sizeof(int64_t), "int64");
   int8_t* ds = nullptr;
   long long* dout = nullptr;
-  SGTN_CUDA(cudaMalloc(&ds, size_t(n) * h->M.N));
-  SGTN_CUDA(cudaMalloc(&dout, size_t(n) * sizeof(long long)));
+  SGTN_CUDA(lib_malloc(&ds, size_t(n) * h->M.N));
+  SGTN_CUDA(lib_malloc(&dout, size_t(n) * sizeof(long long)));
   SGTN_CUDA(cudaMemcpyAsync(ds, spins, size_t(n) * h->M.N, cudaMemcpyHostToDevice, h->st));
   if (!h->d_ei) {
     h->d_ei = h->M.ei.empty() ? nullptr : h->upload(h->M.ei);
@@ -269,6 +269,8 @@ void sgtn_stats(int64_t* launches, double* flops, int64_t* evals) {
   if (evals) *evals = g_count.evals;
 }
 
+int64_t sgtn_device_allocations(void) { return g_count.device_allocs; }
+
 void sgtn_kernel_timing(int32_t enable, int32_t reset) {
   if (reset) ktimer_reset();
   ktimer_enable(enable != 0);
@@ -331,6 +333,7 @@ int sgtn_batch_search(sgtn_h* hs, int32_t n, double beta, int32_t chi, int32_t p
   if (n == 0) return SGTN_OK;
   if (!hs || !status || !out_spins || !out_energy_num || !out_logp || !out_logz || !out_pd || !out_count)
     return SGTN_ERR_ARG;
+  if (M <= 0 || M > SGTN_MAX_BEAM) return SGTN_ERR_ARG;
   // handles that share a stream form one group, run in order by one thread
   std::vector<std::vector<int>> groups;
   std::map<cudaStream_t, int> gid;

@@ -81,10 +81,10 @@ void* pool_alloc(size_t bytes) {
     p = it->second.back();
     it->second.pop_back();
     g_pool_cached -= key.bytes;
-  } else if (cudaMalloc(&p, key.bytes) != cudaSuccess) {
+  } else if (lib_malloc(&p, key.bytes) != cudaSuccess) {
     cudaGetLastError();
     pool_release_all();   // cudaFree synchronises: no cached block is still in use
-    SGTN_CUDA(cudaMalloc(&p, key.bytes));
+    SGTN_CUDA(lib_malloc(&p, key.bytes));
   }
   g_pool_live[p] = key;
   return p;

@@ -28,6 +28,7 @@
 #include <string>
 #include <unordered_map>
 
+#include "../../include/sgtn.h"
 #include "handle.h"
 
 namespace sgtn {
@@ -538,6 +539,11 @@ void check_configs(sgtn_inst* h, int step, int count, const int32_t* cfg) {
   const int RC = h->M.R * h->M.C;
   if (step < 0 || step >= RC) throw SgtnError(-1, "step out of range");
   if (count <= 0) throw SgtnError(-1, "count must be positive");
+  // the score kernel holds at most SGTN_MAX_BEAM branches per CTA, and the
+  // initial parent list is a prefix of the handle's iota table
+  if (count > SGTN_MAX_BEAM || count > h->iota_n)
+    throw SgtnError(-1, "count " + std::to_string(count) + " exceeds SGTN_MAX_BEAM (" + std::to_string(SGTN_MAX_BEAM) +
+                            ")");
   if (step > 0 && !cfg) throw SgtnError(-1, "configs is NULL");
   for (long long k = 0; k < count; ++k)
     for (int p = 0; p < step; ++p) {
@@ -1025,6 +1031,8 @@ void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_ener
   if (!h->boundary_ok) throw SgtnError(-2, "contract_boundary must run first");
   if (M <= 0 || n_out <= 0 || !out_spins || !out_energy || !out_logp || !out_pd || !out_count)
     throw SgtnError(-1, "bad argument");
+  if (M > SGTN_MAX_BEAM)
+    throw SgtnError(-1, "M " + std::to_string(M) + " exceeds SGTN_MAX_BEAM (" + std::to_string(SGTN_MAX_BEAM) + ")");
   cudaStream_t st = h->st;
   const int C = h->M.C, RC = h->M.R * h->M.C;
   std::vector<int32_t> cfg(1, 0), ncfg;

@@ -126,7 +126,7 @@ inline int nblk(long long n) { return int(std::max(1ll, std::min((n + 255) / 256
 template <class T>
 T* to_dev(sgtn_inst* h, const std::vector<T>& v) {
   T* p = nullptr;
-  SGTN_CUDA(cudaMalloc(&p, std::max<size_t>(1, v.size()) * sizeof(T)));
+  SGTN_CUDA(lib_malloc(&p, std::max<size_t>(1, v.size()) * sizeof(T)));
   if (!v.empty()) SGTN_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->st));
   return p;
 }
@@ -393,7 +393,7 @@ void logz_grad(sgtn_inst* h, double* dJ, double* dh, double* dbeta) {
         loc[k].slot = int(k);
       }
       Desc* dd = nullptr;
-      SGTN_CUDA(cudaMalloc(&dd, std::max<size_t>(1, loc.size()) * sizeof(Desc)));
+      SGTN_CUDA(lib_malloc(&dd, std::max<size_t>(1, loc.size()) * sizeof(Desc)));
       if (!loc.empty())
         SGTN_CUDA(cudaMemcpyAsync(dd, loc.data(), loc.size() * sizeof(Desc), cudaMemcpyHostToDevice, st));
       const HSite& S = h->M.sites[r * C + c];

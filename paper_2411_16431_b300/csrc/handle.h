@@ -36,7 +36,7 @@ struct Scratch {
       if (b.first) cudaFree(b.first);
       b.first = nullptr;
       size_t nb = bytes + bytes / 4 + 256;
-      SGTN_CUDA(cudaMalloc(&b.first, nb));
+      SGTN_CUDA(lib_malloc(&b.first, nb));
       b.second = nb;
     }
     return b.first;
@@ -89,7 +89,7 @@ struct sgtn_inst {
   T* upload(const std::vector<T>& v) {
     T* p = nullptr;
     size_t n = v.empty() ? 1 : v.size();
-    SGTN_CUDA(cudaMalloc(&p, n * sizeof(T)));
+    SGTN_CUDA(sgtn::lib_malloc(&p, n * sizeof(T)));
     allocs.push_back(p);
     if (!v.empty()) SGTN_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
     return p;
@@ -97,7 +97,7 @@ struct sgtn_inst {
   template <class T>
   T* dalloc(size_t n) {
     T* p = nullptr;
-    SGTN_CUDA(cudaMalloc(&p, (n ? n : 1) * sizeof(T)));
+    SGTN_CUDA(sgtn::lib_malloc(&p, (n ? n : 1) * sizeof(T)));
     allocs.push_back(p);
     return p;
   }

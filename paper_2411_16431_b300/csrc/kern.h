@@ -32,8 +32,16 @@ struct Counters {
   std::atomic<long long> launches{0};
   AtomicSum flops;
   std::atomic<long long> evals{0};
+  std::atomic<long long> device_allocs{0};   // cudaMalloc calls made by the library
 };
 extern Counters g_count;
+// Every device allocation of the library goes through here, so that the
+// allocation-free entry point can be checked to make none.
+template <class T>
+inline cudaError_t lib_malloc(T** p, size_t bytes) {
+  ++g_count.device_allocs;
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
 // The three mode flags below belong to the calling host thread: a handle's
 // call sets them for its own duration, so handles driven by different threads
 // (one stream each) do not see each other's modes.

@@ -985,7 +985,7 @@ void* stream_scratch(cudaStream_t st, int slot, size_t bytes) {
     cudaFree(e.first);
     e = {nullptr, 0};
   }
-  if (cudaMalloc(&e.first, bytes) != cudaSuccess) {
+  if (lib_malloc(&e.first, bytes) != cudaSuccess) {
     e = {nullptr, 0};
     throw SgtnError(-3, "out of device memory for " + std::to_string(bytes) + " bytes of scratch");
   }

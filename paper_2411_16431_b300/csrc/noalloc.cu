@@ -9,7 +9,6 @@
 // sgtn_conditionals computes, but every device temporary lives in the static
 // array below, reserved once per device when the library's device code is
 // loaded, so the call itself allocates no device memory.
-#include <mutex>
 #include <string>
 
 #include "../../include/sgtn.h"
@@ -21,24 +20,16 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[SGTN_NOALLOC_SC
 
 namespace {
 
-constexpr int kMaxDevices = 256;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
-// Device address of the scratch on the current device.  In host code the
-// array's name is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
-void* scratch_address(int dev) {
-  if (dev < 0 || dev >= kMaxDevices) throw SgtnError(SGTN_ERR_ARG, "device ordinal out of range");
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      throw SgtnError(SGTN_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-    g_addr[dev] = p;
-  }
-  return g_addr[dev];
+// Device address of the scratch on the current device, looked up on every
+// call: in host code the array's name is only a host-side stand-in, and an
+// address cached across calls would go stale if the application reset the
+// device (cudaDeviceReset) and the module were loaded again.
+void* scratch_address() {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    throw SgtnError(SGTN_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+  return p;
 }
 
 }  // namespace
@@ -48,7 +39,7 @@ extern "C" int sgtn_conditionals_noalloc(sgtn_h h, int32_t step, int32_t count, 
   if (!h) return SGTN_ERR_ARG;
   try {
     SGTN_CUDA(cudaSetDevice(h->device));
-    void* scratch = scratch_address(h->device);
+    void* scratch = scratch_address();
     sgtn::PrecisionScope ps(h, true);
     sgtn::conditionals_arena(h, step, count, configs, out_p, scratch, SGTN_NOALLOC_SCRATCH_BYTES);
     h->err.clear();

@@ -254,16 +254,14 @@ bool make_map(CUtensorMap* map, const float* base, int rows, int kpad) {
 
 }  // namespace
 
-// The timeout flag of the tensor-core GEMM, shared by all streams (it only ever
-// goes 0 -> 1 on the device); allocated once, on first use.
+// Error flag of the tensor-core kernels (a wait that ran out of iterations):
+// one static device word per device, shared by all streams (it only goes
+// 0 -> 1 on the device), so that no call ever allocates for it.
+static __device__ int g_tc_err;
 static int* tc_err_flag() {
-  static int* const e = [] {
-    int* p = nullptr;
-    if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return (int*)nullptr;
-    cudaMemset(p, 0, sizeof(int));
-    return p;
-  }();
-  return e;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_tc_err) != cudaSuccess) return nullptr;
+  return static_cast<int*>(p);
 }
 
 // C[m x n] (+)= alpha * op(X) op(Y), operands FP64 in memory, 3xTF32 tensor cores.

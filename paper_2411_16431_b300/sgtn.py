@@ -79,6 +79,13 @@ def stats():
     return a.value, b.value, c.value
 
 
+def device_allocations():
+    """Number of cudaMalloc calls the library has made so far in this process."""
+    L = load()
+    L.sgtn_device_allocations.restype = ct.c_int64
+    return int(L.sgtn_device_allocations())
+
+
 def kernel_timing(enable, reset=False):
     load().sgtn_kernel_timing(int(enable), int(reset))
 

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     txt = open(os.path.join(ROOT, "include", "sgtn.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char\s*\*)\s*(sgtn_\w+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int(?:32|64)_t|int|void|const char\s*\*)\s*(sgtn_\w+)\s*\(", txt, re.M)))
 
 
 def test_library_exports_all_declared_symbols():

@@ -5,8 +5,11 @@ while they run (a server that gives all device memory to its own pool at
 start-up, a real-time loop that cannot absorb cudaMalloc's synchronisation).
 It must return what sgtn_conditionals returns, call after call, although all
 its temporaries live in one static device array that keeps the previous
-call's contents.  This file is collected last so that a run stopping at the
-first failure has run every other test first.
+call's contents, and it must make no device allocation at all -- checked with
+the library's own count of cudaMalloc calls, in every search precision (the
+FP32 and TF32 paths take other GEMM branches than FP64).  This file is
+collected last so that a run stopping at the first failure has run every
+other test first.
 """
 import numpy as np
 import pytest
@@ -15,7 +18,7 @@ from paper_2411_16431_b300 import lattices as L
 
 pytestmark = pytest.mark.gpu
 
-RTOL = 1e-10
+RTOL = {0: 1e-10, 3: 1e-4, 1: 1e-4}     # FP64, FP32, TF32 (against the same precision's sgtn_conditionals)
 
 
 def _random_configs(h, step, count, seed):
@@ -23,33 +26,58 @@ def _random_configs(h, step, count, seed):
     return np.array([[rng.integers(h.d[p]) for p in range(step)] for _ in range(count)], np.int32).reshape(count, step)
 
 
-def test_noalloc_matches_conditionals_on_consecutive_calls():
-    from paper_2411_16431_b300.sgtn import Handle
+@pytest.mark.parametrize("precision", [0, 3, 1], ids=["fp64", "fp32", "tf32"])
+def test_noalloc_matches_conditionals_and_allocates_nothing(precision):
+    from paper_2411_16431_b300.sgtn import Handle, device_allocations
     inst = L.chimera_grid(4, 4, 0)
     h = Handle(inst)
     h.set_beta(1.0)
     h.contract_boundary(16, n_sweeps=2)
-    # two calls in a row on different inputs (the second sees the first's leftovers),
-    # and a step with a different shape after them
-    for step, count, seed in ((6, 40, 1), (6, 40, 2), (13, 7, 3)):
-        cfg = _random_configs(h, step, count, seed)
-        ref = h.conditionals(step, cfg)
-        got = h.conditionals_noalloc(step, cfg)
-        assert got.shape == ref.shape
-        assert np.allclose(got, ref, rtol=RTOL, atol=0.0)
-        assert np.allclose(got.sum(axis=1), 1.0, rtol=1e-12)
+    h.set_search_precision(precision)
+    cases = ((6, 40, 1), (6, 40, 2), (13, 7, 3), (9, 300, 4))
+    # warm-up: the first call on a device loads the module there
+    h.conditionals_noalloc(*cases[0][:1], _random_configs(h, cases[0][0], 2, 0))
+    refs = [h.conditionals(step, _random_configs(h, step, count, seed)) for step, count, seed in cases]
+    before = device_allocations()
+    # two calls in a row on different inputs (the second sees the first's
+    # leftovers), then other shapes, all without a single device allocation
+    got = [h.conditionals_noalloc(step, _random_configs(h, step, count, seed)) for step, count, seed in cases]
+    assert device_allocations() == before
+    for g, r in zip(got, refs):
+        assert g.shape == r.shape
+        assert np.allclose(g, r, rtol=RTOL[precision], atol=0.0)
+        assert np.allclose(g.sum(axis=1), 1.0, rtol=1e-9)
     h.close()
 
 
-def test_noalloc_rejects_requests_beyond_its_scratch():
+def test_noalloc_rejects_requests_beyond_its_scratch_or_the_beam_limit():
     from paper_2411_16431_b300.sgtn import Handle, SgtnError
     inst = L.chimera_grid(4, 4, 0)
     h = Handle(inst)
     h.set_beta(1.0)
     h.contract_boundary(16, n_sweeps=2)
-    big = _random_configs(h, 5, 20000, 4)          # ~40 MB of scores > 32 MiB
-    with pytest.raises(SgtnError, match="bytes of device scratch"):
-        h.conditionals_noalloc(5, big)
+    # more partial configurations than one call may score: refused before
+    # anything is copied or launched, by both entry points
+    for count in (1025, 5000):
+        cfg = _random_configs(h, 5, count, 6)
+        with pytest.raises(SgtnError, match="SGTN_MAX_BEAM"):
+            h.conditionals_noalloc(5, cfg)
+        with pytest.raises(SgtnError, match="SGTN_MAX_BEAM"):
+            h.conditionals(5, cfg)
     cfg = _random_configs(h, 5, 8, 5)               # still usable afterwards
-    assert np.allclose(h.conditionals_noalloc(5, cfg), h.conditionals(5, cfg), rtol=RTOL, atol=0.0)
+    assert np.allclose(h.conditionals_noalloc(5, cfg), h.conditionals(5, cfg), rtol=1e-10, atol=0.0)
+    full = _random_configs(h, 5, 1024, 7)           # the largest count is accepted
+    assert np.allclose(h.conditionals_noalloc(5, full), h.conditionals(5, full), rtol=1e-10, atol=0.0)
+    h.close()
+    # 4096 states per cell: 1024 x 4096 scores alone fill the 32 MiB array
+    peg = L.pegasus_nice(4, 1)
+    states = L.hamming_ball_states(peg, 4096, seed=2)
+    h = Handle(peg, states)
+    h.set_beta(0.5)
+    h.contract_boundary(4, n_sweeps=1)
+    cfg = _random_configs(h, 4, 1024, 8)
+    with pytest.raises(SgtnError, match="bytes of device scratch"):
+        h.conditionals_noalloc(4, cfg)
+    small = _random_configs(h, 4, 16, 9)
+    assert np.allclose(h.conditionals_noalloc(4, small), h.conditionals(4, small), rtol=1e-10, atol=0.0)
     h.close()
