@@ -9,6 +9,7 @@ deltas) and then runs textbook dense MPS algebra with numpy.
 
 Modules
 -------
+energy  the exact Ising energy of Eq. (1) (int64 numerators)
 potts   clustering of Ising spins into Potts variables (Sec. III, Eqs. 2-4)
 peps    dense row MPOs, zipper + variational boundary MPS, log Z (Figs. 5-8, Eq. 9)
 search  conditional marginals and branch-and-bound with boundary merging (Eqs. 5-8, Figs. 3, 6)

@@ -37,6 +37,7 @@ from collections import deque
 
 import numpy as np
 
+from .energy import energy_num
 from .peps import boundary_mps
 from .potts import PottsModel
 from .search import boundary_key, boundary_pairs, conditional_scores, merge_and_cut
@@ -95,7 +96,7 @@ def search_droplets(inst, beta, chi, M, max_dE, min_hamming, n_sweeps=2, states=
         return pm.spins_of_config(cfg)
 
     def e_placed(cfg):
-        return inst.energy_num(spins(cfg))          # unplaced spins are 0: only the placed part counts
+        return energy_num(inst, spins(cfg))          # unplaced spins are 0: only the placed part counts
 
     beam = [((), 0.0)]
     drops = {(): []}

@@ -23,14 +23,19 @@ Index conventions (readings where the figures are missing):
 * MPS tensors are stored [sigma][chi_left][chi_right].
 
 Contraction (Fig. 8): psi_{R-1} is the trivial MPS; psi_{r-1} ~ Trunc(T_r psi_r)
-for r = R-1..1.  Each step: left-canonicalise psi_r (QR); zipper right to
-left starting from a 1x1x1 connecting tensor, keeping the top 2 chi singular
-values of each dashed-box tensor (dense SVD here: the plain definition of the
-optimal rank-k truncation); ``n_sweeps`` one-site variational sweeps
-maximising the overlap with T_r psi_r (Fig. 8d); cut to chi by an SVD sweep;
-``n_sweeps`` more sweeps at chi.  Singular values below ``RANK_TOL`` times the
-largest are dropped, in truncations and in every orthonormalisation (exact
-zeros would otherwise leave part of a bond basis arbitrary).
+for r = R-1..1.  Each step (Sec. III.B, "Variational zipper algorithm"):
+left-canonicalise psi_r; zipper right to left starting from a 1x1x1
+connecting tensor, keeping the top 2 chi singular values of each dashed-box
+tensor (dense SVD here: the plain definition of the optimal rank-k
+truncation), and after EACH zipper step one sweep of one-site variational
+optimisation of the instantaneous stage (Fig. 8d): the tensors built so far
+(columns c..C-1, or the ``window`` columns next to the zipper centre) are
+re-optimised to maximise their overlap with the product of the MPO and MPS
+columns c..C-1, whose left bond is left open (the connecting tensor is the
+centre of that stage); then the 2 chi -> chi cut by an SVD sweep and
+``n_sweeps`` full sweeps at chi.  Singular values below ``RANK_TOL`` times
+the largest are dropped, in truncations and in every orthonormalisation
+(exact zeros would otherwise leave part of a bond basis arbitrary).
 log Z = offset + log-norms + log <T_0 | psi_0>.
 """
 from __future__ import annotations
@@ -141,7 +146,7 @@ class TransposedRowMPO:
         return self._W[c]
 
 
-def upper_boundary_mps(pm: PottsModel, mpos, chi: int, n_sweeps: int = 2):
+def upper_boundary_mps(pm: PottsModel, mpos, chi: int, n_sweeps: int = 2, window: int = 0):
     """E_0..E_{R-1}: E_r covers rows 0..r-1 as a function of row r's up classes.
 
     Built top-down with the same row step (zipper, sweeps, cut) applied to the
@@ -152,7 +157,7 @@ def upper_boundary_mps(pm: PottsModel, mpos, chi: int, n_sweeps: int = 2):
     E[0] = trivial_mps(C)
     for r in range(R - 1):
         A, ln = E[r]
-        E[r + 1] = row_step(TransposedRowMPO(mpos[r]), A, ln, chi, n_sweeps)
+        E[r + 1] = row_step(TransposedRowMPO(mpos[r]), A, ln, chi, n_sweeps, window)
     return E
 
 
@@ -206,29 +211,6 @@ def keep_count(s, cap):
     return min(cap, k)
 
 
-def zipper(mpo: RowMPO, A, lognorm, chi_cap):
-    """Right-to-left zipper of Fig. 8(c) with SVD truncation to chi_cap; returns right-canonical MPS.
-
-    ``A`` must be left-canonical (Fig. 8c starts from that form).
-    """
-    C = len(A)
-    K = np.ones((1, 1, 1))
-    out = [None] * C
-    for c in range(C - 1, -1, -1):
-        W = mpo.dense(c)
-        theta = np.einsum("abus,sij,bjk->aiuk", W, A[c], K, optimize=True)
-        bl, al, u, kk = theta.shape
-        Uu, s, Vh = np.linalg.svd(theta.reshape(bl * al, u * kk), full_matrices=False)
-        k = keep_count(s, chi_cap)
-        out[c] = Vh[:k].reshape(k, u, kk).transpose(1, 0, 2)
-        K = (Uu[:, :k] * s[:k]).reshape(bl, al, k)
-        n = np.linalg.norm(K)
-        lognorm += np.log(n)
-        K = K / n
-    out[0] = out[0] * K.reshape(())         # K is 1x1x1 holding +-1
-    return out, lognorm
-
-
 def _opt(L, W, A, R):
     """Optimal one-site tensor phi_c[u, a, a'] = sum L[a,bl,i] W[bl,br,u,s] A[s,i,j] R[a',br,j]."""
     t = np.einsum("sij,cBj->siBc", A, R)                 # [s, i, br, a']
@@ -248,6 +230,95 @@ def _upd_R(R, phi, W, A):
     t = np.einsum("sij,cBj->siBc", A, R)                 # [s, i, br, a']
     t = np.einsum("bBus,siBc->buic", W, t, optimize=True)  # [bl, u, i, a']
     return np.einsum("uac,buic->abi", phi, t, optimize=True)
+
+
+def stage_sweep(Ws, A, phi, K, c0, e):
+    """One-site variational sweep of the zipper's instantaneous stage (Fig. 8d).
+
+    At zipper column c0 the approximation of the target Y = (W_c0 A_c0) ...
+    (W_{C-1} A_{C-1}) -- the MPO-MPS product of the columns done so far, its
+    left bond (bl, al) left open -- is K phi[c0] ... phi[C-1], with K[bl, al, k]
+    the connecting tensor (the centre) and phi right-canonical.  The sweep
+    re-optimises phi[c0..e] one tensor at a time, left to right and back, each
+    update being the exact maximiser of the overlap with Y given all other
+    tensors (in canonical form); tensors right of e stay fixed.  Returns the
+    new K = <phi[c0..] | Y> (the optimal centre for the new phi).
+    """
+    C = len(A)
+    # right environments of the fixed tensors e+1..C-1, then of the window
+    R = [None] * C
+    Rt = np.ones((1, 1, 1))
+    for j in range(C - 1, e, -1):
+        Rt = _upd_R(Rt, phi[j], Ws[j], A[j])
+    R[e] = Rt
+    for j in range(e, c0, -1):
+        R[j - 1] = _upd_R(R[j], phi[j], Ws[j], A[j])
+    # the centre moves from K onto phi[c0]: K's orthonormal factor becomes
+    # the left environment of column c0 (the open bond is its "basis")
+    bl, al, k = K.shape
+    Q, _ = orthonormalise(K.reshape(bl * al, k))
+    L = [None] * C
+    L[c0] = Q.reshape(bl, al, Q.shape[1]).transpose(2, 0, 1)      # [a, bl, i]
+    for j in range(c0, e + 1):
+        t = _opt(L[j], Ws[j], A[j], R[j])
+        if j < e:
+            u, a, b = t.shape
+            Qj, _ = orthonormalise(t.reshape(u * a, b))
+            phi[j] = Qj.reshape(u, a, Qj.shape[1])
+            L[j + 1] = _upd_L(L[j], phi[j], Ws[j], A[j])
+        else:
+            phi[j] = t
+    Rc = R[e]
+    for j in range(e, c0 - 1, -1):
+        t = _opt(L[j], Ws[j], A[j], Rc)
+        u, a, b = t.shape
+        Qr, _ = orthonormalise(t.transpose(1, 0, 2).reshape(a, u * b).T)
+        phi[j] = Qr.T.reshape(Qr.shape[1], u, b).transpose(1, 0, 2)
+        Rc = _upd_R(Rc, phi[j], Ws[j], A[j])
+    return phi, Rc.transpose(1, 2, 0)                                 # [bl, al, k]
+
+
+def zipper(mpo: RowMPO, A, lognorm, chi_cap, window=0, trace=None):
+    """Right-to-left zipper of Fig. 8(c) with a variational sweep after each step.
+
+    ``A`` must be left-canonical (Fig. 8c starts from that form).  At column c
+    the dashed-box tensor Theta = (W_c A_c) K is truncated by an SVD to at most
+    ``chi_cap`` values (new tensor V^T, right-canonical; K <- U S), then the
+    instantaneous stage is swept (``stage_sweep``) over columns c..e with
+    e = C-1 (``window`` <= 0: every tensor built so far) or
+    e = min(C-1, c + window - 1).  Returns the right-canonical MPS with the
+    norm of the last connecting tensor (a 1x1x1 tensor) in ``lognorm`` and its
+    sign in column 0.  ``trace`` (a list, optional) receives (c, tensors of
+    columns c..C-1, connecting tensor after the step's sweep, connecting
+    tensor before it) after every zipper step, both connecting tensors on the
+    scale of the input MPS.
+    """
+    C = len(A)
+    Ws = [mpo.dense(c) for c in range(C)]
+    K = np.ones((1, 1, 1))
+    ln = lognorm
+    out = [None] * C
+    for c in range(C - 1, -1, -1):
+        theta = np.einsum("abus,sij,bjk->aiuk", Ws[c], A[c], K, optimize=True)
+        bl, al, u, kk = theta.shape
+        Uu, s, Vh = np.linalg.svd(theta.reshape(bl * al, u * kk), full_matrices=False)
+        k = keep_count(s, chi_cap)
+        out[c] = Vh[:k].reshape(k, u, kk).transpose(1, 0, 2)
+        K = (Uu[:, :k] * s[:k]).reshape(bl, al, k)
+        e = C - 1 if window <= 0 else min(C - 1, c + window - 1)
+        K_before = K * np.exp(ln - lognorm) if trace is not None else None
+        if e > c:
+            # the sweep's centre is computed from Y itself, so its scale is
+            # relative to the input MPS alone
+            out, K = stage_sweep(Ws, A, out, K, c, e)
+            ln = lognorm
+        if trace is not None:
+            trace.append((c, [t.copy() for t in out[c:]], K * np.exp(ln - lognorm), K_before))
+        n = np.linalg.norm(K)
+        ln += np.log(n)
+        K = K / n
+    out[0] = out[0] * K.reshape(())         # K is 1x1x1 holding +-1
+    return out, ln
 
 
 def right_canonical(phi):
@@ -317,13 +388,11 @@ def normalise_centre(phi, lognorm, centre):
     return phi, lognorm + np.log(n)
 
 
-def row_step(mpo: RowMPO, A, lognorm, chi, n_sweeps):
-    """psi_{r-1} ~ T_r psi_r: zipper at 2 chi, sweeps, cut to chi, sweeps (Fig. 8; two-step truncation)."""
+def row_step(mpo: RowMPO, A, lognorm, chi, n_sweeps, window=0):
+    """psi_{r-1} ~ T_r psi_r (Fig. 8; Sec. III.B): zipper at 2 chi with a sweep
+    after every zipper step, cut to chi, ``n_sweeps`` sweeps at chi."""
     A, lognorm = left_canonical(A, lognorm)
-    phi, ln = zipper(mpo, A, lognorm, 2 * chi)
-    for _ in range(n_sweeps):
-        phi = variational_sweep(mpo, A, phi)
-        phi, ln = normalise_centre(phi, lognorm, 0)
+    phi, ln = zipper(mpo, A, lognorm, 2 * chi, window)
     phi = svd_cut(phi, chi)
     phi, ln = normalise_centre(phi, ln, len(phi) - 1)
     for _ in range(n_sweeps):
@@ -332,7 +401,7 @@ def row_step(mpo: RowMPO, A, lognorm, chi, n_sweeps):
     return phi, ln
 
 
-def boundary_mps(pm: PottsModel, beta: float, chi: int, n_sweeps: int = 2):
+def boundary_mps(pm: PottsModel, beta: float, chi: int, n_sweeps: int = 2, window: int = 0):
     """All boundary MPSs psi_0..psi_{R-1} (psi_r covers rows below r) and log Z (Eq. 9)."""
     R, C = pm.R, pm.C
     mpos = [RowMPO(pm, r, beta) for r in range(R)]
@@ -340,7 +409,7 @@ def boundary_mps(pm: PottsModel, beta: float, chi: int, n_sweeps: int = 2):
     psis[R - 1] = trivial_mps(C)
     for r in range(R - 1, 0, -1):
         A, ln = psis[r]
-        psis[r - 1] = row_step(mpos[r], A, ln, chi, n_sweeps)
+        psis[r - 1] = row_step(mpos[r], A, ln, chi, n_sweeps, window)
     logz = log_offset(pm, beta) + top_row_log_overlap(mpos[0], *psis[0])
     return logz, psis, mpos
 

@@ -18,6 +18,8 @@ from __future__ import annotations
 
 import numpy as np
 
+from .energy import energy_num
+
 # neighbour directions of site (r, c): name -> (dr, dc)
 DIRS = {"r": (0, 1), "l": (0, -1), "d": (1, 0), "u": (-1, 0),
         "dr": (1, 1), "dl": (1, -1), "ur": (-1, 1), "ul": (-1, -1)}
@@ -163,4 +165,4 @@ class PottsModel:
 
     def state_energy_num(self, config) -> int:
         """Energy numerator of a full Potts configuration (state index per site)."""
-        return self.inst.energy_num(self.spins_of_config(config))
+        return energy_num(self.inst, self.spins_of_config(config))

@@ -21,19 +21,23 @@ probable survive.  p_d is the largest log-probability ever discarded (Sec.
 III.A, last paragraph).
 
 Readings: negative scores (possible with an approximate boundary MPS) are
-clamped to zero and counted.  Integer couplings make exactly degenerate
-candidates common, and two correct implementations round differently, so
-log-probabilities within TIE_REL (relative) of each other count as equal and
-are ordered by configuration (lexicographically smaller first, in placement
-order): in a merge group every candidate within tolerance of the group's
-maximum is a tie and the smallest configuration wins; at the top-M cut the
-candidates within tolerance of the M-th value form a tie class filled in
-configuration order.
+clamped to zero and counted.  "Keep the most probable" (Fig. 3d-e) needs a
+rule for equal probabilities, and integer couplings make exactly degenerate
+candidates common; their log-probabilities, computed along different
+contraction paths, differ only by rounding, so "equal" is read as "within
+TIE_REL (relative)", and equal candidates are ordered by configuration
+(lexicographically smaller first, in placement order): in a merge group
+every candidate within tolerance of the group's maximum is a tie and the
+smallest configuration wins; at the top-M cut the candidates within tolerance
+of the M-th value form a tie class filled in configuration order.  A winner
+is therefore never less probable than the most probable candidate it beats
+by more than the tolerance.
 """
 from __future__ import annotations
 
 import numpy as np
 
+from .energy import energy_num
 from .peps import boundary_mps
 from .potts import DIRS, PottsModel
 
@@ -145,10 +149,14 @@ def boundary_key(pm, pairs, cfg):
     return tuple(pm.sites[p].proj[d].of_state[cfg[p]] for (p, l, d) in pairs)
 
 
-def search(inst, beta, chi, M, n_sweeps=2, states=None, psis=None):
-    """Branch and bound over all clusters; returns the final beam sorted by (-log p, configuration)."""
+def search(inst, beta, chi, M, n_sweeps=2, states=None, psis=None, window=0, trace=None):
+    """Branch and bound over all clusters; returns the final beam sorted by (-log p, configuration).
+
+    ``trace`` (a list, optional) receives one (beam, largest log p discarded
+    at that step) pair per step.
+    """
     pm = PottsModel(inst, states)
-    logz, psis_, mpos = boundary_mps(pm, beta, chi, n_sweeps)
+    logz, psis_, mpos = boundary_mps(pm, beta, chi, n_sweeps, window)
     psis = psis_ if psis is None else psis
     C = pm.C
     beam = [((), 0.0)]
@@ -171,8 +179,10 @@ def search(inst, beta, chi, M, n_sweeps=2, states=None, psis=None):
                     (cand, lp + float(np.log(s[x] / tot))))
         beam, pd_step = merge_and_cut(cands, M)
         pd = max(pd, pd_step)
+        if trace is not None:
+            trace.append((list(beam), pd_step))
     configs = [b[0] for b in beam]
     spins = np.array([pm.spins_of_config(cfg) for cfg in configs], dtype=np.int8)
-    energies = np.array([inst.energy_num(s) for s in spins], dtype=np.int64)
+    energies = np.array([energy_num(inst, s) for s in spins], dtype=np.int64)
     return dict(configs=configs, logp=np.array([b[1] for b in beam]), pd=pd, spins=spins,
                 energy_num=energies, logz=logz, clamps=clamps, evals=evals, pm=pm, psis=psis, mpos=mpos)

@@ -449,3 +449,264 @@ def test_search_tie_rule_on_a_flat_landscape():
     assert res["configs"][0] == (0,) * (inst.rows * inst.cols)
     assert int(res["energy_num"][0]) == 0
     assert abs(res["logp"][0] + inst.n_spins * np.log(2)) < 1e-10
+
+
+# --- the zipper's instantaneous-stage sweep and the cut (Sec. III.B, Fig. 8) ---------
+
+def _chain(tensors, first_open):
+    """Dense product of column tensors G_j[bond_in, bond_out, u] over the columns, the
+    first bond_in left open when ``first_open`` (result [bond_in, physical...])."""
+    Y = tensors[0]
+    for G in tensors[1:]:
+        Y = np.einsum("xbp,bcu->xcpu", Y, G).reshape(Y.shape[0], G.shape[1], -1)
+    assert Y.shape[1] == 1
+    return Y[:, 0, :] if first_open else Y[0, 0, :]
+
+
+def _mpo_mps_columns(Ws, A, c0):
+    """(W_j A_j)[(bl, i), (br, j), u] for the columns c0..C-1 (plain einsum of the definitions)."""
+    out = []
+    for W, a in zip(Ws[c0:], A[c0:]):
+        G = np.einsum("abus,sij->aibju", W, a)
+        out.append(G.reshape(G.shape[0] * G.shape[1], G.shape[2] * G.shape[3], G.shape[4]))
+    return out
+
+
+def _random_right_canonical(rng, dims, bonds):
+    """phi[j][u, a, b] with orthonormal rows of the (a) x (u, b) matrix, right bond of the last = 1."""
+    phi = []
+    for j, u in enumerate(dims):
+        a, b = bonds[j], bonds[j + 1]
+        Q, _ = np.linalg.qr(rng.standard_normal((u * b, a)))
+        phi.append(Q.T.reshape(a, u, b).transpose(1, 0, 2))
+    return phi
+
+
+@pytest.mark.parametrize("e_off", [None, 1], ids=["full", "window2"])
+def test_stage_sweep_centre_is_projection_and_captured_weight_grows(e_off):
+    """One sweep of the zipper's instantaneous stage (Fig. 8d) over columns c0..e with the
+    left bond open: the returned centre is the projection <phi|Y> of the dense target Y
+    (the MPO-MPS product of columns c0..C-1), the new phi are right-canonical, tensors right
+    of e are untouched, and the captured weight |<phi|Y>|^2 never decreases (each one-site
+    update maximises the overlap) and does grow from a random start."""
+    from oracle.peps import RowMPO, left_canonical, stage_sweep
+    inst = L.kings_grid(3, 5, 7)
+    pm = PottsModel(inst)
+    mpo = RowMPO(pm, 1, 0.9)
+    C = pm.C
+    Ws = [mpo.dense(c) for c in range(C)]
+    rng = np.random.default_rng(5)
+    bonds_A = [1, 2, 3, 3, 2, 1]
+    A = [rng.standard_normal((mpo.cols[c]["nsig"], bonds_A[c], bonds_A[c + 1])) for c in range(C)]
+    A, _ = left_canonical(A, 0.0)
+    c0 = 1
+    e = C - 1 if e_off is None else c0 + e_off
+    dims = [mpo.cols[c]["nU"] for c in range(c0, C)]
+    phi = [None] * c0 + _random_right_canonical(rng, dims, [2, 2, 2, 2, 1])
+    Y = _chain(_mpo_mps_columns(Ws, A, c0), True)                    # [(bl, al), P]
+    Phi = _chain([p.transpose(1, 2, 0) for p in phi[c0:]], True)    # [k, P]
+    assert np.allclose(Phi @ Phi.T, np.eye(Phi.shape[0]), atol=1e-12)
+    K0 = Y @ Phi.T
+    bl, al = Ws[c0].shape[0], A[c0].shape[1]
+    kept = [p.copy() for p in phi[e + 1:]]
+    new, K = stage_sweep(Ws, A, list(phi), K0.reshape(bl, al, -1), c0, e)
+    Phi2 = _chain([p.transpose(1, 2, 0) for p in new[c0:]], True)
+    assert np.allclose(Phi2 @ Phi2.T, np.eye(Phi2.shape[0]), atol=1e-12)
+    Kd = K.reshape(bl * al, -1)
+    assert np.allclose(Kd, Y @ Phi2.T, rtol=0, atol=1e-12 * np.abs(Kd).max())
+    for a, b in zip(kept, new[e + 1:]):
+        assert np.array_equal(a, b)
+    w0, w1 = np.sum(K0 ** 2), np.sum(Kd ** 2)
+    assert w1 >= w0 * (1 - 1e-12) and w1 > w0 * (1 + 1e-6)
+    # a second sweep from the first's output does not lose weight either
+    _, K2 = stage_sweep(Ws, A, list(new), K, c0, e)
+    assert np.sum(K2 ** 2) >= w1 * (1 - 1e-12)
+
+
+def test_two_column_row_reaches_eckart_young():
+    """A single two-column row applied to the trivial MPS is the matrix v[u0, u1] of the row's
+    Boltzmann weights summed per pair of up-exposure patterns (by enumeration of the row's
+    spins).  One bond is truncated, so the best bond-chi MPS is the truncated SVD of v
+    (Eckart-Young); the zipper with its sweeps, the cut and repeated sweeps (block power
+    iteration on v) must reach it: same direction to 1e-10, captured weight = the kept
+    singular values' share."""
+    inst = L.chimera_grid(2, 2, 3)
+    beta = 0.6
+    row = [i for i in range(inst.n_spins) if inst.site_of_spin[i] >= 2]           # row 1 spins
+    in_row = np.zeros(inst.n_spins, bool)
+    in_row[row] = True
+    up = {c: [] for c in (0, 1)}
+    for i, j in zip(inst.ei.tolist(), inst.ej.tolist()):
+        for a, b in ((i, j), (j, i)):
+            if in_row[a] and not in_row[b]:
+                up[int(inst.site_of_spin[a]) - 2].append(a)
+    up = {c: sorted(set(v)) for c, v in up.items()}
+    S = brute.all_spins(len(row)).astype(np.int64)
+    pos = {g: k for k, g in enumerate(row)}
+    E = np.zeros(len(S), np.int64)
+    for i, j, J in zip(inst.ei.tolist(), inst.ej.tolist(), inst.j_num.tolist()):
+        if in_row[i] and in_row[j]:
+            E += J * S[:, pos[i]] * S[:, pos[j]]
+    for i in row:
+        E += int(inst.h_num[i]) * S[:, pos[i]]
+    w = np.exp(-beta * (E - E.min()) / inst.denom)
+    pat = [sum(((S[:, pos[g]] < 0).astype(np.int64) << k) for k, g in enumerate(up[c])) for c in (0, 1)]
+    v = np.zeros((1 << len(up[0]), 1 << len(up[1])))
+    np.add.at(v, (pat[0], pat[1]), w)
+    sv = np.linalg.svd(v, compute_uv=False)
+    chi = next(k for k in range(1, len(sv) - 1) if sv[k] < 0.5 * sv[k - 1])
+    U, s, Vh = np.linalg.svd(v)
+    v_chi = (U[:, :chi] * s[:chi]) @ Vh[:chi]
+    _, psis, _ = boundary_mps(PottsModel(inst), beta, chi=chi, n_sweeps=30)
+    A, ln = psis[0]
+    assert A[0].shape[2] == chi
+    from oracle.peps import mps_dense
+    phi = mps_dense(A)
+    phi_hat = phi / np.linalg.norm(phi)
+    assert np.allclose(phi_hat, v_chi / np.linalg.norm(v_chi), rtol=0, atol=1e-10)
+    # the overlap with v captures exactly the kept share of the weight
+    fid = np.sum(phi_hat * v) ** 2 / np.sum(v * v)
+    assert abs(fid - np.sum(s[:chi] ** 2) / np.sum(s ** 2)) < 1e-10
+
+
+# --- the bounding with a real top-M cut (Fig. 3d-e, Eq. 7) ------------------------------
+
+def _site_states_of_spins(pm, S):
+    """Cluster state index of every spin configuration, per site (full enumeration: index = pattern)."""
+    X = np.zeros((len(S), len(pm.sites)), np.int64)
+    for t, site in enumerate(pm.sites):
+        for k, g in enumerate(site.spins):
+            X[:, t] |= (S[:, g] < 0).astype(np.int64) << k
+    return X
+
+
+@pytest.mark.parametrize("M", [1, 3, 8])
+@pytest.mark.parametrize("inst", [L.kings_grid(4, 4, 3), L.square_grid(3, 5, 12),
+                                  L.slice_cells(L.chimera_grid(4, 4, 0), 2, 1)], ids=lambda i: i.name)
+def test_top_m_cut_matches_brute_force_partial_marginals(inst, M):
+    """With an exact contraction, every step's beam is a top-M set of the previous beam's
+    extensions after merging by boundary (Eq. 7), with the exact partial marginals
+    p(x_1..x_n) = sum over completions of exp(-beta H) / Z by enumeration: kept candidates
+    lie in distinct boundary groups, each is its group's most probable, no discarded group
+    is more probable than a kept one, min(M, #groups) are kept, and p_d is the most
+    probable candidate not kept."""
+    beta = 1.1
+    trace = []
+    res = search(inst, beta, chi=256, M=M, n_sweeps=1, trace=trace)
+    pm = res["pm"]
+    S = brute.all_spins(inst.n_spins)
+    lw = -beta * brute.energies_num(inst, S) / inst.denom
+    lz = float(np.logaddexp.reduce(lw))
+    X = _site_states_of_spins(pm, S)
+    nb = {}
+    for i, j in zip(inst.ei.tolist(), inst.ej.tolist()):
+        nb.setdefault(i, set()).add(j)
+        nb.setdefault(j, set()).add(i)
+    site_of = inst.site_of_spin
+    tol = 1e-9
+    beam = [()]
+    for n, (kept, pd_step) in enumerate(trace):
+        exposed = sorted(g for g in range(inst.n_spins) if site_of[g] <= n and any(site_of[q] > n for q in nb.get(g, ())))
+        cand = {}
+        for cfg in beam:
+            m = np.all(X[:, :n] == np.array(cfg, np.int64)[None, :], axis=1) if n else np.ones(len(S), bool)
+            for x in range(pm.sites[n].d):
+                mm = m & (X[:, n] == x)
+                lp = float(np.logaddexp.reduce(lw[mm])) - lz
+                c = cfg + (x,)
+                spins = pm.spins_of_config(c + (0,) * (len(pm.sites) - n - 1))
+                cand[c] = (lp, tuple(int(spins[g]) for g in exposed))
+        groups = {}
+        for c, (lp, key) in cand.items():
+            groups[key] = max(groups.get(key, -np.inf), lp)
+        kcfg = [c for c, _ in kept]
+        assert len(kcfg) == min(M, len(groups))
+        assert len(set(cand[c][1] for c in kcfg)) == len(kcfg)
+        for c, lp in kept:
+            assert abs(lp - cand[c][0]) < tol
+            assert cand[c][0] >= groups[cand[c][1]] - tol
+        kept_keys = set(cand[c][1] for c in kcfg)
+        worst_kept = min(cand[c][0] for c in kcfg)
+        for key, top in groups.items():
+            if key not in kept_keys:
+                assert top <= worst_kept + tol
+        rest = [lp for c, (lp, _) in cand.items() if c not in set(kcfg)]
+        if rest:
+            assert abs(pd_step - max(rest)) < tol
+        else:
+            assert pd_step == -np.inf
+        beam = kcfg
+
+
+def test_tie_rule_never_prefers_a_less_probable_candidate_beyond_the_tolerance():
+    """merge_and_cut on random groups with exact and near ties (the rule that makes
+    degenerate candidates deterministic): a merge winner is never less probable than its
+    group's best by more than the tie tolerance, no discarded group beats a kept one by
+    more than it, and where all log-probabilities are well separated the result is the
+    plain argmax per group and the plain top-M."""
+    from oracle.search import merge_and_cut, tie_tol
+    rng = np.random.default_rng(11)
+    for trial in range(300):
+        M = int(rng.integers(1, 6))
+        base = rng.choice([-3.0, -2.0, -2.0 + 1e-13, -1.5, -1.5 - 4e-12], size=int(rng.integers(1, 15)))
+        sep = trial % 2 == 1
+        if sep:
+            base = -rng.permutation(np.arange(len(base))) * 0.37 - 1.0
+        cands = {}
+        for i, lp in enumerate(base):
+            key = int(rng.integers(0, 4))
+            cands.setdefault(key, []).append(((int(rng.integers(0, 9)), i), float(lp)))
+        kept, pd = merge_and_cut(cands, M)
+        best = {k: max(lp for _, lp in g) for k, g in cands.items()}
+        key_of = {cfg: k for k, g in cands.items() for cfg, _ in g}
+        assert len(kept) == min(M, len(cands))
+        for cfg, lp in kept:
+            assert lp >= best[key_of[cfg]] - tie_tol(best[key_of[cfg]])
+        worst = min(lp for _, lp in kept)
+        kept_keys = {key_of[c] for c, _ in kept}
+        for k, b in best.items():
+            if k not in kept_keys:
+                assert b <= worst + tie_tol(worst)
+        allc = [t for g in cands.values() for t in g]
+        rest = [lp for cfg, lp in allc if cfg not in {c for c, _ in kept}]
+        assert pd == (max(rest) if rest else -np.inf)
+        if sep:
+            winners = sorted(((max(g, key=lambda t: t[1])) for g in cands.values()), key=lambda t: -t[1])[:M]
+            assert [c for c, _ in kept] == [c for c, _ in winners]
+
+
+@pytest.mark.parametrize("window", [0, 2])
+def test_every_zipper_step_is_followed_by_a_sweep_of_its_stage(window):
+    """Sec. III.B: each zipper step is followed by a variational sweep of the instantaneous
+    stage.  At every step the connecting tensor is the projection <phi[c..]|Y_c> of the
+    stage's target Y_c (the dense MPO-MPS product of columns c..C-1) onto the tensors built
+    so far -- the zipper's own truncation already gives that -- and the sweep can only raise
+    the captured weight |<phi[c..]|Y_c>|^2; it does raise it on this truncated row, while a
+    zipper without the sweeps (window 1) leaves every stage as the truncation made it."""
+    from oracle.peps import RowMPO, left_canonical, zipper
+    inst = L.kings_grid(3, 5, 7)
+    pm = PottsModel(inst)
+    mpo = RowMPO(pm, 1, 1.3)
+    C = pm.C
+    Ws = [mpo.dense(c) for c in range(C)]
+    rng = np.random.default_rng(8)
+    bonds_A = [1, 2, 4, 4, 2, 1]
+    A = [rng.standard_normal((mpo.cols[c]["nsig"], bonds_A[c], bonds_A[c + 1])) for c in range(C)]
+    A, ln = left_canonical(A, 0.0)
+
+    def stages(w):
+        trace = []
+        zipper(mpo, A, ln, 2, window=w, trace=trace)
+        gains = []
+        for c, tens, K, Kb in trace:
+            Y = _chain(_mpo_mps_columns(Ws, A, c), True)
+            Phi = _chain([p.transpose(1, 2, 0) for p in tens], True)
+            P = Y @ Phi.T
+            assert np.allclose(K.reshape(P.shape), P, rtol=0, atol=1e-11 * np.abs(P).max())
+            gains.append(np.sum(K ** 2) / np.sum(Kb ** 2) - 1.0)
+        assert len(gains) == C
+        return gains
+
+    g = stages(window)
+    assert min(g) > -1e-12 and max(g) > 1e-6
+    assert max(abs(x) for x in stages(1)) < 1e-12     # no sweeps: nothing changes after the truncation
