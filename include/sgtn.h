@@ -85,8 +85,10 @@ int sgtn_set_beta(sgtn_h h, double beta);
 
 /* Boundary-MPS contraction of Sec. III.B (Figs. 6-8): for r = R-1 .. 1,
  * psi_{r-1} ~ T_r psi_r by the right-to-left zipper keeping 2*chi singular
- * values, n_sweeps one-site variational sweeps, a cut to chi and n_sweeps
- * more sweeps.  All boundary MPSs stay resident on the device for the
+ * values, each zipper step followed by a one-site variational sweep of the
+ * instantaneous stage (Sec. III.B "Variational zipper algorithm", Fig. 8d;
+ * its range is set by sgtn_set_zipper_window), then a cut to chi and
+ * n_sweeps full sweeps at chi.  All boundary MPSs stay resident on the device for the
  * branch step.  precision: SGTN_FP64 (everything in double) or a mixed mode
  * (contractions on tensor cores, truncation and log-norms in double).
  *   out_logz            log Z of Eq. (9) (may be NULL); NaN when the
@@ -106,9 +108,12 @@ int sgtn_contract_boundary(sgtn_h h, int32_t chi, int32_t precision, int32_t n_s
 int sgtn_conditionals(sgtn_h h, int32_t step, int32_t count, const int32_t* configs, double* out_p);
 
 /* Largest number of partial configurations one call scores together: `count`
- * of sgtn_conditionals(_noalloc), `in_count` of sgtn_branch_step and the beam
- * width M of sgtn_search / sgtn_batch_search / sgtn_search_droplets.  Larger
- * values return SGTN_ERR_ARG before anything is copied or launched. */
+ * of sgtn_conditionals(_noalloc) and `in_count` of sgtn_branch_step (larger
+ * values return SGTN_ERR_ARG before anything is copied or launched), and the
+ * number of live branches in sgtn_search / sgtn_batch_search /
+ * sgtn_search_droplets: M itself may be larger (a cap the bounding never
+ * reaches), but a step whose beam would exceed SGTN_MAX_BEAM returns
+ * SGTN_ERR_ARG before its launches. */
 #define SGTN_MAX_BEAM 1024
 
 /* One branch-and-bound step (Sec. III.A, Fig. 3): branch every input
@@ -225,6 +230,16 @@ int sgtn_site_dims(sgtn_h h, int32_t site, int32_t* d);
  * fix it, e.g. an FP64 boundary (exact log Z) with FP32 conditional scores.
  * SGTN_ERR_ARG for any other value. */
 int sgtn_set_search_precision(sgtn_h h, int32_t precision);
+
+/* Range of the variational sweep that follows each zipper step of
+ * sgtn_contract_boundary (Sec. III.B, "Variational zipper algorithm", Fig.
+ * 8d): the sweep re-optimises the boundary-MPS tensors built so far, or, to
+ * limit the effort as the paper allows, only the `window` tensors next to the
+ * zipper centre.  0 (the default): every tensor built so far; 1: no sweep
+ * (the plain zipper of Fig. 8c); w > 1: columns c..c+w-1 after the step at
+ * column c.  Takes effect at the next sgtn_contract_boundary (and
+ * sgtn_logz_grad); SGTN_ERR_ARG for a negative value. */
+int sgtn_set_zipper_window(sgtn_h h, int32_t window);
 
 int sgtn_boundary_info(sgtn_h h, int32_t* unconverged_cuts, int32_t* precision);
 int sgtn_mps_shape(sgtn_h h, int32_t row, int32_t* phys, int32_t* bond, double* lognorm);

@@ -227,6 +227,13 @@ int sgtn_set_search_precision(sgtn_h h, int32_t precision) {
   });
 }
 
+int sgtn_set_zipper_window(sgtn_h h, int32_t window) {
+  return guarded(h, [&] {
+    if (window < 0) throw SgtnError(SGTN_ERR_ARG, "zipper window must be >= 0");
+    h->zipper_window = window;
+  });
+}
+
 int sgtn_boundary_info(sgtn_h h, int32_t* unconverged_cuts, int32_t* precision) {
   return guarded(h, [&] {
     if (unconverged_cuts) *unconverged_cuts = h->unconverged_cuts;
@@ -333,7 +340,6 @@ int sgtn_batch_search(sgtn_h* hs, int32_t n, double beta, int32_t chi, int32_t p
   if (n == 0) return SGTN_OK;
   if (!hs || !status || !out_spins || !out_energy_num || !out_logp || !out_logz || !out_pd || !out_count)
     return SGTN_ERR_ARG;
-  if (M <= 0 || M > SGTN_MAX_BEAM) return SGTN_ERR_ARG;
   // handles that share a stream form one group, run in order by one thread
   std::vector<std::vector<int>> groups;
   std::map<cudaStream_t, int> gid;

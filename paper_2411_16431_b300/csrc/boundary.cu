@@ -1182,40 +1182,53 @@ SvdOut theta_svd(RowCtx& X, int c, const ThetaOp& T, int cap) {
   return profiled(h, "", T.m, T.n, [&] { return svd_subspace_op(h, T.m, T.n, cap, mul, tmul); });
 }
 
-// One left-right-left sweep of one-site overlap maximisation (Fig. 8d).
-// Environments are rescaled by powers of two after every update (they would
-// under- or overflow, in FP32 first); only the right environment's scale
-// reaches the final centre, and its logarithm is returned.
-double variational_sweep(RowCtx& X, std::vector<Ten>& phi, bool canonical) {
+// Right environments of a row step, kept across the zipper's stages: R[c] is
+// the environment of columns c+1..C-1 at bond (c, c+1), stored
+// [(bl, chl) of column c+1] x [left bond of phi[c+1]] (R[C-1] = 1), and its
+// value is exp(lg[c]) times the stored one (environments are rescaled by
+// powers of two: they would leave the floating-point range).  The zipper's
+// connecting tensor after column c is R[c-1].
+struct RightEnvs {
+  std::vector<double*> R;
+  std::vector<double> lg;
+  explicit RightEnvs(int C) : R(C, nullptr), lg(C, 0.0) {}
+  RightEnvs(const RightEnvs&) = delete;
+  RightEnvs& operator=(const RightEnvs&) = delete;
+  ~RightEnvs() {
+    for (auto& p : R) dfree(p);
+  }
+  void set(int c, double* p, double l) {
+    if (R[c] != p) dfree(R[c]);
+    R[c] = p;
+    lg[c] = l;
+  }
+};
+
+// One sweep of one-site overlap maximisation (Fig. 8d) over columns c0..e of
+// phi, left to right and back.  The target is the MPO-MPS product of columns
+// c0..C-1 with its left bond open when c0 > 0 (the instantaneous stage of the
+// zipper); phi must be right-canonical on c0..C-1, Lc0 [phi[c0].a x (bl, chl)
+// of column c0] is the left environment at c0 (taken over, freed here) and
+// RE.R[c0..e] must hold the environments of the current phi.  Each update is
+// the exact maximiser given the other tensors, made orthonormal by an SVD.
+// Afterwards phi[c0..e] are right-canonical and RE.R[c0-1..e-1] refreshed:
+// for c0 > 0, RE.R[c0-1] is the new connecting tensor (the optimal centre of
+// the stage); for c0 = 0 the centre stays in phi[0] (unnormalised) and the
+// log-scale of its right environment is returned.
+double sweep_range(RowCtx& X, std::vector<Ten>& phi, int c0, int e, double* Lc0, RightEnvs& RE) {
   sgtn_inst* h = X.h;
   TagScope tag("sweep");
-  const bool renorm = true;
   const int C = (int)phi.size();
-  // phi coming from the zipper or from a previous sweep is already right-
-  // canonical (orthonormal rows right of a centre at column 0): bringing it
-  // there again would only change the gauge
-  if (!canonical) right_canonical(X, phi);
-  std::vector<double*> Renv(C, nullptr), Lenv(C, nullptr);
-  Renv[C - 1] = dmalloc(1);
-  fill(Renv[C - 1], 1, 1.0, h->st);
-  for (int c = C - 1; c > 0; --c) {
-    ThetaOp T = theta_op(X, c, Renv[c], phi[c].b);
-    Renv[c - 1] = theta_right(X, c, T, phi[c]);
-    double dummy = 0.0;
-    if (renorm) rescale_pow2(h, Renv[c - 1], (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, dummy);
-  }
-  Lenv[0] = dmalloc(1);
-  fill(Lenv[0], 1, 1.0, h->st);
-  for (int c = 0; c < C; ++c) {
-    const Column& K_ = X.col(c);
-    ThetaOp T = theta_op(X, c, Renv[c], phi[c].b);
-    int a = phi[c].a;
+  std::vector<double*> Lenv(C, nullptr);
+  Lenv[c0] = Lc0;
+  for (int c = c0; c <= e; ++c) {
+    ThetaOp T = theta_op(X, c, RE.R[c], phi[c].b);
+    const int a = phi[c].a;
     double* t = theta_left(X, c, T, Lenv[c], a);
-    (void)K_;
     dfree(phi[c].p);
     phi[c].p = t;
     phi[c].u = X.nout(c);
-    if (c < C - 1) {
+    if (c < e) {
       SvdOut o = svd(h, t, a * X.nout(c), phi[c].b, 1 << 30);
       double* Q = left_factor(h, o, a * X.nout(c));
       dfree(phi[c].p);
@@ -1224,22 +1237,17 @@ double variational_sweep(RowCtx& X, std::vector<Ten>& phi, bool canonical) {
       o.release();
       Lenv[c + 1] = update_L(X, c, Lenv[c], phi[c]);
       double dummy = 0.0;
-      if (renorm) rescale_pow2(h, Lenv[c + 1], (long long)phi[c].b * X.col(c).nBR() * X.chr(c), dummy);
+      rescale_pow2(h, Lenv[c + 1], (long long)phi[c].b * X.col(c).nBR() * X.chr(c), dummy);
       // the next site's left bond is now o.k; its right bond is unchanged
       phi[c + 1].a = phi[c].b;
     }
   }
-  for (auto& p : Renv) dfree(p);
-  double* Rc = dmalloc(1);
-  fill(Rc, 1, 1.0, h->st);
-  double rc_log = 0.0;
-  for (int c = C - 1; c >= 0; --c) {
-    const Column& K_ = X.col(c);
-    ThetaOp T = theta_op(X, c, Rc, phi[c].b);
-    int a = phi[c].a;
-    long long n = (long long)X.nout(c) * phi[c].b;
+  double rc_log = RE.lg[e];
+  for (int c = e; c >= c0; --c) {
+    ThetaOp T = theta_op(X, c, RE.R[c], phi[c].b);
+    const int a = phi[c].a;
+    const long long n = (long long)X.nout(c) * phi[c].b;
     double* t = theta_left(X, c, T, Lenv[c], a);
-    (void)K_;
     dfree(phi[c].p);
     phi[c].p = t;
     if (c > 0) {
@@ -1250,15 +1258,37 @@ double variational_sweep(RowCtx& X, std::vector<Ten>& phi, bool canonical) {
       phi[c].a = o.k;
       o.release();
       double* Rn = theta_right(X, c, T, phi[c]);
-      dfree(Rc);
-      Rc = Rn;
-      if (renorm) rescale_pow2(h, Rc, (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, rc_log);
-      phi[c - 1].b = phi[c].a;
+      rescale_pow2(h, Rn, (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, rc_log);
+      RE.set(c - 1, Rn, rc_log);
+      if (c > c0) phi[c - 1].b = phi[c].a;
     }
   }
-  dfree(Rc);
   for (auto& p : Lenv) dfree(p);
   return rc_log;
+}
+
+// One full left-right-left sweep (c0 = 0, e = C-1) from freshly built right
+// environments; returns the log-scale of the centre phi[0].
+double variational_sweep(RowCtx& X, std::vector<Ten>& phi, bool canonical) {
+  sgtn_inst* h = X.h;
+  const int C = (int)phi.size();
+  // phi coming from the zipper or from a previous sweep is already right-
+  // canonical (orthonormal rows right of a centre at column 0): bringing it
+  // there again would only change the gauge
+  if (!canonical) right_canonical(X, phi);
+  RightEnvs RE(C);
+  RE.R[C - 1] = dmalloc(1);
+  fill(RE.R[C - 1], 1, 1.0, h->st);
+  double lg = 0.0;
+  for (int c = C - 1; c > 0; --c) {
+    ThetaOp T = theta_op(X, c, RE.R[c], phi[c].b);
+    double* Rn = theta_right(X, c, T, phi[c]);
+    rescale_pow2(h, Rn, (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, lg);
+    RE.set(c - 1, Rn, lg);
+  }
+  double* L0 = dmalloc(1);
+  fill(L0, 1, 1.0, h->st);
+  return sweep_range(X, phi, 0, C - 1, L0, RE);
 }
 
 // cut a right-canonical phi (centre 0) to bond chi; returns worst retained ratio
@@ -1344,52 +1374,91 @@ void compute_ahat(RowCtx& X) {
   }
 }
 
-// out ~ T A (T = the row MPO of X, possibly transposed / dense); A is left-canonicalised in place
+// Sign of a 1x1 device tensor, folded into phi[0] when negative (the
+// zipper's last connecting tensor carries the overall sign of the row).
+void absorb_sign(sgtn_inst* h, const double* K, Ten& phi0) {
+  double kv = 0;
+  SGTN_CUDA(cudaMemcpyAsync(&kv, K, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  h->sync();
+  if (kv < 0) {
+    double* m1 = h->ws.get<double>("minus_one", 1);
+    fill(m1, 1, -1.0, h->st);
+    scale_by_inv(phi0.p, phi0.n(), m1, h->st);
+  }
+}
+
+// out ~ T A (T = the row MPO of X, possibly transposed / dense); A is left-canonicalised in place.
+// Sec. III.B "Variational zipper algorithm": right to left, each zipper step
+// (SVD truncation of the dashed-box tensor to 2 chi values, Fig. 8c) is
+// followed by a one-site sweep of the instantaneous stage over the columns
+// built so far, or over the h->zipper_window columns next to the zipper
+// centre (Fig. 8d); then the cut to chi and n_sweeps full sweeps at chi.
 void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& worst) {
   sgtn_inst* h = X.h;
   const int C = h->M.C;
   left_canonical(h, A);
   X.A = &A;
   if (!X.dense) compute_ahat(X);
-  // zipper
   std::vector<Ten> phi(C);
-  double* K = dmalloc(1);
-  fill(K, 1, 1.0, h->st);
-  int kp = 1;
+  RightEnvs RE(C);
+  RE.R[C - 1] = dmalloc(1);
+  fill(RE.R[C - 1], 1, 1.0, h->st);
+  const int w = h->zipper_window;
   double ln = A.lognorm;
   for (int c = C - 1; c >= 0; --c) {
     const Column& K_ = X.col(c);
-    ThetaOp T = theta_op(X, c, K, kp);
-    int m = K_.nBL() * X.chl(c);
-    TagScope tag("zipper");
-    SvdOut o = theta_svd(X, c, T, 2 * chi);
+    const int kp = c == C - 1 ? 1 : phi[c + 1].a;
+    const int m = K_.nBL() * X.chl(c);
+    SvdOut o;
+    {
+      TagScope tag("zipper");
+      ThetaOp T = theta_op(X, c, RE.R[c], kp);
+      o = theta_svd(X, c, T, 2 * chi);
+    }
     phi[c].p = o.Vt;
     o.Vt = nullptr;
     phi[c].a = o.k;
     phi[c].u = X.nout(c);
     phi[c].b = kp;
-    dfree(K);
-    K = o.US;
-    o.US = nullptr;
-    normalise(h, K, (long long)m * o.k, ln);
-    kp = o.k;
-    o.release();
-  }
-  {
-    double kv = 0;
-    SGTN_CUDA(cudaMemcpyAsync(&kv, K, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    h->sync();
-    if (kv < 0) {
-      double* m1 = h->ws.get<double>("minus_one", 1);
-      fill(m1, 1, -1.0, h->st);
-      scale_by_inv(phi[0].p, phi[0].n(), m1, h->st);
+    const int e = w <= 0 ? C - 1 : std::min(C - 1, c + w - 1);
+    if (e > c) {
+      // the centre moves from the connecting tensor K = U S onto phi[c]: U^T
+      // is the left environment of column c (for c = 0, K is 1x1 and the
+      // sweep recomputes the centre from scratch)
+      double* L0 = nullptr;
+      if (c > 0) {
+        double* Q = left_factor(h, o, m);
+        L0 = dmalloc((long long)o.k * m);
+        permute3(Q, m, o.k, 1, L0, h->st);
+        dfree(Q);
+      } else {
+        L0 = dmalloc(1);
+        fill(L0, 1, 1.0, h->st);
+      }
+      o.release();
+      const double lg = sweep_range(X, phi, c, e, L0, RE);
+      // the stage's centre is computed from the target itself: its scale is
+      // relative to the input MPS alone
+      if (c > 0) {
+        ln = A.lognorm + RE.lg[c - 1];
+        normalise(h, RE.R[c - 1], (long long)m * phi[c].a, ln);
+        RE.lg[c - 1] = ln - A.lognorm;
+      } else {
+        ln = A.lognorm + lg;
+        normalise(h, phi[0].p, phi[0].n(), ln);
+      }
+    } else {
+      double* K = o.US;
+      o.US = nullptr;
+      o.release();
+      normalise(h, K, (long long)m * phi[c].a, ln);
+      if (c > 0) {
+        RE.set(c - 1, K, ln - A.lognorm);
+      } else {
+        absorb_sign(h, K, phi[0]);
+        dfree(K);
+      }
     }
-  }
-  dfree(K);
-  for (int s = 0; s < n_sweeps; ++s) {
-    double extra = variational_sweep(X, phi, true);
-    ln = A.lognorm + extra;
-    normalise(h, phi[0].p, phi[0].n(), ln);
   }
   worst = std::max(worst, svd_cut(X, phi, chi));
   normalise(h, phi[C - 1].p, phi[C - 1].n(), ln);

@@ -1031,8 +1031,6 @@ void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_ener
   if (!h->boundary_ok) throw SgtnError(-2, "contract_boundary must run first");
   if (M <= 0 || n_out <= 0 || !out_spins || !out_energy || !out_logp || !out_pd || !out_count)
     throw SgtnError(-1, "bad argument");
-  if (M > SGTN_MAX_BEAM)
-    throw SgtnError(-1, "M " + std::to_string(M) + " exceeds SGTN_MAX_BEAM (" + std::to_string(SGTN_MAX_BEAM) + ")");
   cudaStream_t st = h->st;
   const int C = h->M.C, RC = h->M.R * h->M.C;
   std::vector<int32_t> cfg(1, 0), ncfg;
@@ -1056,6 +1054,11 @@ void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_ener
   if (dopt) book.reset(new DropletBook(h, *dopt));
   for (int step = 0; step < RC; ++step) {
     const int r = step / C, c = step % C, K = count;
+    // M may exceed SGTN_MAX_BEAM (a cap the bounding never reaches, e.g. to
+    // disable the top-M cut on a narrow lattice); the live beam may not
+    if (K > SGTN_MAX_BEAM)
+      throw SgtnError(-1, "the beam grew to " + std::to_string(K) + " branches, above SGTN_MAX_BEAM (" +
+                              std::to_string(SGTN_MAX_BEAM) + "): lower M");
     Step S;
     S.h = h;
     S.n = step;

@@ -111,6 +111,44 @@ def test_truncated_boundary_matches_oracle(Handle, case):
         assert np.allclose(v, vo, rtol=1e-8, atol=1e-10)
 
 
+@pytest.mark.parametrize("window", [1, 2, 3])
+@pytest.mark.parametrize("case", [CASES[0], CASES[2]], ids=lambda c: f"{c[0].name}_chi{c[2]}")
+def test_zipper_window_matches_oracle(Handle, case, window):
+    """The sweep after each zipper step limited to the `window` columns next to the
+    zipper centre (Sec. III.B allows it); window 1 is the plain zipper of Fig. 8c."""
+    inst, beta, chi, ns = case
+    lz_o, psis, _ = boundary_mps(PottsModel(inst), beta, chi, ns, window=window)
+    h = Handle(inst)
+    h.set_zipper_window(window)
+    h.set_beta(beta)
+    lz, _ = h.contract_boundary(chi, n_sweeps=ns)
+    assert abs(lz - lz_o) < RTOL * abs(lz_o)
+    for r in range(inst.rows):
+        ts, _ = h.mps(r)
+        v, vo = mps_dense(ts), mps_dense(psis[r][0])
+        v, vo = v / np.linalg.norm(v), vo / np.linalg.norm(vo)
+        assert np.allclose(v, vo, rtol=1e-8, atol=1e-10)
+
+
+def test_beam_limit_is_checked_before_any_launch(Handle):
+    """More than SGTN_MAX_BEAM partial configurations are refused up front by the
+    branch step, and by the search once its live beam would exceed it (the
+    handle stays usable)."""
+    from paper_2411_16431_b300.sgtn import SgtnError
+    inst = L.chimera_grid(3, 3, 1)
+    h = Handle(inst)
+    h.set_beta(1.0)
+    h.contract_boundary(8, n_sweeps=1)
+    rng = np.random.default_rng(0)
+    for count in (1025, 5000):
+        cfg = rng.integers(0, 256, size=(count, 2)).astype(np.int32)
+        with pytest.raises(SgtnError, match="SGTN_MAX_BEAM"):
+            h.branch_step(2, 16, cfg, np.zeros(count))
+    with pytest.raises(SgtnError, match="SGTN_MAX_BEAM"):
+        h.search(1500)                       # 256 x 256 candidates at the second step
+    assert h.search(8)["energy_num"].shape == (1,)
+
+
 @pytest.mark.parametrize("case", CASES[:3], ids=lambda c: f"{c[0].name}_chi{c[2]}")
 def test_conditionals_match_oracle(Handle, case):
     """Conditional marginals on probable partial configurations (the ones a search
