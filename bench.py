@@ -115,6 +115,45 @@ def _measured_bf16():
 TF32_PEAK_TFLOPS = _measured_bf16() * 0.5
 
 
+def measure_peaks():
+    """Dense GEMM peaks of this GPU measured here (cuBLAS through torch, CUDA events, best of
+    several): FP64 (DGEMM 4096^3), FP32 (SGEMM 8192^3, TF32 off), TF32 (8192^3, TF32 on).
+    B300's FP64 rate is far below its FP32 and tensor rates, so the FP64 kernels of the
+    truncation are judged against the FP64 figure measured on the same box."""
+    import torch
+    out = {}
+    dev = torch.device("cuda")
+    prev = torch.backends.cuda.matmul.allow_tf32
+    for name, n, dtype, tf32, reps in (("fp64_tflops", 4096, torch.float64, False, 5),
+                                       ("fp32_tflops", 8192, torch.float32, False, 5),
+                                       ("tf32_tflops", 8192, torch.float32, True, 10)):
+        try:
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, device=dev, dtype=dtype)
+            b = torch.randn(n, n, device=dev, dtype=dtype)
+            torch.matmul(a, b)
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[name] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+            del a, b
+        except Exception:
+            out[name] = None
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    out["how"] = "torch.matmul (cuBLAS), CUDA events, best of 5-10: FP64 4096^3, FP32 (TF32 off) and TF32 8192^3"
+    return out
+
+
+MEASURED = {}
+
+
 def clocks_sampler(dev_index):
     q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -259,13 +298,21 @@ def run_reference(args, wl):
 
 
 def peak_of(name):
-    """(peak in TFLOP/s, bound, source) of a timed kernel label, from its arithmetic."""
+    """(peak in TFLOP/s, bound, source) of a timed kernel label, from its arithmetic: the
+    GEMM peak of the same arithmetic measured on this machine (measure_peaks), else derived."""
     if name.startswith("tc_gemm"):
+        if MEASURED.get("tf32_tflops"):
+            return (MEASURED["tf32_tflops"] / 3.0, "tensor",
+                    "measured TF32 cuBLAS peak on this box / 3 (three products per 3xTF32)")
         return (TF32_PEAK_TFLOPS / 3.0, "tensor",
                 "measured bf16 burst peak x 1/2 (tf32 nominal ratio) / 3 (three products per 3xTF32)")
     if name.endswith("_f32"):
+        if MEASURED.get("fp32_tflops"):
+            return (MEASURED["fp32_tflops"], "alu", "measured FP32 (TF32 off) cuBLAS peak on this box")
         return (FP32_PEAK_TFLOPS, "alu", "derived: 148 SMs x 128 FFMA/clk x 2 flop x 2032 MHz")
-    return (FP64_PEAK_GFLOPS / 1e3, "alu", "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2032 MHz (no measured FP64 peak)")
+    if MEASURED.get("fp64_tflops"):
+        return (MEASURED["fp64_tflops"], "alu", "measured FP64 DGEMM peak on this box")
+    return (FP64_PEAK_GFLOPS / 1e3, "alu", "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2032 MHz")
 
 
 def roofline_of(kt, names):
@@ -322,6 +369,8 @@ def run_native(args, wl):
             hs.append(hk)
         return hs
 
+    if rank == 0:
+        MEASURED.update(measure_peaks())
     handles = make_handles()
     h = handles[0]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > 126 MB L2
@@ -398,6 +447,35 @@ def run_native(args, wl):
         evals_all = evals
     kt = {n: sgtn.kernel_time(n) for n in sgtn.kernel_names()}
     unconverged = h.boundary_info()[0]
+    # the FP64 arm of the "mixed vs FP64" comparison: the same step with every contraction
+    # and score in FP64, timed the same way (1 warm-up, up to 2 steps) in the same process
+    fp64_arm = None
+    logz64 = None
+    if (prec, sprec) != (0, -1) and n_tr == 1:
+        for hk in handles:
+            hk.set_search_precision(0)
+        t64 = []
+        ev64 = 0
+        for i in range(1 + max(1, min(2, args.steps))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e_a = sgtn.stats()[2]
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.set_beta(wl["beta"])
+            logz64 = h.contract_boundary(wl["chi"], precision=0, n_sweeps=wl["sweeps"])[0]
+            r64 = h.search(wl["M"])
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i > 0:
+                t64.append(a.elapsed_time(b))
+                ev64 += sgtn.stats()[2] - e_a
+        fp64_arm = {"precision": "fp64", "value": ev64 / (sum(t64) * 1e-3), "unit": "marginal evals/s",
+                    "steps": len(t64), "warmup": 1, "ms_per_step": sum(t64) / len(t64),
+                    "logz": float(logz64) if np.isfinite(logz64) else None,
+                    "energy_num": int(r64["energy_num"][0])}
+        for hk in handles:
+            hk.set_search_precision(sprec)
     # boundary contraction timed alone for its TFLOP/s
     torch.cuda.synchronize()
     h.set_beta(wl["beta"])
@@ -410,20 +488,22 @@ def run_native(args, wl):
     bound_ms = a.elapsed_time(b)
     if n_tr > 1:
         bflops = (sgtn.stats()[1] - fa) * args.steps   # one instance's boundary, timed alone
-    # stated error of a mixed-precision boundary: log Z against the FP64 boundary (untimed)
+    # stated error of the timed arm's log Z against the separately computed FP64 boundary of
+    # the FP64 arm (for an FP64 boundary the arithmetic is the same, so it is 0 exactly)
     fin = (lambda v: float(v) if np.isfinite(v) else None)   # JSON has no NaN: an undefined log Z is null
-    logz_err = {"logz": fin(logz), "logz_fp64": fin(logz), "rel_err": 0.0, "boundary": "fp64"} if prec == 0 else None
-    if prec != 0:
-        lz64 = h.contract_boundary(wl["chi"], precision=0, n_sweeps=wl["sweeps"])[0]
-        ok = np.isfinite(logz) and np.isfinite(lz64)
-        logz_err = {"logz": logz if np.isfinite(logz) else None, "logz_fp64": lz64 if np.isfinite(lz64) else None,
-                    "rel_err": abs(logz - lz64) / abs(lz64) if ok else None}
+    if logz64 is None and prec != 0:
+        logz64 = h.contract_boundary(wl["chi"], precision=0, n_sweeps=wl["sweeps"])[0]
+    lz64 = logz if logz64 is None else logz64
+    ok = np.isfinite(logz) and np.isfinite(lz64)
+    logz_err = {"logz": fin(logz), "logz_fp64": fin(lz64), "rel_err": abs(logz - lz64) / abs(lz64) if ok else None,
+                "boundary": "fp64" if prec == 0 else args.precision,
+                "reference": "FP64 arm's boundary" if logz64 is not None else "the timed FP64 boundary itself"}
     # stated marginal error of the mixed search arithmetic: conditionals along the best
     # configuration at 8 steps, mixed against FP64 scores on the same (FP64) boundary (untimed)
     marg_err = None
     if (sprec != -1 or prec != 0) and n_tr == 1 and wl.get("transforms", 1) == 1:
         if prec != 0:
-            h.contract_boundary(wl["chi"], precision=0, n_sweeps=wl["sweeps"])   # (already FP64 after logz_check)
+            h.contract_boundary(wl["chi"], precision=0, n_sweeps=wl["sweeps"])
         marg_err = marginal_check(h, inst, states, res["spins"][0], sprec if sprec != -1 else prec)
         h.set_search_precision(sprec)
     # end to end through the public API from host buffers: build (H2D) .. results (D2H)
@@ -470,6 +550,9 @@ def run_native(args, wl):
                                                             "count_of_best": drop_count[0]},
             "boundary_tflops": (bflops / args.steps) / (bound_ms * 1e-3) / 1e12,
             "boundary_ms": bound_ms,
+            "fp64_arm": fp64_arm,
+            "mixed_over_fp64": (evals_all / (t_ms * 1e-3)) / fp64_arm["value"] if fp64_arm else None,
+            "measured_peaks": MEASURED or None,
             "logz_check": logz_err,
             "marginal_check": marg_err,
             "roofline": roof, "roofline_contraction": roof_c, "kernel_times": shares,

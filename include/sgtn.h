@@ -269,6 +269,22 @@ int sgtn_mps_tensor(sgtn_h h, int32_t row, int32_t col, double* out);
 #define SGTN_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 int sgtn_conditionals_noalloc(sgtn_h h, int32_t step, int32_t count, const int32_t* configs, double* out_p);
 
+/* Dense product C[m x n] = X[m x k] Y[k x n] (row-major FP64 device
+ * arrays) with the library's own GEMM in `precision` (the paper has no
+ * counterpart: this is the building block of every contraction of the method,
+ * exposed so that its arithmetic can be checked and timed on its own).
+ * SGTN_FP64: FP64 SIMT.  SGTN_FP32: FP32 SIMT (FP32 products and sums).
+ * SGTN_TF32: tcgen05 tensor cores (TMA-fed, TMEM accumulators) with 3xTF32
+ * splitting -- the operands split into TF32 high and low parts, the three
+ * products hi*hi + hi*lo + lo*hi summed in FP32 -- when m >= 128, n >= 64
+ * and k >= 32, else FP32 SIMT; |error| <= (2^-20 + k 2^-24) (|X| |Y|)_ij.
+ * `stream` is a cudaStream_t (NULL: the legacy default stream); the call is
+ * asynchronous except for SGTN_TF32, which synchronises to read the kernel's
+ * timeout flag (SGTN_ERR_TIMEOUT if a bounded wait gave up).  SGTN_ERR_ARG
+ * for non-positive sizes, NULL pointers or another precision. */
+int sgtn_gemm(int32_t precision, int32_t m, int32_t n, int32_t k, const double* X, const double* Y, double* C,
+              void* stream);
+
 /* Process-wide diagnostics (the paper has no counterpart): cumulative
  * number of kernel launches issued by this library, algorithmic
  * floating-point operations of its contractions (2 m n k per gathered

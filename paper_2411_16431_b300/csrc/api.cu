@@ -278,6 +278,35 @@ void sgtn_stats(int64_t* launches, double* flops, int64_t* evals) {
 
 int64_t sgtn_device_allocations(void) { return g_count.device_allocs; }
 
+int sgtn_gemm(int32_t precision, int32_t m, int32_t n, int32_t k, const double* X, const double* Y, double* C,
+              void* stream) {
+  if (m <= 0 || n <= 0 || k <= 0 || !X || !Y || !C) return SGTN_ERR_ARG;
+  if (precision != SGTN_FP64 && precision != SGTN_FP32 && precision != SGTN_TF32) return SGTN_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  struct Modes {   // the thread's contraction modes for this call only
+    Modes(int p) {
+      g_compute_f32 = p != SGTN_FP64;
+      g_use_tc = p == SGTN_TF32;
+    }
+    ~Modes() {
+      g_compute_f32 = false;
+      g_use_tc = false;
+    }
+  };
+  try {
+    Modes md(precision);
+    gemm(X, false, k, Y, false, n, C, n, m, n, k, 1.0, 0, st);
+    if (cudaGetLastError() != cudaSuccess) return SGTN_ERR_CUDA;
+    if (precision == SGTN_TF32 && tc_gemm_take_error(st)) return SGTN_ERR_TIMEOUT;
+    return SGTN_OK;
+  } catch (const SgtnError& e) {
+    cudaGetLastError();
+    return e.code;
+  } catch (const std::exception&) {
+    return SGTN_ERR_CUDA;
+  }
+}
+
 void sgtn_kernel_timing(int32_t enable, int32_t reset) {
   if (reset) ktimer_reset();
   ktimer_enable(enable != 0);

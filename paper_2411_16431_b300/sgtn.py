@@ -80,6 +80,24 @@ def stats():
     return a.value, b.value, c.value
 
 
+def gemm(X, Y, precision, stream=None):
+    """C = X @ Y (torch float64 CUDA tensors) with the library's GEMM in the given precision."""
+    import torch
+    X, Y = X.contiguous(), Y.contiguous()
+    m, k = X.shape
+    k2, n = Y.shape
+    assert k == k2 and X.dtype == Y.dtype == torch.float64 and X.is_cuda and Y.is_cuda
+    C = torch.empty((m, n), dtype=torch.float64, device=X.device)
+    L = load()
+    L.sgtn_gemm.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                            ct.c_void_p]
+    st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    rc = L.sgtn_gemm(precision, m, n, k, X.data_ptr(), Y.data_ptr(), C.data_ptr(), st)
+    if rc != 0:
+        raise SgtnError(f"sgtn_gemm failed: {rc}")
+    return C
+
+
 def device_allocations():
     """Number of cudaMalloc calls the library has made so far in this process."""
     L = load()

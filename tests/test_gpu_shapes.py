@@ -1,0 +1,169 @@
+"""Parity at the benchmark's shapes, through the C ABI.
+
+The largest benchmark truncates at chi = 64 (2 chi = 128 kept by the zipper)
+and cuts the beam at M = 1024.  The dense oracle cannot hold 24-spin Pegasus
+cells, so these shapes are checked on instances it can: Chimera grids with all
+256 states per cell.  Also here: the library's GEMM (the building block of
+every contraction) element by element against a float64 product, with the
+error bound of each precision.
+"""
+import numpy as np
+import pytest
+
+from oracle import brute
+from oracle.peps import boundary_mps
+from oracle.potts import PottsModel
+from oracle.search import boundary_key, boundary_pairs, conditional_scores, merge_and_cut
+from oracle.search import search as oracle_search
+from paper_2411_16431_b300 import lattices as L
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10
+CHI64 = L.chimera_grid(6, 6, 2)
+
+
+@pytest.fixture(scope="module")
+def chi64():
+    from paper_2411_16431_b300.sgtn import Handle
+    pm = PottsModel(CHI64)
+    lz_o, psis, mpos = boundary_mps(pm, 1.0, 64, 1)
+    h = Handle(CHI64)
+    h.set_beta(1.0)
+    lz, _ = h.contract_boundary(64, n_sweeps=1)
+    yield dict(pm=pm, lz_o=lz_o, psis=psis, mpos=mpos, h=h, lz=lz)
+    h.close()
+
+
+def _overlap(A, B):
+    E = np.ones((1, 1))
+    for a, b in zip(A, B):
+        E = np.einsum("ab,sai,sbj->ij", E, a, b, optimize=True)
+    return float(E.reshape(()))
+
+
+def test_chi64_boundary_matches_oracle(chi64):
+    """log Z to 1e-10 and every boundary MPS equal as a unit vector (|<a|b>| = 1 to 1e-13),
+    with bonds at the chi = 64 cap."""
+    assert abs(chi64["lz"] - chi64["lz_o"]) < RTOL * abs(chi64["lz_o"])
+    psis = chi64["psis"]
+    assert max(max(t.shape[1] for t in p[0]) for p in psis) == 64
+    for r in range(CHI64.rows):
+        ts, _ = chi64["h"].mps(r)
+        A = psis[r][0]
+        assert [t.shape for t in ts] == [a.shape for a in A]
+        ov = _overlap(ts, A) / np.sqrt(_overlap(ts, ts) * _overlap(A, A))
+        assert abs(abs(ov) - 1.0) < 1e-13, (r, ov)
+
+
+@pytest.mark.parametrize("step", [7, 12, 20])
+def test_chi64_branch_step_with_1024_branches(chi64, step):
+    """One branch step of 1024 seeded partial configurations x 256 states (262,144
+    candidates), merged by Eq. (7) and cut to M = 1024: the kept beam, its log p and p_d
+    equal the oracle's."""
+    pm, psis, mpos, h = chi64["pm"], chi64["psis"], chi64["mpos"], chi64["h"]
+    C = CHI64.cols
+    r, c = divmod(step, C)
+    rng = np.random.default_rng(100 + step)
+    K, M = 1024, 1024
+    cfgs = rng.integers(0, 256, size=(K, step)).astype(np.int32)
+    logp = -rng.uniform(0.0, 30.0, K)
+    pairs = boundary_pairs(pm, step)
+    cands = {}
+    for cf, l0 in zip(map(tuple, cfgs.tolist()), logp.tolist()):
+        s = np.maximum(conditional_scores(pm, 1.0, mpos[r], psis[r], cf, r, c), 0)
+        for x in np.nonzero(s > 0)[0]:
+            cand = cf + (int(x),)
+            cands.setdefault(boundary_key(pm, pairs, cand), []).append((cand, l0 + float(np.log(s[x] / s.sum()))))
+    want, pd_o = merge_and_cut(cands, M)
+    oc, ol, pd = h.branch_step(step, M, cfgs, logp)
+    got = sorted(zip(map(tuple, oc.tolist()), ol.tolist()))
+    want = sorted(want)
+    assert len(got) == len(want) == M
+    assert [g[0] for g in got] == [w[0] for w in want]
+    assert np.allclose([g[1] for g in got], [w[1] for w in want], rtol=RTOL, atol=0)
+    assert abs(pd - pd_o) <= RTOL * abs(pd_o)
+
+
+def test_search_with_beam_1024_matches_oracle():
+    """The full search at M = 1024 (the cached per-row environments of the search, not the
+    stateless branch step): Chimera 4x4, all 256 states, chi = 16."""
+    from paper_2411_16431_b300.sgtn import Handle
+    inst = L.chimera_grid(4, 4, 5)
+    ref = oracle_search(inst, 1.0, chi=16, M=1024, n_sweeps=1)
+    h = Handle(inst)
+    h.set_beta(1.0)
+    h.contract_boundary(16, n_sweeps=1)
+    res = h.search(1024)
+    assert np.array_equal(res["spins"], ref["spins"])
+    assert np.array_equal(res["energy_num"], ref["energy_num"])
+    assert np.allclose(res["logp"], ref["logp"], rtol=RTOL, atol=0)
+    assert abs(res["pd"] - ref["pd"]) <= RTOL * abs(ref["pd"])
+    h.close()
+
+
+@pytest.mark.parametrize("inst", [L.slice_cells(L.chimera_grid(4, 4, 1), 2, 1), L.kings_grid(4, 4, 3)],
+                         ids=lambda i: i.name)
+def test_exact_conditionals_relative_parity(inst):
+    """Untruncated boundary (every term of a score positive): every conditional marginal with
+    p > 1e-300 within 1e-10 relative of the oracle and of brute force, also the smallest ones."""
+    from paper_2411_16431_b300.sgtn import Handle
+    beta = 1.3
+    pm = PottsModel(inst)
+    _, psis, mpos = boundary_mps(pm, beta, 256, 1)
+    h = Handle(inst)
+    h.set_beta(beta)
+    h.contract_boundary(256, n_sweeps=1)
+    rng = np.random.default_rng(4)
+    S = brute.all_spins(inst.n_spins)
+    E = brute.energies_num(inst, S) / inst.denom
+    for n in range(1, inst.rows * inst.cols):
+        r, c = divmod(n, inst.cols)
+        cfgs = [tuple(int(rng.integers(pm.sites[p].d)) for p in range(n)) for _ in range(4)]
+        got = h.conditionals(n, np.array(cfgs, np.int32))
+        for k, cf in enumerate(cfgs):
+            s = conditional_scores(pm, beta, mpos[r], psis[r], cf, r, c)
+            assert np.all(s > 0)
+            po = s / s.sum()
+            ok = po > 1e-300
+            assert np.allclose(got[k][ok], po[ok], rtol=RTOL, atol=0)
+            # brute force: p(x | placed) by summing exp(-beta H) over completions
+            m = np.ones(len(S), bool)
+            for p, x in enumerate(cf):
+                m &= np.all(S[:, pm.sites[p].spins] == pm.sites[p].spinvals[x][None, :], axis=1)
+            w = np.exp(-beta * (E[m] - E[m].min()))
+            site = pm.sites[n]
+            pb = np.array([w[np.all(S[m][:, site.spins] == site.spinvals[x][None, :], axis=1)].sum()
+                           for x in range(site.d)])
+            pb /= pb.sum()
+            assert np.allclose(got[k], pb, rtol=1e-9, atol=0)
+
+
+# --- the library's GEMM against a float64 product ---------------------------------------
+
+GEMM_SHAPES = [(128, 64, 32), (1024, 512, 2048), (300, 200, 1000), (2048, 128, 128), (256, 128, 13568),
+               (97, 33, 17)]
+
+
+@pytest.mark.parametrize("shape", GEMM_SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("prec", [0, 3, 1], ids=["fp64", "fp32", "tf32"])
+def test_gemm_elementwise_error_bound(shape, prec):
+    """|C - X Y| <= bound * (|X| |Y|) element by element, X Y in float64 on the host:
+    FP64 k 2^-52; FP32 (2^-23 + k 2^-24); TF32 (3xTF32 tensor cores for m >= 128, n >= 64,
+    k >= 32, else FP32) (2^-20 + k 2^-24) -- the split drops lo*lo (2^-22 of |x||y|), each
+    split rounds (2^-22 twice), and the sum runs in FP32."""
+    import torch
+    from paper_2411_16431_b300.sgtn import gemm
+    m, n, k = shape
+    g = torch.Generator().manual_seed(m * 7 + n * 3 + k)
+    X = torch.randn(m, k, generator=g, dtype=torch.float64)
+    Y = torch.randn(k, n, generator=g, dtype=torch.float64)
+    # a spread of magnitudes inside rows and columns, as in normalised MPS tensors
+    X *= torch.exp(torch.randn(m, 1, generator=g, dtype=torch.float64))
+    Y *= torch.exp(torch.randn(1, n, generator=g, dtype=torch.float64))
+    ref = (X @ Y).numpy()
+    absprod = (X.abs() @ Y.abs()).numpy()
+    got = gemm(X.cuda(), Y.cuda(), prec).cpu().numpy()
+    bound = {0: k * 2.0 ** -52, 3: 2.0 ** -23 + k * 2.0 ** -24, 1: 2.0 ** -20 + k * 2.0 ** -24}[prec]
+    err = np.abs(got - ref)
+    assert np.all(err <= bound * absprod + 1e-300), float(np.max(err / absprod))
