@@ -60,7 +60,7 @@ extern thread_local bool g_no_alloc;
 // `bytes` long, reused by every later call on that stream (stream order keeps
 // the uses apart).  Growing it waits for the stream.  nullptr if it would have
 // to grow while g_no_alloc is set.
-enum ScratchSlot { SC_SEG_PART, SC_SPLITK_PART, SC_CHOL_T, SC_JAC_FLAGS, SC_JAC_FRO, SC_TC_BUF, SC_NSLOT };
+enum ScratchSlot { SC_SEG_PART, SC_SPLITK_PART, SC_CHOL_T, SC_JAC_FLAGS, SC_JAC_FRO, SC_TC_BUF, SC_KPART, SC_NSLOT };
 void* stream_scratch(cudaStream_t st, int slot, size_t bytes);
 void stream_scratch_release(cudaStream_t st);
 
@@ -118,6 +118,10 @@ struct SegGemm {
   // in a fixed order (deterministic)
   const int32_t *vseg_ptr = nullptr, *vfirst = nullptr;
   int nvseg = 0;
+  // set by the launcher, not by callers: each segment's (term, k-chunk)
+  // sequence is cut into kpart contiguous parts, one CTA each, whose partial
+  // blocks are summed in part order afterwards (small grids fill the GPU)
+  int kpart = 1;
 };
 void seg_gemm(const SegGemm& a, cudaStream_t st);
 

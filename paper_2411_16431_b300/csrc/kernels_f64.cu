@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
   constexpr int XL = (BM * TK + 255) / 256, YL = (TK * BN + 255) / 256;
   __shared__ CT Xs[2][TK][BM + 1];
   __shared__ CT Ys[2][TK][BN + 1];
-  const int seg = blockIdx.x;
+  const int seg = blockIdx.x / a.kpart, part = blockIdx.x % a.kpart;
   const int i0 = blockIdx.y * BM, j0 = blockIdx.z * BN;
   const int tid = threadIdx.x;
   const int ty = tid / 16, tx = tid % 16;
@@ -61,11 +61,15 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
     t1 = seg + 1;
     ooff = (long long)seg * a.ors;
   }
+  if (a.kpart > 1) ooff = (long long)blockIdx.x * a.ors;   // partial block of (segment, part)
   if ((a.tri & 1) && i0 >= j0 + BN) return;   // wholly below the diagonal: not needed
   int k_base = a.splitk ? seg * a.splitk : 0;
   if (a.tri & 2) qlen = max(0, min(qlen, j0 + BN - k_base));   // Y[k][j] = 0 for k > j
   const int nk = (qlen + TK - 1) / TK;
-  const int nsteps = (t1 - t0) * nk;
+  const int nall = (t1 - t0) * nk;
+  // this CTA's share of the segment's (term, k-chunk) sequence
+  const int sbeg = int((long long)nall * part / a.kpart), send = int((long long)nall * (part + 1) / a.kpart);
+  const int nsteps = send - sbeg;
   const bool x_kfast = (a.xs_k == 1), y_jfast = (a.ys_j == 1);
   // per-term operand offsets and scales
   auto term = [&](int t, long long& xoff, long long& yoff, double& cf, const double*& cs) {
@@ -85,7 +89,8 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
     }
   };
   CT xr[XL], yr[YL];
-  auto load = [&](int step) {
+  auto load = [&](int lstep) {
+    const int step = sbeg + lstep;
     const int t = t0 + step / nk, k0 = (step % nk) * TK;
     long long xoff, yoff;
     double cf;
@@ -170,6 +175,27 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
       const double val = a.alpha * double(acc[u][v]);
       *o = a.accumulate ? *o + val : val;
     }
+  }
+}
+
+// Sum of the kpart partial blocks P[seg * kpart + part] (p x s, row-major) of
+// each segment, in part order, into the segment's output block.
+__global__ void kpart_reduce_kernel(const double* P, int nseg, int kpart, int p, int s, SegGemm a) {
+  const long long blk = (long long)p * s, total = (long long)nseg * blk;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int g = int(e / blk);
+    const long long r = e % blk;
+    const int i = int(r / s), j = int(r % s);
+    double v = 0.0;
+    for (int q = 0; q < kpart; ++q) v += P[((long long)g * kpart + q) * blk + r];
+    long long ooff;
+    if (a.seg_ptr)
+      ooff = a.out_by_seg ? (long long)g * a.ors : (long long)a.seg_or[g] * a.ors + (long long)a.seg_oc[g] * a.ocs;
+    else
+      ooff = (long long)g * a.ors;
+    double* o = a.O + ooff + (long long)i * a.os_i + (long long)j * a.os_j;
+    *o = a.accumulate ? *o + a.alpha * v : a.alpha * v;
   }
 }
 
@@ -1106,12 +1132,41 @@ std::string ktimer_names() {
 }
 
 namespace {
-void launch_seg(const SegGemm& a, cudaStream_t st) {
+void launch_seg(const SegGemm& a_in, cudaStream_t st) {
+  SegGemm a = a_in;
   // tile shape from the block shape: rows 16 / 32 / 64, columns 32 / 64
   const int bm = a.tile_m ? a.tile_m : a.p <= 16 ? 16 : a.p <= 32 ? 32 : 64;
   const int bn = a.tile_n ? a.tile_n : a.s <= 32 ? 32 : 64;
-  dim3 grid(a.nseg, (a.p + bm - 1) / bm, (a.s + bn - 1) / bn);
-  auto go = [&](auto kern) { kern<<<grid, 256, 0, st>>>(a); };
+  const long long tiles = (long long)((a.p + bm - 1) / bm) * ((a.s + bn - 1) / bn);
+  // A grid of fewer CTAs than two per SM leaves most of the GPU idle (B300's
+  // FP64 rate per SM is low, so one long segment on one SM takes long): cut
+  // each segment's (term, k-chunk) sequence into parts of at least four steps,
+  // one CTA each, into scratch blocks summed afterwards in part order.
+  int kpart = 1;
+  double* part = nullptr;
+  if (!a.splitk && !a.tri && !g_no_alloc) {
+    const long long ctas = (long long)a.nseg * tiles;
+    const double steps = (a.seg_ptr ? double(a.nterm) / a.nseg : 1.0) * ((a.q + TK - 1) / TK);
+    if (ctas < 296 && steps >= 8) {
+      kpart = int(std::min<double>({double((296 + ctas - 1) / ctas), steps / 4.0, 64.0}));
+      if (kpart >= 2)
+        part = static_cast<double*>(
+            stream_scratch(st, SC_KPART, size_t(kpart) * a.nseg * a.p * a.s * sizeof(double)));
+      if (!part) kpart = 1;
+    }
+  }
+  SegGemm b = a;
+  if (kpart > 1) {
+    b.kpart = kpart;
+    b.O = part;
+    b.os_i = a.s;
+    b.os_j = 1;
+    b.ors = (long long)a.p * a.s;
+    b.alpha = 1.0;
+    b.accumulate = 0;
+  }
+  dim3 grid(a.nseg * kpart, (a.p + bm - 1) / bm, (a.s + bn - 1) / bn);
+  auto go = [&](auto kern) { kern<<<grid, 256, 0, st>>>(b); };
   if (a.f32) {
     if (bm == 16) bn == 32 ? go(seg_gemm_kernel<float, 16, 32>) : go(seg_gemm_kernel<float, 16, 64>);
     else if (bm == 32) bn == 32 ? go(seg_gemm_kernel<float, 32, 32>) : go(seg_gemm_kernel<float, 32, 64>);
@@ -1122,6 +1177,12 @@ void launch_seg(const SegGemm& a, cudaStream_t st) {
     else bn == 32 ? go(seg_gemm_kernel<double, 64, 32>) : go(seg_gemm_kernel<double, 64, 64>);
   }
   ++g_count.launches;
+  if (kpart > 1) {
+    const long long total = (long long)a.nseg * a.p * a.s;
+    const int nb = int(std::min<long long>((total + 255) / 256, 148 * 16));
+    kpart_reduce_kernel<<<nb, 256, 0, st>>>(part, a.nseg, kpart, a.p, a.s, a);
+    ++g_count.launches;
+  }
 }
 }  // namespace
 

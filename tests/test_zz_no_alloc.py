@@ -66,10 +66,19 @@ def test_noalloc_rejects_requests_beyond_its_scratch_or_the_beam_limit():
             h.conditionals(5, cfg)
     cfg = _random_configs(h, 5, 8, 5)               # still usable afterwards
     assert np.allclose(h.conditionals_noalloc(5, cfg), h.conditionals(5, cfg), rtol=1e-10, atol=0.0)
-    # within the beam limit but beyond the static array: 1024 branches at this step need
-    # about 52 MB of environments and scores, more than the 32 MiB the array holds
-    full = _random_configs(h, 5, 1024, 7)
+    full = _random_configs(h, 5, 1024, 7)           # the largest count fits the array here
+    assert np.allclose(h.conditionals_noalloc(5, full), h.conditionals(5, full), rtol=1e-10, atol=0.0)
+    h.close()
+    # 4096 states per 24-spin cell: the projected boundary MPS of the row alone outgrows the
+    # 32 MiB array (about 52 MB for 16 branches), so the call is refused with the byte
+    # count; sgtn_conditionals serves it
+    peg = L.pegasus_nice(4, 1)
+    states = L.hamming_ball_states(peg, 4096, seed=2)
+    h = Handle(peg, states)
+    h.set_beta(0.5)
+    h.contract_boundary(4, n_sweeps=1)
+    cfg = _random_configs(h, 4, 16, 9)
     with pytest.raises(SgtnError, match="bytes of device scratch"):
-        h.conditionals_noalloc(5, full)
-    assert np.allclose(h.conditionals_noalloc(5, cfg), h.conditionals(5, cfg), rtol=1e-10, atol=0.0)
+        h.conditionals_noalloc(4, cfg)
+    assert h.conditionals(4, cfg).shape == (16, 4096)
     h.close()
