@@ -47,12 +47,24 @@ WORKLOADS = {
                        # the oracle's dense row MPOs cannot hold d=256 cells: its timed sample is a
                        # 2x2-cell Pegasus slice (P3 nice) with 32 states per cell
                        oracle_sample=_PEG_SAMPLE),
+    "pegasus5x5_d4096": dict(desc="Pegasus P6 nice, 5x5 cells of 24 spins (600 spins), d=4096 states per cell "
+                                  "(Hamming ball around a seeded reference), iid J,h in {+-1..+-7}/7, beta=1, chi=32, "
+                                  "M=256",
+                             make=lambda seed: L.pegasus_nice(6, seed),
+                             states=lambda inst, seed: L.hamming_ball_states(inst, 4096, seed=seed + 1),
+                             beta=1.0, chi=32, M=256, sweeps=2, d=4096, oracle_sample=_PEG_SAMPLE),
     "pegasus15x15": dict(desc="Pegasus P16 nice, 15x15 cells of 24 spins (5400 spins), d=256 states per cell "
                               "(Hamming ball around a seeded reference), iid J,h in {+-1..+-7}/7, beta=2, chi=64, "
                               "M=1024",
                          make=lambda seed: L.pegasus_nice(16, seed),
                          states=lambda inst, seed: L.hamming_ball_states(inst, 256, seed=seed + 1),
                          beta=2.0, chi=64, M=1024, sweeps=2, d=256, oracle_sample=dict(_PEG_SAMPLE)),
+    "pegasus15x15_d4096": dict(desc="Pegasus P16 nice, 15x15 cells of 24 spins (5400 spins), d=4096 states per cell "
+                                    "(Hamming ball around a seeded reference), iid J,h in {+-1..+-7}/7, beta=2, "
+                                    "chi=64, M=1024",
+                               make=lambda seed: L.pegasus_nice(16, seed),
+                               states=lambda inst, seed: L.hamming_ball_states(inst, 4096, seed=seed + 1),
+                               beta=2.0, chi=64, M=1024, sweeps=2, d=4096, oracle_sample=dict(_PEG_SAMPLE)),
     "pegasus15x15_planted": dict(
         desc="Pegasus P16 nice, 15x15 cells, planted frustrated 4-cycles (ground energy known), d=256 states per "
              "cell around the planted state, beta=2, chi=64, M=1024",
