@@ -141,8 +141,11 @@ def test_exact_conditionals_relative_parity(inst):
 
 # --- the library's GEMM against a float64 product ---------------------------------------
 
+# m >= 128, n >= 64, k >= 32 take the dense tensor-core GEMM in TF32 mode, smaller ones the
+# segmented SIMT kernel (a k tail in 97 x 33 x 17; a long reduction split over CTAs in
+# 64 x 48 x 300 and 100 x 100 x 2000)
 GEMM_SHAPES = [(128, 64, 32), (1024, 512, 2048), (300, 200, 1000), (2048, 128, 128), (256, 128, 13568),
-               (97, 33, 17)]
+               (97, 33, 17), (64, 48, 300), (100, 100, 2000), (40, 127, 65)]
 
 
 @pytest.mark.parametrize("shape", GEMM_SHAPES, ids=lambda s: "x".join(map(str, s)))
