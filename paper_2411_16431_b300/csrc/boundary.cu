@@ -570,12 +570,23 @@ bool cqr_orth(sgtn_inst* h, const double* M, int len, int k, double* Q, bool fir
   };
   const double* cur = M;
   for (int pass = 0; pass < 4; ++pass) {
-    gram_upper(cur, k, G, k, len, st);                                 // G = cur^T cur (upper)
+    // G = cur^T cur (upper).  A first factor taken in FP32 only preconditions
+    // (the FP64 passes after it restore orthogonality, and cur R^{-1} keeps
+    // the span exactly), so its Gram matrix is formed in FP32 too: the
+    // product of the tall operand is the costliest step of the pass
+    const bool g32 = pass == 0 && first_f32;
+    if (g32) g_compute_f32 = true;
+    gram_upper(cur, k, G, k, len, st);
+    g_compute_f32 = false;
     gram_stats(G, k, dstat, st);
     bool last = pass == 3;
     if (pass == 0) {
       bool ok = chol(0.0, first_f32);
-      if (!ok && first_f32) ok = chol(0.0, false);
+      if (!ok && first_f32) {
+        gram_upper(cur, k, G, k, len, st);                             // FP64 Gram for the FP64 factor
+        gram_stats(G, k, dstat, st);
+        ok = chol(0.0, false);
+      }
       if (!ok) {
         const double tr = hstat[1];
         if (!(tr > 0) || !std::isfinite(tr)) return false;

@@ -26,6 +26,7 @@
 #include <memory>
 #include <numeric>
 #include <string>
+#include <type_traits>
 #include <unordered_map>
 
 #include "../../include/sgtn.h"
@@ -176,6 +177,67 @@ __global__ void score_kernel(int K, int d, int chl, int chr, int nG, int nE, int
     }
   for (int j = 0; j < 4; ++j) {
     int k = threadIdx.x + j * blockDim.x;
+    if (k >= K) break;
+    s[(long long)k * d + x] = f[(long long)u_x[x] * K + k] * w[x] * double(acc[j]);
+  }
+}
+
+// Same scores for left bonds up to CHL (16, 32 or 64): each thread holds its
+// branch's left-environment vector E_k[(lam, g)] in registers (read once per
+// (g, e) instead of once per right index), and the staged block
+// Ahat[(pd, e, g)] is read from shared memory in 16-byte vectors that every
+// thread of a warp shares (broadcast), CHL rows zero-padded.
+template <class CT, int CHL>
+__global__ void __launch_bounds__(256) score_reg_kernel(int K, int d, int chl, int chr, int nG, int nE, int nPdr,
+                                                        const double* E, const double* Ahat, const double* Ft,
+                                                        const double* f, const double* w, const int32_t* lam_x,
+                                                        const int32_t* u_x, const int32_t* pd_x, const int32_t* pr_x,
+                                                        const int32_t* pdr_x, double* s) {
+  constexpr int V = 16 / sizeof(CT);
+  using Vec = typename std::conditional<sizeof(CT) == 4, float4, double2>::type;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  CT* As = reinterpret_cast<CT*>(smraw);   // CHL x ldA
+  const int ldA = (chr + V - 1) / V * V;
+  const int x = blockIdx.x;
+  CT acc[4] = {0, 0, 0, 0};
+  for (int g = 0; g < nG; ++g)
+    for (int e = 0; e < nE; ++e) {
+      const double* A = Ahat + (((long long)pd_x[x] * nE + e) * nG + g) * chl * chr;
+      __syncthreads();
+      for (int i = threadIdx.x; i < CHL * ldA; i += blockDim.x) {
+        const int al = i / ldA, ar = i % ldA;
+        As[i] = (al < chl && ar < chr) ? CT(A[al * chr + ar]) : CT(0);
+      }
+      __syncthreads();
+      const double* Eb = E + (long long)(lam_x[x] * nG + g) * chl * K;
+      const double* Fb = Ft + (((long long)pr_x[x] * nE + e) * nPdr + pdr_x[x]) * chr * K;
+      for (int j = 0; j < 4; ++j) {
+        const int k = threadIdx.x + j * blockDim.x;
+        if (k >= K) break;
+        CT ev[CHL];
+#pragma unroll
+        for (int al = 0; al < CHL; ++al) ev[al] = al < chl ? CT(Eb[(long long)al * K + k]) : CT(0);
+        CT a2 = 0;
+        for (int ar0 = 0; ar0 < chr; ar0 += V) {
+          CT t[V];
+#pragma unroll
+          for (int v = 0; v < V; ++v) t[v] = CT(0);
+#pragma unroll
+          for (int al = 0; al < CHL; ++al) {
+            const Vec a = *reinterpret_cast<const Vec*>(As + al * ldA + ar0);
+            const CT* av = reinterpret_cast<const CT*>(&a);
+#pragma unroll
+            for (int v = 0; v < V; ++v) t[v] = fma(ev[al], av[v], t[v]);
+          }
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+            if (ar0 + v < chr) a2 = fma(t[v], CT(Fb[(long long)(ar0 + v) * K + k]), a2);
+        }
+        acc[j] += a2;
+      }
+    }
+  for (int j = 0; j < 4; ++j) {
+    const int k = threadIdx.x + j * blockDim.x;
     if (k >= K) break;
     s[(long long)k * d + x] = f[(long long)u_x[x] * K + k] * w[x] * double(acc[j]);
   }
@@ -453,16 +515,37 @@ void compute_scores(Step& S, const double* Ft) {
   int thr = std::min(256, std::max(32, ((K + 3) / 4 + 31) / 32 * 32));
   if (K > 4 * thr) throw SgtnError(-1, "beam too large for the score kernel");
   double sc_fl = 2.0 * K * D.d * (double)Kc.nG * Kc.nE * chl * (chr + 1);
+  // left bonds up to 64 (every chi <= 64): the register form
+  auto reg = [&](auto ct, auto chlmax) {
+    using CT = decltype(ct);
+    constexpr int CHL = decltype(chlmax)::value;
+    constexpr int V = 16 / sizeof(CT);
+    const size_t smem = size_t(CHL) * ((chr + V - 1) / V * V) * sizeof(CT);
+    score_reg_kernel<CT, CHL><<<D.d, thr, smem, st>>>(K, D.d, chl, chr, Kc.nG, Kc.nE, Kc.nPdr, S.E, S.Ahat[c], Ft,
+                                                      S.f[c], D.w, D.lam_x, D.u_x, D.cls[DD], D.cls[DR_], D.cls[DDR],
+                                                      S.s);
+  };
+  using I16 = std::integral_constant<int, 16>;
+  using I32 = std::integral_constant<int, 32>;
+  using I64 = std::integral_constant<int, 64>;
   if (g_compute_f32) {
     KTimer tsc("score_f32", st, sc_fl);
-    score_kernel<float><<<D.d, thr, size_t(chl) * chr * sizeof(float), st>>>(
-        K, D.d, chl, chr, Kc.nG, Kc.nE, Kc.nPdr, S.E, S.Ahat[c], Ft, S.f[c], D.w, D.lam_x, D.u_x, D.cls[DD],
-        D.cls[DR_], D.cls[DDR], S.s);
+    if (chl <= 16) reg(float(), I16());
+    else if (chl <= 32) reg(float(), I32());
+    else if (chl <= 64) reg(float(), I64());
+    else
+      score_kernel<float><<<D.d, thr, size_t(chl) * chr * sizeof(float), st>>>(
+          K, D.d, chl, chr, Kc.nG, Kc.nE, Kc.nPdr, S.E, S.Ahat[c], Ft, S.f[c], D.w, D.lam_x, D.u_x, D.cls[DD],
+          D.cls[DR_], D.cls[DDR], S.s);
   } else {
     KTimer tsc("score_f64", st, sc_fl);
-    score_kernel<double><<<D.d, thr, size_t(chl) * chr * sizeof(double), st>>>(
-        K, D.d, chl, chr, Kc.nG, Kc.nE, Kc.nPdr, S.E, S.Ahat[c], Ft, S.f[c], D.w, D.lam_x, D.u_x, D.cls[DD],
-        D.cls[DR_], D.cls[DDR], S.s);
+    if (chl <= 16) reg(double(), I16());
+    else if (chl <= 32) reg(double(), I32());
+    else if (chl <= 64) reg(double(), I64());
+    else
+      score_kernel<double><<<D.d, thr, size_t(chl) * chr * sizeof(double), st>>>(
+          K, D.d, chl, chr, Kc.nG, Kc.nE, Kc.nPdr, S.E, S.Ahat[c], Ft, S.f[c], D.w, D.lam_x, D.u_x, D.cls[DD],
+          D.cls[DR_], D.cls[DDR], S.s);
   }
   ++g_count.launches;
 }
