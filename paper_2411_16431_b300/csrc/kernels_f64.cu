@@ -26,16 +26,20 @@ constexpr int TK = 16;
 // BM x BN tile of one output segment and runs over the flattened (term,
 // k-chunk) sequence of that segment: the operand tiles of the next step are
 // loaded into registers while the current ones are multiplied out of shared
-// memory (one barrier per step).  Thread (ty, tx) accumulates rows ty + 16u
-// and columns tx + 16v of the tile in the arithmetic type CT.  Term coefficients and column
+// memory (one barrier per step).  Thread (ty, tx) accumulates rows
+// ty RM + u and columns tx RN + v of the tile (RM = BM / 16, RN = BN / 16) in
+// the arithmetic type CT.  Term coefficients and column
 // scales are applied to the Y tile as it is stored.  Tile loads run along
 // whichever operand index has unit stride, so they coalesce.
 template <class CT, int BM, int BN>
 __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
   constexpr int RM = BM / 16, RN = BN / 16;
   constexpr int XL = (BM * TK + 255) / 256, YL = (TK * BN + 255) / 256;
-  __shared__ CT Xs[2][TK][BM + 1];
-  __shared__ CT Ys[2][TK][BN + 1];
+  // rows padded by 16 bytes: every row starts 16-byte aligned, so a thread's
+  // RM (RN) contiguous tile entries come in vector loads
+  constexpr int PAD = 16 / int(sizeof(CT));
+  __shared__ __align__(16) CT Xs[2][TK][BM + PAD];
+  __shared__ __align__(16) CT Ys[2][TK][BN + PAD];
   const int seg = blockIdx.x / a.kpart, part = blockIdx.x % a.kpart;
   const int i0 = blockIdx.y * BM, j0 = blockIdx.z * BN;
   const int tid = threadIdx.x;
@@ -152,9 +156,9 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
     for (int kk = 0; kk < TK; ++kk) {
       CT xv[RM], yv[RN];
 #pragma unroll
-      for (int u = 0; u < RM; ++u) xv[u] = Xs[buf][kk][ty + 16 * u];
+      for (int u = 0; u < RM; ++u) xv[u] = Xs[buf][kk][ty * RM + u];
 #pragma unroll
-      for (int v = 0; v < RN; ++v) yv[v] = Ys[buf][kk][tx + 16 * v];
+      for (int v = 0; v < RN; ++v) yv[v] = Ys[buf][kk][tx * RN + v];
 #pragma unroll
       for (int u = 0; u < RM; ++u)
 #pragma unroll
@@ -165,11 +169,11 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(SegGemm a) {
   }
 #pragma unroll
   for (int u = 0; u < RM; ++u) {
-    const int i = i0 + ty + 16 * u;
+    const int i = i0 + ty * RM + u;
     if (i >= a.p) continue;
 #pragma unroll
     for (int v = 0; v < RN; ++v) {
-      const int j = j0 + tx + 16 * v;
+      const int j = j0 + tx * RN + v;
       if (j >= a.s) continue;
       double* o = a.O + ooff + (long long)i * a.os_i + (long long)j * a.os_j;
       const double val = a.alpha * double(acc[u][v]);
