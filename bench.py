@@ -102,14 +102,15 @@ for _name in ("kings50x50",):
     WORKLOADS[_name + "_x8"] = dict(WORKLOADS[_name], transforms=8,
                                     desc=WORKLOADS[_name]["desc"] + "; all 8 grid symmetries per step, concurrently")
 DEFAULT = "pegasus15x15"
-# precision name -> (boundary precision, search precision or -1, dtype label)
-PRECISIONS = {"fp64": (0, -1, "f64"),
-              "fp32": (3, -1, "f32 contractions, f64 truncation"),
-              "tf32": (1, -1, "3xtf32 tensor cores + f32 contractions, f64 truncation"),
-              "fp64_tf32search": (0, 1, "f64 boundary, 3xtf32/f32 conditional scores")}
-# the default meets the log Z <= 1e-6 bound of the mixed-vs-FP64 comparison exactly (FP64
-# boundary); "tf32" is faster with a log Z error of a few 1e-6 at beta = 2
-DEFAULT_PRECISION = "fp64_tf32search"
+# precision name -> (boundary precision, search precision or -1, dtype label, FP64 final sweeps)
+PRECISIONS = {"fp64": (0, -1, "f64", False),
+              "fp32": (3, -1, "f32 contractions, f64 truncation", False),
+              "tf32": (1, -1, "3xtf32 tensor cores + f32 contractions, f64 truncation", False),
+              "tf32_polish": (1, -1, "3xtf32 tensor cores + f32 contractions, f64 truncation and final sweeps", True),
+              "fp64_tf32search": (0, 1, "f64 boundary, 3xtf32/f32 conditional scores", False)}
+# the default: a mixed boundary whose sweeps after the cut run in FP64 (about 1.5e-7 log Z
+# error at beta = 2 on P16, where the plain TF32 boundary sits near 1e-6), mixed scores
+DEFAULT_PRECISION = "tf32_polish"
 # FP64 peak of a B300 derived from unit counts: 148 SMs x 2 DFMA/clk/SM x 2 flop x 2032 MHz
 FP64_PEAK_GFLOPS = 148 * 2 * 2 * 2.032
 # FP32 SIMT peak from unit counts (148 SMs x 128 FMA/clk x 2 flop x 2032 MHz)
@@ -363,7 +364,7 @@ def run_native(args, wl):
     stream = torch.cuda.current_stream()
     inst = wl["make"](args.seed + rank)
     states = wl["states"](inst, args.seed + rank) if wl["states"] else None
-    prec, sprec, dtype_name = PRECISIONS[args.precision]
+    prec, sprec, dtype_name, polish = PRECISIONS[args.precision]
     # the units of one step: the instance, or its first n grid symmetries, or a batch of
     # independent instances; every unit on its own stream when there are several
     if "batch" in wl:
@@ -383,6 +384,7 @@ def run_native(args, wl):
         for k, (ti, tst) in enumerate(units):
             hk = sgtn.Handle(ti, tst, stream=t_streams[k].cuda_stream)
             hk.set_search_precision(sprec)
+            hk.set_final_sweeps_fp64(polish)
             hs.append(hk)
         return hs
 

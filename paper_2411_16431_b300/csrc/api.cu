@@ -234,6 +234,10 @@ int sgtn_set_zipper_window(sgtn_h h, int32_t window) {
   });
 }
 
+int sgtn_set_final_sweeps_fp64(sgtn_h h, int32_t on) {
+  return guarded(h, [&] { h->f64_final_sweeps = on != 0; });
+}
+
 int sgtn_boundary_info(sgtn_h h, int32_t* unconverged_cuts, int32_t* precision) {
   return guarded(h, [&] {
     if (unconverged_cuts) *unconverged_cuts = h->unconverged_cuts;

@@ -28,6 +28,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -1474,6 +1475,10 @@ void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& wo
   worst = std::max(worst, svd_cut(X, phi, chi));
   normalise(h, phi[C - 1].p, phi[C - 1].n(), ln);
   for (int s = 0; s < n_sweeps; ++s) {
+    // optionally the sweeps after the cut in FP64 also in a mixed contraction:
+    // they converge the MPS toward the fixed point of the FP64 target
+    std::unique_ptr<F64Scope> f64;
+    if (h->f64_final_sweeps) f64.reset(new F64Scope());
     double extra = variational_sweep(X, phi, s > 0);   // svd_cut leaves phi left-canonical
     ln = A.lognorm + extra;
     normalise(h, phi[0].p, phi[0].n(), ln);

@@ -75,6 +75,7 @@ struct sgtn_inst {
   std::vector<sgtn::MPS> psi;             // psi[r] covers rows r+1..R-1
   int chi = 0, precision = 0, n_sweeps = 0;
   int zipper_window = 0;                  // columns swept after each zipper step; 0: all built so far
+  bool f64_final_sweeps = false;          // the sweeps after the cut in FP64 in a mixed contraction
   int search_precision = -1;              // conditionals / branch step / search; -1: as the boundary
   bool boundary_ok = false;
   double logz = 0.0, worst_sv = 0.0;

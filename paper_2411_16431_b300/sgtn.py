@@ -39,6 +39,7 @@ def load():
                                    _I32P, _F64P]
     L.sgtn_set_search_precision.argtypes = [ct.c_void_p, ct.c_int32]
     L.sgtn_set_zipper_window.argtypes = [ct.c_void_p, ct.c_int32]
+    L.sgtn_set_final_sweeps_fp64.argtypes = [ct.c_void_p, ct.c_int32]
     L.sgtn_kernel_names.argtypes = [ct.c_char_p, ct.c_int32]
     L.sgtn_kernel_names.restype = ct.c_int32
     L.sgtn_search.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I8P, _I64P, _F64P, _F64P, _I32P]
@@ -188,6 +189,10 @@ class Handle:
     def set_zipper_window(self, window):
         """Columns swept after each zipper step (0: all built so far, 1: no sweep)."""
         self._ck(self.L.sgtn_set_zipper_window(self.h, int(window)))
+
+    def set_final_sweeps_fp64(self, on=True):
+        """Mixed contractions: run the sweeps after the cut to chi in FP64."""
+        self._ck(self.L.sgtn_set_final_sweeps_fp64(self.h, int(bool(on))))
 
     def set_search_precision(self, precision):
         """Precision of conditionals / branch_step / search (-1: as the last contract_boundary)."""

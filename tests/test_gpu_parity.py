@@ -436,16 +436,19 @@ MIXED_CASES = [(L.chimera_grid(4, 4, 0), None, 1.0, 16, 2), (L.kings_grid(5, 6, 
                (PEGP, PEGP_STATES, 2.0, 8, 2)]
 
 
+@pytest.mark.parametrize("polish", [False, True], ids=["mixed", "fp64_final_sweeps"])
 @pytest.mark.parametrize("prec", ["FP32", "TF32"])
 @pytest.mark.parametrize("case", MIXED_CASES, ids=lambda c: c[0].name)
-def test_mixed_precision_error_is_small(Handle, case, prec):
-    """FP32 contractions with FP64 truncation: log Z within 1e-6 relative of the FP64 oracle,
-    marginals within 1e-4, same final configuration and exact int64 energy."""
+def test_mixed_precision_error_is_small(Handle, case, prec, polish):
+    """FP32 contractions with FP64 truncation (and optionally FP64 sweeps after the cut):
+    log Z within 1e-6 relative of the FP64 oracle, marginals within 1e-4, same final
+    configuration and exact int64 energy."""
     from paper_2411_16431_b300 import sgtn
     P = getattr(sgtn, prec)
     inst, states, beta, chi, ns = case
     lz_o, psis, mpos = boundary_mps(PottsModel(inst, states), beta, chi, ns)
     h = Handle(inst, states)
+    h.set_final_sweeps_fp64(polish)
     h.set_beta(beta)
     lz, _ = h.contract_boundary(chi, precision=P, n_sweeps=ns)
     assert abs(lz - lz_o) < 1e-6 * abs(lz_o)
@@ -454,6 +457,20 @@ def test_mixed_precision_error_is_small(Handle, case, prec):
     res = h.search(16)
     assert np.array_equal(res["energy_num"], ref["energy_num"])
     assert np.allclose(res["logp"], ref["logp"], rtol=1e-4)
+
+
+def test_fp64_final_sweeps_leave_an_fp64_contraction_unchanged(Handle):
+    """The FP64 final-sweeps option only acts on mixed contractions: an FP64 boundary with it
+    set is bit-identical to one without."""
+    inst, beta, chi, ns = CASES[0]
+    out = []
+    for on in (False, True):
+        h = Handle(inst)
+        h.set_final_sweeps_fp64(on)
+        h.set_beta(beta)
+        out.append(h.contract_boundary(chi, n_sweeps=ns)[0])
+        h.close()
+    assert out[0] == out[1]
 
 
 def test_fp64_boundary_with_fp32_search(Handle):
