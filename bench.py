@@ -313,7 +313,7 @@ def run_reference(args, wl):
 def peak_of(name):
     """(peak in TFLOP/s, bound, source) of a timed kernel label, from its arithmetic: the
     GEMM peak of the same arithmetic measured on this machine (measure_peaks), else derived."""
-    if name.startswith("tc_gemm"):
+    if name.startswith("tc_gemm") or name.endswith("_tc"):
         if MEASURED.get("tf32_tflops"):
             return (MEASURED["tf32_tflops"] / 3.0, "tensor",
                     "measured TF32 cuBLAS peak on this box / 3 (three products per 3xTF32)")

@@ -253,6 +253,27 @@ int sgtn_set_zipper_window(sgtn_h h, int32_t window);
  * effect on an SGTN_FP64 contraction. */
 int sgtn_set_final_sweeps_fp64(sgtn_h h, int32_t on);
 
+/* How the one-site updates of the variational sweeps (Fig. 8d) are made
+ * orthonormal before the sweep moves on.  Only the span of an updated tensor
+ * matters there (the next update projects the target onto it again) and
+ * nothing is truncated, so where the truncated SVD would keep every direction
+ * any orthonormal basis of the same span gives the same boundary MPS in
+ * another gauge, without the SVD's Jacobi rotations.  mode 1 (the default):
+ * one CholeskyQR pass, Q1 = M R^{-1}, when its FP64 Cholesky factor R keeps
+ * every pivot above 1e-10 of its diagonal entry and ||M||_F ||R^{-1}||_F <
+ * 1e12 for the matrix M being orthonormalised (an upper bound on its
+ * condition number, so no singular value falls below the rank rule's 1e-12
+ * of the largest), then one Newton step toward the polar factor,
+ * Q = Q1 (3 I - Q1^T Q1) / 2, accepted when max |Q1^T Q1 - I| <= 1e-6 (its
+ * orthogonality error is then about the square of that or less); otherwise
+ * the SVD.  mode 0:
+ * always the SVD.  The paper leaves the orthonormalisation open.
+ * SGTN_ERR_ARG for any other mode. */
+int sgtn_set_sweep_orthonormalisation(sgtn_h h, int32_t mode);
+/* Sweep orthonormalisations done so far on this handle by CholeskyQR2 and by
+ * the SVD (either pointer may be NULL). */
+int sgtn_sweep_orthonormalisations(sgtn_h h, int64_t* by_qr, int64_t* by_svd);
+
 int sgtn_boundary_info(sgtn_h h, int32_t* unconverged_cuts, int32_t* precision);
 int sgtn_mps_shape(sgtn_h h, int32_t row, int32_t* phys, int32_t* bond, double* lognorm);
 int sgtn_mps_tensor(sgtn_h h, int32_t row, int32_t col, double* out);
@@ -296,6 +317,28 @@ int sgtn_conditionals_noalloc(sgtn_h h, int32_t step, int32_t count, const int32
  * for non-positive sizes, NULL pointers or another precision. */
 int sgtn_gemm(int32_t precision, int32_t m, int32_t n, int32_t k, const double* X, const double* Y, double* C,
               void* stream);
+
+/* The segmented gathered product behind the sparse site diagram of Fig. 7(b)
+ * (Sec. III.B, "Employing sparsity of tensors": one chi x chi product per
+ * cluster state, weighted by its Boltzmann factor, summed into the block of
+ * its projected indices), exposed to test the library's contraction kernels
+ * on their own.  All pointers are device memory; the call is asynchronous on
+ * `stream` (NULL: the default stream) except for SGTN_TF32, which synchronises
+ * to read the kernels' timeout flag.  For segment g = 0..nseg-1:
+ *   O[g] = sum_{t = seg_ptr[g]}^{seg_ptr[g+1]-1} c_t X[xr[t]] Y[yr[t]],
+ * c_t = coef[cidx[t]] (1 if cidx is NULL), X[i] the i-th of nx row-major
+ * p x q blocks of X, Y[j] the j-th of ny row-major q x s blocks of Y, O[g]
+ * the g-th row-major p x s block of O (overwritten; zero for an empty
+ * segment).  seg_ptr has nseg + 1 nondecreasing entries from 0 to nterm;
+ * 0 <= xr[t] < nx and 0 <= yr[t] < ny are the caller's to ensure.
+ * precision: SGTN_FP64 or SGTN_FP32 (SIMT kernel), SGTN_TF32 (3xTF32 on the
+ * tcgen05 tensor cores, operand tiles brought in by TMA, when p >= 32,
+ * q >= 16, s >= 16 and q, s are even; else FP32).  SGTN_ERR_ARG for
+ * non-positive sizes, NULL arrays or another precision; SGTN_ERR_TIMEOUT if
+ * a bounded wait of the tensor-core kernel gave up. */
+int sgtn_seg_gemm(int32_t precision, int32_t p, int32_t q, int32_t s, int32_t nseg, int32_t nterm, int32_t nx,
+                  int32_t ny, const int32_t* seg_ptr, const int32_t* xr, const int32_t* yr, const int32_t* cidx,
+                  const double* coef, const double* X, const double* Y, double* O, void* stream);
 
 /* Process-wide diagnostics (the paper has no counterpart): cumulative
  * number of kernel launches issued by this library, algorithmic

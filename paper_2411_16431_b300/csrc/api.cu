@@ -238,6 +238,20 @@ int sgtn_set_final_sweeps_fp64(sgtn_h h, int32_t on) {
   return guarded(h, [&] { h->f64_final_sweeps = on != 0; });
 }
 
+int sgtn_set_sweep_orthonormalisation(sgtn_h h, int32_t mode) {
+  return guarded(h, [&] {
+    if (mode != 0 && mode != 1) throw SgtnError(SGTN_ERR_ARG, "sweep orthonormalisation must be 0 (SVD) or 1 (QR)");
+    h->sweep_qr = mode == 1;
+  });
+}
+
+int sgtn_sweep_orthonormalisations(sgtn_h h, int64_t* by_qr, int64_t* by_svd) {
+  return guarded(h, [&] {
+    if (by_qr) *by_qr = h->sweep_qr_count;
+    if (by_svd) *by_svd = h->sweep_svd_count;
+  });
+}
+
 int sgtn_boundary_info(sgtn_h h, int32_t* unconverged_cuts, int32_t* precision) {
   return guarded(h, [&] {
     if (unconverged_cuts) *unconverged_cuts = h->unconverged_cuts;
@@ -300,6 +314,66 @@ int sgtn_gemm(int32_t precision, int32_t m, int32_t n, int32_t k, const double* 
   try {
     Modes md(precision);
     gemm(X, false, k, Y, false, n, C, n, m, n, k, 1.0, 0, st);
+    if (cudaGetLastError() != cudaSuccess) return SGTN_ERR_CUDA;
+    if (precision == SGTN_TF32 && tc_gemm_take_error(st)) return SGTN_ERR_TIMEOUT;
+    return SGTN_OK;
+  } catch (const SgtnError& e) {
+    cudaGetLastError();
+    return e.code;
+  } catch (const std::exception&) {
+    return SGTN_ERR_CUDA;
+  }
+}
+
+int sgtn_seg_gemm(int32_t precision, int32_t p, int32_t q, int32_t s, int32_t nseg, int32_t nterm, int32_t nx,
+                  int32_t ny, const int32_t* seg_ptr, const int32_t* xr, const int32_t* yr, const int32_t* cidx,
+                  const double* coef, const double* X, const double* Y, double* O, void* stream) {
+  if (p <= 0 || q <= 0 || s <= 0 || nseg <= 0 || nterm < 0 || nx <= 0 || ny <= 0) return SGTN_ERR_ARG;
+  if (!seg_ptr || !xr || !yr || !X || !Y || !O || (cidx && !coef)) return SGTN_ERR_ARG;
+  if (precision != SGTN_FP64 && precision != SGTN_FP32 && precision != SGTN_TF32) return SGTN_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  struct Modes {   // the thread's contraction modes for this call only
+    Modes(int pr) {
+      g_compute_f32 = pr != SGTN_FP64;
+      g_use_tc = pr == SGTN_TF32;
+    }
+    ~Modes() {
+      g_compute_f32 = false;
+      g_use_tc = false;
+    }
+  };
+  try {
+    Modes md(precision);
+    SegGemm a;
+    a.name = "seg_gemm";
+    a.X = X;
+    a.Y = Y;
+    a.O = O;
+    a.p = p;
+    a.q = q;
+    a.s = s;
+    a.xs_i = q;
+    a.xs_k = 1;
+    a.xrs = (long long)p * q;
+    a.ys_k = s;
+    a.ys_j = 1;
+    a.yrs = (long long)q * s;
+    a.os_i = s;
+    a.os_j = 1;
+    a.ors = (long long)p * s;
+    a.out_by_seg = 1;
+    a.seg_ptr = seg_ptr;
+    a.xr = xr;
+    a.yr = yr;
+    a.xc = xr;   // the kernels read a column index per term; with xcs = ycs = 0 it adds nothing
+    a.yc = yr;
+    a.cidx = cidx;
+    a.coef = cidx ? coef : nullptr;
+    a.nseg = nseg;
+    a.nterm = nterm;
+    a.x_rows = (long long)nx * p;
+    a.y_rows = (long long)ny * q;
+    seg_gemm(a, st);
     if (cudaGetLastError() != cudaSuccess) return SGTN_ERR_CUDA;
     if (precision == SGTN_TF32 && tc_gemm_take_error(st)) return SGTN_ERR_TIMEOUT;
     return SGTN_OK;

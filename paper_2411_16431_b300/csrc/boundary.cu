@@ -208,6 +208,7 @@ SvdOut svd(sgtn_inst* h, const double* Th, int m, int n, int cap) {
 
 SvdOut svd_jacobi(sgtn_inst* h, const double* Th, int m, int n, int cap);
 bool cqr_orth(sgtn_inst* h, const double* M, int len, int k, double* Q, bool first_f32);
+bool orth_qr(sgtn_inst* h, const double* M, int m, int n, bool rows, double* Q);
 bool svd_tall_cqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o);
 bool svd_tall_cqr3(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o);
 bool svd_tall_rrcqr(sgtn_inst* h, const double* M, int m, int n, int cap, SvdOut& o);
@@ -609,6 +610,70 @@ bool cqr_orth(sgtn_inst* h, const double* M, int len, int k, double* Q, bool fir
   return true;
 }
 
+// Orthonormal basis of the span of M by CholeskyQR, for the orthonormalisations
+// of the variational sweeps, where only the span matters (the next one-site
+// update projects the target onto it again) and no truncation is asked for.
+// rows = false: M is m x n (m >= n), Q (m x n) gets orthonormal columns with
+// the column span of M; rows = true: M is m x n (m <= n), Q (m x n) gets
+// orthonormal rows with the row space of M.  Taken only when the truncated SVD
+// would keep every direction: the unshifted FP64 Cholesky factor R of the
+// Gram matrix succeeds with every pivot above 1e-10 of its diagonal entry (a
+// scale-invariant condition under which two passes reach rounding-level
+// orthogonality, also for vectors of very different norms) and
+// ||M||_F ||R^{-1}||_F -- an upper bound on sigma_max / sigma_min, since
+// sigma_max <= ||M||_F and 1 / sigma_min = ||R^{-1}||_2 <= ||R^{-1}||_F --
+// stays below 1 / RANK_TOL, so the rank rule would drop nothing.  The first
+// pass leaves vectors Q1 whose Gram matrix is I + E with |E| about
+// cond^2 x 1e-16; instead of a second Cholesky pass, one step of the Newton
+// iteration for the polar factor, Q = Q1 (3 I - Q1^T Q1) / 2, leaves an
+// orthogonality error of O(|E|^2), accepted when max |E| <= 1e-6 (so at most
+// about 1e-12; well-conditioned vectors reach rounding level).  Returns false
+// otherwise (the caller then takes the SVD); Q is then unspecified.
+bool orth_qr(sgtn_inst* h, const double* M, int m, int n, bool rows, double* Q) {
+  F64Scope f64;
+  cudaStream_t st = h->st;
+  const int k = rows ? m : n, len = rows ? n : m;   // k vectors of length len
+  if (k < 1 || len < k || k > h->dense_svd_max) return false;
+  double* G = h->ws.get<double>("oq_G", size_t(k) * k);
+  double* R = h->ws.get<double>("oq_R", size_t(k) * k);
+  double* Ri = h->ws.get<double>("oq_Ri", size_t(k) * k);
+  double* T = h->ws.get<double>("oq_T", size_t(len) * k);
+  double* dv = h->ws.get<double>("oq_vals", 4);   // minratio, max |G - I|, trace, ||R^{-1}||_F
+  int* status = h->ws.get<int>("oq_status", 2);
+  // upper triangle of the Gram matrix of the vectors
+  auto gram = [&](const double* X) {
+    if (rows) gemm(X, false, len, X, true, len, G, k, k, k, len, 1.0, 0, st, 1);
+    else gram_upper(X, k, G, k, len, st);
+  };
+  // out = X R^{-1} (columns) or R^{-T} X (rows)
+  auto apply = [&](const double* X, double* out) {
+    if (rows) gemm(Ri, true, k, X, false, len, out, len, k, len, k, 1.0, 0, st);
+    else gemm(X, false, k, Ri, false, k, out, k, len, k, k, 1.0, 0, st, 2);
+  };
+  gram(M);
+  gram_stats(G, k, dv + 1, st);
+  cholesky_inv(G, k, 0.0, R, Ri, status, st, false, dv);
+  fro_norm(Ri, (long long)k * k, dv + 3, st);
+  double hv[4];
+  int hs = 0;
+  SGTN_CUDA(cudaMemcpyAsync(hv, dv, sizeof(hv), cudaMemcpyDeviceToHost, st));
+  SGTN_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  h->sync();
+  // ||M||_F^2 = trace(G)
+  const double bound = std::sqrt(hv[2]) * hv[3];
+  if (hs != 0 || !(hv[0] > 1e-10) || !(bound < 1.0 / RANK_TOL)) return false;
+  apply(M, T);
+  gram(T);
+  gram_stats(G, k, dv + 1, st);
+  polar_factor(G, k, R, st);
+  if (rows) gemm(R, false, k, T, false, len, Q, len, k, len, k, 1.0, 0, st);   // Q = S Q1
+  else gemm(T, false, k, R, false, k, Q, k, len, k, k, 1.0, 0, st);            // Q = Q1 S
+  double dev = 0.0;
+  SGTN_CUDA(cudaMemcpyAsync(&dev, dv + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+  h->sync();
+  return dev <= 1e-6;
+}
+
 // Same, with Theta given only through Y = Theta Q and Z = Theta^T Y.  Each
 // iteration orthonormalises both products by CholeskyQR (Y before it is
 // multiplied back, so that no condition number is squared); every second
@@ -807,6 +872,8 @@ void site_diagram(RowCtx& X, int c, const double* Kt, int kp, double* Th) {
   a.coef = X.h->ds[X.r * X.h->M.C + c].w;
   a.nseg = K_.theta.nseg;
   a.nterm = K_.theta.nterm;
+  a.x_rows = (long long)K_.nA() * chl;
+  a.y_rows = (long long)K_.nK() * chr;
   seg_gemm(a, X.h->st);
 }
 
@@ -895,6 +962,8 @@ double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
   a.coef = h->ds[X.r * h->M.C + c].w;
   a.nseg = K_.lupd.nseg;
   a.nterm = K_.lupd.nterm;
+  a.x_rows = (long long)np * phi.b;
+  a.y_rows = (long long)K_.nA() * chl;
   seg_gemm(a, h->st);
   // Lnext[b][br][chr] = sum_k Wk[k][br] Ltil[k][b][chr]   (batched over b)
   double* Ln = dmalloc((long long)phi.b * K_.nBR() * chr);
@@ -1013,6 +1082,8 @@ ThetaOp theta_op(RowCtx& X, int c, const double* K, int kp) {
   a.coef = h->ds[X.r * h->M.C + c].w;
   a.nseg = K_.theta.nseg;
   a.nterm = K_.theta.nterm;
+  a.x_rows = (long long)K_.nA() * T.chl;
+  a.y_rows = (long long)K_.nK() * X.chr(c);
   seg_gemm(a, h->st);
   return T;
 }
@@ -1222,7 +1293,10 @@ struct RightEnvs {
 // zipper); phi must be right-canonical on c0..C-1, Lc0 [phi[c0].a x (bl, chl)
 // of column c0] is the left environment at c0 (taken over, freed here) and
 // RE.R[c0..e] must hold the environments of the current phi.  Each update is
-// the exact maximiser given the other tensors, made orthonormal by an SVD.
+// the exact maximiser given the other tensors, made orthonormal by a
+// CholeskyQR pass and a polar correction where the truncated SVD would keep
+// every direction (orth_qr: only the span matters, the next update projects
+// onto it again), else by that SVD.
 // Afterwards phi[c0..e] are right-canonical and RE.R[c0-1..e-1] refreshed:
 // for c0 > 0, RE.R[c0-1] is the new connecting tensor (the optimal centre of
 // the stage); for c0 = 0 the centre stays in phi[0] (unnormalised) and the
@@ -1241,12 +1315,22 @@ double sweep_range(RowCtx& X, std::vector<Ten>& phi, int c0, int e, double* Lc0,
     phi[c].p = t;
     phi[c].u = X.nout(c);
     if (c < e) {
-      SvdOut o = svd(h, t, a * X.nout(c), phi[c].b, 1 << 30);
-      double* Q = left_factor(h, o, a * X.nout(c));
-      dfree(phi[c].p);
-      phi[c].p = Q;
-      phi[c].b = o.k;
-      o.release();
+      const int m = a * X.nout(c);
+      double* Q = h->sweep_qr ? dmalloc((long long)m * phi[c].b) : nullptr;
+      if (Q && orth_qr(h, t, m, phi[c].b, false, Q)) {
+        ++h->sweep_qr_count;
+        dfree(phi[c].p);
+        phi[c].p = Q;
+      } else {
+        dfree(Q);
+        ++h->sweep_svd_count;
+        SvdOut o = svd(h, t, m, phi[c].b, 1 << 30);
+        Q = left_factor(h, o, m);
+        dfree(phi[c].p);
+        phi[c].p = Q;
+        phi[c].b = o.k;
+        o.release();
+      }
       Lenv[c + 1] = update_L(X, c, Lenv[c], phi[c]);
       double dummy = 0.0;
       rescale_pow2(h, Lenv[c + 1], (long long)phi[c].b * X.col(c).nBR() * X.chr(c), dummy);
@@ -1263,12 +1347,21 @@ double sweep_range(RowCtx& X, std::vector<Ten>& phi, int c0, int e, double* Lc0,
     dfree(phi[c].p);
     phi[c].p = t;
     if (c > 0) {
-      SvdOut o = svd(h, t, a, int(n), 1 << 30);
-      dfree(phi[c].p);
-      phi[c].p = o.Vt;
-      o.Vt = nullptr;
-      phi[c].a = o.k;
-      o.release();
+      double* Q = h->sweep_qr ? dmalloc((long long)a * n) : nullptr;
+      if (Q && orth_qr(h, t, a, int(n), true, Q)) {
+        ++h->sweep_qr_count;
+        dfree(phi[c].p);
+        phi[c].p = Q;
+      } else {
+        dfree(Q);
+        ++h->sweep_svd_count;
+        SvdOut o = svd(h, t, a, int(n), 1 << 30);
+        dfree(phi[c].p);
+        phi[c].p = o.Vt;
+        o.Vt = nullptr;
+        phi[c].a = o.k;
+        o.release();
+      }
       double* Rn = theta_right(X, c, T, phi[c]);
       rescale_pow2(h, Rn, (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, rc_log);
       RE.set(c - 1, Rn, rc_log);

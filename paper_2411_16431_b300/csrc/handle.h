@@ -76,15 +76,17 @@ struct sgtn_inst {
   int chi = 0, precision = 0, n_sweeps = 0;
   int zipper_window = 0;                  // columns swept after each zipper step; 0: all built so far
   bool f64_final_sweeps = false;          // the sweeps after the cut in FP64 in a mixed contraction
+  bool sweep_qr = true;                   // sweep orthonormalisations by CholeskyQR where the rank rule keeps all
   int search_precision = -1;              // conditionals / branch step / search; -1: as the boundary
   bool boundary_ok = false;
   double logz = 0.0, worst_sv = 0.0;
   sgtn::Scratch ws;
   int32_t* iota = nullptr;                // 0..iota_n-1
-  int dense_svd_max = 320;
-  long long bs_min_entries = 1ll << 22;
-  int unconverged_cuts = 0;               // iterative truncations stopped at their cap (no gap)   // keep Theta block-sparse when dense would exceed this
-  int32_t *d_ei = nullptr, *d_ej = nullptr, *d_jn = nullptr, *d_hn = nullptr;   // edges for energies                // exact Jacobi up to this many vectors, subspace iteration above
+  int dense_svd_max = 320;                // exact Jacobi up to this many vectors, subspace iteration above
+  long long bs_min_entries = 1ll << 22;   // keep Theta block-sparse when dense would exceed this
+  int unconverged_cuts = 0;               // iterative truncations stopped at their cap (no gap)
+  long long sweep_qr_count = 0, sweep_svd_count = 0;   // sweep orthonormalisations by each route
+  int32_t *d_ei = nullptr, *d_ej = nullptr, *d_jn = nullptr, *d_hn = nullptr;   // edges for energies
   int iota_n = 0;
 
   template <class T>

@@ -122,8 +122,17 @@ struct SegGemm {
   // sequence is cut into kpart contiguous parts, one CTA each, whose partial
   // blocks are summed in part order afterwards (small grids fill the GPU)
   int kpart = 1;
+  // table mode, optional: rows of X (blocks xr * (xrs / xs_i) + i) and of Y
+  // (yr * (yrs / ys_k) + k) that exist in memory.  When set, a TF32-mode call
+  // with row-major blocks may run on the tensor cores (seg_mma), whose tile
+  // copies are bounded by these extents.
+  long long x_rows = 0, y_rows = 0;
 };
 void seg_gemm(const SegGemm& a, cudaStream_t st);
+// Tensor-core form of seg_gemm (3xTF32 on tcgen05): whether a call can take
+// it, and the launch (false if nothing was launched).
+bool seg_mma_ok(const SegGemm& a);
+bool seg_mma(const SegGemm& a, cudaStream_t st);
 
 // Plain row-major GEMM helper on top of seg_gemm: O[m x n] = alpha * op(X) op(Y)
 void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, long long ldy, double* O,
@@ -167,6 +176,11 @@ bool tc_gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, 
 int tc_gemm_take_error(cudaStream_t st);
 // deterministic pseudo-random numbers in [-1, 1] (SplitMix64 of seed + index)
 void pseudo_random(double* x, long long n, unsigned long long seed, cudaStream_t st);
+// S = (3 I - G) / 2 (k x k) from the upper triangle of a symmetric G: for a
+// Gram matrix G = Q^T Q = I + E of nearly orthonormal vectors, Q S is
+// orthonormal to O(|E|^2) (first step of the Newton iteration for the polar
+// factor) and spans the same space
+void polar_factor(const double* G, int k, double* S, cudaStream_t st);
 // R[i][j] += Q[i*ldq + j] for j < k  (R is rows x k, Q is rows x ldq)
 void add_cols(double* R, const double* Q, int rows, int k, int ldq, cudaStream_t st);
 // generic permutation of an nd-array (nd <= 6): out axis k = in axis perm[k]

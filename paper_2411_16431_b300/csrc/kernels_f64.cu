@@ -1136,7 +1136,8 @@ std::string ktimer_names() {
 }
 
 namespace {
-void launch_seg(const SegGemm& a_in, cudaStream_t st) {
+void launch_seg(const SegGemm& a_in, cudaStream_t st, bool tc) {
+  if (tc && seg_mma(a_in, st)) return;
   SegGemm a = a_in;
   // tile shape from the block shape: rows 16 / 32 / 64, columns 32 / 64
   const int bm = a.tile_m ? a.tile_m : a.p <= 16 ? 16 : a.p <= 32 ? 32 : 64;
@@ -1195,7 +1196,9 @@ void seg_gemm(const SegGemm& a_in, cudaStream_t st) {
   if (g_compute_f32) a.f32 = 1;
   if (a.nseg <= 0 || a.p <= 0 || a.s <= 0) return;
   double fl = 2.0 * a.p * a.q * a.s * double(a.seg_ptr ? a.nterm : (a.splitk ? 1 : a.nseg));
-  const std::string nm = std::string(a.name ? a.name : "seg_gemm") + (a.f32 ? "_f32" : "_f64");
+  // TF32 mode: row-major gathered blocks go to the tensor cores (3xTF32)
+  const bool tc = a.f32 && g_use_tc && seg_mma_ok(a);
+  const std::string nm = std::string(a.name ? a.name : "seg_gemm") + (tc ? "_tc" : a.f32 ? "_f32" : "_f64");
   const bool split = a.seg_ptr && a.vseg_ptr && a.nvseg > a.nseg && !g_no_alloc;
   static const bool trace = std::getenv("SGTN_TRACE_GEMM") != nullptr;
   if (trace)
@@ -1203,7 +1206,7 @@ void seg_gemm(const SegGemm& a_in, cudaStream_t st) {
             a.seg_ptr ? a.nterm : (long long)a.nseg, a.p, a.q, a.s, a.splitk, split ? a.nvseg : 0);
   KTimer t(nm.c_str(), st, fl);
   if (!split) {
-    launch_seg(a, st);
+    launch_seg(a, st, tc);
   } else {
     double* part = static_cast<double*>(
         stream_scratch(st, SC_SEG_PART, size_t(a.nvseg) * a.p * a.s * sizeof(double)));
@@ -1217,7 +1220,7 @@ void seg_gemm(const SegGemm& a_in, cudaStream_t st) {
     b.ors = (long long)a.p * a.s;
     b.alpha = 1.0;
     b.accumulate = 0;
-    launch_seg(b, st);
+    launch_seg(b, st, tc);
     long long total = (long long)a.nseg * a.p * a.s;
     int nb = int(std::min<long long>((total + 255) / 256, 148 * 16));
     seg_reduce_kernel<<<nb, 256, 0, st>>>(part, a.vfirst, a.nseg, a.p, a.s, a);
@@ -1500,6 +1503,23 @@ void scale_by_inv(double* x, long long n, const double* norm, cudaStream_t st) {
 
 void pseudo_random(double* x, long long n, unsigned long long seed, cudaStream_t st) {
   pseudo_random_kernel<<<blocks_for(n), 256, 0, st>>>(x, n, seed);
+  ++g_count.launches;
+}
+
+namespace {
+// S = (3 I - G) / 2 from the upper triangle of a symmetric G (k x k)
+__global__ void polar_factor_kernel(const double* G, int k, double* S) {
+  const long long n = (long long)k * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int i = int(e / k), j = int(e % k);
+    const double g = i <= j ? G[(long long)i * k + j] : G[(long long)j * k + i];
+    S[e] = (i == j ? 1.5 : 0.0) - 0.5 * g;
+  }
+}
+}  // namespace
+
+void polar_factor(const double* G, int k, double* S, cudaStream_t st) {
+  polar_factor_kernel<<<blocks_for((long long)k * k), 256, 0, st>>>(G, k, S);
   ++g_count.launches;
 }
 

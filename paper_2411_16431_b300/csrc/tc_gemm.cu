@@ -13,9 +13,11 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
+#include "convert.h"
 #include "kern.h"
 
 namespace sgtn {
@@ -307,6 +309,521 @@ bool tc_gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, 
 }
 
 
+
+// ---------------------------------------------------------------------------
+// Segmented gathered GEMM on the tensor cores (the TF32-mode form of seg_gemm
+// for row-major blocks):  O[seg] (+)= alpha * sum_{t in seg} coef_t X_t Y_t,
+// X_t a p x q block (row pitch xs_i), Y_t a q x s block (row pitch ys_k).
+// This is the sparse site diagram of Fig. 7(b) -- a sum over cluster states of
+// chi x chi products of gathered MPS and environment blocks, each weighted by
+// the state's Boltzmann factor -- and the environment updates built the same
+// way.  Persistent CTAs (one per SM) walk their share of the work items
+// (segment, 128-row tile, BN-column tile) and, inside an item, the flattened
+// (term, 32-wide k-chunk) sequence:
+//   warp 0: TMA copies of the FP64 X tile (p rows, at most 128, x 32) and Y
+//     tile (32 x BN) of the next chunk into a 3- to 6-stage shared-memory ring (the
+//     lanes fetch the term indices and coefficients of 32 items at a time);
+//   warps 4-11: each chunk's FP64 tiles are converted to FP32 on their bit
+//     patterns (B300 runs FP64 instructions, conversions included, at a small
+//     fraction of its FP32 and integer rates), scaled (Y by the term's
+//     coefficient, rows k >= q zeroed), split into TF32 high and low parts and
+//     written back in place in the 128-byte-swizzled K-major layout the MMA
+//     reads (the FP64 tile and its two TF32 halves take the same bytes);
+//   warp 1 (one lane): 3 x 4 tcgen05.mma kind::tf32 (hi*hi + hi*lo + lo*hi)
+//     per chunk into one of four TMEM accumulators (128 lanes x BN columns);
+//   warps 12-15: when an item's last chunk is multiplied, its accumulator is
+//     read with tcgen05.ld and written (or added) to O in FP64, while the MMAs
+//     of the next items go to the other accumulators.
+// Every wait is bounded: on a time-out the CTA records the error, stops, waits
+// (bounded) for its own copies and MMAs in flight and frees its tensor memory.
+namespace {
+
+constexpr int SG_BM = 128, SG_BK = 32, SG_NACC = 4, SG_MAXST = 6;
+constexpr int SG_A_BYTES = SG_BM * SG_BK * 8;                 // FP64 X tile = TF32 hi + lo
+// a stage holds the X tile and a 32 x BN FP64 Y tile; as many stages as fit
+// in 216 KB (3 for BN = 128 up to 6 for BN = 16)
+template <int BN>
+struct SgRing {
+  static constexpr int kStageBytes = SG_A_BYTES + BN * SG_BK * 8;
+  static constexpr int kStages = (216 * 1024 / kStageBytes) < SG_MAXST ? (216 * 1024 / kStageBytes) : SG_MAXST;
+  static constexpr int kSmem = kStages * kStageBytes + 1024;
+};
+constexpr int SG_NCONV = 8;                                  // converter warps
+constexpr int SG_THREADS = 32 * (4 + SG_NCONV + 4);
+
+struct SegMmaArgs {
+  const int32_t *seg_ptr, *seg_or, *seg_oc, *xr, *yr, *cidx;
+  const double* coef;
+  long long xrow_unit, yrow_unit;   // tensor rows per unit of xr / yr
+  int p, q, s, nseg, ntm, ntn, out_by_seg, accumulate;
+  int bmx;   // rows of an X tile copied: p rounded up to 8, at most 128
+  long long ors, ocs, os_i;
+  double* O;
+  double alpha;
+  int* err;
+};
+
+__device__ inline bool sg_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  const uint32_t addr = smem_u32(bar);
+  for (long long it = 0; it < SPIN_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255) == 255 && *abort_flag) return false;
+  }
+  return false;
+}
+// D (+)= A B, kind::tf32, instruction descriptor idesc; accumulate = 0 starts D afresh
+__device__ inline void sg_mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ inline void sg_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// split an FP32 value into TF32 parts (10 mantissa bits, nearest on the
+// dropped bits): the high part and the TF32 rounding of the exact remainder,
+// in FP32 and integer arithmetic only
+__device__ inline float sg_cvt(double v) { return f64_to_f32_int(v); }
+__device__ inline void sg_split(float f, float& hi, float& lo) {
+  const uint32_t b = (__float_as_uint(f) + 0x1000u) & 0xFFFFE000u;
+  hi = __uint_as_float(b);
+  lo = __uint_as_float((__float_as_uint(f - hi) + 0x1000u) & 0xFFFFE000u);
+}
+// byte offset of 4 consecutive TF32 (k = 4 c .. 4 c + 3) of row r in a
+// 128-byte-swizzled K-major tile whose base is 1024-byte aligned
+__device__ inline uint32_t sw128(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
+// What the producer tells the other roles about the chunk in a stage: the
+// term's coefficient, the chunk's k offset, and whether it opens or closes a
+// work item (or, with SG_STOP, that no chunk follows).
+constexpr int SG_FIRST = 1, SG_LAST = 2, SG_STOP = 4;
+struct SgMeta {
+  double cf;
+  int kc, flags;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(SG_THREADS, 1)
+    seg_mma_3xtf32_kernel(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mY,
+                          const __grid_constant__ SegMmaArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[SG_MAXST], conv[SG_MAXST], empty[SG_MAXST], accf[SG_NACC], acce[SG_NACC],
+      fin;
+  __shared__ SgMeta meta[SG_MAXST];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_flag;
+  __shared__ uint32_t issued[SG_MAXST];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per_seg = a.ntm * a.ntn;
+  const int nitems = a.nseg * per_seg;
+  const int nk = (a.q + SG_BK - 1) / SG_BK;
+  constexpr uint32_t B_BYTES = BN * SG_BK * 8;
+  constexpr int SG_STAGES = SgRing<BN>::kStages, SG_STAGE_BYTES = SgRing<BN>::kStageBytes;
+  constexpr uint32_t TMEM_COLS = 128 * SG_NACC;   // SG_NACC accumulators of up to 128 columns
+  constexpr uint32_t IDESC_SG = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                ((uint32_t)(SG_BM >> 4) << 24);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < SG_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], SG_NCONV);
+      mbar_init(&empty[s], 1);
+      issued[s] = 0;
+    }
+    for (int b = 0; b < SG_NACC; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 4);
+    }
+    mbar_init(&fin, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_sh;
+  volatile int* abt = &abort_flag;
+
+  if (warp == 0) {
+    // producer (whole warp): the lanes load the segment bounds and first-term
+    // indices of 32 work items at once (most segments hold one term), lane 0
+    // fills the ring
+    uint32_t g = 0;
+    bool run = true;
+    const int G = gridDim.x;
+    for (int base = blockIdx.x; base < nitems && run; base += 32 * G) {
+      const int my = base + lane * G;
+      int mt0 = 0, mt1 = 0, mxr = 0, myr = 0;
+      double mcf = 1.0;
+      if (my < nitems) {
+        const int seg = my / per_seg;
+        mt0 = a.seg_ptr[seg];
+        mt1 = a.seg_ptr[seg + 1];
+        if (mt1 > mt0) {
+          mxr = a.xr[mt0];
+          myr = a.yr[mt0];
+          if (a.coef) mcf = a.coef[a.cidx[mt0]];
+        }
+      }
+      for (int e = 0; e < 32 && run; ++e) {
+        const int it = base + e * G;
+        if (it >= nitems) break;
+        const int r = it % per_seg;
+        const int i0 = (r / a.ntn) * SG_BM, j0 = (r % a.ntn) * BN;
+        const int t0 = __shfl_sync(0xffffffffu, mt0, e), t1 = __shfl_sync(0xffffffffu, mt1, e);
+        int txr = __shfl_sync(0xffffffffu, mxr, e), tyr = __shfl_sync(0xffffffffu, myr, e);
+        double cf = __shfl_sync(0xffffffffu, mcf, e);
+        for (int t = t0; t < t1 && run; ++t) {
+          if (t > t0) {   // further terms of a segment: one load per term
+            txr = a.xr[t];
+            tyr = a.yr[t];
+            cf = a.coef ? a.coef[a.cidx[t]] : 1.0;
+          }
+          const int xrow = int((long long)txr * a.xrow_unit) + i0;
+          const int yrow = int((long long)tyr * a.yrow_unit);
+          for (int kc = 0; kc < nk; ++kc, ++g) {
+            const int s = g % SG_STAGES;
+            // lane 0 waits for the stage to drain; the verdict is the warp's
+            int ok = 1;
+            if (lane == 0 && g >= SG_STAGES) ok = sg_wait(&empty[s], ((g / SG_STAGES) - 1) & 1, abt);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+              if (lane == 0) atomicExch(&abort_flag, 1);
+              run = false;
+              break;
+            }
+            if (lane == 0) {
+              meta[s].cf = cf;
+              meta[s].kc = kc;
+              meta[s].flags = (t == t0 && kc == 0 ? SG_FIRST : 0) | (t == t1 - 1 && kc == nk - 1 ? SG_LAST : 0);
+              unsigned char* st = smem + s * SG_STAGE_BYTES;
+              mbar_expect_tx(&full[s], a.bmx * (SG_BK * 8) + B_BYTES);
+              tma_load_2d(st, &mX, &full[s], kc * SG_BK, xrow);
+              tma_load_2d(st + SG_A_BYTES, &mY, &full[s], j0, yrow + kc * SG_BK);
+              issued[s] += 1;
+            }
+            __syncwarp();
+          }
+        }
+      }
+    }
+    // sentinel: a stage with no data whose meta says that no chunk follows
+    if (run && lane == 0) {
+      const int s = g % SG_STAGES;
+      if (g >= SG_STAGES && !sg_wait(&empty[s], ((g / SG_STAGES) - 1) & 1, abt)) {
+        atomicExch(&abort_flag, 1);
+      } else {
+        meta[s].flags = SG_STOP;
+        sg_arrive(&full[s]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: follows the chunks' meta; one accumulator per work item
+      uint32_t g = 0, n = 0, buf = 0;
+      for (;; ++g) {
+        const int s = g % SG_STAGES;
+        if (!sg_wait(&conv[s], (g / SG_STAGES) & 1, abt)) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        const int fl = meta[s].flags;
+        if (fl & SG_STOP) break;
+        if (fl & SG_FIRST) {
+          buf = n % SG_NACC;
+          if (n >= SG_NACC && !sg_wait(&acce[buf], ((n / SG_NACC) - 1) & 1, abt)) {
+            atomicExch(&abort_flag, 1);
+            break;
+          }
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + buf * 128;
+        unsigned char* st = smem + s * SG_STAGE_BYTES;
+        const uint64_t ahi = smem_desc(st), alo = smem_desc(st + SG_A_BYTES / 2);
+        const uint64_t bhi = smem_desc(st + SG_A_BYTES), blo = smem_desc(st + SG_A_BYTES + B_BYTES / 2);
+#pragma unroll
+        for (int kk = 0; kk < SG_BK / 8; ++kk) {
+          const uint64_t o = (uint64_t)((kk * 32) >> 4);
+          sg_mma(d, ahi + o, bhi + o, IDESC_SG, ((fl & SG_FIRST) && kk == 0) ? 0u : 1u);
+          sg_mma(d, ahi + o, blo + o, IDESC_SG, 1u);
+          sg_mma(d, alo + o, bhi + o, IDESC_SG, 1u);
+        }
+        mma_commit(&empty[s]);
+        if (fl & SG_LAST) {
+          mma_commit(&accf[buf]);
+          ++n;
+        }
+      }
+      // every MMA this thread issued has completed before the memory is freed
+      mma_commit(&fin);
+      if (!mbar_wait(&fin, 0)) atomicExch(&abort_flag, 1);
+    }
+  } else if (warp >= 4 && warp < 4 + SG_NCONV) {
+    // converters: FP64 tiles -> scaled TF32 hi / lo, in place, swizzled K-major.
+    // Work units of 4 consecutive k (one 16-byte TF32 chunk): X units go
+    // lane-fast along a row's 8 chunks (a warp reads 4 rows of 256 bytes and
+    // writes 4 swizzled rows, no bank conflicts), Y units lane-fast along the
+    // columns j (contiguous reads); rows of X at or past bmx were not copied
+    // (the MMA rows they feed are not stored)
+    const int ct = threadIdx.x - 128;
+    constexpr int NT = 32 * SG_NCONV;
+    constexpr int AU = (SG_BM * 8 + NT - 1) / NT, BU = (BN * 8 + NT - 1) / NT;
+    for (uint32_t g = 0;; ++g) {
+      const int s = g % SG_STAGES;
+      if (!sg_wait(&full[s], (g / SG_STAGES) & 1, abt)) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      const SgMeta m = meta[s];
+      if (!(m.flags & SG_STOP)) {
+        unsigned char* st = smem + s * SG_STAGE_BYTES;
+        float4 af[AU], bf[BU];
+#pragma unroll
+        for (int u = 0; u < AU; ++u) {
+          const int i = ct + NT * u, r = i >> 3, c = i & 7;
+          if (r < a.bmx) {
+            const double2 v0 = *reinterpret_cast<const double2*>(st + r * (SG_BK * 8) + c * 32);
+            const double2 v1 = *reinterpret_cast<const double2*>(st + r * (SG_BK * 8) + c * 32 + 16);
+            af[u] = make_float4(sg_cvt(v0.x), sg_cvt(v0.y), sg_cvt(v1.x), sg_cvt(v1.y));
+          }
+        }
+        const double* yt = reinterpret_cast<const double*>(st + SG_A_BYTES);
+        const float cf = sg_cvt(m.cf);
+        const int kq = a.q - m.kc * SG_BK;   // rows of Y at or past kq lie beyond this block
+#pragma unroll
+        for (int u = 0; u < BU; ++u) {
+          const int i = ct + NT * u, j = i % BN, c = i / BN;
+          if (c < 8) {
+            const int k = 4 * c;
+            bf[u] = make_float4(k < kq ? cf * sg_cvt(yt[k * BN + j]) : 0.0f,
+                                k + 1 < kq ? cf * sg_cvt(yt[(k + 1) * BN + j]) : 0.0f,
+                                k + 2 < kq ? cf * sg_cvt(yt[(k + 2) * BN + j]) : 0.0f,
+                                k + 3 < kq ? cf * sg_cvt(yt[(k + 3) * BN + j]) : 0.0f);
+          }
+        }
+        // every read of the FP64 tiles is done before their bytes are overwritten
+        asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+#pragma unroll
+        for (int u = 0; u < AU; ++u) {
+          const int i = ct + NT * u, r = i >> 3, c = i & 7;
+          if (r < a.bmx) {
+            float4 hi, lo;
+            sg_split(af[u].x, hi.x, lo.x);
+            sg_split(af[u].y, hi.y, lo.y);
+            sg_split(af[u].z, hi.z, lo.z);
+            sg_split(af[u].w, hi.w, lo.w);
+            const uint32_t off = sw128(r, c);
+            *reinterpret_cast<float4*>(st + off) = hi;
+            *reinterpret_cast<float4*>(st + SG_A_BYTES / 2 + off) = lo;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < BU; ++u) {
+          const int i = ct + NT * u, j = i % BN, c = i / BN;
+          if (c < 8) {
+            float4 hi, lo;
+            sg_split(bf[u].x, hi.x, lo.x);
+            sg_split(bf[u].y, hi.y, lo.y);
+            sg_split(bf[u].z, hi.z, lo.z);
+            sg_split(bf[u].w, hi.w, lo.w);
+            const uint32_t off = sw128(j, c);
+            *reinterpret_cast<float4*>(st + SG_A_BYTES + off) = hi;
+            *reinterpret_cast<float4*>(st + SG_A_BYTES + B_BYTES / 2 + off) = lo;
+          }
+        }
+        // generic-proxy writes made visible to the tensor cores' async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      __syncwarp();
+      if (lane == 0) sg_arrive(&conv[s]);
+      if (m.flags & SG_STOP) break;
+    }
+  } else if (warp >= 4 + SG_NCONV) {
+    // epilogue: warp 12 + q reads TMEM lanes / tile rows 32 q .. 32 q + 31 (the
+    // lanes load the output offsets of 32 items at once); an item without
+    // terms is a zero block and uses no accumulator
+    const int qd = warp - (4 + SG_NCONV);
+    const int G = gridDim.x;
+    uint32_t n = 0;
+    bool run = true;
+    for (int base = blockIdx.x; base < nitems && run; base += 32 * G) {
+      const int my = base + lane * G;
+      int mnone = 1;
+      long long mooff = 0;
+      if (my < nitems) {
+        const int seg = my / per_seg;
+        mnone = a.seg_ptr[seg + 1] == a.seg_ptr[seg];
+        mooff = a.out_by_seg ? (long long)seg * a.ors
+                             : (long long)a.seg_or[seg] * a.ors + (long long)a.seg_oc[seg] * a.ocs;
+      }
+      for (int e = 0; e < 32; ++e) {
+        const int it = base + e * G;
+        if (it >= nitems) break;
+        const int r = it % per_seg;
+        const int i0 = (r / a.ntn) * SG_BM, j0 = (r % a.ntn) * BN;
+        const bool none = __shfl_sync(0xffffffffu, mnone, e);
+        const long long ooff = __shfl_sync(0xffffffffu, mooff, e);
+        const int row = i0 + qd * 32 + lane;
+        const bool rows_here = i0 + qd * 32 < a.p;   // this warp's quarter of the tile holds output rows
+        if (none) {
+          if (row < a.p && !a.accumulate) {
+            double* o = a.O + ooff + (long long)row * a.os_i;
+            for (int col = j0; col < min(a.s, j0 + BN); ++col) o[col] = 0.0;
+          }
+          continue;
+        }
+        const uint32_t buf = n % SG_NACC;
+        int ok = 1;
+        if (lane == 0) ok = sg_wait(&accf[buf], (n / SG_NACC) & 1, abt);
+        if (!__shfl_sync(0xffffffffu, ok, 0)) {
+          if (lane == 0) atomicExch(&abort_flag, 1);
+          run = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (rows_here) {
+#pragma unroll
+          for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t rr[16];
+            const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + buf * 128 + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
+                  "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]),
+                  "=r"(rr[14]), "=r"(rr[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < a.p) {
+              double* o = a.O + ooff + (long long)row * a.os_i;
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) {
+                const int col = j0 + c0 + jj;
+                if (col < a.s) {
+                  const double v = a.alpha * (double)__uint_as_float(rr[jj]);
+                  o[col] = a.accumulate ? o[col] + v : v;
+                }
+              }
+            }
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) sg_arrive(&acce[buf]);
+        ++n;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && abort_flag) {
+    atomicExch(a.err, 1);
+    // the copies still in flight land before the shared memory is released
+    for (int s = 0; s < SG_STAGES; ++s)
+      if (issued[s]) mbar_wait(&full[s], (issued[s] - 1) & 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+bool make_map_f64(CUtensorMap* map, const double* base, long long rows, int cols, long long pitch, int box_cols,
+                  int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch * 8};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void*)base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool seg_mma_ok(const SegGemm& a) {
+  if (!a.seg_ptr || a.splitk || a.tri || a.cs || a.kpart != 1) return false;
+  if (a.xs_k != 1 || a.ys_j != 1 || a.os_j != 1) return false;
+  if ((a.xc && a.xcs) || (a.yc && a.ycs)) return false;
+  if (a.x_rows <= 0 || a.y_rows <= 0 || a.x_rows >= (1ll << 31) || a.y_rows >= (1ll << 31)) return false;
+  if (a.xs_i % 2 || a.ys_k % 2 || a.q > a.xs_i || a.s > a.ys_k) return false;   // 16-byte row pitches
+  if (a.xrs % a.xs_i || a.yrs % a.ys_k) return false;                          // blocks start on a row
+  if ((uintptr_t)a.X % 16 || (uintptr_t)a.Y % 16) return false;
+  // small blocks leave most of a 128-row MMA tile empty: the SIMT kernel is faster there
+  if (a.p < 32 || a.q < 16 || a.s < 16) return false;
+  return true;
+}
+
+bool seg_mma(const SegGemm& a, cudaStream_t st) {
+  if (!seg_mma_ok(a)) return false;
+  int* const err = tc_err_flag();
+  if (!err) return false;
+  const int bn = a.s <= 16 ? 16 : a.s <= 32 ? 32 : a.s <= 64 ? 64 : 128;
+  CUtensorMap mX, mY;
+  const int bmx = std::min(SG_BM, (a.p + 7) / 8 * 8);
+  if (!make_map_f64(&mX, a.X, a.x_rows, a.q, a.xs_i, SG_BK, bmx) ||
+      !make_map_f64(&mY, a.Y, a.y_rows, a.s, a.ys_k, bn, SG_BK))
+    return false;
+  SegMmaArgs g;
+  g.seg_ptr = a.seg_ptr;
+  g.seg_or = a.seg_or;
+  g.seg_oc = a.seg_oc;
+  g.xr = a.xr;
+  g.yr = a.yr;
+  g.cidx = a.cidx;
+  g.coef = a.coef;
+  g.xrow_unit = a.xrs / a.xs_i;
+  g.yrow_unit = a.yrs / a.ys_k;
+  g.p = a.p;
+  g.q = a.q;
+  g.s = a.s;
+  g.nseg = a.nseg;
+  g.ntm = (a.p + SG_BM - 1) / SG_BM;
+  g.ntn = (a.s + bn - 1) / bn;
+  g.out_by_seg = a.out_by_seg;
+  g.accumulate = a.accumulate;
+  g.bmx = bmx;
+  g.ors = a.ors;
+  g.ocs = a.ocs;
+  g.os_i = a.os_i;
+  g.O = a.O;
+  g.alpha = a.alpha;
+  g.err = err;
+  static int nsm = [] {
+    int dev = 0, n = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+  }();
+  const long long items = (long long)g.nseg * g.ntm * g.ntn;
+  if (items <= 0) return true;
+  const int grid = int(std::min<long long>(items, nsm));
+  auto go = [&](auto kern, int smem_bytes) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    kern<<<grid, SG_THREADS, smem_bytes, st>>>(mX, mY, g);
+  };
+  if (bn == 16) go(seg_mma_3xtf32_kernel<16>, SgRing<16>::kSmem);
+  else if (bn == 32) go(seg_mma_3xtf32_kernel<32>, SgRing<32>::kSmem);
+  else if (bn == 64) go(seg_mma_3xtf32_kernel<64>, SgRing<64>::kSmem);
+  else go(seg_mma_3xtf32_kernel<128>, SgRing<128>::kSmem);
+  ++g_count.launches;
+  return true;
+}
 
 // 1 if any tensor-core GEMM timed out since the last call (then cleared)
 int tc_gemm_take_error(cudaStream_t st) {

@@ -40,6 +40,8 @@ def load():
     L.sgtn_set_search_precision.argtypes = [ct.c_void_p, ct.c_int32]
     L.sgtn_set_zipper_window.argtypes = [ct.c_void_p, ct.c_int32]
     L.sgtn_set_final_sweeps_fp64.argtypes = [ct.c_void_p, ct.c_int32]
+    L.sgtn_set_sweep_orthonormalisation.argtypes = [ct.c_void_p, ct.c_int32]
+    L.sgtn_sweep_orthonormalisations.argtypes = [ct.c_void_p, _I64P, _I64P]
     L.sgtn_kernel_names.argtypes = [ct.c_char_p, ct.c_int32]
     L.sgtn_kernel_names.restype = ct.c_int32
     L.sgtn_search.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _I8P, _I64P, _F64P, _F64P, _I32P]
@@ -97,6 +99,31 @@ def gemm(X, Y, precision, stream=None):
     if rc != 0:
         raise SgtnError(f"sgtn_gemm failed: {rc}")
     return C
+
+
+def seg_gemm(X, Y, seg_ptr, xr, yr, coef, precision, stream=None):
+    """O[g] = sum over the terms t of segment g of coef[t] X[xr[t]] Y[yr[t]] with the
+    library's segmented contraction kernel.  X: (nx, p, q), Y: (ny, q, s) float64 CUDA
+    tensors; seg_ptr (nseg + 1), xr, yr (nterm) int32 and coef (nterm) float64 CUDA
+    tensors (coef may be None: all ones).  Returns O (nseg, p, s)."""
+    import torch
+    X, Y = X.contiguous(), Y.contiguous()
+    nx, p, q = X.shape
+    ny, q2, s = Y.shape
+    assert q == q2 and X.dtype == Y.dtype == torch.float64 and X.is_cuda and Y.is_cuda
+    nseg, nterm = seg_ptr.numel() - 1, xr.numel()
+    O = torch.empty((nseg, p, s), dtype=torch.float64, device=X.device)
+    cidx = torch.arange(nterm, dtype=torch.int32, device=X.device) if coef is not None else None
+    L = load()
+    L.sgtn_seg_gemm.argtypes = [ct.c_int32] * 8 + [ct.c_void_p] * 9
+    st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    rc = L.sgtn_seg_gemm(precision, p, q, s, nseg, nterm, nx, ny, seg_ptr.data_ptr(), xr.data_ptr(), yr.data_ptr(),
+                         cidx.data_ptr() if cidx is not None else None,
+                         coef.contiguous().data_ptr() if coef is not None else None, X.data_ptr(), Y.data_ptr(),
+                         O.data_ptr(), st)
+    if rc != 0:
+        raise SgtnError(f"sgtn_seg_gemm failed: {rc}")
+    return O
 
 
 def device_allocations():
@@ -193,6 +220,16 @@ class Handle:
     def set_final_sweeps_fp64(self, on=True):
         """Mixed contractions: run the sweeps after the cut to chi in FP64."""
         self._ck(self.L.sgtn_set_final_sweeps_fp64(self.h, int(bool(on))))
+
+    def set_sweep_orthonormalisation(self, mode):
+        """1: CholeskyQR plus a polar correction in the sweeps where the SVD would keep every direction (default); 0: always the SVD."""
+        self._ck(self.L.sgtn_set_sweep_orthonormalisation(self.h, int(mode)))
+
+    def sweep_orthonormalisations(self):
+        """(sweep orthonormalisations done by CholeskyQR, done by the SVD) on this handle so far."""
+        q, v = ct.c_int64(), ct.c_int64()
+        self._ck(self.L.sgtn_sweep_orthonormalisations(self.h, ct.byref(q), ct.byref(v)))
+        return q.value, v.value
 
     def set_search_precision(self, precision):
         """Precision of conditionals / branch_step / search (-1: as the last contract_boundary)."""

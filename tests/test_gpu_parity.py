@@ -130,6 +130,44 @@ def test_zipper_window_matches_oracle(Handle, case, window):
         assert np.allclose(v, vo, rtol=1e-8, atol=1e-10)
 
 
+SWEEP_ORTH_CASES = [(L.chimera_grid(4, 4, 0), None, 1.0, 16, 2), (L.kings_grid(5, 6, 4), None, 1.0, 3, 2),
+                    (L.pegasus_nice(4, 0), L.hamming_ball_states(L.pegasus_nice(4, 0), 96, seed=1), 1.0, 12, 1)]
+
+
+@pytest.mark.parametrize("case", SWEEP_ORTH_CASES, ids=lambda c: f"{c[0].name}_chi{c[3]}")
+def test_sweep_orthonormalisation_by_qr_matches_svd(Handle, case):
+    """The variational sweeps (Fig. 8d) orthonormalise each updated tensor by
+    a CholeskyQR pass and a polar correction where the SVD would keep every
+    direction: the same boundary MPSs in another gauge, so log Z, the MPSs as
+    vectors and the search agree with the SVD route, and both with the oracle."""
+    inst, states, beta, chi, ns = case
+    lz_o, psis, _ = boundary_mps(PottsModel(inst, states), beta, chi, ns)
+    out = {}
+    for mode in (1, 0):
+        h = Handle(inst, states)
+        h.set_sweep_orthonormalisation(mode)
+        h.set_beta(beta)
+        lz, _ = h.contract_boundary(chi, n_sweeps=ns)
+        nqr, nsvd = h.sweep_orthonormalisations()
+        assert (nqr > 0) if mode == 1 else (nqr == 0 and nsvd > 0)
+        assert abs(lz - lz_o) < RTOL * abs(lz_o)
+        vecs = []
+        for r in range(inst.rows):
+            ts, _ = h.mps(r)
+            v = mps_dense(ts)
+            vecs.append(v / np.linalg.norm(v))
+            vo = mps_dense(psis[r][0])
+            assert np.allclose(vecs[-1], vo / np.linalg.norm(vo), rtol=1e-8, atol=1e-10)
+        out[mode] = (lz, vecs, h.search(16))
+        h.close()
+    assert abs(out[1][0] - out[0][0]) < 1e-12 * abs(out[0][0])
+    for a, b in zip(out[1][1], out[0][1]):
+        assert np.allclose(a, b, rtol=1e-9, atol=1e-11)
+    assert np.array_equal(out[1][2]["spins"], out[0][2]["spins"])
+    assert np.array_equal(out[1][2]["energy_num"], out[0][2]["energy_num"])
+    assert np.allclose(out[1][2]["logp"], out[0][2]["logp"], rtol=1e-11)
+
+
 def test_beam_limit_is_checked_before_any_launch(Handle):
     """More than SGTN_MAX_BEAM partial configurations are refused up front by the
     branch step, and by the search once its live beam would exceed it (the

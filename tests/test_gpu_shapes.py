@@ -170,3 +170,58 @@ def test_gemm_elementwise_error_bound(shape, prec):
     bound = {0: k * 2.0 ** -52, 3: 2.0 ** -23 + k * 2.0 ** -24, 1: 2.0 ** -20 + k * 2.0 ** -24}[prec]
     err = np.abs(got - ref)
     assert np.all(err <= bound * absprod + 1e-300), float(np.max(err / absprod))
+
+
+# --- the segmented contraction kernel (sparse site diagram, Fig. 7b) ----------------------
+
+# (p, q, s): chi 64 site diagram with a 2 chi right bond, chi 32 site diagram, an environment
+# update, ragged tails in k (40 = 32 + 8) and columns (48, 200: partial column tiles), two row
+# tiles (160), and blocks too small for a 128-row tensor-core tile (SIMT in TF32 mode)
+SEG_SHAPES = [(64, 64, 128), (32, 32, 64), (128, 64, 64), (96, 40, 48), (160, 32, 200), (16, 16, 16), (40, 18, 30)]
+
+
+@pytest.mark.parametrize("shape", SEG_SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("prec", [0, 3, 1], ids=["fp64", "fp32", "tf32"])
+def test_seg_gemm_elementwise_error_bound(shape, prec):
+    """O[g] = sum_t c_t X[xr_t] Y[yr_t] against float64 on the host, element by element:
+    FP64 within K 2^-52, FP32 within (2^-23 + K 2^-24), TF32 (3xTF32 tensor cores where the
+    shape allows) within (2^-20 + K 2^-24), of sum_t |c_t| |X_t| |Y_t|, K = the summed
+    length of the segment's reductions.  Segments of 0..7 terms (empty ones give zero
+    blocks), operands shared between terms, coefficients spread over six orders."""
+    import torch
+    from paper_2411_16431_b300.sgtn import seg_gemm, kernel_timing, kernel_time
+    p, q, s = shape
+    g = torch.Generator().manual_seed(p * 131 + q * 17 + s)
+    nx, ny, nseg = 37, 29, 300
+    X = torch.randn(nx, p, q, generator=g, dtype=torch.float64)
+    Y = torch.randn(ny, q, s, generator=g, dtype=torch.float64)
+    X *= torch.exp(torch.randn(nx, p, 1, generator=g, dtype=torch.float64))
+    Y *= torch.exp(torch.randn(ny, 1, s, generator=g, dtype=torch.float64))
+    cnt = torch.randint(0, 8, (nseg,), generator=g)
+    cnt[:3] = 0
+    seg_ptr = torch.zeros(nseg + 1, dtype=torch.int64)
+    seg_ptr[1:] = torch.cumsum(cnt, 0)
+    nterm = int(seg_ptr[-1])
+    xr = torch.randint(0, nx, (nterm,), generator=g)
+    yr = torch.randint(0, ny, (nterm,), generator=g)
+    coef = torch.exp(3.0 * torch.randn(nterm, generator=g, dtype=torch.float64))
+    ref = np.zeros((nseg, p, s))
+    absref = np.zeros((nseg, p, s))
+    Xn, Yn, cn = X.numpy(), Y.numpy(), coef.numpy()
+    for k in range(nseg):
+        for t in range(int(seg_ptr[k]), int(seg_ptr[k + 1])):
+            ref[k] += cn[t] * (Xn[xr[t]] @ Yn[yr[t]])
+            absref[k] += abs(cn[t]) * (np.abs(Xn[xr[t]]) @ np.abs(Yn[yr[t]]))
+    kernel_timing(True, reset=True)
+    i32 = dict(dtype=torch.int32, device="cuda")
+    got = seg_gemm(X.cuda(), Y.cuda(), seg_ptr.to(**i32), xr.to(**i32), yr.to(**i32), coef.cuda(), prec)
+    torch.cuda.synchronize()
+    kernel_timing(False)
+    got = got.cpu().numpy()
+    K = (cnt.numpy() * q).reshape(nseg, 1, 1)
+    bound = {0: K * 2.0 ** -52, 3: 2.0 ** -23 + K * 2.0 ** -24, 1: 2.0 ** -20 + K * 2.0 ** -24}[prec]
+    err = np.abs(got - ref)
+    assert np.all(err <= bound * absref + 1e-300), float(np.max(err / np.maximum(absref, 1e-300)))
+    assert np.all(got[:3] == 0.0)
+    tensor_cores = prec == 1 and p >= 32 and q >= 16 and s >= 16 and q % 2 == 0 and s % 2 == 0
+    assert (kernel_time("seg_gemm_tc") is not None) == tensor_cores
