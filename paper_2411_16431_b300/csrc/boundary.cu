@@ -967,6 +967,15 @@ double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
   seg_gemm(a, h->st);
   // Lnext[b][br][chr] = sum_k Wk[k][br] Ltil[k][b][chr]   (batched over b)
   double* Ln = dmalloc((long long)phi.b * K_.nBR() * chr);
+  if (g_use_tc && g_compute_f32) {
+    // TF32 mode: one product Wk^T [nBR x nK] Ltil [nK x (b, chr)] (large
+    // enough for the dense tensor-core GEMM), then (br, b) -> (b, br)
+    const long long n = (long long)phi.b * chr;
+    double* C = h->ws.get<double>("lupd_C", size_t(K_.nBR()) * n);
+    gemm(K_.Wk, true, K_.nBR(), Lt, false, n, C, n, K_.nBR(), int(n), K_.nK(), 1.0, 0, h->st);
+    permute3(C, K_.nBR(), phi.b, chr, Ln, h->st);
+    return Ln;
+  }
   SegGemm g;
   g.name = "env_update";
   g.X = K_.Wk;
