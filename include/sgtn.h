@@ -340,6 +340,21 @@ int sgtn_seg_gemm(int32_t precision, int32_t p, int32_t q, int32_t s, int32_t ns
                   int32_t ny, const int32_t* seg_ptr, const int32_t* xr, const int32_t* yr, const int32_t* cidx,
                   const double* coef, const double* X, const double* Y, double* O, void* stream);
 
+/* Cholesky factor and inverse used by the CholeskyQR orthonormalisations of
+ * the truncation (Sec. III.B; the paper truncates by SVD and does not fix
+ * how), exposed to test the kernel on its own.  All pointers are device
+ * memory: G (n x n, row-major; only its upper triangle is read), outputs
+ * R (upper triangular, R^T R = G + shift I) and Rinv = R^{-1} (n x n,
+ * row-major, zero below the diagonal; Rinv may be G), status[0] = 0, or
+ * j + 1 for the first pivot j that was not positive (it is then replaced by
+ * 1 and the factorisation goes on), minratio[0] (may be NULL) = the smallest
+ * pivot over the matching diagonal entry of G + shift I.  FP64; orders up
+ * to 48 on one CTA, larger ones as a recursive blocked factorisation (one-CTA
+ * diagonal blocks, off-diagonal GEMMs over many CTAs).  Asynchronous on
+ * `stream`.  SGTN_ERR_ARG for n <= 0 or a NULL output. */
+int sgtn_cholesky(int32_t n, double shift, const double* G, double* R, double* Rinv, int32_t* status,
+                  double* minratio, void* stream);
+
 /* Process-wide diagnostics (the paper has no counterpart): cumulative
  * number of kernel launches issued by this library, algorithmic
  * floating-point operations of its contractions (2 m n k per gathered

@@ -385,6 +385,24 @@ int sgtn_seg_gemm(int32_t precision, int32_t p, int32_t q, int32_t s, int32_t ns
   }
 }
 
+int sgtn_cholesky(int32_t n, double shift, const double* G, double* R, double* Rinv, int32_t* status,
+                  double* minratio, void* stream) {
+  if (n <= 0 || !G || !R || !Rinv || !status) return SGTN_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  try {
+    g_compute_f32 = false;
+    g_use_tc = false;
+    cholesky_inv(G, n, shift, R, Rinv, status, st, false, minratio);
+    if (cudaGetLastError() != cudaSuccess) return SGTN_ERR_CUDA;
+    return SGTN_OK;
+  } catch (const SgtnError& e) {
+    cudaGetLastError();
+    return e.code;
+  } catch (const std::exception&) {
+    return SGTN_ERR_CUDA;
+  }
+}
+
 void sgtn_kernel_timing(int32_t enable, int32_t reset) {
   if (reset) ktimer_reset();
   ktimer_enable(enable != 0);

@@ -126,6 +126,24 @@ def seg_gemm(X, Y, seg_ptr, xr, yr, coef, precision, stream=None):
     return O
 
 
+def cholesky(G, shift=0.0, stream=None):
+    """(R, R^{-1}, status, minratio) of the library's FP64 Cholesky of G (+ shift I), a float64 CUDA tensor."""
+    import torch
+    G = G.contiguous()
+    n = G.shape[0]
+    R = torch.empty_like(G)
+    Ri = torch.empty_like(G)
+    stat = torch.zeros(1, dtype=torch.int32, device=G.device)
+    mr = torch.zeros(1, dtype=torch.float64, device=G.device)
+    L = load()
+    L.sgtn_cholesky.argtypes = [ct.c_int32, ct.c_double] + [ct.c_void_p] * 6
+    st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    rc = L.sgtn_cholesky(n, shift, G.data_ptr(), R.data_ptr(), Ri.data_ptr(), stat.data_ptr(), mr.data_ptr(), st)
+    if rc != 0:
+        raise SgtnError(f"sgtn_cholesky failed: {rc}")
+    return R, Ri, int(stat.item()), float(mr.item())
+
+
 def device_allocations():
     """Number of cudaMalloc calls the library has made so far in this process."""
     L = load()

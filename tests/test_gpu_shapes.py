@@ -225,3 +225,34 @@ def test_seg_gemm_elementwise_error_bound(shape, prec):
     assert np.all(got[:3] == 0.0)
     tensor_cores = prec == 1 and p >= 32 and q >= 16 and s >= 16 and q % 2 == 0 and s % 2 == 0
     assert (kernel_time("seg_gemm_tc") is not None) == tensor_cores
+
+
+# --- the Cholesky factor and inverse of the CholeskyQR orthonormalisations ---------------
+
+@pytest.mark.parametrize("n", [20, 48, 49, 64, 100, 128, 160, 176, 177, 240])
+def test_cholesky_factor_and_inverse(n):
+    """R^T R = G and R R^{-1} = I to FP64 rounding (relative to the condition of G) for the
+    orders of the truncation's Gram matrices: one-CTA (n <= 48) and recursive blocked
+    (n > 48, splits at 16-row multiples) forms; the pivot ratio is the smallest Schur-
+    complement pivot over the diagonal of G (computed here from numpy's factor); a matrix
+    with a negative pivot reports the first failing position."""
+    import torch
+    from paper_2411_16431_b300.sgtn import cholesky
+    rng = np.random.default_rng(n)
+    X = rng.standard_normal((3 * n, n)) * np.exp(rng.standard_normal(n))   # graded columns
+    G = X.T @ X
+    Rn = np.linalg.cholesky(G).T
+    R, Ri, status, mr = cholesky(torch.tensor(G, device="cuda"))
+    R, Ri = R.cpu().numpy(), Ri.cpu().numpy()
+    assert status == 0
+    assert np.allclose(np.tril(R, -1), 0.0) and np.allclose(np.tril(Ri, -1), 0.0)
+    assert np.allclose(R, Rn, rtol=1e-9, atol=1e-12 * np.abs(Rn).max())
+    assert np.abs(R.T @ R - G).max() <= 1e-13 * np.abs(G).max() * n
+    assert np.abs(R @ Ri - np.eye(n)).max() <= 1e-10
+    assert abs(mr - np.min(np.diag(Rn) ** 2 / np.diag(G))) <= 1e-9 * mr
+    # an indefinite matrix: the first non-positive pivot is reported (position + 1)
+    Gb = G.copy()
+    j = n // 2
+    Gb[j, j] = 0.5 * (Rn[:j, j] ** 2).sum()   # Schur complement at j becomes negative
+    _, _, status_b, _ = cholesky(torch.tensor(Gb, device="cuda"))
+    assert status_b == j + 1
