@@ -107,7 +107,9 @@ PRECISIONS = {"fp64": (0, -1, "f64", False),
               "fp32": (3, -1, "f32 contractions, f64 truncation", False),
               "tf32": (1, -1, "3xtf32 tensor cores + f32 contractions, f64 truncation", False),
               "tf32_polish": (1, -1, "3xtf32 tensor cores + f32 contractions, f64 truncation and final sweeps", True),
-              "fp64_tf32search": (0, 1, "f64 boundary, 3xtf32/f32 conditional scores", False)}
+              "fp64_tf32search": (0, 1, "f64 boundary, 3xtf32/f32 conditional scores", False),
+              "bf16": (2, -1, "bf16x3 tensor cores (segmented contractions) + 3xtf32 dense + f32, f64 truncation",
+                       False)}
 # the default: a mixed boundary whose sweeps after the cut run in FP64 (about 1.5e-7 log Z
 # error at beta = 2 on P16, where the plain TF32 boundary sits near 1e-6), mixed scores
 DEFAULT_PRECISION = "tf32_polish"
@@ -124,8 +126,9 @@ def _measured_bf16():
         return 1800.0
 
 
+MEASURED_BF16 = _measured_bf16()
 # TF32 dense tensor peak = measured bf16 burst x 1/2 (nominal 1.1 / 2.25 PFLOP/s ratio)
-TF32_PEAK_TFLOPS = _measured_bf16() * 0.5
+TF32_PEAK_TFLOPS = MEASURED_BF16 * 0.5
 
 
 def measure_peaks():
@@ -313,6 +316,9 @@ def run_reference(args, wl):
 def peak_of(name):
     """(peak in TFLOP/s, bound, source) of a timed kernel label, from its arithmetic: the
     GEMM peak of the same arithmetic measured on this machine (measure_peaks), else derived."""
+    if name.endswith("_tc_bf16"):
+        return (MEASURED_BF16 / 6.0, "tensor",
+                "measured bf16 burst peak (MEASURED_PEAKS.json) / 6 (six BF16 products per product)")
     if name.startswith("tc_gemm") or name.endswith("_tc"):
         if MEASURED.get("tf32_tflops"):
             return (MEASURED["tf32_tflops"] / 3.0, "tensor",

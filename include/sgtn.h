@@ -50,8 +50,13 @@ typedef enum {
  * (site diagrams, environments, projections, conditional scores) multiplies
  * and accumulates in FP32 while tensors are stored, truncated (SVD) and
  * normalised (log-norms) in FP64.  SGTN_TF32 (mixed, tensor cores): as FP32,
- * and dense GEMMs large enough for 128 x 128 tiles run on the tcgen05 tensor
- * cores with 3xTF32 splitting (about FP32 accuracy).  BF16 is reserved.
+ * and the sparse site diagrams and environment updates with blocks of at
+ * least 32 x 16 x 16, and dense GEMMs large enough for 128 x 128 tiles, run on
+ * the tcgen05 tensor cores with 3xTF32 splitting (about FP32 accuracy).
+ * SGTN_BF16 (mixed, tensor cores): as SGTN_TF32, but the sparse site diagrams
+ * and environment updates split each operand into three BF16 slices and add
+ * the six products of slice orders up to 2 (kind::f16 MMAs, FP32
+ * accumulation; about FP32 accuracy again); dense GEMMs stay 3xTF32.
  * The conditionals, branch step and search run in the precision of the last
  * sgtn_contract_boundary unless sgtn_set_search_precision chose another. */
 typedef enum { SGTN_FP64 = 0, SGTN_TF32 = 1, SGTN_BF16 = 2, SGTN_FP32 = 3 } sgtn_precision;
@@ -226,8 +231,9 @@ int sgtn_site_dims(sgtn_h h, int32_t site, int32_t* d);
 /* Precision of sgtn_conditionals, sgtn_conditionals_noalloc, sgtn_branch_step
  * and sgtn_search on this handle (the paper has no counterpart: its branch
  * and bound runs in the precision of its contraction).  -1 (the default)
- * follows the last sgtn_contract_boundary; SGTN_FP64, SGTN_FP32 or SGTN_TF32
- * fix it, e.g. an FP64 boundary (exact log Z) with FP32 conditional scores.
+ * follows the last sgtn_contract_boundary; SGTN_FP64, SGTN_FP32, SGTN_TF32 or
+ * SGTN_BF16 fix it, e.g. an FP64 boundary (exact log Z) with FP32 conditional
+ * scores.
  * SGTN_ERR_ARG for any other value. */
 int sgtn_set_search_precision(sgtn_h h, int32_t precision);
 
@@ -241,7 +247,7 @@ int sgtn_set_search_precision(sgtn_h h, int32_t precision);
  * sgtn_logz_grad); SGTN_ERR_ARG for a negative value. */
 int sgtn_set_zipper_window(sgtn_h h, int32_t window);
 
-/* In a mixed-precision sgtn_contract_boundary (SGTN_FP32 or SGTN_TF32), run
+/* In a mixed-precision sgtn_contract_boundary (SGTN_FP32, SGTN_TF32 or SGTN_BF16), run
  * the n_sweeps full variational sweeps that follow the cut to chi (Fig. 8d)
  * with FP64 contractions (on != 0; default off).  The zipper stages, which
  * hold most of the work, stay in the mixed precision; the final sweeps then

@@ -134,8 +134,8 @@ int sgtn_contract_boundary(sgtn_h h, int32_t chi, int32_t precision, int32_t n_s
   return guarded(h, [&] {
     if (!h->beta_set) throw SgtnError(SGTN_ERR_STATE, "set_beta must run first");
     if (chi < 1 || n_sweeps < 0 || n_sweeps > 100) throw SgtnError(SGTN_ERR_ARG, "bad chi or n_sweeps");
-    if (precision != SGTN_FP64 && precision != SGTN_FP32 && precision != SGTN_TF32)
-      throw SgtnError(SGTN_ERR_ARG, "precision must be SGTN_FP64, SGTN_FP32 or SGTN_TF32 in this build");
+    if (precision != SGTN_FP64 && precision != SGTN_FP32 && precision != SGTN_TF32 && precision != SGTN_BF16)
+      throw SgtnError(SGTN_ERR_ARG, "precision must be SGTN_FP64, SGTN_FP32, SGTN_TF32 or SGTN_BF16");
     h->precision = precision;
     PrecisionScope ps(h, false);
     contract_boundary(h, chi, n_sweeps);
@@ -221,8 +221,9 @@ int sgtn_energies(sgtn_h h, int32_t n, const int8_t* spins, int64_t* out) {
 
 int sgtn_set_search_precision(sgtn_h h, int32_t precision) {
   return guarded(h, [&] {
-    if (precision != -1 && precision != SGTN_FP64 && precision != SGTN_FP32 && precision != SGTN_TF32)
-      throw SgtnError(SGTN_ERR_ARG, "search precision must be -1, SGTN_FP64, SGTN_FP32 or SGTN_TF32");
+    if (precision != -1 && precision != SGTN_FP64 && precision != SGTN_FP32 && precision != SGTN_TF32 &&
+        precision != SGTN_BF16)
+      throw SgtnError(SGTN_ERR_ARG, "search precision must be -1, SGTN_FP64, SGTN_FP32, SGTN_TF32 or SGTN_BF16");
     h->search_precision = precision;
   });
 }
@@ -330,16 +331,19 @@ int sgtn_seg_gemm(int32_t precision, int32_t p, int32_t q, int32_t s, int32_t ns
                   const double* coef, const double* X, const double* Y, double* O, void* stream) {
   if (p <= 0 || q <= 0 || s <= 0 || nseg <= 0 || nterm < 0 || nx <= 0 || ny <= 0) return SGTN_ERR_ARG;
   if (!seg_ptr || !xr || !yr || !X || !Y || !O || (cidx && !coef)) return SGTN_ERR_ARG;
-  if (precision != SGTN_FP64 && precision != SGTN_FP32 && precision != SGTN_TF32) return SGTN_ERR_ARG;
+  if (precision != SGTN_FP64 && precision != SGTN_FP32 && precision != SGTN_TF32 && precision != SGTN_BF16)
+    return SGTN_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   struct Modes {   // the thread's contraction modes for this call only
     Modes(int pr) {
       g_compute_f32 = pr != SGTN_FP64;
-      g_use_tc = pr == SGTN_TF32;
+      g_use_tc = pr == SGTN_TF32 || pr == SGTN_BF16;
+      g_tc_bf16 = pr == SGTN_BF16;
     }
     ~Modes() {
       g_compute_f32 = false;
       g_use_tc = false;
+      g_tc_bf16 = false;
     }
   };
   try {
@@ -375,7 +379,7 @@ int sgtn_seg_gemm(int32_t precision, int32_t p, int32_t q, int32_t s, int32_t ns
     a.y_rows = (long long)ny * q;
     seg_gemm(a, st);
     if (cudaGetLastError() != cudaSuccess) return SGTN_ERR_CUDA;
-    if (precision == SGTN_TF32 && tc_gemm_take_error(st)) return SGTN_ERR_TIMEOUT;
+    if ((precision == SGTN_TF32 || precision == SGTN_BF16) && tc_gemm_take_error(st)) return SGTN_ERR_TIMEOUT;
     return SGTN_OK;
   } catch (const SgtnError& e) {
     cudaGetLastError();

@@ -162,12 +162,14 @@ void pool_trim(cudaStream_t st);
 struct PrecisionScope {
   PrecisionScope(const sgtn_inst* h, bool search) {
     const int p = (search && h->search_precision >= 0) ? h->search_precision : h->precision;
-    g_compute_f32 = p == 3 || p == 1;
-    g_use_tc = p == 1;
+    g_compute_f32 = p == 3 || p == 1 || p == 2;
+    g_use_tc = p == 1 || p == 2;
+    g_tc_bf16 = p == 2;
   }
   ~PrecisionScope() {
     g_compute_f32 = false;
     g_use_tc = false;
+    g_tc_bf16 = false;
   }
 };
 }  // namespace sgtn

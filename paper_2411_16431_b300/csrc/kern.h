@@ -51,6 +51,10 @@ extern thread_local bool g_compute_f32;
 // When set (with g_compute_f32), dense GEMMs large enough for 128 x 128 tiles
 // run on tcgen05 tensor cores (3xTF32).
 extern thread_local bool g_use_tc;
+// When set (with g_use_tc), the segmented tensor-core contractions split
+// their operands into three BF16 slices (kind::f16 MMAs) instead of two TF32
+// parts; dense GEMMs stay 3xTF32.
+extern thread_local bool g_tc_bf16;
 // When set, the GEMM helpers allocate no device memory of their own (no
 // split-K or split-segment partial buffers): set by the allocation-free entry
 // point for the duration of its call.

@@ -1198,7 +1198,8 @@ void seg_gemm(const SegGemm& a_in, cudaStream_t st) {
   double fl = 2.0 * a.p * a.q * a.s * double(a.seg_ptr ? a.nterm : (a.splitk ? 1 : a.nseg));
   // TF32 mode: row-major gathered blocks go to the tensor cores (3xTF32)
   const bool tc = a.f32 && g_use_tc && seg_mma_ok(a);
-  const std::string nm = std::string(a.name ? a.name : "seg_gemm") + (tc ? "_tc" : a.f32 ? "_f32" : "_f64");
+  const std::string nm =
+      std::string(a.name ? a.name : "seg_gemm") + (tc ? (g_tc_bf16 ? "_tc_bf16" : "_tc") : a.f32 ? "_f32" : "_f64");
   const bool split = a.seg_ptr && a.vseg_ptr && a.nvseg > a.nseg && !g_no_alloc;
   static const bool trace = std::getenv("SGTN_TRACE_GEMM") != nullptr;
   if (trace)
@@ -1231,6 +1232,7 @@ void seg_gemm(const SegGemm& a_in, cudaStream_t st) {
 
 thread_local bool g_compute_f32 = false;
 thread_local bool g_use_tc = false;
+thread_local bool g_tc_bf16 = false;
 thread_local bool g_no_alloc = false;
 
 void gemm(const double* X, bool tx, long long ldx, const double* Y, bool ty, long long ldy, double* O, long long ldo,

@@ -17,6 +17,8 @@
 #include <cstdint>
 #include <mutex>
 
+#include <cuda_bf16.h>
+
 #include "convert.h"
 #include "kern.h"
 
@@ -385,6 +387,47 @@ __device__ inline void sg_mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t 
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// byte offset of 4 consecutive TF32 (k = 4 c .. 4 c + 3) of row r in a
+// 128-byte-swizzled K-major tile whose base is 1024-byte aligned
+__device__ inline uint32_t sw128(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+// D (+)= A B, kind::f16 with BF16 operands
+__device__ inline void sg_mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// three BF16 slices of an FP32 value, f = hi + mid + lo up to the last 24
+// bits (round to nearest at each slice; the remainders are exact in FP32)
+__device__ inline void sg_split_bf16x3(float f, uint16_t& h, uint16_t& m, uint16_t& l) {
+  const __nv_bfloat16 bh = __float2bfloat16_rn(f);
+  const float r1 = f - __bfloat162float(bh);
+  const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(bm);
+  const __nv_bfloat16 bl = __float2bfloat16_rn(r2);
+  h = __bfloat16_as_ushort(bh);
+  m = __bfloat16_as_ushort(bm);
+  l = __bfloat16_as_ushort(bl);
+}
+// 4 consecutive k (chunk c of 4, k = 4c .. 4c+3) of row r as BF16 slices in
+// 128-byte-swizzled K-major tiles: the high slice in bytes 0-63 of the row
+// of tile t0, the middle slice in bytes 64-127, the low slice in bytes 0-63
+// of tile t1
+__device__ inline void sg_store_bf16x3(unsigned char* t0, unsigned char* t1, int r, int c, float4 v) {
+  uint16_t h[4], m[4], l[4];
+  sg_split_bf16x3(v.x, h[0], m[0], l[0]);
+  sg_split_bf16x3(v.y, h[1], m[1], l[1]);
+  sg_split_bf16x3(v.z, h[2], m[2], l[2]);
+  sg_split_bf16x3(v.w, h[3], m[3], l[3]);
+  auto pack = [](const uint16_t* x) {
+    return make_uint2((uint32_t)x[0] | ((uint32_t)x[1] << 16), (uint32_t)x[2] | ((uint32_t)x[3] << 16));
+  };
+  const uint32_t in16 = 8u * (uint32_t)(c & 1);   // byte offset inside the 16-byte chunk
+  *reinterpret_cast<uint2*>(t0 + sw128(r, c >> 1) + in16) = pack(h);
+  *reinterpret_cast<uint2*>(t0 + sw128(r, 4 + (c >> 1)) + in16) = pack(m);
+  *reinterpret_cast<uint2*>(t1 + sw128(r, c >> 1) + in16) = pack(l);
+}
 __device__ inline void sg_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -397,9 +440,6 @@ __device__ inline void sg_split(float f, float& hi, float& lo) {
   hi = __uint_as_float(b);
   lo = __uint_as_float((__float_as_uint(f - hi) + 0x1000u) & 0xFFFFE000u);
 }
-// byte offset of 4 consecutive TF32 (k = 4 c .. 4 c + 3) of row r in a
-// 128-byte-swizzled K-major tile whose base is 1024-byte aligned
-__device__ inline uint32_t sw128(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
 
 // What the producer tells the other roles about the chunk in a stage: the
 // term's coefficient, the chunk's k offset, and whether it opens or closes a
@@ -410,7 +450,7 @@ struct SgMeta {
   int kc, flags;
 };
 
-template <int BN>
+template <int BN, bool BF>
 __global__ void __launch_bounds__(SG_THREADS, 1)
     seg_mma_3xtf32_kernel(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mY,
                           const __grid_constant__ SegMmaArgs a) {
@@ -429,8 +469,9 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
   constexpr uint32_t B_BYTES = BN * SG_BK * 8;
   constexpr int SG_STAGES = SgRing<BN>::kStages, SG_STAGE_BYTES = SgRing<BN>::kStageBytes;
   constexpr uint32_t TMEM_COLS = 128 * SG_NACC;   // SG_NACC accumulators of up to 128 columns
-  constexpr uint32_t IDESC_SG = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                                ((uint32_t)(SG_BM >> 4) << 24);
+  // kind::tf32 (operand format 2) or kind::f16 with BF16 operands (format 1); D in FP32
+  constexpr uint32_t IDESC_SG = (1u << 4) | ((BF ? 1u : 2u) << 7) | ((BF ? 1u : 2u) << 10) |
+                                ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(SG_BM >> 4) << 24);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < SG_STAGES; ++s) {
@@ -554,12 +595,28 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
         unsigned char* st = smem + s * SG_STAGE_BYTES;
         const uint64_t ahi = smem_desc(st), alo = smem_desc(st + SG_A_BYTES / 2);
         const uint64_t bhi = smem_desc(st + SG_A_BYTES), blo = smem_desc(st + SG_A_BYTES + B_BYTES / 2);
+        if constexpr (BF) {
+          // each 128-byte row holds [high slice | middle slice] of the 32 k of the
+          // chunk, the second tile the low slice: per 16-wide k step, the six
+          // products of slices whose orders add up to at most 2 (about FP32 accuracy)
 #pragma unroll
-        for (int kk = 0; kk < SG_BK / 8; ++kk) {
-          const uint64_t o = (uint64_t)((kk * 32) >> 4);
-          sg_mma(d, ahi + o, bhi + o, IDESC_SG, ((fl & SG_FIRST) && kk == 0) ? 0u : 1u);
-          sg_mma(d, ahi + o, blo + o, IDESC_SG, 1u);
-          sg_mma(d, alo + o, bhi + o, IDESC_SG, 1u);
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint64_t o = (uint64_t)((kk * 32) >> 4), om = (uint64_t)((64 + kk * 32) >> 4);
+            sg_mma_bf16(d, ahi + o, bhi + o, IDESC_SG, ((fl & SG_FIRST) && kk == 0) ? 0u : 1u);
+            sg_mma_bf16(d, ahi + o, bhi + om, IDESC_SG, 1u);
+            sg_mma_bf16(d, ahi + om, bhi + o, IDESC_SG, 1u);
+            sg_mma_bf16(d, ahi + o, blo + o, IDESC_SG, 1u);
+            sg_mma_bf16(d, alo + o, bhi + o, IDESC_SG, 1u);
+            sg_mma_bf16(d, ahi + om, bhi + om, IDESC_SG, 1u);
+          }
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < SG_BK / 8; ++kk) {
+            const uint64_t o = (uint64_t)((kk * 32) >> 4);
+            sg_mma(d, ahi + o, bhi + o, IDESC_SG, ((fl & SG_FIRST) && kk == 0) ? 0u : 1u);
+            sg_mma(d, ahi + o, blo + o, IDESC_SG, 1u);
+            sg_mma(d, alo + o, bhi + o, IDESC_SG, 1u);
+          }
         }
         mma_commit(&empty[s]);
         if (fl & SG_LAST) {
@@ -620,28 +677,36 @@ __global__ void __launch_bounds__(SG_THREADS, 1)
         for (int u = 0; u < AU; ++u) {
           const int i = ct + NT * u, r = i >> 3, c = i & 7;
           if (r < a.bmx) {
-            float4 hi, lo;
-            sg_split(af[u].x, hi.x, lo.x);
-            sg_split(af[u].y, hi.y, lo.y);
-            sg_split(af[u].z, hi.z, lo.z);
-            sg_split(af[u].w, hi.w, lo.w);
-            const uint32_t off = sw128(r, c);
-            *reinterpret_cast<float4*>(st + off) = hi;
-            *reinterpret_cast<float4*>(st + SG_A_BYTES / 2 + off) = lo;
+            if constexpr (BF) {
+              sg_store_bf16x3(st, st + SG_A_BYTES / 2, r, c, af[u]);
+            } else {
+              float4 hi, lo;
+              sg_split(af[u].x, hi.x, lo.x);
+              sg_split(af[u].y, hi.y, lo.y);
+              sg_split(af[u].z, hi.z, lo.z);
+              sg_split(af[u].w, hi.w, lo.w);
+              const uint32_t off = sw128(r, c);
+              *reinterpret_cast<float4*>(st + off) = hi;
+              *reinterpret_cast<float4*>(st + SG_A_BYTES / 2 + off) = lo;
+            }
           }
         }
 #pragma unroll
         for (int u = 0; u < BU; ++u) {
           const int i = ct + NT * u, j = i % BN, c = i / BN;
           if (c < 8) {
-            float4 hi, lo;
-            sg_split(bf[u].x, hi.x, lo.x);
-            sg_split(bf[u].y, hi.y, lo.y);
-            sg_split(bf[u].z, hi.z, lo.z);
-            sg_split(bf[u].w, hi.w, lo.w);
-            const uint32_t off = sw128(j, c);
-            *reinterpret_cast<float4*>(st + SG_A_BYTES + off) = hi;
-            *reinterpret_cast<float4*>(st + SG_A_BYTES + B_BYTES / 2 + off) = lo;
+            if constexpr (BF) {
+              sg_store_bf16x3(st + SG_A_BYTES, st + SG_A_BYTES + B_BYTES / 2, j, c, bf[u]);
+            } else {
+              float4 hi, lo;
+              sg_split(bf[u].x, hi.x, lo.x);
+              sg_split(bf[u].y, hi.y, lo.y);
+              sg_split(bf[u].z, hi.z, lo.z);
+              sg_split(bf[u].w, hi.w, lo.w);
+              const uint32_t off = sw128(j, c);
+              *reinterpret_cast<float4*>(st + SG_A_BYTES + off) = hi;
+              *reinterpret_cast<float4*>(st + SG_A_BYTES + B_BYTES / 2 + off) = lo;
+            }
           }
         }
         // generic-proxy writes made visible to the tensor cores' async proxy
@@ -817,10 +882,17 @@ bool seg_mma(const SegGemm& a, cudaStream_t st) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     kern<<<grid, SG_THREADS, smem_bytes, st>>>(mX, mY, g);
   };
-  if (bn == 16) go(seg_mma_3xtf32_kernel<16>, SgRing<16>::kSmem);
-  else if (bn == 32) go(seg_mma_3xtf32_kernel<32>, SgRing<32>::kSmem);
-  else if (bn == 64) go(seg_mma_3xtf32_kernel<64>, SgRing<64>::kSmem);
-  else go(seg_mma_3xtf32_kernel<128>, SgRing<128>::kSmem);
+  if (g_tc_bf16) {
+    if (bn == 16) go(seg_mma_3xtf32_kernel<16, true>, SgRing<16>::kSmem);
+    else if (bn == 32) go(seg_mma_3xtf32_kernel<32, true>, SgRing<32>::kSmem);
+    else if (bn == 64) go(seg_mma_3xtf32_kernel<64, true>, SgRing<64>::kSmem);
+    else go(seg_mma_3xtf32_kernel<128, true>, SgRing<128>::kSmem);
+  } else {
+    if (bn == 16) go(seg_mma_3xtf32_kernel<16, false>, SgRing<16>::kSmem);
+    else if (bn == 32) go(seg_mma_3xtf32_kernel<32, false>, SgRing<32>::kSmem);
+    else if (bn == 64) go(seg_mma_3xtf32_kernel<64, false>, SgRing<64>::kSmem);
+    else go(seg_mma_3xtf32_kernel<128, false>, SgRing<128>::kSmem);
+  }
   ++g_count.launches;
   return true;
 }

@@ -475,7 +475,7 @@ MIXED_CASES = [(L.chimera_grid(4, 4, 0), None, 1.0, 16, 2), (L.kings_grid(5, 6, 
 
 
 @pytest.mark.parametrize("polish", [False, True], ids=["mixed", "fp64_final_sweeps"])
-@pytest.mark.parametrize("prec", ["FP32", "TF32"])
+@pytest.mark.parametrize("prec", ["FP32", "TF32", "BF16"])
 @pytest.mark.parametrize("case", MIXED_CASES, ids=lambda c: c[0].name)
 def test_mixed_precision_error_is_small(Handle, case, prec, polish):
     """FP32 contractions with FP64 truncation (and optionally FP64 sweeps after the cut):

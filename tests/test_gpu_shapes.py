@@ -56,6 +56,23 @@ def test_chi64_boundary_matches_oracle(chi64):
         assert abs(abs(ov) - 1.0) < 1e-13, (r, ov)
 
 
+@pytest.mark.parametrize("prec", ["TF32", "BF16"])
+def test_chi64_mixed_boundary_on_tensor_cores(chi64, prec):
+    """At chi = 64 the sparse site diagrams and environment updates of a TF32 or BF16
+    contraction run on the tensor cores (3xTF32, or three BF16 slices and six products):
+    log Z within 1e-6 relative of the FP64 oracle."""
+    from paper_2411_16431_b300 import sgtn
+    h = sgtn.Handle(CHI64)
+    h.set_beta(1.0)
+    sgtn.kernel_timing(True, reset=True)
+    lz, _ = h.contract_boundary(64, precision=getattr(sgtn, prec), n_sweeps=1)
+    sgtn.kernel_timing(False)
+    suffix = "_tc_bf16" if prec == "BF16" else "_tc"
+    assert sgtn.kernel_time("site_diagram" + suffix) is not None
+    assert abs(lz - chi64["lz_o"]) < 1e-6 * abs(chi64["lz_o"])
+    h.close()
+
+
 @pytest.mark.parametrize("step", [7, 12, 20])
 def test_chi64_branch_step_with_1024_branches(chi64, step):
     """One branch step of 1024 seeded partial configurations x 256 states (262,144
@@ -181,13 +198,14 @@ SEG_SHAPES = [(64, 64, 128), (32, 32, 64), (128, 64, 64), (96, 40, 48), (160, 32
 
 
 @pytest.mark.parametrize("shape", SEG_SHAPES, ids=lambda s: "x".join(map(str, s)))
-@pytest.mark.parametrize("prec", [0, 3, 1], ids=["fp64", "fp32", "tf32"])
+@pytest.mark.parametrize("prec", [0, 3, 1, 2], ids=["fp64", "fp32", "tf32", "bf16"])
 def test_seg_gemm_elementwise_error_bound(shape, prec):
     """O[g] = sum_t c_t X[xr_t] Y[yr_t] against float64 on the host, element by element:
     FP64 within K 2^-52, FP32 within (2^-23 + K 2^-24), TF32 (3xTF32 tensor cores where the
-    shape allows) within (2^-20 + K 2^-24), of sum_t |c_t| |X_t| |Y_t|, K = the summed
-    length of the segment's reductions.  Segments of 0..7 terms (empty ones give zero
-    blocks), operands shared between terms, coefficients spread over six orders."""
+    shape allows) and BF16 (three BF16 slices per operand, six products) within
+    (2^-20 + K 2^-24), of sum_t |c_t| |X_t| |Y_t|, K = the summed length of the segment's
+    reductions.  Segments of 0..7 terms (empty ones give zero blocks), operands shared
+    between terms, coefficients spread over six orders."""
     import torch
     from paper_2411_16431_b300.sgtn import seg_gemm, kernel_timing, kernel_time
     p, q, s = shape
@@ -219,12 +237,14 @@ def test_seg_gemm_elementwise_error_bound(shape, prec):
     kernel_timing(False)
     got = got.cpu().numpy()
     K = (cnt.numpy() * q).reshape(nseg, 1, 1)
-    bound = {0: K * 2.0 ** -52, 3: 2.0 ** -23 + K * 2.0 ** -24, 1: 2.0 ** -20 + K * 2.0 ** -24}[prec]
+    bound = {0: K * 2.0 ** -52, 3: 2.0 ** -23 + K * 2.0 ** -24, 1: 2.0 ** -20 + K * 2.0 ** -24,
+             2: 2.0 ** -20 + K * 2.0 ** -24}[prec]
     err = np.abs(got - ref)
     assert np.all(err <= bound * absref + 1e-300), float(np.max(err / np.maximum(absref, 1e-300)))
     assert np.all(got[:3] == 0.0)
-    tensor_cores = prec == 1 and p >= 32 and q >= 16 and s >= 16 and q % 2 == 0 and s % 2 == 0
-    assert (kernel_time("seg_gemm_tc") is not None) == tensor_cores
+    tensor_cores = prec in (1, 2) and p >= 32 and q >= 16 and s >= 16 and q % 2 == 0 and s % 2 == 0
+    label = "seg_gemm_tc_bf16" if prec == 2 else "seg_gemm_tc"
+    assert (kernel_time(label) is not None) == tensor_cores
 
 
 # --- the Cholesky factor and inverse of the CholeskyQR orthonormalisations ---------------
