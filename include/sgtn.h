@@ -328,20 +328,25 @@ int sgtn_gemm(int32_t precision, int32_t m, int32_t n, int32_t k, const double* 
  * (Sec. III.B, "Employing sparsity of tensors": one chi x chi product per
  * cluster state, weighted by its Boltzmann factor, summed into the block of
  * its projected indices), exposed to test the library's contraction kernels
- * on their own.  All pointers are device memory; the call is asynchronous on
- * `stream` (NULL: the default stream) except for SGTN_TF32, which synchronises
- * to read the kernels' timeout flag.  For segment g = 0..nseg-1:
+ * on their own.  All pointers are device memory; the work runs on `stream`
+ * (NULL: the default stream), which the call synchronises to check the term
+ * tables first and, in SGTN_TF32 and SGTN_BF16, to read the tensor-core
+ * kernel's timeout flag afterwards.  For segment g = 0..nseg-1:
  *   O[g] = sum_{t = seg_ptr[g]}^{seg_ptr[g+1]-1} c_t X[xr[t]] Y[yr[t]],
  * c_t = coef[cidx[t]] (1 if cidx is NULL), X[i] the i-th of nx row-major
  * p x q blocks of X, Y[j] the j-th of ny row-major q x s blocks of Y, O[g]
  * the g-th row-major p x s block of O (overwritten; zero for an empty
- * segment).  seg_ptr has nseg + 1 nondecreasing entries from 0 to nterm;
- * 0 <= xr[t] < nx and 0 <= yr[t] < ny are the caller's to ensure.
+ * segment).  seg_ptr has nseg + 1 nondecreasing entries from 0 to nterm,
+ * 0 <= xr[t] < nx, 0 <= yr[t] < ny and 0 <= cidx[t] < nterm (coef holds
+ * nterm values); the call copies these tables to the host and checks them
+ * (synchronising the stream) before it launches anything.
  * precision: SGTN_FP64 or SGTN_FP32 (SIMT kernel), SGTN_TF32 (3xTF32 on the
  * tcgen05 tensor cores, operand tiles brought in by TMA, when p >= 32,
- * q >= 16, s >= 16 and q, s are even; else FP32).  SGTN_ERR_ARG for
- * non-positive sizes, NULL arrays or another precision; SGTN_ERR_TIMEOUT if
- * a bounded wait of the tensor-core kernel gave up. */
+ * q >= 16, s >= 16 and q, s are even; else FP32), SGTN_BF16 (the same
+ * tensor-core kernel with three BF16 slices per operand and six kind::f16
+ * products; else FP32).  SGTN_ERR_ARG for non-positive sizes, NULL arrays,
+ * an index out of range or another precision; SGTN_ERR_TIMEOUT if a bounded
+ * wait of the tensor-core kernel gave up. */
 int sgtn_seg_gemm(int32_t precision, int32_t p, int32_t q, int32_t s, int32_t nseg, int32_t nterm, int32_t nx,
                   int32_t ny, const int32_t* seg_ptr, const int32_t* xr, const int32_t* yr, const int32_t* cidx,
                   const double* coef, const double* X, const double* Y, double* O, void* stream);

@@ -347,6 +347,25 @@ int sgtn_seg_gemm(int32_t precision, int32_t p, int32_t q, int32_t s, int32_t ns
     }
   };
   try {
+    // the term tables are checked on the host before anything is launched:
+    // an index out of range would make the kernels read outside X or Y
+    {
+      std::vector<int32_t> hp(size_t(nseg) + 1), hx(nterm), hy(nterm), hc(cidx ? nterm : 0);
+      SGTN_CUDA(cudaMemcpyAsync(hp.data(), seg_ptr, hp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      if (nterm) {
+        SGTN_CUDA(cudaMemcpyAsync(hx.data(), xr, hx.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        SGTN_CUDA(cudaMemcpyAsync(hy.data(), yr, hy.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        if (cidx) SGTN_CUDA(cudaMemcpyAsync(hc.data(), cidx, hc.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      }
+      SGTN_CUDA(cudaStreamSynchronize(st));
+      if (hp[0] != 0 || hp[nseg] != nterm) return SGTN_ERR_ARG;
+      for (int g = 0; g < nseg; ++g)
+        if (hp[g + 1] < hp[g]) return SGTN_ERR_ARG;
+      for (int t = 0; t < nterm; ++t) {
+        if (hx[t] < 0 || hx[t] >= nx || hy[t] < 0 || hy[t] >= ny) return SGTN_ERR_ARG;
+        if (cidx && (hc[t] < 0 || hc[t] >= nterm)) return SGTN_ERR_ARG;
+      }
+    }
     Modes md(precision);
     SegGemm a;
     a.name = "seg_gemm";

@@ -276,3 +276,18 @@ def test_cholesky_factor_and_inverse(n):
     Gb[j, j] = 0.5 * (Rn[:j, j] ** 2).sum()   # Schur complement at j becomes negative
     _, _, status_b, _ = cholesky(torch.tensor(Gb, device="cuda"))
     assert status_b == j + 1
+
+
+def test_seg_gemm_rejects_indices_out_of_range():
+    """An X or Y block index outside the operands is refused before any launch."""
+    import torch
+    from paper_2411_16431_b300.sgtn import seg_gemm, SgtnError
+    X = torch.zeros(4, 32, 16, dtype=torch.float64, device="cuda")
+    Y = torch.zeros(3, 16, 16, dtype=torch.float64, device="cuda")
+    i32 = dict(dtype=torch.int32, device="cuda")
+    seg_ptr = torch.tensor([0, 2], **i32)
+    for xr, yr in (([0, 4], [0, 1]), ([0, 1], [3, 0]), ([-1, 0], [0, 0])):
+        with pytest.raises(SgtnError):
+            seg_gemm(X, Y, seg_ptr, torch.tensor(xr, **i32), torch.tensor(yr, **i32), None, 1)
+    with pytest.raises(SgtnError):   # seg_ptr must end at the number of terms
+        seg_gemm(X, Y, torch.tensor([0, 3], **i32), torch.tensor([0, 1], **i32), torch.tensor([0, 1], **i32), None, 0)
