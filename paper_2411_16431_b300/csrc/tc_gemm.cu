@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
+#include <vector>
 
 #include <cuda_bf16.h>
 
@@ -879,7 +880,17 @@ bool seg_mma(const SegGemm& a, cudaStream_t st) {
   if (items <= 0) return true;
   const int grid = int(std::min<long long>(items, nsm));
   auto go = [&](auto kern, int smem_bytes) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    // the shared-memory limit is raised once per kernel variant (the first call
+    // of each variant in the process; cudaFuncSetAttribute is thread-safe)
+    static std::mutex attr_mu;
+    static std::vector<const void*> raised;
+    {
+      std::lock_guard<std::mutex> lk(attr_mu);
+      if (std::find(raised.begin(), raised.end(), (const void*)kern) == raised.end()) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        raised.push_back((const void*)kern);
+      }
+    }
     kern<<<grid, SG_THREADS, smem_bytes, st>>>(mX, mY, g);
   };
   if (g_tc_bf16) {

@@ -622,3 +622,51 @@ def test_droplets_match_oracle(Handle, case):
         t[F] *= -1
         assert inst.energy_num(t) == res["energy_num"] + dE
     h.close()
+
+
+def test_differentiation_configuration_pegasus8x8(Handle):
+    """The differentiation configuration: Pegasus P9 nice (8 x 8 cells, 1536 spins), chi 32,
+    beta from the geometric sweep 0.25 .. 4 in 8 steps, 32 states per cell (the dense
+    gradient path holds cells of this size).  dlogZ/dbeta against central finite differences
+    (step 1e-4) and dlogZ/dJ, dlogZ/dh on a few couplings and fields against central
+    differences on a refined integer grid (denominator 7 x 20000, one unit moved).  The
+    boundary is truncated here, so the adjoint (isometries held fixed, reading C10) and
+    the finite differences of the computed log Z agree to the truncation error."""
+    inst = L.pegasus_nice(9, 0)
+    states = L.hamming_ball_states(inst, 32, seed=1)
+    chi, ns = 32, 2
+    h = Handle(inst, states)
+    for beta in (0.25, 0.25 * 16 ** (4 / 7), 4.0):
+        h.set_beta(beta)
+        h.contract_boundary(chi, n_sweeps=ns)
+        dJ, dh, db = h.logz_grad()
+        eps = 1e-4
+        lz = []
+        for b in (beta + eps, beta - eps):
+            h.set_beta(b)
+            lz.append(h.contract_boundary(chi, n_sweeps=ns)[0])
+        fd = (lz[0] - lz[1]) / (2 * eps)
+        assert abs(db - fd) < 1e-4 * abs(fd), (beta, db, fd)
+    h.close()
+    beta, K = 0.25 * 16 ** (4 / 7), 20000
+    h = Handle(inst, states)
+    h.set_beta(beta)
+    h.contract_boundary(chi, n_sweeps=ns)
+    dJ, dh, _ = h.logz_grad()
+    h.close()
+    rng = np.random.default_rng(5)
+    for kind, e in [("J", int(i)) for i in rng.choice(inst.n_edges, 3, replace=False)] + \
+                   [("h", int(i)) for i in rng.choice(inst.n_spins, 2, replace=False)]:
+        vals = []
+        for sgn in (+1, -1):
+            jn = inst.j_num.astype(np.int64) * K
+            hn = inst.h_num.astype(np.int64) * K
+            (jn if kind == "J" else hn)[e] += sgn
+            I = L.Instance(inst.n_spins, inst.ei, inst.ej, jn, hn, 7 * K, inst.site_of_spin, inst.rows, inst.cols)
+            hk = Handle(I, states)
+            hk.set_beta(beta)
+            vals.append(hk.contract_boundary(chi, n_sweeps=ns)[0])
+            hk.close()
+        fd = (vals[0] - vals[1]) / (2.0 / (7 * K))
+        got = dJ[e] if kind == "J" else dh[e]
+        assert abs(got - fd) < 1e-3 * max(1.0, abs(fd)), (kind, e, got, fd)
