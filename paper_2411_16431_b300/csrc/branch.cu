@@ -1116,6 +1116,18 @@ void search(sgtn_inst* h, int M, int n_out, int8_t* out_spins, int64_t* out_ener
     throw SgtnError(-1, "bad argument");
   cudaStream_t st = h->st;
   const int C = h->M.C, RC = h->M.R * h->M.C;
+  {
+    // with large clusters the boundary's workspaces (named buffers and cached
+    // pool blocks, kept for the next contraction) can hold most of the device
+    // memory: when less than a quarter is free they are released here (the
+    // boundary MPSs stay); later calls allocate again what they need
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr < tot / 4) {
+      h->sync();
+      pool_trim(st);
+      h->ws.release();
+    }
+  }
   std::vector<int32_t> cfg(1, 0), ncfg;
   std::vector<double> lp(1, 0.0), nlp;
   int count = 1;
