@@ -606,6 +606,9 @@ __global__ void __launch_bounds__(128) jacobi_coop_kernel(double* X, int len, in
 // minratio[0] = min(minratio[0], smallest pivot / (G_jj + shift)).  T is the
 // arithmetic type (float: a cheap factor whose rounding a later FP64 pass
 // removes); memory stays FP64.
+__device__ __forceinline__ float chol_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double chol_rsqrt(double x) { return rsqrt(x); }
+
 template <class T>
 __global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* W, int n, int ld, double shift, double* R,
                                                             double* Rinv, const double* Gd, int* status,
@@ -613,7 +616,7 @@ __global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* W, int
   extern __shared__ __align__(16) unsigned char chol_smem[];
   T* A = reinterpret_cast<T*>(chol_smem);   // n x n
   T* row = A + n * n;                       // n: staged row / 1 / R_jj
-  T* gd = row + n;                          // n: diagonal of G + shift I
+  T* gd = row + n;                          // n: 1 / diagonal of G + shift I
   __shared__ int fail;
   __shared__ T piv[2];   // sqrt of the current pivot and its reciprocal
   __shared__ double mr;  // smallest pivot / (diagonal of G + shift)
@@ -622,16 +625,21 @@ __global__ void __launch_bounds__(1024) cholesky_inv_kernel(const double* W, int
     const int i = e / n, j = e % n;
     A[e] = j >= i ? T(W[(long long)i * ld + j] + (i == j ? shift : 0.0)) : T(0);
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) gd[i] = T(Gd[(long long)i * (ld + 1)] + shift);
+  // reciprocals of the diagonal of G + shift I, all in parallel: a division
+  // (about 640 cycles of dependent FP64 latency on B300) stays off the chain
+  // of pivots, which is the kernel's critical path
+  for (int i = threadIdx.x; i < n; i += blockDim.x) gd[i] = T(1.0 / (Gd[(long long)i * (ld + 1)] + shift));
   __syncthreads();
-  // thread 0 takes each pivot (square root and reciprocal once, shared)
+  // thread 0 takes each pivot: one reciprocal square root (the pivot's square
+  // root is d times it) instead of a square root followed by a division
   auto take_pivot = [&](int j) {
     const T d = A[j * n + j];
     const bool bad = !(d > T(0));
     if (bad && !fail) fail = j + 1;
-    mr = fmin(mr, double(d / gd[j]));
-    piv[0] = bad ? T(1) : T(sqrt(d));
-    piv[1] = T(1) / piv[0];
+    mr = fmin(mr, double(d * gd[j]));
+    const T ri = bad ? T(1) : chol_rsqrt(d);
+    piv[1] = ri;
+    piv[0] = bad ? T(1) : d * ri;
   };
   if (threadIdx.x == 0) {
     fail = 0;
