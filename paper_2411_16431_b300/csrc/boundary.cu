@@ -869,7 +869,7 @@ void site_diagram(RowCtx& X, int c, const double* Kt, int kp, double* Th) {
   a.yr = K_.theta.yr;
   a.yc = K_.theta.yc;
   a.cidx = K_.theta.cidx;
-  a.coef = X.h->ds[X.r * X.h->M.C + c].w;
+  a.coef = X.wts(c);
   a.nseg = K_.theta.nseg;
   a.nterm = K_.theta.nterm;
   a.x_rows = (long long)K_.nA() * chl;
@@ -879,7 +879,6 @@ void site_diagram(RowCtx& X, int c, const double* Kt, int kp, double* Th) {
 
 // Theta for column c with right tensor K ([nBR][chr][kp]); returns scratch pointer
 double* theta_of(RowCtx& X, int c, const double* K, int kp) {
-  if (X.dense) return theta_dense(X, c, K, kp);
   double* Kt = absorb(X, c, K, kp, "ktil");
   const Column& K_ = X.col(c);
   double* Th = X.h->ws.get<double>("theta", size_t(K_.nBL()) * X.chl(c) * K_.nU * kp);
@@ -889,7 +888,6 @@ double* theta_of(RowCtx& X, int c, const double* K, int kp) {
 
 // L env update: Lnext [b][br][chr] from L [a][bl][chl] and phi_c [a][u][b]
 double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
-  if (X.dense) return update_L_dense(X, c, L, phi);
   sgtn_inst* h = X.h;
   const Column& K_ = X.col(c);
   int chl = X.chl(c), chr = X.chr(c);
@@ -959,7 +957,7 @@ double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
   a.yr = K_.lupd.yr;
   a.yc = K_.lupd.yc;
   a.cidx = K_.lupd.cidx;
-  a.coef = h->ds[X.r * h->M.C + c].w;
+  a.coef = X.wts(c);
   a.nseg = K_.lupd.nseg;
   a.nterm = K_.lupd.nterm;
   a.x_rows = (long long)np * phi.b;
@@ -1051,7 +1049,7 @@ ThetaOp theta_op(RowCtx& X, int c, const double* K, int kp) {
   T.m = T.nbl * T.chl;
   T.n = T.nout * kp;
   sgtn_inst* h = X.h;
-  if (X.dense || (long long)T.m * T.n <= h->bs_min_entries) {
+  if ((long long)T.m * T.n <= h->bs_min_entries) {
     T.dense = theta_of(X, c, K, kp);
     return T;
   }
@@ -1088,7 +1086,7 @@ ThetaOp theta_op(RowCtx& X, int c, const double* K, int kp) {
   a.yr = K_.theta.yr;
   a.yc = K_.theta.yc;
   a.cidx = K_.theta.cidx;
-  a.coef = h->ds[X.r * h->M.C + c].w;
+  a.coef = X.wts(c);
   a.nseg = K_.theta.nseg;
   a.nterm = K_.theta.nterm;
   a.x_rows = (long long)K_.nA() * T.chl;
@@ -1501,7 +1499,7 @@ void absorb_sign(sgtn_inst* h, const double* K, Ten& phi0) {
   }
 }
 
-// out ~ T A (T = the row MPO of X, possibly transposed / dense); A is left-canonicalised in place.
+// out ~ T A (T = the row MPO of X); A is left-canonicalised in place.
 // Sec. III.B "Variational zipper algorithm": right to left, each zipper step
 // (SVD truncation of the dashed-box tensor to 2 chi values, Fig. 8c) is
 // followed by a one-site sweep of the instantaneous stage over the columns
@@ -1512,7 +1510,7 @@ void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& wo
   const int C = h->M.C;
   left_canonical(h, A);
   X.A = &A;
-  if (!X.dense) compute_ahat(X);
+  compute_ahat(X);
   std::vector<Ten> phi(C);
   RightEnvs RE(C);
   RE.R[C - 1] = dmalloc(1);

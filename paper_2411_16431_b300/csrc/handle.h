@@ -68,6 +68,7 @@ struct sgtn_inst {
   std::vector<int64_t*> dE;               // [site*4+k] compressed energies
   std::vector<double*> dB;                // [site*4+k] bond factors exp(-beta (Ebar - min))
   std::vector<sgtn::Column> cols;         // [r*C + c]
+  sgtn::GradTables grad;                  // the gradient path's tables (built on first use)
   std::vector<void*> allocs;              // static allocations
   double beta = 0.0;
   bool beta_set = false;
@@ -112,6 +113,10 @@ struct sgtn_inst {
 namespace sgtn {
 // setup.cu
 void setup_device(sgtn_inst* h);
+void build_column_tables(sgtn_inst* h, Column& K, const std::vector<int32_t>& lam, const std::vector<int32_t>& u,
+                         const std::vector<int32_t>& pd, const std::vector<int32_t>& pr,
+                         const std::vector<int32_t>& pdr);
+void build_pair_table(sgtn_inst* h, TermTable& tt, const std::vector<int32_t>& xr, const std::vector<int32_t>& yr);
 void set_beta_device(sgtn_inst* h, double beta);
 void free_mps(MPS& m);
 // boundary.cu

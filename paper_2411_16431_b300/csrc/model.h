@@ -110,6 +110,21 @@ struct Column {
   double* Wk = nullptr;   // [nK][nBR]
 };
 
+// Tables of the gradient path, built on its first call.  tcols[r*C + c]
+// (rows 0..R-2) is the transposed row MPO T_r^T written as a forward-form
+// column over virtual states y = (x, sigma); xl / msig / pair_x index the
+// environment correlators of column r*C + c.
+struct GradTables {
+  bool built = false;
+  std::vector<Column> tcols;
+  std::vector<double*> tw, tbh;    // per virtual state weights, horizontal tables Bh' (per beta)
+  std::vector<int> npur;           // classes of the site below toward the right neighbour
+  std::vector<TermTable> xl;       // one segment per ((lam, u) pair, g)
+  std::vector<TermTable> msig;     // one segment per sigma
+  std::vector<int32_t*> pair_x;    // (lam, u) pair of every state
+  std::vector<int> npairs;
+};
+
 struct MPS {
   int C = 0;
   std::vector<int> phys, bond;     // phys[C], bond[C+1]

@@ -25,23 +25,23 @@ struct SvdOut {
   void release();
 };
 
-// One row MPO applied to an MPS.  Sparse projector form by default; with
-// `dense` the columns are given as dense tensors Wd[c] = [bl][br][out][in]
-// (used for the transposed MPO of the top-down pass and for the gradient
-// sandwiches, on instances whose interfaces are small).
+// One row MPO applied to an MPS, in the sparse projector form of its
+// columns.  cols / w, when set, replace the row's columns and per-state
+// weights (the top-down pass of the gradient applies the transposed MPO,
+// written as forward-form columns over virtual states).
 struct RowCtx {
   sgtn_inst* h = nullptr;
   int r = 0;
   const MPS* A = nullptr;       // the MPS being multiplied (left-canonical in row_step_ctx)
-  std::vector<double*> Ahat;    // sparse: per column [nA][chl][chr]
-  bool dense = false;
-  bool transposed = false;      // dense and the MPO is T_r^T (out = sigma, in = u)
-  std::vector<double*> Wd;      // dense: per column
-  const Column& col(int c) const { return h->cols[r * h->M.C + c]; }
+  std::vector<double*> Ahat;    // per column [nA][chl][chr]
+  const Column* cols = nullptr;
+  const double* const* w = nullptr;
+  const Column& col(int c) const { return cols ? cols[c] : h->cols[r * h->M.C + c]; }
+  const double* wts(int c) const { return w ? w[c] : h->ds[r * h->M.C + c].w; }
   int chl(int c) const { return A->bond[c]; }
   int chr(int c) const { return A->bond[c + 1]; }
-  int nout(int c) const { return transposed ? col(c).nSig : col(c).nU; }
-  int nin(int c) const { return transposed ? col(c).nU : col(c).nSig; }
+  int nout(int c) const { return col(c).nU; }
+  int nin(int c) const { return col(c).nSig; }
 };
 
 double* dmalloc(long long n);
@@ -54,9 +54,7 @@ double* theta_of(RowCtx& X, int c, const double* K, int kp);
 double* update_L(RowCtx& X, int c, const double* L, const Ten& phi);
 double* update_R(RowCtx& X, int c, const double* ThR, const Ten& phi);
 void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& worst);
-// dense implementations (grad.cu)
-double* theta_dense(RowCtx& X, int c, const double* K, int kp);
-double* update_L_dense(RowCtx& X, int c, const double* L, const Ten& phi);
+void compute_ahat(RowCtx& X);
 
 }  // namespace detail
 }  // namespace sgtn

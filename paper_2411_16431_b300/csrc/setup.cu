@@ -73,6 +73,78 @@ struct TermBuilder {
 
 }  // namespace
 
+// Term tables of a column from its per-state classes (Lam x, U x, pd x, pr x,
+// pdr x; the column's class counts must be set): the site diagram (segments
+// (bl, u), terms (x, g, e)), the right-environment form (segments bl), the
+// left-environment update (segments (pr, e, pdr)) with its (u, bl) pairs, and
+// the block-sparse groupings of the site-diagram output.
+void build_column_tables(sgtn_inst* h, Column& K, const std::vector<int32_t>& lam, const std::vector<int32_t>& u,
+                         const std::vector<int32_t>& pd, const std::vector<int32_t>& pr,
+                         const std::vector<int32_t>& pdr) {
+  const int d = int(lam.size());
+  TermBuilder tb;
+  for (int x = 0; x < d; ++x)
+    for (int g = 0; g < K.nG; ++g)
+      for (int e = 0; e < K.nE; ++e) {
+        int bl = lam[x] * K.nG + g;
+        int ablk = (pd[x] * K.nE + e) * K.nG + g;
+        int kblk = (pr[x] * K.nE + e) * K.nPdr + pdr[x];
+        tb.add(int64_t(bl) * K.nU + u[x], bl, u[x], ablk, 0, kblk, 0, x, u[x]);
+      }
+  tb.finish(h, K.theta);
+  for (int x = 0; x < d; ++x)
+    for (int g = 0; g < K.nG; ++g)
+      for (int e = 0; e < K.nE; ++e) {
+        int bl = lam[x] * K.nG + g;
+        int ablk = (pd[x] * K.nE + e) * K.nG + g;
+        int kblk = (pr[x] * K.nE + e) * K.nPdr + pdr[x];
+        tb.add(bl, bl, 0, ablk, 0, kblk, 0, x, u[x]);
+      }
+  tb.finish(h, K.renv);
+  for (int x = 0; x < d; ++x)
+    for (int g = 0; g < K.nG; ++g)
+      for (int e = 0; e < K.nE; ++e) {
+        int bl = lam[x] * K.nG + g;
+        int ablk = (pd[x] * K.nE + e) * K.nG + g;
+        int kblk = (pr[x] * K.nE + e) * K.nPdr + pdr[x];
+        tb.add(kblk, kblk, 0, u[x], bl, ablk, 0, x, u[x]);
+      }
+  tb.finish(h, K.lupd);
+  {
+    // distinct (u, bl) pairs read by the lupd terms: the left-environment
+    // update forms its intermediate only for these
+    std::map<std::pair<int32_t, int32_t>, int32_t> pid;
+    std::vector<int32_t> tp(K.lupd.nterm);
+    for (int t = 0; t < K.lupd.nterm; ++t) {
+      auto key = std::make_pair(K.lupd.h_xr[t], K.lupd.h_xc[t]);
+      auto it = pid.find(key);
+      if (it == pid.end()) it = pid.emplace(key, int32_t(pid.size())).first;
+      tp[t] = it->second;
+    }
+    for (auto& kv : pid) tb.add(kv.second, kv.second, 0, kv.first.first, 0, kv.first.second, 0, 0, 0);
+    tb.finish(h, K.lpairs);
+    K.lupd_pair = h->upload(tp);
+  }
+  // groupings of the site-diagram output blocks (one block per theta segment)
+  for (int sg = 0; sg < K.theta.nseg; ++sg) {
+    int bl = K.theta.h_seg_or[sg], uu = K.theta.h_seg_oc[sg];
+    tb.add(bl, bl, 0, sg, 0, uu, 0, 0, 0);
+  }
+  tb.finish(h, K.bs_rows);
+  for (int sg = 0; sg < K.theta.nseg; ++sg) {
+    int bl = K.theta.h_seg_or[sg], uu = K.theta.h_seg_oc[sg];
+    tb.add(uu, uu, 0, sg, bl, bl, sg, 0, 0);
+  }
+  tb.finish(h, K.bs_cols);
+}
+
+// One term per segment i (in order): block rows xr[i] of X and yr[i] of Y.
+void build_pair_table(sgtn_inst* h, TermTable& tt, const std::vector<int32_t>& xr, const std::vector<int32_t>& yr) {
+  TermBuilder tb;
+  for (size_t i = 0; i < xr.size(); ++i) tb.add(int64_t(i), int32_t(i), 0, xr[i], 0, yr[i], 0, 0, 0);
+  tb.finish(h, tt);
+}
+
 void setup_device(sgtn_inst* h) {
   Model& M = h->M;
   const int R = M.R, C = M.C;
@@ -150,66 +222,8 @@ void setup_device(sgtn_inst* h) {
         K.bdl_na = M.tab[size_t(r * C + c + 1) * 4 + 3].nA;
         K.bdl_nb = M.tab[size_t(r * C + c + 1) * 4 + 3].nB;
       }
-      // term tables
-      const std::vector<int32_t>& lam = S.Lam.of_state;
-      const std::vector<int32_t>& u = S.U.of_state;
-      const std::vector<int32_t>& pd = S.proj[DD].of_state;
-      const std::vector<int32_t>& pr = S.proj[DR_].of_state;
-      const std::vector<int32_t>& pdr = S.proj[DDR].of_state;
-      TermBuilder tb;
-      for (int x = 0; x < S.d; ++x)
-        for (int g = 0; g < K.nG; ++g)
-          for (int e = 0; e < K.nE; ++e) {
-            int bl = lam[x] * K.nG + g;
-            int ablk = (pd[x] * K.nE + e) * K.nG + g;
-            int kblk = (pr[x] * K.nE + e) * K.nPdr + pdr[x];
-            tb.add(int64_t(bl) * K.nU + u[x], bl, u[x], ablk, 0, kblk, 0, x, u[x]);
-          }
-      tb.finish(h, K.theta);
-      for (int x = 0; x < S.d; ++x)
-        for (int g = 0; g < K.nG; ++g)
-          for (int e = 0; e < K.nE; ++e) {
-            int bl = lam[x] * K.nG + g;
-            int ablk = (pd[x] * K.nE + e) * K.nG + g;
-            int kblk = (pr[x] * K.nE + e) * K.nPdr + pdr[x];
-            tb.add(bl, bl, 0, ablk, 0, kblk, 0, x, u[x]);
-          }
-      tb.finish(h, K.renv);
-      for (int x = 0; x < S.d; ++x)
-        for (int g = 0; g < K.nG; ++g)
-          for (int e = 0; e < K.nE; ++e) {
-            int bl = lam[x] * K.nG + g;
-            int ablk = (pd[x] * K.nE + e) * K.nG + g;
-            int kblk = (pr[x] * K.nE + e) * K.nPdr + pdr[x];
-            tb.add(kblk, kblk, 0, u[x], bl, ablk, 0, x, u[x]);
-          }
-      tb.finish(h, K.lupd);
-      {
-        // distinct (u, bl) pairs read by the lupd terms: the left-environment
-        // update forms its intermediate only for these
-        std::map<std::pair<int32_t, int32_t>, int32_t> pid;
-        std::vector<int32_t> tp(K.lupd.nterm);
-        for (int t = 0; t < K.lupd.nterm; ++t) {
-          auto key = std::make_pair(K.lupd.h_xr[t], K.lupd.h_xc[t]);
-          auto it = pid.find(key);
-          if (it == pid.end()) it = pid.emplace(key, int32_t(pid.size())).first;
-          tp[t] = it->second;
-        }
-        for (auto& kv : pid) tb.add(kv.second, kv.second, 0, kv.first.first, 0, kv.first.second, 0, 0, 0);
-        tb.finish(h, K.lpairs);
-        K.lupd_pair = h->upload(tp);
-      }
-      // groupings of the site-diagram output blocks (one block per theta segment)
-      for (int sg = 0; sg < K.theta.nseg; ++sg) {
-        int bl = K.theta.h_seg_or[sg], uu = K.theta.h_seg_oc[sg];
-        tb.add(bl, bl, 0, sg, 0, uu, 0, 0, 0);
-      }
-      tb.finish(h, K.bs_rows);
-      for (int sg = 0; sg < K.theta.nseg; ++sg) {
-        int bl = K.theta.h_seg_or[sg], uu = K.theta.h_seg_oc[sg];
-        tb.add(uu, uu, 0, sg, bl, bl, sg, 0, 0);
-      }
-      tb.finish(h, K.bs_cols);
+      build_column_tables(h, K, S.Lam.of_state, S.U.of_state, S.proj[DD].of_state, S.proj[DR_].of_state,
+                          S.proj[DDR].of_state);
       K.Wa = h->dalloc<double>(size_t(K.nA()) * K.nSig);
       K.Wk = h->dalloc<double>(size_t(K.nK()) * K.nBR());
       maxn = std::max({maxn, S.d, K.nU, K.nSig, K.nBL(), K.nBR()});
