@@ -207,12 +207,18 @@ int sgtn_lbp(sgtn_h h, int32_t n_iter, int32_t k, int32_t* out_index, double* ou
  * k, dh[i] = -beta <s_i>, *dbeta = -<H>, evaluated as environment
  * correlators: row r is averaged in the sandwich <E_r| T_r |psi_r> of the
  * bottom-up boundary MPS psi_r and an upper boundary MPS E_r built top-down
- * with the same chi and sweeps.  Exact when the contraction is exact; with
- * truncation it differs from the derivative of the computed log Z by the
- * truncation error.  Requires contract_boundary with n_sweeps >= 1; the row
- * MPO columns are handled densely here, so each column tensor
- * (left bond x right bond x up classes x down classes) must stay below 2^26
- * entries (SGTN_ERR_ARG otherwise).  dJ[n_edges], dh[n_spins]: host buffers. */
+ * with the same chi, sweeps and zipper window.  The row MPOs stay in their
+ * sparse projector form throughout (Fig. 7): the transposed MPO of the
+ * top-down pass is a column over (state, lower class) pairs, and dZ/dW is
+ * formed only where a state reads it, so any cell size the contraction
+ * takes is accepted.  Exact when the contraction is exact; with truncation
+ * (chi, or the rank rule dropping singular values below 1e-12 of the
+ * largest, which at low temperature can remove parts of E_r that the
+ * sandwich weights heavily) it differs from the derivative of the computed
+ * log Z by the truncation error.  FP64 throughout.  Requires
+ * contract_boundary with n_sweeps >= 1 (SGTN_ERR_ARG otherwise; SGTN_ERR_STATE
+ * before any contraction); SGTN_ERR_NUMERICAL if an environment has a zero or
+ * non-finite norm.  dJ[n_edges], dh[n_spins]: host buffers. */
 int sgtn_logz_grad(sgtn_h h, double* dJ, double* dh, double* dbeta);
 
 /* Exact int64 energies (numerators over denom) of n configurations of +-1
