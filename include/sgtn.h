@@ -215,7 +215,11 @@ int sgtn_lbp(sgtn_h h, int32_t n_iter, int32_t k, int32_t* out_index, double* ou
  * (chi, or the rank rule dropping singular values below 1e-12 of the
  * largest, which at low temperature can remove parts of E_r that the
  * sandwich weights heavily) it differs from the derivative of the computed
- * log Z by the truncation error.  FP64 throughout.  Requires
+ * log Z by the truncation error.  Precision: that of the last
+ * contract_boundary (with SGTN_FP32, SGTN_TF32 or SGTN_BF16 the contractions
+ * of the top-down pass and of the sandwiches run in that arithmetic, while
+ * truncations, environment norms, the correlator sums and the outputs stay
+ * FP64; with SGTN_FP64 everything is FP64).  Requires
  * contract_boundary with n_sweeps >= 1 (SGTN_ERR_ARG otherwise; SGTN_ERR_STATE
  * before any contraction); SGTN_ERR_NUMERICAL if an environment has a zero or
  * non-finite norm.  dJ[n_edges], dh[n_spins]: host buffers. */

@@ -208,6 +208,7 @@ int sgtn_search_droplets(sgtn_h h, int32_t M, int64_t max_dE_num, int32_t min_ha
 int sgtn_logz_grad(sgtn_h h, double* dJ, double* dh, double* dbeta) {
   return guarded(h, [&] {
     if (!dh || !dbeta || (!dJ && !h->M.ei.empty())) throw SgtnError(SGTN_ERR_ARG, "null output");
+    PrecisionScope ps(h, false);
     logz_grad(h, dJ, dh, dbeta);
   });
 }

@@ -374,6 +374,28 @@ def test_logz_grad_block_sparse_and_subspace_routes(Handle, monkeypatch, case):
     assert abs(db - db_o) < 1e-9 * max(1.0, abs(db_o))
 
 
+def test_logz_grad_mixed_precision_close_to_fp64(Handle):
+    """The gradient after a mixed-precision contraction runs its contractions in
+    that arithmetic (FP64 truncation, norms and sums): within 2e-5 of the FP64
+    gradient (relative to the largest entry) on Pegasus 5 x 5 cells with 64
+    states, in FP32, TF32 and BF16 (the BF16 mode keeps three slices, about
+    FP32 accurate)."""
+    from paper_2411_16431_b300 import sgtn
+    inst = L.pegasus_nice(6, 0)
+    states = L.hamming_ball_states(inst, 64, seed=2)
+    h = Handle(inst, states)
+    h.set_beta(1.0)
+    h.contract_boundary(16, n_sweeps=2)
+    ref = h.logz_grad()
+    for prec in (sgtn.FP32, sgtn.TF32, sgtn.BF16):
+        h.contract_boundary(16, precision=prec, n_sweeps=2)
+        got = h.logz_grad()
+        for a, b in zip(got[:2], ref[:2]):
+            assert np.max(np.abs(a - b)) < 2e-5 * np.max(np.abs(b)), prec
+        assert abs(got[2] - ref[2]) < 2e-5 * abs(ref[2]), prec
+    h.close()
+
+
 def test_logz_grad_exact_equals_brute_force(Handle):
     inst, beta = L.slice_cells(L.chimera_grid(4, 4, 2), 2, 1), 1.3
     h = Handle(inst)
