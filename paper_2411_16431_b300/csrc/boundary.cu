@@ -800,6 +800,27 @@ double* right_factor(sgtn_inst* h, const SvdOut& o, int n) {
   return Rm;
 }
 
+// Frobenius norm of x read back to the host, as it is (0, inf or NaN included).
+double norm_value(sgtn_inst* h, const double* x, long long n) {
+  double* d = h->ws.get<double>("norm_out", 1);
+  fro_norm(x, n, d, h->st);
+  double v = 0;
+  SGTN_CUDA(cudaMemcpyAsync(&v, d, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  h->sync();
+  return v;
+}
+
+// Change of an adaptive weight exponent from the norm v of the result it
+// produced: 0 when v lies within 2^+-40, else the power of two that brings it
+// near 1 (+100 for a result that underflowed to zero, -100 for one that
+// overflowed).
+int exp_step(double v) {
+  if (!std::isfinite(v)) return -100;
+  if (!(v > 0.0)) return 100;
+  const int ex = std::ilogb(v);
+  return (ex >= -40 && ex <= 40) ? 0 : -ex;
+}
+
 double norm_host(sgtn_inst* h, const double* x, long long n, bool allow_zero) {
   double* d = h->ws.get<double>("norm_out", 1);
   fro_norm(x, n, d, h->st);
@@ -834,7 +855,25 @@ double* absorb(RowCtx& X, int c, const double* K, int kp, const char* name) {
   return Kt;
 }
 
-// Theta [(bl, chl) x (u, kp)] of the sparse site diagram
+constexpr double kLn2 = 0.69314718055994530942;
+
+// Exponent s of column c's weights in the current arithmetic: the FP32, TF32
+// and BF16 contractions multiply by w 2^s (exact in FP64) so that products
+// that would fall out of FP32's range stay in it; 0 in FP64 or without hints.
+int weight_exp(const RowCtx& X, int c) { return (g_compute_f32 && X.sexp) ? X.sexp[c] : 0; }
+
+// The weights of column c times 2^s (a scratch copy unless s = 0).
+const double* weights_for(RowCtx& X, int c, int s) {
+  if (s == 0) return X.wts(c);
+  const int d = X.col(c).d;
+  double* w = X.h->ws.get<double>("w_scaled", d);
+  copy(w, X.wts(c), d, X.h->st);
+  scale_pow2(w, d, -s, X.h->st);
+  return w;
+}
+
+// Theta [(bl, chl) x (u, kp)] of the sparse site diagram, 2^weight_exp times
+// the true one
 void site_diagram(RowCtx& X, int c, const double* Kt, int kp, double* Th) {
   const Column& K_ = X.col(c);
   int chl = X.chl(c), chr = X.chr(c);
@@ -869,7 +908,7 @@ void site_diagram(RowCtx& X, int c, const double* Kt, int kp, double* Th) {
   a.yr = K_.theta.yr;
   a.yc = K_.theta.yc;
   a.cidx = K_.theta.cidx;
-  a.coef = X.wts(c);
+  a.coef = weights_for(X, c, weight_exp(X, c));
   a.nseg = K_.theta.nseg;
   a.nterm = K_.theta.nterm;
   a.x_rows = (long long)K_.nA() * chl;
@@ -957,7 +996,7 @@ double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
   a.yr = K_.lupd.yr;
   a.yc = K_.lupd.yc;
   a.cidx = K_.lupd.cidx;
-  a.coef = X.wts(c);
+  a.coef = weights_for(X, c, (g_compute_f32 && X.lexp) ? X.lexp[c] : 0);   // the scale is not kept
   a.nseg = K_.lupd.nseg;
   a.nterm = K_.lupd.nterm;
   a.x_rows = (long long)np * phi.b;
@@ -994,6 +1033,27 @@ double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
   g.nseg = phi.b;
   seg_gemm(g, h->st);
   return Ln;
+}
+
+// Left-environment update rescaled by a power of two to a norm near 1; in the
+// mixed arithmetic its weight exponent (X.lexp) is adapted until the result's
+// norm lies within 2^+-40 (at most four retries).
+double* update_L_adapt(RowCtx& X, int c, const double* L, const Ten& phi) {
+  sgtn_inst* h = X.h;
+  const long long n = (long long)phi.b * X.col(c).nBR() * X.chr(c);
+  for (int tries = 0;; ++tries) {
+    double* Ln = update_L(X, c, L, phi);
+    const double v = norm_value(h, Ln, n);
+    const int step = (g_compute_f32 && X.lexp && tries < 4) ? exp_step(v) : 0;
+    if (step == 0) {
+      if (!std::isfinite(v) || !(v > 0.0)) throw SgtnError(-4, "zero or non-finite norm");
+      const int e = (int)std::lround(std::log2(v));
+      if (e != 0) scale_pow2(Ln, n, e, h->st);
+      return Ln;
+    }
+    X.lexp[c] += step;
+    dfree(Ln);
+  }
 }
 
 // R env update: Rprev[(bl, chl)][a] = Theta_R phi^T
@@ -1037,6 +1097,7 @@ struct ThetaOp {
   double* dense = nullptr;
   double* blocks = nullptr;
   int m = 0, n = 0, chl = 0, kp = 0, nseg = 0, nbl = 0, nout = 0;
+  int s = 0;   // the stored Theta is 2^s times the true one (weight_exp)
 };
 
 ThetaOp theta_op(RowCtx& X, int c, const double* K, int kp) {
@@ -1048,6 +1109,7 @@ ThetaOp theta_op(RowCtx& X, int c, const double* K, int kp) {
   T.nout = X.nout(c);
   T.m = T.nbl * T.chl;
   T.n = T.nout * kp;
+  T.s = weight_exp(X, c);
   sgtn_inst* h = X.h;
   if ((long long)T.m * T.n <= h->bs_min_entries) {
     T.dense = theta_of(X, c, K, kp);
@@ -1086,7 +1148,7 @@ ThetaOp theta_op(RowCtx& X, int c, const double* K, int kp) {
   a.yr = K_.theta.yr;
   a.yc = K_.theta.yc;
   a.cidx = K_.theta.cidx;
-  a.coef = X.wts(c);
+  a.coef = weights_for(X, c, T.s);
   a.nseg = K_.theta.nseg;
   a.nterm = K_.theta.nterm;
   a.x_rows = (long long)K_.nA() * T.chl;
@@ -1338,16 +1400,16 @@ double sweep_range(RowCtx& X, std::vector<Ten>& phi, int c0, int e, double* Lc0,
         phi[c].b = o.k;
         o.release();
       }
-      Lenv[c + 1] = update_L(X, c, Lenv[c], phi[c]);
-      double dummy = 0.0;
-      rescale_pow2(h, Lenv[c + 1], (long long)phi[c].b * X.col(c).nBR() * X.chr(c), dummy);
+      Lenv[c + 1] = update_L_adapt(X, c, Lenv[c], phi[c]);
       // the next site's left bond is now o.k; its right bond is unchanged
       phi[c + 1].a = phi[c].b;
     }
   }
   double rc_log = RE.lg[e];
+  int s_c0 = 0;
   for (int c = e; c >= c0; --c) {
     ThetaOp T = theta_op(X, c, RE.R[c], phi[c].b);
+    if (c == c0) s_c0 = T.s;
     const int a = phi[c].a;
     const long long n = (long long)X.nout(c) * phi[c].b;
     double* t = theta_left(X, c, T, Lenv[c], a);
@@ -1371,11 +1433,14 @@ double sweep_range(RowCtx& X, std::vector<Ten>& phi, int c0, int e, double* Lc0,
       }
       double* Rn = theta_right(X, c, T, phi[c]);
       rescale_pow2(h, Rn, (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, rc_log);
+      rc_log -= T.s * kLn2;
       RE.set(c - 1, Rn, rc_log);
       if (c > c0) phi[c - 1].b = phi[c].a;
     }
   }
   for (auto& p : Lenv) dfree(p);
+  // for c0 = 0 the centre phi[0] came from column 0's (scaled) Theta
+  if (c0 == 0) rc_log -= s_c0 * kLn2;
   return rc_log;
 }
 
@@ -1396,6 +1461,7 @@ double variational_sweep(RowCtx& X, std::vector<Ten>& phi, bool canonical) {
     ThetaOp T = theta_op(X, c, RE.R[c], phi[c].b);
     double* Rn = theta_right(X, c, T, phi[c]);
     rescale_pow2(h, Rn, (long long)X.col(c).nBL() * X.chl(c) * phi[c].a, lg);
+    lg -= T.s * kLn2;
     RE.set(c - 1, Rn, lg);
   }
   double* L0 = dmalloc(1);
@@ -1522,10 +1588,29 @@ void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& wo
     const int kp = c == C - 1 ? 1 : phi[c + 1].a;
     const int m = K_.nBL() * X.chl(c);
     SvdOut o;
+    int ts = 0;
     {
       TagScope tag("zipper");
-      ThetaOp T = theta_op(X, c, RE.R[c], kp);
-      o = theta_svd(X, c, T, 2 * chi);
+      // in the mixed arithmetic the weights' exponent is adapted until the
+      // largest singular value of Theta lies within 2^+-40 (a result that
+      // left FP32's range entirely raises the weights by 2^100)
+      for (int tries = 0;; ++tries) {
+        ThetaOp T = theta_op(X, c, RE.R[c], kp);
+        ts = T.s;
+        const bool adapt = g_compute_f32 && X.sexp && tries < 4;
+        try {
+          o = theta_svd(X, c, T, 2 * chi);
+        } catch (const SgtnError& err) {
+          if (!adapt || err.code != -4) throw;
+          X.sexp[c] += 100;
+          continue;
+        }
+        if (!adapt || !(o.sig[0] > 0.0) || !std::isfinite(o.sig[0])) break;
+        const int ex = std::ilogb(o.sig[0]);
+        if (ex >= -40 && ex <= 40) break;
+        X.sexp[c] -= ex;
+        o.release();
+      }
     }
     phi[c].p = o.Vt;
     o.Vt = nullptr;
@@ -1564,6 +1649,7 @@ void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& wo
       o.US = nullptr;
       o.release();
       normalise(h, K, (long long)m * phi[c].a, ln);
+      ln -= ts * kLn2;
       if (c > 0) {
         RE.set(c - 1, K, ln - A.lognorm);
       } else {
@@ -1610,10 +1696,13 @@ void row_step(sgtn_inst* h, int r, int chi, int n_sweeps, MPS& out, double& wors
   RowCtx X;
   X.h = h;
   X.r = r;
+  X.sexp = &h->theta_exp[size_t(r) * h->M.C];
+  X.lexp = &h->lenv_exp[size_t(r) * h->M.C];
   row_step_ctx(X, h->psi[r], chi, n_sweeps, out, worst);
 }
 
 double top_overlap(sgtn_inst* h) {
+  F64Scope f64;   // one row: FP64, no weight scaling
   const int C = h->M.C;
   MPS& A = h->psi[0];
   RowCtx X;

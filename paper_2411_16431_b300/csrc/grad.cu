@@ -226,6 +226,8 @@ void build_grad_tables(sgtn_inst* h) {
   G.msig.assign(R * C, TermTable());
   G.pair_x.assign(R * C, nullptr);
   G.npairs.assign(R * C, 0);
+  G.texp.assign(R * C, 0);
+  G.tlexp.assign(R * C, 0);
   auto iota_v = [](int n) {
     std::vector<int32_t> v(n);
     std::iota(v.begin(), v.end(), 0);
@@ -445,6 +447,8 @@ void logz_grad(sgtn_inst* h, double* dJ, double* dh, double* dbeta) {
   if (!h->grad.built) build_grad_tables(h);
   set_grad_beta(h);
   GradTables& G = h->grad;
+  std::fill(G.texp.begin(), G.texp.end(), 0);
+  std::fill(G.tlexp.begin(), G.tlexp.end(), 0);
   // top-down upper boundary MPSs E_0..E_{R-1}: E_{r+1} ~ T_r^T E_r
   std::vector<MPS> E(R);
   E[0].C = C;
@@ -463,6 +467,8 @@ void logz_grad(sgtn_inst* h, double* dJ, double* dh, double* dbeta) {
     X.r = r;
     X.cols = &G.tcols[r * C];
     X.w = &G.tw[r * C];
+    X.sexp = &G.texp[size_t(r) * C];
+    X.lexp = &G.tlexp[size_t(r) * C];
     row_step_ctx(X, E[r], h->chi, h->n_sweeps, E[r + 1], worst);
   }
   // expectations: slots [edges | spins]
@@ -519,6 +525,8 @@ void logz_grad(sgtn_inst* h, double* dJ, double* dh, double* dbeta) {
     X.h = h;
     X.r = r;
     X.A = &h->psi[r];
+    X.sexp = &h->theta_exp[size_t(r) * C];   // the bottom-up pass's exponents (any scale cancels here)
+    X.lexp = &h->lenv_exp[size_t(r) * C];
     compute_ahat(X);
     // bra tensors of E_r as [a][u][b]
     std::vector<Ten> bra(C);
@@ -534,18 +542,27 @@ void logz_grad(sgtn_inst* h, double* dJ, double* dh, double* dbeta) {
     fill(Re[C - 1], 1, 1.0, st);
     // environments scaled to unit norm as they are built (their raw size
     // follows the Boltzmann factors and can leave the floating-point range)
+    // (mixed arithmetic: each step's weight exponent is adapted until the
+    // result's norm lies within 2^+-40, as in the row step)
     double scale = 0.0;
     for (int c = C - 1; c > 0; --c) {
-      double* Th = theta_of(X, c, Re[c], bra[c].b);
-      Re[c - 1] = update_R(X, c, Th, bra[c]);
-      normalise(h, Re[c - 1], (long long)X.col(c).nBL() * X.chl(c) * bra[c].a, scale);
+      const long long n = (long long)X.col(c).nBL() * X.chl(c) * bra[c].a;
+      for (int tries = 0;; ++tries) {
+        double* Th = theta_of(X, c, Re[c], bra[c].b);
+        double* Rn = update_R(X, c, Th, bra[c]);
+        const int step = (g_compute_f32 && tries < 4) ? exp_step(norm_value(h, Rn, n)) : 0;
+        if (step == 0) {
+          Re[c - 1] = Rn;
+          break;
+        }
+        X.sexp[c] += step;
+        dfree(Rn);
+      }
+      normalise(h, Re[c - 1], n, scale);
     }
     Le[0] = dmalloc(1);
     fill(Le[0], 1, 1.0, st);
-    for (int c = 0; c + 1 < C; ++c) {
-      Le[c + 1] = update_L(X, c, Le[c], bra[c]);
-      normalise(h, Le[c + 1], (long long)bra[c].b * X.col(c).nBR() * X.chr(c), scale);
-    }
+    for (int c = 0; c + 1 < C; ++c) Le[c + 1] = update_L_adapt(X, c, Le[c], bra[c]);
     for (int c = 0; c < C; ++c) {
       const int rc = r * C + c;
       const Column& K = X.col(c);

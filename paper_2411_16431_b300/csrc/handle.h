@@ -69,6 +69,8 @@ struct sgtn_inst {
   std::vector<double*> dB;                // [site*4+k] bond factors exp(-beta (Ebar - min))
   std::vector<sgtn::Column> cols;         // [r*C + c]
   sgtn::GradTables grad;                  // the gradient path's tables (built on first use)
+  std::vector<int> theta_exp;             // [r*C + c] weight exponents of the mixed contractions
+  std::vector<int> lenv_exp;              // [r*C + c] the same for the left-environment updates
   std::vector<void*> allocs;              // static allocations
   double beta = 0.0;
   bool beta_set = false;

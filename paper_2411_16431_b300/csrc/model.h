@@ -123,6 +123,7 @@ struct GradTables {
   std::vector<TermTable> msig;     // one segment per sigma
   std::vector<int32_t*> pair_x;    // (lam, u) pair of every state
   std::vector<int> npairs;
+  std::vector<int> texp, tlexp;    // weight exponents of the transposed columns (Theta, left updates)
 };
 
 struct MPS {

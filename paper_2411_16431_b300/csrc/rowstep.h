@@ -36,6 +36,12 @@ struct RowCtx {
   std::vector<double*> Ahat;    // per column [nA][chl][chr]
   const Column* cols = nullptr;
   const double* const* w = nullptr;
+  // per column: power-of-two exponent s of the weights in the FP32 / TF32 /
+  // BF16 contractions (the site-diagram results are then 2^s times the true
+  // ones; the log-scale bookkeeping takes s off).  Learned by the zipper,
+  // kept across calls; unused in FP64.  nullptr: no scaling.
+  int* sexp = nullptr;
+  int* lexp = nullptr;   // the same for the left-environment updates (their scale is not kept)
   const Column& col(int c) const { return cols ? cols[c] : h->cols[r * h->M.C + c]; }
   const double* wts(int c) const { return w ? w[c] : h->ds[r * h->M.C + c].w; }
   int chl(int c) const { return A->bond[c]; }
@@ -55,6 +61,9 @@ double* update_L(RowCtx& X, int c, const double* L, const Ten& phi);
 double* update_R(RowCtx& X, int c, const double* ThR, const Ten& phi);
 void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& worst);
 void compute_ahat(RowCtx& X);
+double norm_value(sgtn_inst* h, const double* x, long long n);
+int exp_step(double v);
+double* update_L_adapt(RowCtx& X, int c, const double* L, const Ten& phi);
 
 }  // namespace detail
 }  // namespace sgtn

@@ -233,6 +233,8 @@ void setup_device(sgtn_inst* h) {
   std::iota(io.begin(), io.end(), 0);
   h->iota = h->upload(io);
   h->psi.assign(R, MPS());
+  h->theta_exp.assign(R * C, 0);
+  h->lenv_exp.assign(R * C, 0);
   h->sync();
 }
 
@@ -268,6 +270,9 @@ void set_beta_device(sgtn_inst* h, double beta) {
       build_Wk(K.Wk, K.nPr, K.nE, K.nPdr, K.nLR, K.nGR, K.l_pl, K.l_pdl, Bh, K.bh_nb, Bdr, K.bdr_nb, h->st);
     }
   h->check();
+  // the weights' exponents of the mixed contractions depend on beta: learn them afresh
+  std::fill(h->theta_exp.begin(), h->theta_exp.end(), 0);
+  std::fill(h->lenv_exp.begin(), h->lenv_exp.end(), 0);
   h->log_offset = off;
   h->beta = beta;
   h->beta_set = true;
