@@ -811,14 +811,15 @@ double norm_value(sgtn_inst* h, const double* x, long long n) {
 }
 
 // Change of an adaptive weight exponent from the norm v of the result it
-// produced: 0 when v lies within 2^+-40, else the power of two that brings it
-// near 1 (+100 for a result that underflowed to zero, -100 for one that
-// overflowed).
+// produced: 0 while v lies within 2^+-100 (FP32 reaches 2^-126 in normal
+// numbers; nothing is recomputed for results that are merely small), else the
+// power of two that brings it near 1 (+100 for a result that underflowed to
+// zero, -100 for one that overflowed).
 int exp_step(double v) {
   if (!std::isfinite(v)) return -100;
   if (!(v > 0.0)) return 100;
   const int ex = std::ilogb(v);
-  return (ex >= -40 && ex <= 40) ? 0 : -ex;
+  return (ex >= -100 && ex <= 100) ? 0 : -ex;
 }
 
 double norm_host(sgtn_inst* h, const double* x, long long n, bool allow_zero) {
@@ -1036,8 +1037,8 @@ double* update_L(RowCtx& X, int c, const double* L, const Ten& phi) {
 }
 
 // Left-environment update rescaled by a power of two to a norm near 1; in the
-// mixed arithmetic its weight exponent (X.lexp) is adapted until the result's
-// norm lies within 2^+-40 (at most four retries).
+// mixed arithmetic its weight exponent (X.lexp) is adapted when the result's
+// norm leaves 2^+-100 (at most four retries).
 double* update_L_adapt(RowCtx& X, int c, const double* L, const Ten& phi) {
   sgtn_inst* h = X.h;
   const long long n = (long long)phi.b * X.col(c).nBR() * X.chr(c);
@@ -1591,9 +1592,9 @@ void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& wo
     int ts = 0;
     {
       TagScope tag("zipper");
-      // in the mixed arithmetic the weights' exponent is adapted until the
-      // largest singular value of Theta lies within 2^+-40 (a result that
-      // left FP32's range entirely raises the weights by 2^100)
+      // in the mixed arithmetic the weights' exponent is adapted when the
+      // largest singular value of Theta leaves 2^+-100 (a result that left
+      // FP32's range entirely raises the weights by 2^100)
       for (int tries = 0;; ++tries) {
         ThetaOp T = theta_op(X, c, RE.R[c], kp);
         ts = T.s;
@@ -1607,7 +1608,7 @@ void row_step_ctx(RowCtx& X, MPS& A, int chi, int n_sweeps, MPS& out, double& wo
         }
         if (!adapt || !(o.sig[0] > 0.0) || !std::isfinite(o.sig[0])) break;
         const int ex = std::ilogb(o.sig[0]);
-        if (ex >= -40 && ex <= 40) break;
+        if (ex >= -100 && ex <= 100) break;
         X.sexp[c] -= ex;
         o.release();
       }

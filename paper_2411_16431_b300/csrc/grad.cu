@@ -542,8 +542,8 @@ void logz_grad(sgtn_inst* h, double* dJ, double* dh, double* dbeta) {
     fill(Re[C - 1], 1, 1.0, st);
     // environments scaled to unit norm as they are built (their raw size
     // follows the Boltzmann factors and can leave the floating-point range)
-    // (mixed arithmetic: each step's weight exponent is adapted until the
-    // result's norm lies within 2^+-40, as in the row step)
+    // (mixed arithmetic: a step's weight exponent is adapted when the
+    // result's norm leaves 2^+-100, as in the row step)
     double scale = 0.0;
     for (int c = C - 1; c > 0; --c) {
       const long long n = (long long)X.col(c).nBL() * X.chl(c) * bra[c].a;
