@@ -710,3 +710,70 @@ def test_every_zipper_step_is_followed_by_a_sweep_of_its_stage(window):
     g = stages(window)
     assert min(g) > -1e-12 and max(g) > 1e-6
     assert max(abs(x) for x in stages(1)) < 1e-12     # no sweeps: nothing changes after the truncation
+
+
+# --- the transposed row MPO as a column over (state, lower class) pairs -------
+def _dense_column(col):
+    """W[(lam,g)][(lam',g')][u][sigma] = sum_x [Lam x = lam, U x = u] [pul sigma = g] T[x, lam', g', sigma]."""
+    T = col["T"]
+    nG, nsig = col["nGl"], col["nsig"]
+    W = np.zeros((col["nLam"] * nG, col["nLR"] * col["nGR"], col["nU"], nsig))
+    for x in range(T.shape[0]):
+        for sg in range(nsig):
+            bl = col["lam_x"][x] * nG + col["pul"][sg]
+            W[bl, :, col["u_x"][x], sg] += T[x, :, :, sg].reshape(-1)
+    return W
+
+
+@pytest.mark.parametrize("inst,states", [
+    (L.pegasus_nice(4, 3), "ball12"), (L.kings_grid(3, 3, 5), None), (L.chimera_grid(3, 2, 4), None)],
+    ids=["pegasus3x3_12states", "kings3x3", "chimera3x2"])
+def test_transposed_column_as_virtual_states(inst, states):
+    """The gradient's top-down pass applies T_r^T written as a forward-form column
+    over virtual states y = (x, sigma): left bond Lam x nG + pul sigma, output
+    sigma, input u_x through an identity table, right-bond factor
+    Bh'[(pr, pur)][lam'] = Bh[pr][pl lam'] Bdl[pdl lam'][pur], Bdr unchanged,
+    weight w_x Bv[pd_x][pu sigma].  Built here from the bond tables and
+    compared element by element with the transpose (u <-> sigma) of the
+    oracle's dense column."""
+    from oracle.peps import RowMPO
+    if states == "ball12":
+        states = L.hamming_ball_states(inst, 12, seed=2)
+    pm = PottsModel(inst, states)
+    beta = 0.7
+    mpo0 = RowMPO(pm, 0, beta)
+    for r in range(pm.R - 1):
+        mpo = RowMPO(pm, r, beta)
+        for c in range(pm.C):
+            col = mpo.cols[c]
+            W = _dense_column(col)
+            S, below, right = pm.site(r, c), pm.site(r + 1, c), pm.site(r, c + 1)
+            w = np.exp(-beta * (S.E - S.E.min()) / inst.denom)
+            sig = pm.joint(r + 1, c, ("u", "ul", "ur"))
+            pu, pul, pur = (pm.component(sig, below, k) for k in ("u", "ul", "ur"))
+            nPur = below.proj["ur"].n
+            if right is not None:
+                lamR = pm.joint(r, c + 1, ("l", "dl"))
+                pl, pdl = pm.component(lamR, right, "l"), pm.component(lamR, right, "dl")
+                Bdl = mpo._B(r, c + 1, "dl")
+            else:
+                pl = pdl = np.zeros(1, dtype=np.int64)
+                Bdl = np.ones((1, 1))
+            Bv, Bh, Bdr = mpo._B(r, c, "d"), mpo._B(r, c, "r"), mpo._B(r, c, "dr")
+            nPr = S.proj["r"].n
+            # Bh'[(pr, pur)][lam'] = Bh[pr][pl lam'] Bdl[pdl lam'][pur]
+            Bhp = np.zeros((nPr * nPur, col["nLR"]))
+            for pr in range(nPr):
+                for q in range(nPur):
+                    Bhp[pr * nPur + q] = Bh[pr, pl] * Bdl[pdl, q]
+            nG, nU, nsig = col["nGl"], col["nU"], col["nsig"]
+            Wt = np.zeros((col["nLam"] * nG, col["nLR"] * col["nGR"], nsig, nU))
+            for x in range(S.d):
+                for sg in range(nsig):
+                    bl = col["lam_x"][x] * nG + pul[sg]                 # Lam' y
+                    wy = w[x] * Bv[S.proj["d"].of_state[x], pu[sg]]      # w'_y
+                    prp = S.proj["r"].of_state[x] * nPur + pur[sg]       # pr' y
+                    right_factor = (Bhp[prp][:, None] * Bdr[S.proj["dr"].of_state[x]][None, :]).reshape(-1)
+                    Wt[bl, :, sg, col["u_x"][x]] += wy * right_factor    # out sigma, in u_x (identity Bv')
+            assert np.allclose(Wt, W.transpose(0, 1, 3, 2), rtol=1e-13, atol=0)
+    assert mpo0.cols[0]["nU"] == 1   # the top row has no upper classes: E_0 is the trivial MPS
